@@ -1,0 +1,234 @@
+"""HI-NQS CPU oracle (FP64) -- TEST INFRASTRUCTURE ONLY.
+
+Plain, slow and independent of the CUDA path: the arithmetic lives in
+`hinqs_oracle.c` (explicit occupied-spin-orbital lists, literal operator
+application, see that file's header); this module compiles it with gcc, loads
+it with ctypes and adds the numpy-level steps:
+
+* build_subspace   -- particle-number filter (Sec. 2.1 "residual particle-number
+                      filter") and set semantics (Step 1 dedupe) by np.unique,
+                      giving the SQD product subspace of Step 3.
+* ground_state_dense -- Step 3 exact diagonalisation of the projected H by
+                      numpy.linalg.eigh (a library primitive) on the dense matrix.
+* lanczos          -- Step 3 for subspaces too large for a dense matrix: Lanczos
+                      with full reorthogonalisation on the matrix-free sigma.
+
+Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
+this package.  The CUDA library never loads it.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "hinqs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library in place (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                               "-Wall", "-o", tmp, _SRC])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        P = ctypes.c_void_p
+        i32, i64, dbl = ctypes.c_int, ctypes.c_int64, ctypes.c_double
+        lib.oracle_sigma.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, P, i64, i32]
+        lib.oracle_dense_h.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P]
+        lib.oracle_diag.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, i64]
+        lib.oracle_links.argtypes = [i32, i32, P, P, P, i64, P, P, P, P, P, P, P, P, P]
+        lib.oracle_rdm.argtypes = [i32, P, i64, P, i64, P, P, P, i32]
+        lib.oracle_marginals.argtypes = [P, i64, i64, P, P, P]
+        lib.oracle_max_threads.argtypes = []
+        _lib = lib
+    return _lib
+
+
+def _p(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _u64(a):
+    return np.ascontiguousarray(a, dtype=np.uint64)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def popcount(v: int) -> int:
+    return bin(int(v)).count("1")
+
+
+def build_subspace(alpha, beta, n_alpha: int, n_beta: int, drop_bad: bool = True):
+    """Sorted unique alpha and beta strings; strings with the wrong electron
+    count are dropped (drop_bad) or raise ValueError."""
+    out = []
+    for strings, ne in ((alpha, n_alpha), (beta, n_beta)):
+        s = [int(x) for x in np.asarray(strings, dtype=np.uint64).ravel()]
+        good = [x for x in s if popcount(x) == ne]
+        if len(good) != len(s) and not drop_bad:
+            raise ValueError("string with the wrong particle number")
+        out.append(np.unique(np.array(good, dtype=np.uint64)))
+    return out[0], out[1]
+
+
+class Ham:
+    """Integrals in an orthonormal spatial-orbital basis: h[n,n], chemist eri[n,n,n,n]."""
+
+    def __init__(self, h, eri, e_nuc, n_alpha, n_beta):
+        self.h = _f64(h)
+        self.eri = _f64(eri)
+        self.n = self.h.shape[0]
+        self.e_nuc = float(e_nuc)
+        self.n_alpha = int(n_alpha)
+        self.n_beta = int(n_beta)
+
+
+def sigma(H: Ham, sa, sb, c, rows=None, n_threads: int = 0):
+    """sigma = H c on the product subspace (rows: only those outputs)."""
+    lib = _load()
+    sa, sb, c = _u64(sa), _u64(sb), _f64(c)
+    rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    m = len(sa) * len(sb) if rows_a is None else len(rows_a)
+    out = np.zeros(m)
+    rc = lib.oracle_sigma(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc,
+                          _p(sa), len(sa), _p(sb), len(sb), _p(c), _p(out),
+                          _p(rows_a), 0 if rows_a is None else len(rows_a), n_threads)
+    if rc:
+        raise ValueError(f"oracle_sigma failed ({rc})")
+    return out
+
+
+def dense_h(H: Ham, sa, sb):
+    lib = _load()
+    sa, sb = _u64(sa), _u64(sb)
+    N = len(sa) * len(sb)
+    out = np.zeros((N, N))
+    rc = lib.oracle_dense_h(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc,
+                            _p(sa), len(sa), _p(sb), len(sb), _p(out))
+    if rc:
+        raise ValueError(f"oracle_dense_h failed ({rc})")
+    return out
+
+
+def diag(H: Ham, sa, sb, rows=None):
+    lib = _load()
+    sa, sb = _u64(sa), _u64(sb)
+    rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    m = len(sa) * len(sb) if rows_a is None else len(rows_a)
+    out = np.zeros(m)
+    rc = lib.oracle_diag(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc,
+                         _p(sa), len(sa), _p(sb), len(sb), _p(out),
+                         _p(rows_a), 0 if rows_a is None else len(rows_a))
+    if rc:
+        raise ValueError(f"oracle_diag failed ({rc})")
+    return out
+
+
+def links(H: Ham, S, n_e: int):
+    """Same-spin single/double links of the sorted string set S (see oracle_links)."""
+    lib = _load()
+    S = _u64(S)
+    N = len(S)
+    row_ptr = np.zeros(N + 1, dtype=np.int64)
+    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(row_ptr),
+                          None, None, None, None, None, None, None, None)
+    if rc:
+        raise ValueError(f"oracle_links failed ({rc})")
+    nnz = int(row_ptr[-1])
+    out = dict(row_ptr=row_ptr, col=np.zeros(nnz, np.int32), degree=np.zeros(nnz, np.int8),
+               p=np.zeros(nnz, np.uint8), q=np.zeros(nnz, np.uint8), r=np.zeros(nnz, np.uint8),
+               s=np.zeros(nnz, np.uint8), sign=np.zeros(nnz, np.int8), hval=np.zeros(nnz))
+    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(row_ptr), _p(out["col"]),
+                          _p(out["degree"]), _p(out["p"]), _p(out["q"]), _p(out["r"]),
+                          _p(out["s"]), _p(out["sign"]), _p(out["hval"]))
+    if rc:
+        raise ValueError(f"oracle_links failed ({rc})")
+    return out
+
+
+def rdm(n: int, sa, sb, c, want2: bool = True, n_threads: int = 0):
+    """Spin-summed 1-RDM (n,n) and 2-RDM (n,n,n,n) of the state c as given."""
+    lib = _load()
+    sa, sb, c = _u64(sa), _u64(sb), _f64(c)
+    g1 = np.zeros((n, n))
+    g2 = np.zeros((n, n, n, n)) if want2 else None
+    rc = lib.oracle_rdm(n, _p(sa), len(sa), _p(sb), len(sb), _p(c), _p(g1), _p(g2), n_threads)
+    if rc:
+        raise ValueError(f"oracle_rdm failed ({rc})")
+    return g1, g2
+
+
+def marginals(c, Na: int, Nb: int, want_w: bool = False):
+    lib = _load()
+    c = _f64(c)
+    pa, pb = np.zeros(Na), np.zeros(Nb)
+    w = np.zeros(Na * Nb) if want_w else None
+    rc = lib.oracle_marginals(_p(c), Na, Nb, _p(pa), _p(pb), _p(w))
+    if rc:
+        raise ValueError(f"oracle_marginals failed ({rc})")
+    return (pa, pb, w) if want_w else (pa, pb)
+
+
+def ground_state_dense(H: Ham, sa, sb):
+    """(E0, c0) of the projected Hamiltonian by dense numpy.linalg.eigh."""
+    Hm = dense_h(H, sa, sb)
+    evals, evecs = np.linalg.eigh(Hm)
+    return float(evals[0]), evecs[:, 0]
+
+
+def lanczos(H: Ham, sa, sb, tol: float = 1e-10, max_iter: int = 400, seed: int = 7,
+            n_threads: int = 0):
+    """Lowest eigenpair by Lanczos with full reorthogonalisation (Golub & Van Loan,
+    Sec. 10.1), on the matrix-free oracle sigma.  Returns (E0, c0, residual norm)."""
+    N = len(sa) * len(sb)
+    rng = np.random.default_rng(seed)
+    q = rng.standard_normal(N)
+    q /= np.linalg.norm(q)
+    Q = [q]
+    alphas, betas = [], []
+    theta, y = None, None
+    for j in range(min(max_iter, N)):
+        w = sigma(H, sa, sb, Q[j], n_threads=n_threads)
+        a = float(Q[j] @ w)
+        alphas.append(a)
+        w = w - a * Q[j] - (betas[-1] * Q[j - 1] if j > 0 else 0.0)
+        Qm = np.array(Q)
+        for _ in range(2):
+            w = w - Qm.T @ (Qm @ w)
+        b = float(np.linalg.norm(w))
+        T = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
+        ev, evec = np.linalg.eigh(T)
+        theta, y = ev[0], evec[:, 0]
+        # residual of the Ritz pair = |b * last component of y|
+        if abs(b * y[-1]) < tol or b < 1e-14 or j + 1 == N:
+            break
+        betas.append(b)
+        Q.append(w / b)
+    x = np.array(Q[:len(y)]).T @ y
+    x /= np.linalg.norm(x)
+    r = sigma(H, sa, sb, x, n_threads=n_threads) - theta * x
+    return float(theta), x, float(np.linalg.norm(r))
+
+
+def energy_from_rdm(H: Ham, g1, g2, norm2: float = 1.0):
+    """<c|H|c> = sum h g1 + 1/2 sum (pq|rs) g2 + E_nuc <c|c>."""
+    return float(np.sum(H.h * g1) + 0.5 * np.sum(H.eri * g2) + H.e_nuc * norm2)
