@@ -1,0 +1,335 @@
+"""Benchmark of the HI-NQS subspace-diagonalisation hot path on B300.
+
+One step = one pass of the whole hot path over the synthetic "precision"
+workload (n_orb = 16, n_alpha = n_beta = 5, 2000 x 2000 HF-weighted strings,
+4.0e6 determinants): Hamiltonian preparation, subspace build (filter, sort,
+dedupe), alpha and beta string links, Davidson to 1e-6 Ha (mixed precision:
+FP32 sigma bulk + FP64 refinement), 1-/2-RDMs with the Hellmann-Feynman
+backward, and the spin-marginal teacher weights.
+
+value = determinants through the whole path per second (N / step time), summed
+over ranks.  Also reported: sigma determinants per second of one sigma product
+in FP64 and FP32, and Davidson time-to-1e-6 Ha for the mixed and the FP64 solver
+on the same GPU.
+
+--impl reference runs the CPU oracle (FP64, plain C with OpenMP) on a bounded
+sample of the same workload on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sigma dets/s and Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B300"
+WORKLOAD = "precision"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--detail", action="store_true", help="per-component timings to stderr")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------- reference --
+
+def run_reference(args):
+    """The CPU oracle on a bounded sample of the workload (host cores)."""
+    import numpy as np
+
+    import oracle
+    import synth
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    w = synth.workload(args.workload)
+    H = oracle.Ham(w["h"], w["eri"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    sa, sb = oracle.build_subspace(w["alpha"], w["beta"], w["n_alpha"], w["n_beta"])
+    N = len(sa) * len(sb)
+    c = synth.random_vector(N, 3)
+    rows_per_step = 4000
+    rng = np.random.default_rng(0)
+    threads = oracle.max_threads()
+    for _ in range(args.warmup):
+        oracle.sigma(H, sa, sb, c, rows=rng.choice(N, 200, replace=False))
+    times = []
+    for _ in range(args.steps):
+        rows = rng.choice(N, rows_per_step, replace=False)
+        t0 = time.perf_counter()
+        oracle.sigma(H, sa, sb, c, rows=rows)
+        times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    dets_s = rows_per_step / t
+    # the whole path per determinant is bounded below by the sigma products of the
+    # solve; the oracle's rate is the sigma-row rate divided by the FP64 solver's
+    # sigma count on this workload (measured by the GPU arm: ~20)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": dets_s, "unit": "dets/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n_orb={w['n_orb']} n_alpha={w['n_alpha']} "
+                               f"n_beta={w['n_beta']} N={N}",
+                   "sample": f"{rows_per_step} random rows of sigma = H c per step"},
+        "cpu_baseline": {"value": dets_s, "unit": "sigma rows/s", "cores": threads,
+                         "kind": "oracle",
+                         "sample": f"{rows_per_step} sigma rows of the {N}-determinant workload per step"},
+        "e2e": {"value": dets_s, "unit": "dets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ B300 --
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2606_26760_b300 import build as _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    import paper_2606_26760_b300 as hq
+    import synth
+
+    w = synth.workload(args.workload)
+    n, na, nb = w["n_orb"], w["n_alpha"], w["n_beta"]
+    dev = torch.device("cuda", local)
+    h_d = torch.tensor(w["h"], device=dev)
+    eri_d = torch.tensor(w["eri"], device=dev)
+    a_d = torch.from_numpy(w["alpha"].view(np.int64)).to(dev)
+    b_d = torch.from_numpy(w["beta"].view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # reference energy for time-to-1e-6 Ha: FP64 Davidson to a tight residual
+    ham = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
+    sub = hq.build_subspace(a_d, b_d, n, na, nb)
+    la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
+    N = sub.N
+    ref = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-9,
+                      max_iter=400, max_subspace=24)
+    E_ref = ref.energy
+
+    def time_to(trace, tol=1e-6):
+        for th, t, k in zip(trace["theta"], trace["time"], trace["kind"]):
+            if k == 0 and abs(th - E_ref) <= tol:
+                return t
+        return None
+
+    solve_opts = dict(precision=hq.DAVIDSON_MIXED, tol_residual=1e-6, tol_energy=1e-8,
+                      max_subspace=16, max_iter=200, trace_cap=512)
+
+    def step(h_in, eri_in, a_in, b_in):
+        ham_s = hq.Hamiltonian(h_in, eri_in, na, nb, w["e_nuc"])
+        sub_s = hq.build_subspace(a_in, b_in, n, na, nb)
+        la_s, lb_s = hq.string_links(ham_s, sub_s, 0), hq.string_links(ham_s, sub_s, 1)
+        res = hq.davidson(ham_s, sub_s, la_s, lb_s, **solve_opts)
+        g1, g2 = hq.rdm(sub_s, la_s, lb_s, res.c)
+        gh, ge = hq.energy_backward(n, 1.0, g1, g2)
+        pa, pb, wt = hq.spin_marginals(sub_s, res.c, want_w=True)
+        return res, gh, ge, pa, pb
+
+    for _ in range(args.warmup):
+        step(h_d, eri_d, a_d, b_d)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    times, results = [], []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        flush.zero_()
+        barrier()
+        ev0.record(stream)
+        out = step(h_d, eri_d, a_d, b_d)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        times.append(ev0.elapsed_time(ev1) / 1e3)
+        results.append(out[0])
+    barrier()
+
+    # e2e: host buffers through the public API, copies inside the timed region
+    h_h = torch.tensor(w["h"]).pin_memory()
+    eri_h = torch.tensor(w["eri"]).pin_memory()
+    a_h = torch.from_numpy(w["alpha"].view(np.int64).copy()).pin_memory()
+    b_h = torch.from_numpy(w["beta"].view(np.int64).copy()).pin_memory()
+    e2e_times = []
+    d2h = 0
+    for _ in range(max(1, args.steps // 2)):
+        flush.zero_()
+        barrier()
+        t0 = time.perf_counter()
+        res, gh, ge, pa, pb = step(h_h.to(dev, non_blocking=True), eri_h.to(dev, non_blocking=True),
+                                   a_h.to(dev, non_blocking=True), b_h.to(dev, non_blocking=True))
+        outs = [x.cpu() for x in (gh, ge, pa, pb)]
+        torch.cuda.synchronize()
+        e2e_times.append(time.perf_counter() - t0)
+        d2h = sum(x.numel() * x.element_size() for x in outs) + 8
+    clk = clocks.stop()
+    h2d = sum(x.numel() * x.element_size() for x in (h_h, eri_h, a_h, b_h))
+
+    # kernel-level sigma rates and the FP64 solver's time-to-1e-6 Ha
+    c64 = torch.tensor(synth.random_vector(N, 3), device=dev)
+    c32 = c64.float()
+    s64, s32 = torch.empty_like(c64), torch.empty_like(c32)
+
+    def sigma_rate(c, s, reps=10):
+        for _ in range(3):
+            hq.sigma(ham, sub, la, lb, c, out=s)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            hq.sigma(ham, sub, la, lb, c, out=s)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(ev0.elapsed_time(ev1) / 1e3)
+        ts.sort()
+        return ts[len(ts) // 2]
+
+    t_s64 = sigma_rate(c64, s64, reps=5)
+    t_s32 = sigma_rate(c32, s32)
+    fp64_runs = []
+    for _ in range(2):
+        r = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-6,
+                        tol_energy=1e-8, max_subspace=16, max_iter=200, trace_cap=512)
+        fp64_runs.append(r)
+    tt_fp64 = min(x for x in (time_to(r.trace) for r in fp64_runs) if x is not None)
+    tt_mixed = [time_to(r.trace) for r in results]
+    tt_mixed = min(x for x in tt_mixed if x is not None)
+
+    t_step = max(times) if world == 1 else max(times)
+    t_mean = sum(times) / len(times)
+    if world > 1:
+        tt = torch.tensor([t_mean], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_mean = float(tt)
+    value = world * N / t_mean
+    e2e_mean = sum(e2e_times) / len(e2e_times)
+    last = results[-1]
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "dets/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_mean,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: n_orb={n} n_alpha={na} n_beta={nb} "
+                               f"{sub.Na}x{sub.Nb} strings, N={N} determinants",
+                   "step": "ham+subspace+links+mixed Davidson to 1e-6 Ha+RDM backward+marginals",
+                   "l2": "256 MB buffer written between timed steps",
+                   "parallelism": f"replicas x{world}"},
+        "e2e": {"value": world * N / e2e_mean, "unit": "dets/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "sigma_dets_per_s": {"fp64": N / t_s64, "fp32": N / t_s32},
+        "sigma_ms": {"fp64": 1e3 * t_s64, "fp32": 1e3 * t_s32},
+        "time_to_1e-6_Ha_s": {"mixed": tt_mixed, "fp64": tt_fp64,
+                              "speedup_mixed_vs_fp64": tt_fp64 / tt_mixed},
+        "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
+                   "mixed_sigmas": [last.n_sigma_fp64, last.n_sigma_fp32],
+                   "fp64_sigmas": fp64_runs[-1].n_sigma_fp64},
+        "clocks": clk,
+    }
+    if args.detail:
+        print(json.dumps({"trace_mixed": results[-1].trace, "trace_fp64": fp64_runs[-1].trace}),
+              file=sys.stderr)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

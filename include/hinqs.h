@@ -1,0 +1,247 @@
+/*
+ * hinqs.h -- C ABI of the HI-NQS subspace-diagonalisation library for B300 (sm_103a).
+ *
+ * The library implements the classical half of the HI-NQS sample-diagonalise-
+ * update loop of arXiv 2606.26760: the second-quantised Hamiltonian of Sec. 2.2
+ * restricted to the SQD product subspace of sampled alpha and beta strings
+ * (Step 3), its Slater-Condon matrix elements, the sigma product H c inside a
+ * Davidson solve for the ground state (Step 3), the 1- and 2-RDMs that give the
+ * Hellmann-Feynman gradient of the energy, and the spin-marginal teacher weights
+ * of Step 4 (Eqs. alpha_marginal and beta_marginal).
+ *
+ * Conventions shared by every call
+ *  - Orbitals: n_orb spatial orbitals, 1 <= n_orb <= 64.  An occupation string
+ *    is a uint64 bitmask, bit p set when spatial orbital p is occupied.
+ *  - Integrals: h[p*n+q] (symmetric) and eri[((p*n+q)*n+r)*n+s] = (pq|rs) in
+ *    chemist order with the 8-fold real symmetry, FP64.  The Hamiltonian is
+ *    H = sum_pq h_pq E_pq + 1/2 sum_pqrs (pq|rs)(E_pq E_rs - delta_qr E_ps) + E_nuc,
+ *    the spin-free form of the Sec. 2.2 Hamiltonian.
+ *  - Determinant |I_a I_b> = prod_{p in I_a, ascending} a+_{p,alpha}
+ *    prod_{r in I_b, ascending} a+_{r,beta} |0> (alpha block first).
+ *  - Subspace: the product of the sorted unique alpha strings S_a (N_a of them)
+ *    and beta strings S_b (N_b); determinant index I = i_a * N_b + i_b, so a
+ *    vector c is an N_a x N_b row-major matrix (alpha index slow).
+ *  - Pointers: every array argument is a DEVICE pointer owned by the caller unless
+ *    its comment says "host".  Opaque handles are owned by the library and freed
+ *    with the matching *_destroy call.
+ *  - Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every call is stream-ordered; calls that return values to host
+ *    memory synchronise the stream first.
+ *  - Errors: every call returns an int status (HINQS_OK = 0, positive =
+ *    warning, negative = error, see below); on error the outputs are undefined and
+ *    hinqs_last_error_message() describes the cause (thread-local).
+ *  - Memory: handles and per-call workspaces are allocated by the library from
+ *    the stream-ordered CUDA memory pool (cudaMallocAsync).
+ */
+#ifndef HINQS_H
+#define HINQS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define HINQS_OK 0
+#define HINQS_NOT_CONVERGED 1        /* warning: outputs hold the last iterate */
+#define HINQS_ERR_ARG (-1)           /* invalid argument (NULL, size, range) */
+#define HINQS_ERR_PARTICLE_NUMBER (-2) /* string with the wrong electron count */
+#define HINQS_ERR_ASYMMETRIC (-3)    /* integrals violate the required symmetry */
+#define HINQS_ERR_OOM (-4)           /* device allocation failed */
+#define HINQS_ERR_CUDA (-5)          /* CUDA runtime error */
+#define HINQS_ERR_TIMEOUT (-6)       /* a bounded device-side wait gave up */
+#define HINQS_ERR_EMPTY (-7)         /* empty subspace */
+
+/* ------------------------------------------------------------------ flags */
+/* hinqs_build_subspace */
+#define HINQS_DROP_BAD 0x0      /* drop strings with the wrong popcount (default) */
+#define HINQS_ERROR_BAD 0x1     /* ... or fail with HINQS_ERR_PARTICLE_NUMBER */
+#define HINQS_FULL_SPACE 0x2    /* ignore the input strings, enumerate all C(n,k) */
+/* hinqs_ham_create */
+#define HINQS_CHECK_SYMMETRY 0x1 /* verify h and eri symmetry (tolerance 1e-12 relative) */
+
+/* sigma precision */
+#define HINQS_PREC_FP64 0   /* c, sigma: double; FP64 arithmetic */
+#define HINQS_PREC_FP32 1   /* c, sigma: float; FP32 arithmetic */
+
+/* Davidson precision */
+#define HINQS_DAVIDSON_FP64 0   /* every sigma in FP64 */
+#define HINQS_DAVIDSON_MIXED 1  /* FP32 sigma bulk + FP64 residual refinement */
+
+typedef struct hinqs_ham_s hinqs_ham;
+typedef struct hinqs_subspace_s hinqs_subspace;
+typedef struct hinqs_links_s hinqs_links;
+
+/* Thread-local description of the last error (never NULL). */
+const char* hinqs_last_error_message(void);
+/* Library version string. */
+const char* hinqs_version(void);
+
+/* ---------------------------------------------------------- Hamiltonian --
+ * Prepare the second-quantised Hamiltonian of Sec. 2.2 ("Given a
+ * second-quantized molecular Hamiltonian ... in an orthonormal orbital basis").
+ *   h      device, FP64 [n_orb*n_orb], copied
+ *   eri    device, FP64 [n_orb^4] chemist (pq|rs), copied
+ *   n_alpha, n_beta  electron counts of the fixed (n_alpha, n_beta) sector
+ *                    (Sec. 2.1: S_z = (n_alpha - n_beta)/2 is fixed)
+ *   e_nuc  constant added to every diagonal element (Step 3: E0 = E_corr + E_nuc)
+ *   flags  HINQS_CHECK_SYMMETRY: fail with HINQS_ERR_ASYMMETRIC when h is not
+ *          symmetric or eri lacks the 8-fold symmetry (relative 1e-12)
+ * Errors: HINQS_ERR_ARG (n_orb outside 1..64, counts outside 0..n_orb, NULL),
+ *         HINQS_ERR_ASYMMETRIC, HINQS_ERR_OOM, HINQS_ERR_CUDA. */
+int hinqs_ham_create(const double* h, const double* eri, int n_orb, int n_alpha, int n_beta,
+                     double e_nuc, int flags, hinqs_ham** out, void* stream);
+int hinqs_ham_destroy(hinqs_ham* ham);
+
+/* ------------------------------------------------------------- subspace --
+ * Build the SQD product subspace S_a x S_b from sampled strings (Step 1 removes
+ * duplicates; Sec. 2.1 keeps a residual particle-number filter as a safety net;
+ * Step 3 diagonalises in the subspace spanned by the sampled strings).
+ *   alpha  device uint64 [n_a_in] sampled alpha strings (duplicates allowed)
+ *   beta   device uint64 [n_b_in] sampled beta strings
+ *   flags  HINQS_DROP_BAD | HINQS_ERROR_BAD | HINQS_FULL_SPACE
+ *   n_dropped host int64[2] or NULL: wrong-popcount alpha / beta strings dropped
+ * Result: S_a, S_b sorted ascending, unique.  Bits at or above n_orb count as
+ * wrong strings.  Errors: HINQS_ERR_ARG, HINQS_ERR_PARTICLE_NUMBER (with
+ * HINQS_ERROR_BAD), HINQS_ERR_EMPTY (no valid string of a species), HINQS_ERR_OOM. */
+int hinqs_build_subspace(const uint64_t* alpha, int64_t n_a_in, const uint64_t* beta,
+                         int64_t n_b_in, int n_orb, int n_alpha, int n_beta, int flags,
+                         hinqs_subspace** out, int64_t* n_dropped, void* stream);
+/* host outputs N_a, N_b */
+int hinqs_subspace_dims(const hinqs_subspace* sub, int64_t* n_a, int64_t* n_b);
+/* copy S_a [N_a] and S_b [N_b] to device arrays (either may be NULL) */
+int hinqs_subspace_strings(const hinqs_subspace* sub, uint64_t* alpha_out, uint64_t* beta_out,
+                           void* stream);
+int hinqs_subspace_destroy(hinqs_subspace* sub);
+
+/* ---------------------------------------------------------- string links --
+ * Same-spin links of one spin species (spin 0 = alpha, 1 = beta): for every
+ * I in S_spin all J in S_spin whose excitation degree popcount(I xor J)/2 is 1
+ * or 2, i.e. the strings connected to I by a non-zero Hamiltonian element
+ * (the connectivity of Eq. classical_expansion), with the fermionic phase and the
+ * same-spin Slater-Condon element.  Conventions (fixed for bit-exact parity):
+ *   single: hole q in I, particle p in J, J = sign * a+_p a_q I,
+ *           hval = sign * (h_pq + sum_{j in I, j != q} [(pq|jj) - (pj|jq)])
+ *   double: holes q < s, particles p < r, J = sign * a+_p a+_r a_s a_q I,
+ *           hval = sign * ((pq|rs) - (ps|rq))
+ *   sign = (-1)^(number of occupied orbitals passed), by masked popcount.
+ * Links of a row are in ascending J order.  The handle also holds the per-string
+ * same-spin diagonal and the tables sum_{i in I} (ii|xy) used by the sigma.
+ * The handle keeps a pointer to the subspace's strings: destroy it first.
+ * Errors: HINQS_ERR_ARG (spin, handles, n_orb mismatch), HINQS_ERR_OOM. */
+int hinqs_string_links(const hinqs_ham* ham, const hinqs_subspace* sub, int spin,
+                       hinqs_links** out, void* stream);
+/* host outputs: total links, single links, max links of a row */
+int hinqs_links_count(const hinqs_links* links, int64_t* n_links, int64_t* n_singles,
+                      int64_t* max_row);
+/* Export to device arrays sized [N+1] (row_ptr) and [n_links] (others), any
+ * may be NULL.  p,q,r,s follow the conventions above (r = s = 255 for singles). */
+int hinqs_links_export(const hinqs_links* links, int64_t* row_ptr, int32_t* col, int8_t* degree,
+                       uint8_t* p, uint8_t* q, uint8_t* r, uint8_t* s, int8_t* sign,
+                       double* hval, void* stream);
+int hinqs_links_destroy(hinqs_links* links);
+
+/* ------------------------------------------------------------- diagonal --
+ * hdiag[I] = <I|H|I> (FP64, [N_a*N_b]): the H_xx of Step 2 (cold-start ranking)
+ * and of the advantage A(x) = H_xx - E0 of Eq. energy; also the Davidson
+ * preconditioner.  Includes E_nuc. */
+int hinqs_diag(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+               const hinqs_links* lb, double* hdiag, void* stream);
+
+/* ---------------------------------------------------------------- sigma --
+ * sigma = H_B c, the projected Hamiltonian of Step 3 ([H_B]_ij = <x_i|H|x_j>)
+ * applied matrix-free:
+ *   sigma = H_a C + C H_b^T + sum_{pq,rs} (pq|rs) E^a_pq C (E^b_rs)^T + E_nuc C
+ * with C the N_a x N_b matrix of c.  c and sigma are device vectors of
+ * N_a*N_b elements of the precision's type (double for HINQS_PREC_FP64, float
+ * for HINQS_PREC_FP32); sigma is overwritten; c and sigma must not overlap.
+ * la / lb are the alpha / beta links of this ham and subspace. */
+int hinqs_sigma(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                const hinqs_links* lb, const void* c, void* sigma, int precision, void* stream);
+
+/* ------------------------------------------------------------- Davidson --
+ * Lowest eigenpair of H_B by Davidson's method (Step 3, Davidson 1975), with an
+ * optional warm start from a previous eigenvector (Step 3 warm-starts from the
+ * previous iteration).  Preconditioner t = r / (H_diag - theta) with
+ * |H_diag - theta| floored at denom_floor (sign kept); classical Gram-Schmidt
+ * applied twice; restart at max_subspace keeping the current and previous Ritz
+ * vectors; projected eigenproblem, orthogonalisation, residual norms and the final
+ * energy in FP64 on the device.  Converged when ||H x - theta x||_2 <= tol_residual
+ * (x of unit norm) and |theta - theta_prev| <= tol_energy.
+ * HINQS_DAVIDSON_MIXED runs the bulk of the sigma products in FP32 and refines
+ * with FP64 residuals: each outer cycle evaluates H x in FP64 and solves for the
+ * correction in a subspace whose coupling to x uses that FP64 product. */
+typedef struct hinqs_davidson_opts {
+  int precision;        /* HINQS_DAVIDSON_FP64 | HINQS_DAVIDSON_MIXED */
+  int max_iter;         /* cap on sigma products (all precisions), e.g. 200 */
+  int max_subspace;     /* m_max >= 3, e.g. 16 */
+  double tol_residual;  /* e.g. 1e-8 */
+  double tol_energy;    /* e.g. 1e-10 */
+  double denom_floor;   /* e.g. 1e-4 */
+  double inner_tol;     /* mixed: inner solve stops when its residual falls by this factor (e.g. 1e-3) */
+  int trace_cap;        /* capacity of the host trace arrays below (0 = none) */
+  double* trace_theta;  /* host [trace_cap] or NULL: theta per iteration (incl. E_nuc) */
+  double* trace_resid;  /* host [trace_cap] or NULL: residual norm estimate per iteration */
+  double* trace_time;   /* host [trace_cap] or NULL: seconds since the call began */
+  int* trace_kind;      /* host [trace_cap] or NULL: 0 = FP64 iterate, 1 = FP32 inner iterate */
+} hinqs_davidson_opts;
+
+typedef struct hinqs_davidson_info {
+  int status;           /* HINQS_OK or HINQS_NOT_CONVERGED */
+  int iterations;       /* Davidson iterations */
+  int n_sigma_fp64;     /* FP64 sigma products */
+  int n_sigma_fp32;     /* FP32 sigma products */
+  int n_restarts;
+  int n_refinements;    /* mixed: outer FP64 refinement cycles */
+  int trace_len;        /* entries written to the trace arrays */
+  double energy;        /* final energy (FP64 Rayleigh quotient, incl. E_nuc) */
+  double residual;      /* final FP64 ||H x - E x||_2 */
+  double seconds;       /* wall time of the call */
+} hinqs_davidson_info;
+
+/* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace). */
+void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
+
+/*   guess   device FP64 [N] or NULL (then e_k at argmin H_diag, lowest index on ties)
+ *   energy  host double or NULL: final energy
+ *   c_out   device FP64 [N]: unit-norm eigenvector
+ *   info    host or NULL
+ * Returns HINQS_OK, HINQS_NOT_CONVERGED (max_iter reached; outputs hold the last
+ * iterate), or an error. */
+int hinqs_davidson(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                   const hinqs_links* lb, const double* guess, const hinqs_davidson_opts* opts,
+                   double* energy, double* c_out, hinqs_davidson_info* info, void* stream);
+
+/* ------------------------------------------------------------------ RDMs --
+ * Spin-summed reduced density matrices of the state c (FP64 [N], used as given):
+ *   rdm1[p*n+q]             = sum_s <c|a+_{ps} a_{qs}|c>
+ *   rdm2[((p*n+q)*n+r)*n+s] = sum_{s,t} <c|a+_{ps} a+_{rt} a_{st} a_{qs}|c>
+ *                           = <c|E_pq E_rs - delta_qr E_ps|c>
+ * so <c|H|c> = sum h*rdm1 + 1/2 sum (pq|rs)*rdm2 + E_nuc <c|c>.  For a normalised
+ * eigenvector these are the Hellmann-Feynman derivatives dE/dh_pq = rdm1_pq and
+ * dE/d(pq|rs) = rdm2_pqrs / 2 entrywise (not in the paper: the gradient the
+ * integrals receive when the energy is differentiated).  rdm2 may be NULL. */
+int hinqs_rdm(const hinqs_subspace* sub, const hinqs_links* la, const hinqs_links* lb,
+              const double* c, double* rdm1, double* rdm2, void* stream);
+
+/* grad_h = grad_E * rdm1, grad_eri = grad_E * rdm2 / 2 (device [n^2], [n^4]);
+ * the backward of E(h, eri) given the RDMs of the normalised eigenvector.
+ * grad_eri may be NULL. */
+int hinqs_energy_backward(int n_orb, double grad_E, const double* rdm1, const double* rdm2,
+                          double* grad_h, double* grad_eri, void* stream);
+
+/* ------------------------------------------------------ spin marginals --
+ * Step 4 teacher: spin marginals of |Psi|^2 (Eqs. alpha_marginal, beta_marginal),
+ *   p_alpha[a] = sum_b c[a*N_b+b]^2 / |c|^2,   p_beta[b] = sum_a c[a*N_b+b]^2 / |c|^2,
+ * and optionally the factorised teacher weight normalised over the basis,
+ *   w[a*N_b+b] = p_alpha[a] p_beta[b] / sum_{a',b'} p_alpha[a'] p_beta[b'].
+ *   c device FP64 [N]; p_alpha [N_a], p_beta [N_b], w [N] or NULL. */
+int hinqs_spin_marginals(const hinqs_subspace* sub, const double* c, double* p_alpha,
+                         double* p_beta, double* w, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HINQS_H */

@@ -49,7 +49,7 @@ def _load():
         lib.oracle_sigma.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, P, i64, i32]
         lib.oracle_dense_h.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P]
         lib.oracle_diag.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, i64]
-        lib.oracle_links.argtypes = [i32, i32, P, P, P, i64, P, P, P, P, P, P, P, P, P]
+        lib.oracle_links.argtypes = [i32, i32, P, P, P, i64, P, i64, P, P, P, P, P, P, P, P, P]
         lib.oracle_rdm.argtypes = [i32, P, i64, P, i64, P, P, P, i32]
         lib.oracle_marginals.argtypes = [P, i64, i64, P, P, P]
         lib.oracle_max_threads.argtypes = []
@@ -143,13 +143,17 @@ def diag(H: Ham, sa, sb, rows=None):
     return out
 
 
-def links(H: Ham, S, n_e: int):
-    """Same-spin single/double links of the sorted string set S (see oracle_links)."""
+def links(H: Ham, S, n_e: int, rows=None):
+    """Same-spin single/double links of the sorted string set S (see oracle_links);
+    rows: only those rows (output row k is row rows[k])."""
     lib = _load()
     S = _u64(S)
     N = len(S)
-    row_ptr = np.zeros(N + 1, dtype=np.int64)
-    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(row_ptr),
+    rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    n_out = N if rows_a is None else len(rows_a)
+    nr = 0 if rows_a is None else len(rows_a)
+    row_ptr = np.zeros(n_out + 1, dtype=np.int64)
+    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(rows_a), nr, _p(row_ptr),
                           None, None, None, None, None, None, None, None)
     if rc:
         raise ValueError(f"oracle_links failed ({rc})")
@@ -157,7 +161,8 @@ def links(H: Ham, S, n_e: int):
     out = dict(row_ptr=row_ptr, col=np.zeros(nnz, np.int32), degree=np.zeros(nnz, np.int8),
                p=np.zeros(nnz, np.uint8), q=np.zeros(nnz, np.uint8), r=np.zeros(nnz, np.uint8),
                s=np.zeros(nnz, np.uint8), sign=np.zeros(nnz, np.int8), hval=np.zeros(nnz))
-    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(row_ptr), _p(out["col"]),
+    rc = lib.oracle_links(H.n, n_e, _p(H.h), _p(H.eri), _p(S), N, _p(rows_a), nr, _p(row_ptr),
+                          _p(out["col"]),
                           _p(out["degree"]), _p(out["p"]), _p(out["q"]), _p(out["r"]),
                           _p(out["s"]), _p(out["sign"]), _p(out["hval"]))
     if rc:

@@ -341,19 +341,23 @@ static int in_list(const int *l, int m, int v) {
  * ordered list of I.  hval = <J|H_spin|I>, the part of H whose operators all
  * act on this spin, found by applying H to the one-species determinant I (the
  * other species empty) and collecting the coefficient of J.
- * Call with col == NULL to get only the row counts in row_ptr[1..N]
+ * rows (NULL: all) selects the rows I = rows[k]; output row k holds row rows[k].
+ * Call with col == NULL to get only the row counts in row_ptr[1..n_out]
  * (row_ptr[0] = 0, then prefix sums); the second call fills the records. */
 int oracle_links(int n, int ne, const double *h, const double *eri, const uint64_t *S, int64_t N,
+                 const int64_t *rows, int64_t n_rows,
                  int64_t *row_ptr, int32_t *col, int8_t *degree, uint8_t *p_out, uint8_t *q_out,
                  uint8_t *r_out, uint8_t *s_out, int8_t *sign_out, double *hval) {
     if (n < 1 || n > 64 || ne < 0 || ne > n || !h || !eri || !S || !row_ptr || N < 0) return -1;
     oham H = {n, h, eri, 0.0};
+    int64_t n_out = rows ? n_rows : N;
     if (!col) {
         row_ptr[0] = 0;
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
-        for (int64_t I = 0; I < N; ++I) {
+        for (int64_t k = 0; k < n_out; ++k) {
+            int64_t I = rows ? rows[k] : k;
             int oi[64], ni;
             occ_list(n, S[I], oi, &ni);
             int64_t cnt = 0;
@@ -364,21 +368,22 @@ int oracle_links(int n, int ne, const double *h, const double *eri, const uint64
                     if (!in_list(oj, nj, oi[k])) ++nh;
                 if (nh == 1 || nh == 2) ++cnt;
             }
-            row_ptr[I + 1] = cnt;
+            row_ptr[k + 1] = cnt;
         }
-        for (int64_t I = 0; I < N; ++I) row_ptr[I + 1] += row_ptr[I];
+        for (int64_t k = 0; k < n_out; ++k) row_ptr[k + 1] += row_ptr[k];
         return 0;
     }
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 16)
 #endif
-    for (int64_t I = 0; I < N; ++I) {
+    for (int64_t kr = 0; kr < n_out; ++kr) {
+        int64_t I = rows ? rows[kr] : kr;
         int oi[64], ni;
         occ_list(n, S[I], oi, &ni);
         odet DI;
         DI.ne = ni;
         for (int k = 0; k < ni; ++k) DI.so[k] = oi[k];
-        int64_t pos = row_ptr[I];
+        int64_t pos = row_ptr[kr];
         for (int64_t J = 0; J < N; ++J) {
             int oj[64], nj;
             occ_list(n, S[J], oj, &nj);

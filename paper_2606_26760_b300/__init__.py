@@ -1,0 +1,359 @@
+"""HI-NQS subspace diagonalisation on B300: thin Python binding of libhinqs.so.
+
+Every step of the hot path runs in the library's CUDA kernels; this module only
+marshals arguments (torch tensors provide device memory and the current CUDA
+stream).  There is no CPU fallback: if the library is not built, or no CUDA
+device is present, the calls raise.
+
+Names follow the C ABI in include/hinqs.h:
+    Hamiltonian            hinqs_ham_create      (Sec. 2.2 Hamiltonian)
+    build_subspace         hinqs_build_subspace  (Step 1 dedupe, Sec. 2.1 filter, Step 3 SQD product)
+    string_links           hinqs_string_links    (Slater-Condon connectivity, Eq. classical_expansion)
+    diag                   hinqs_diag            (H_xx of Step 2)
+    sigma                  hinqs_sigma           (projected H applied, Step 3)
+    davidson               hinqs_davidson        (Step 3 Davidson)
+    rdm / energy_backward  hinqs_rdm / hinqs_energy_backward (Hellmann-Feynman gradient)
+    spin_marginals         hinqs_spin_marginals  (Step 4, Eqs. alpha_marginal / beta_marginal)
+    HinqsEnergy            torch.autograd.Function: E(h, eri) with the RDM backward
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass, field
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libhinqs.so")
+
+OK, NOT_CONVERGED = 0, 1
+ERR_ARG, ERR_PARTICLE_NUMBER, ERR_ASYMMETRIC, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_EMPTY = (
+    -1, -2, -3, -4, -5, -6, -7)
+DROP_BAD, ERROR_BAD, FULL_SPACE = 0x0, 0x1, 0x2
+CHECK_SYMMETRY = 0x1
+PREC_FP64, PREC_FP32 = 0, 1
+DAVIDSON_FP64, DAVIDSON_MIXED = 0, 1
+
+
+class HinqsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"hinqs error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("max_subspace", ctypes.c_int), ("tol_residual", ctypes.c_double),
+                ("tol_energy", ctypes.c_double), ("denom_floor", ctypes.c_double),
+                ("inner_tol", ctypes.c_double), ("trace_cap", ctypes.c_int),
+                ("trace_theta", ctypes.POINTER(ctypes.c_double)),
+                ("trace_resid", ctypes.POINTER(ctypes.c_double)),
+                ("trace_time", ctypes.POINTER(ctypes.c_double)),
+                ("trace_kind", ctypes.POINTER(ctypes.c_int))]
+
+
+class _Info(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("iterations", ctypes.c_int),
+                ("n_sigma_fp64", ctypes.c_int), ("n_sigma_fp32", ctypes.c_int),
+                ("n_restarts", ctypes.c_int), ("n_refinements", ctypes.c_int),
+                ("trace_len", ctypes.c_int), ("energy", ctypes.c_double),
+                ("residual", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+
+EXPORTED = [
+    "hinqs_last_error_message", "hinqs_version", "hinqs_ham_create", "hinqs_ham_destroy",
+    "hinqs_build_subspace", "hinqs_subspace_dims", "hinqs_subspace_strings",
+    "hinqs_subspace_destroy", "hinqs_string_links", "hinqs_links_count", "hinqs_links_export",
+    "hinqs_links_destroy", "hinqs_diag", "hinqs_sigma", "hinqs_davidson_default_opts",
+    "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
+]
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libhinqs.so (no compute; works without a GPU)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is not built: run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
+    P, I, I64, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    PI64 = ctypes.POINTER(ctypes.c_int64)
+    lib.hinqs_last_error_message.restype = ctypes.c_char_p
+    lib.hinqs_version.restype = ctypes.c_char_p
+    lib.hinqs_ham_create.argtypes = [P, P, I, I, I, D, I, PP, P]
+    lib.hinqs_ham_destroy.argtypes = [P]
+    lib.hinqs_build_subspace.argtypes = [P, I64, P, I64, I, I, I, I, PP, PI64, P]
+    lib.hinqs_subspace_dims.argtypes = [P, PI64, PI64]
+    lib.hinqs_subspace_strings.argtypes = [P, P, P, P]
+    lib.hinqs_subspace_destroy.argtypes = [P]
+    lib.hinqs_string_links.argtypes = [P, P, I, PP, P]
+    lib.hinqs_links_count.argtypes = [P, PI64, PI64, PI64]
+    lib.hinqs_links_export.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
+    lib.hinqs_links_destroy.argtypes = [P]
+    lib.hinqs_diag.argtypes = [P, P, P, P, P, P]
+    lib.hinqs_sigma.argtypes = [P, P, P, P, P, P, I, P]
+    lib.hinqs_davidson_default_opts.argtypes = [ctypes.POINTER(_Opts)]
+    lib.hinqs_davidson_default_opts.restype = None
+    lib.hinqs_davidson.argtypes = [P, P, P, P, P, ctypes.POINTER(_Opts),
+                                   ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(_Info), P]
+    lib.hinqs_rdm.argtypes = [P, P, P, P, P, P, P]
+    lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
+    lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
+    _lib = lib
+    return lib
+
+
+def _check(rc, allow_warning=False):
+    if rc == OK or (allow_warning and rc > 0):
+        return rc
+    raise HinqsError(rc, _lib.hinqs_last_error_message().decode())
+
+
+def _dev():
+    if not torch.cuda.is_available():
+        raise RuntimeError("hinqs needs a CUDA device; there is no CPU fallback")
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _on_dev(x, dtype):
+    dev = _dev()
+    if isinstance(x, torch.Tensor):
+        return x.to(device=dev, dtype=dtype).contiguous()
+    import numpy as np
+    return torch.from_numpy(np.ascontiguousarray(x)).to(device=dev, dtype=dtype)
+
+
+def _u64(x):
+    import numpy as np
+    if isinstance(x, torch.Tensor):
+        return x.to(device=_dev()).contiguous()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.uint64)).view(np.int64)
+    return torch.from_numpy(a).to(_dev())
+
+
+class Hamiltonian:
+    """Prepared integrals (device copies): h[n,n], eri[n,n,n,n] chemist order."""
+
+    def __init__(self, h, eri, n_alpha: int, n_beta: int, e_nuc: float = 0.0,
+                 check_symmetry: bool = False):
+        lib = load_library()
+        self.h = _on_dev(h, torch.float64)
+        self.eri = _on_dev(eri, torch.float64)
+        self.n = int(self.h.shape[0])
+        self.n_alpha, self.n_beta, self.e_nuc = int(n_alpha), int(n_beta), float(e_nuc)
+        out = ctypes.c_void_p()
+        _check(lib.hinqs_ham_create(_ptr(self.h), _ptr(self.eri), self.n, self.n_alpha,
+                                    self.n_beta, self.e_nuc, CHECK_SYMMETRY if check_symmetry else 0,
+                                    ctypes.byref(out), _stream()))
+        self.handle = out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.hinqs_ham_destroy(self.handle)
+            self.handle = None
+
+
+class Subspace:
+    def __init__(self, handle, n, n_alpha, n_beta, dropped):
+        self.handle = handle
+        self.n, self.n_alpha, self.n_beta = n, n_alpha, n_beta
+        na, nb = ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hinqs_subspace_dims(handle, ctypes.byref(na), ctypes.byref(nb)))
+        self.Na, self.Nb = na.value, nb.value
+        self.N = self.Na * self.Nb
+        self.dropped = dropped
+
+    def strings(self):
+        a = torch.empty(self.Na, dtype=torch.int64, device=_dev())
+        b = torch.empty(self.Nb, dtype=torch.int64, device=_dev())
+        _check(_lib.hinqs_subspace_strings(self.handle, _ptr(a), _ptr(b), _stream()))
+        return a, b
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.hinqs_subspace_destroy(self.handle)
+            self.handle = None
+
+
+def build_subspace(alpha, beta, n_orb: int, n_alpha: int, n_beta: int, flags: int = DROP_BAD):
+    """SQD product subspace from sampled strings (uint64 bitmasks)."""
+    lib = load_library()
+    _dev()
+    a = _u64(alpha) if alpha is not None else None
+    b = _u64(beta) if beta is not None else None
+    out = ctypes.c_void_p()
+    dropped = (ctypes.c_int64 * 2)()
+    _check(lib.hinqs_build_subspace(_ptr(a), 0 if a is None else a.numel(), _ptr(b),
+                                    0 if b is None else b.numel(), n_orb, n_alpha, n_beta, flags,
+                                    ctypes.byref(out), dropped, _stream()))
+    return Subspace(out, n_orb, n_alpha, n_beta, (dropped[0], dropped[1]))
+
+
+class Links:
+    def __init__(self, handle, spin, sub):
+        self.handle, self.spin, self._sub = handle, spin, sub
+        nl, ns, mr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(_lib.hinqs_links_count(handle, ctypes.byref(nl), ctypes.byref(ns), ctypes.byref(mr)))
+        self.n_links, self.n_singles, self.max_row = nl.value, ns.value, mr.value
+
+    def export(self):
+        dev = _dev()
+        N = self._sub.Nb if self.spin else self._sub.Na
+        m = self.n_links
+        out = dict(row_ptr=torch.empty(N + 1, dtype=torch.int64, device=dev),
+                   col=torch.empty(m, dtype=torch.int32, device=dev),
+                   degree=torch.empty(m, dtype=torch.int8, device=dev),
+                   p=torch.empty(m, dtype=torch.uint8, device=dev),
+                   q=torch.empty(m, dtype=torch.uint8, device=dev),
+                   r=torch.empty(m, dtype=torch.uint8, device=dev),
+                   s=torch.empty(m, dtype=torch.uint8, device=dev),
+                   sign=torch.empty(m, dtype=torch.int8, device=dev),
+                   hval=torch.empty(m, dtype=torch.float64, device=dev))
+        _check(_lib.hinqs_links_export(self.handle, *(_ptr(out[k]) for k in (
+            "row_ptr", "col", "degree", "p", "q", "r", "s", "sign", "hval")), _stream()))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.hinqs_links_destroy(self.handle)
+            self.handle = None
+
+
+def string_links(ham: Hamiltonian, sub: Subspace, spin: int) -> Links:
+    out = ctypes.c_void_p()
+    _check(_lib.hinqs_string_links(ham.handle, sub.handle, spin, ctypes.byref(out), _stream()))
+    return Links(out, spin, sub)
+
+
+def diag(ham, sub, la, lb, out=None):
+    out = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if out is None else out
+    _check(_lib.hinqs_diag(ham.handle, sub.handle, la.handle, lb.handle, _ptr(out), _stream()))
+    return out
+
+
+def sigma(ham, sub, la, lb, c, out=None, precision: int | None = None):
+    """sigma = H_B c; precision from c's dtype (float64 -> FP64, float32 -> FP32)."""
+    if precision is None:
+        precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
+    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    if c.dtype != dt or not c.is_cuda or not c.is_contiguous():
+        raise ValueError(f"c must be a contiguous CUDA {dt} tensor")
+    if c.numel() != sub.N:
+        raise ValueError(f"c has {c.numel()} elements, subspace has {sub.N}")
+    out = torch.empty_like(c) if out is None else out
+    _check(_lib.hinqs_sigma(ham.handle, sub.handle, la.handle, lb.handle, _ptr(c), _ptr(out),
+                            precision, _stream()))
+    return out
+
+
+@dataclass
+class DavidsonResult:
+    energy: float
+    c: torch.Tensor
+    status: int
+    iterations: int
+    n_sigma_fp64: int
+    n_sigma_fp32: int
+    n_restarts: int
+    n_refinements: int
+    residual: float
+    seconds: float
+    trace: dict = field(default_factory=dict)
+
+
+def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
+             max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
+             denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
+             out=None) -> DavidsonResult:
+    opts = _Opts()
+    _lib.hinqs_davidson_default_opts(ctypes.byref(opts))
+    opts.precision, opts.max_iter, opts.max_subspace = precision, max_iter, max_subspace
+    opts.tol_residual, opts.tol_energy, opts.denom_floor = tol_residual, tol_energy, denom_floor
+    opts.inner_tol = inner_tol
+    bufs = None
+    if trace_cap > 0:
+        bufs = ((ctypes.c_double * trace_cap)(), (ctypes.c_double * trace_cap)(),
+                (ctypes.c_double * trace_cap)(), (ctypes.c_int * trace_cap)())
+        opts.trace_cap = trace_cap
+        opts.trace_theta = ctypes.cast(bufs[0], ctypes.POINTER(ctypes.c_double))
+        opts.trace_resid = ctypes.cast(bufs[1], ctypes.POINTER(ctypes.c_double))
+        opts.trace_time = ctypes.cast(bufs[2], ctypes.POINTER(ctypes.c_double))
+        opts.trace_kind = ctypes.cast(bufs[3], ctypes.POINTER(ctypes.c_int))
+    c = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if out is None else out
+    if guess is not None and (guess.dtype != torch.float64 or guess.numel() != sub.N):
+        raise ValueError("guess must be a float64 tensor of the subspace size")
+    e = ctypes.c_double()
+    info = _Info()
+    rc = _lib.hinqs_davidson(ham.handle, sub.handle, la.handle, lb.handle, _ptr(guess),
+                             ctypes.byref(opts), ctypes.byref(e), _ptr(c), ctypes.byref(info),
+                             _stream())
+    _check(rc, allow_warning=True)
+    tr = {}
+    if bufs is not None:
+        n = info.trace_len
+        tr = dict(theta=list(bufs[0][:n]), resid=list(bufs[1][:n]), time=list(bufs[2][:n]),
+                  kind=list(bufs[3][:n]))
+    return DavidsonResult(e.value, c, rc, info.iterations, info.n_sigma_fp64, info.n_sigma_fp32,
+                          info.n_restarts, info.n_refinements, info.residual, info.seconds, tr)
+
+
+def rdm(sub, la, lb, c, want2: bool = True):
+    n = sub.n
+    g1 = torch.empty((n, n), dtype=torch.float64, device=_dev())
+    g2 = torch.empty((n, n, n, n), dtype=torch.float64, device=_dev()) if want2 else None
+    _check(_lib.hinqs_rdm(sub.handle, la.handle, lb.handle, _ptr(c), _ptr(g1), _ptr(g2), _stream()))
+    return g1, g2
+
+
+def energy_backward(n_orb, grad_E, rdm1, rdm2):
+    gh = torch.empty_like(rdm1)
+    ge = torch.empty_like(rdm2) if rdm2 is not None else None
+    _check(_lib.hinqs_energy_backward(n_orb, float(grad_E), _ptr(rdm1), _ptr(rdm2), _ptr(gh),
+                                      _ptr(ge), _stream()))
+    return gh, ge
+
+
+def spin_marginals(sub, c, want_w: bool = False):
+    pa = torch.empty(sub.Na, dtype=torch.float64, device=_dev())
+    pb = torch.empty(sub.Nb, dtype=torch.float64, device=_dev())
+    w = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if want_w else None
+    _check(_lib.hinqs_spin_marginals(sub.handle, _ptr(c), _ptr(pa), _ptr(pb), _ptr(w), _stream()))
+    return (pa, pb, w) if want_w else (pa, pb)
+
+
+class HinqsEnergy(torch.autograd.Function):
+    """E0(h, eri) of the projected Hamiltonian (Step 3) with the Hellmann-Feynman
+    backward dE/dh = gamma, dE/d(pq|rs) = Gamma/2 (entrywise)."""
+
+    @staticmethod
+    def forward(ctx, h, eri, sub, n_alpha, n_beta, e_nuc, opts):
+        ham = Hamiltonian(h.detach(), eri.detach(), n_alpha, n_beta, e_nuc)
+        la, lb = string_links(ham, sub, 0), string_links(ham, sub, 1)
+        res = davidson(ham, sub, la, lb, **(opts or {}))
+        ctx.sub, ctx.la, ctx.lb, ctx.c, ctx.n = sub, la, lb, res.c, ham.n
+        ctx.ham = ham
+        return torch.tensor(res.energy, dtype=torch.float64, device=h.device)
+
+    @staticmethod
+    def backward(ctx, grad_E):
+        g1, g2 = rdm(ctx.sub, ctx.la, ctx.lb, ctx.c, want2=ctx.needs_input_grad[1])
+        gh, ge = energy_backward(ctx.n, float(grad_E), g1, g2)
+        return gh, ge, None, None, None, None, None
+
+
+def energy(h, eri, sub, n_alpha, n_beta, e_nuc=0.0, **opts):
+    return HinqsEnergy.apply(h, eri, sub, n_alpha, n_beta, e_nuc, opts)

@@ -1,0 +1,720 @@
+// K8: Davidson eigensolver (Step 3) on the device, FP64 and mixed precision.
+//
+// FP64 mode: the textbook method.  Basis V (orthonormal, FP64), W = H V, projected
+// matrix G = V^T W (FP64, m x m), lowest Ritz pair (theta, y) by parallel cyclic
+// Jacobi in one thread block, residual r = W y - theta V y, correction
+// t = r / (H_diag - theta) with |H_diag - theta| floored, classical Gram-Schmidt
+// twice, restart at m_max keeping the current and previous Ritz vectors.
+//
+// Mixed mode (FP32 bulk, FP64 refinement): outer cycles keep an FP64 unit
+// vector x with its FP64 product s = H x.  Each cycle solves for the correction in
+// the subspace {x} + span{v_1..v_m}, where the v_i and w_i = H v_i are FP32
+// (FP32 sigma) and the projected matrix is FP64 with G_00 = x.s, G_0i = s.v_i
+// (exact coupling through the FP64 product and the symmetry of H) and
+// G_ij = v_i.w_j.  The cycle's Ritz vector becomes the next x.  Rounding in the
+// FP32 products enters only through the correction, so every cycle gains
+// accuracy until the FP64 residual meets the tolerance.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <vector>
+
+#include "hinqs_internal.cuh"
+
+namespace hinqs {
+
+int check_triplet(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                  const hinqs_links_s* lb, const char* who);
+
+constexpr int kMaxSub = 32;
+constexpr int kRedGrid = 2 * kNumSMs;
+constexpr int kRedThreads = 256;
+
+// ---------------------------------------------------------------- kernels --
+
+// partial[b*m + i] = sum over this block's elements of A_i . bvec
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, int64_t lda, int m,
+                                                      const TB* __restrict__ b, int64_t N,
+                                                      double* __restrict__ partial) {
+  double acc[kMaxSub];
+#pragma unroll
+  for (int i = 0; i < kMaxSub; ++i) acc[i] = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double bj = (double)b[j];
+#pragma unroll
+    for (int i = 0; i < kMaxSub; ++i)
+      if (i < m) acc[i] += (double)A[i * lda + j] * bj;
+  }
+  __shared__ double red[kRedThreads / 32][kMaxSub];
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < kMaxSub; ++i) {
+    if (i >= m) break;
+    double v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) red[wid][i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
+    partial[blockIdx.x * m + threadIdx.x] = v;
+  }
+}
+
+// out[i] = sum_b partial[b*m + i] (fixed order: deterministic)
+__global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int m,
+                                  double* __restrict__ out) {
+  int i = threadIdx.x;
+  if (i < m) {
+    double v = 0.0;
+    for (int b = 0; b < nb; ++b) v += partial[b * m + i];
+    out[i] = v;
+  }
+}
+
+// out (FP64) = alpha*out + sum_i coef[i] * A_i      (mode 0: set, 1: add, -1: subtract)
+template <typename TA>
+__global__ void k_lincomb(double* __restrict__ out, const TA* __restrict__ A, int64_t lda, int m,
+                          const double* __restrict__ coef, int64_t N, int mode) {
+  __shared__ double c[kMaxSub];
+  if (threadIdx.x < m) c[threadIdx.x] = coef[threadIdx.x];
+  __syncthreads();
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double v = 0.0;
+    for (int i = 0; i < m; ++i) v += c[i] * (double)A[i * lda + j];
+    if (mode == 0) out[j] = v;
+    else if (mode > 0) out[j] += v;
+    else out[j] -= v;
+  }
+}
+
+// y = x / sqrt(nrm2[0]) with type conversion
+template <typename TO>
+__global__ void k_scale_store(const double* __restrict__ x, const double* __restrict__ nrm2,
+                              TO* __restrict__ y, int64_t N) {
+  double s = 1.0 / sqrt(nrm2[0]);
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x)
+    y[j] = (TO)(x[j] * s);
+}
+
+// Residual and preconditioned correction.
+//   r = y0*s0 + sum_i y[i] W_i - theta*(y0*x0 + sum_i y[i] V_i)
+//   t = r / floor(D - theta);  partial ||r||^2 per block
+// (x0, s0 may be NULL; then y0 is ignored.)
+template <typename TV>
+__global__ void __launch_bounds__(kRedThreads) k_residual(
+    const double* __restrict__ x0, const double* __restrict__ s0, const TV* __restrict__ V,
+    const TV* __restrict__ W, int64_t ld, int m, const double* __restrict__ ritz, /* [0]=theta, [1..]=y */
+    int has_x0, const double* __restrict__ D, double floor_, int64_t N, double* __restrict__ t,
+    double* __restrict__ partial) {
+  __shared__ double y[kMaxSub + 1];
+  __shared__ double red[kRedThreads / 32];
+  if (threadIdx.x <= m + has_x0) y[threadIdx.x] = ritz[1 + threadIdx.x];
+  __syncthreads();
+  const double theta = ritz[0];
+  double acc = 0.0;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    double hx = 0.0, xx = 0.0;
+    int o = 0;
+    if (has_x0) {
+      hx = y[0] * s0[j];
+      xx = y[0] * x0[j];
+      o = 1;
+    }
+    for (int i = 0; i < m; ++i) {
+      hx += y[o + i] * (double)W[i * ld + j];
+      xx += y[o + i] * (double)V[i * ld + j];
+    }
+    double r = hx - theta * xx;
+    acc += r * r;
+    double den = D[j] - theta;
+    if (fabs(den) < floor_) den = (den < 0.0) ? -floor_ : floor_;
+    t[j] = r / den;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w];
+    partial[blockIdx.x] = v;
+  }
+}
+
+// Lowest eigenpair of the symmetric m x m matrix G (row-major, leading dim ldg)
+// by cyclic Jacobi with the round-robin parallel ordering; one block.
+// out[0] = theta, out[1..m] = unit eigenvector (sign: largest component > 0).
+__global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __restrict__ out,
+                     double* __restrict__ all_evals) {
+  __shared__ double A[kMaxSub][kMaxSub + 1];
+  __shared__ double Q[kMaxSub][kMaxSub + 1];
+  __shared__ double cs[kMaxSub / 2][2];
+  __shared__ int pr[kMaxSub / 2][2];
+  __shared__ int order[kMaxSub];
+  __shared__ double offn;
+  const int tid = threadIdx.x;
+  int mm = m + (m & 1);  // even size for the tournament; padded row/col is isolated
+  for (int i = tid; i < mm * mm; i += blockDim.x) {
+    int r = i / mm, c = i % mm;
+    double v = 0.0;
+    if (r < m && c < m) v = 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
+    else if (r == c) v = 1e300;  // padding: never the lowest
+    A[r][c] = v;
+    Q[r][c] = (r == c) ? 1.0 : 0.0;
+  }
+  if (tid < mm) order[tid] = tid;
+  __syncthreads();
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    if (tid == 0) {
+      double s = 0.0, d = 0.0;
+      for (int r = 0; r < m; ++r)
+        for (int c = 0; c < m; ++c) {
+          if (r != c) s += A[r][c] * A[r][c];
+          else d += A[r][c] * A[r][c];
+        }
+      offn = (s <= 1e-30 * d || s == 0.0) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    if (offn > 0.5) break;
+    for (int step = 0; step < mm - 1; ++step) {
+      // pairs of the round-robin schedule
+      if (tid < mm / 2) {
+        int p = order[tid], q = order[mm - 1 - tid];
+        if (p > q) {
+          int t = p;
+          p = q;
+          q = t;
+        }
+        pr[tid][0] = p;
+        pr[tid][1] = q;
+        double apq = A[p][q], c = 1.0, s = 0.0;
+        if (apq != 0.0 && p < m && q < m) {
+          double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[tid][0] = c;
+        cs[tid][1] = s;
+      }
+      __syncthreads();
+      // A <- J^T A (rows p, q)
+      for (int i = tid; i < (mm / 2) * mm; i += blockDim.x) {
+        int k = i / mm, col = i % mm;
+        int p = pr[k][0], q = pr[k][1];
+        double c = cs[k][0], s = cs[k][1];
+        double ap = A[p][col], aq = A[q][col];
+        A[p][col] = c * ap - s * aq;
+        A[q][col] = s * ap + c * aq;
+      }
+      __syncthreads();
+      // A <- A J (cols p, q), Q <- Q J
+      for (int i = tid; i < (mm / 2) * mm; i += blockDim.x) {
+        int k = i / mm, row = i % mm;
+        int p = pr[k][0], q = pr[k][1];
+        double c = cs[k][0], s = cs[k][1];
+        double ap = A[row][p], aq = A[row][q];
+        A[row][p] = c * ap - s * aq;
+        A[row][q] = s * ap + c * aq;
+        double qp = Q[row][p], qq = Q[row][q];
+        Q[row][p] = c * qp - s * qq;
+        Q[row][q] = s * qp + c * qq;
+      }
+      __syncthreads();
+      if (tid == 0) {  // rotate the tournament, order[0] fixed
+        int last = order[mm - 1];
+        for (int k = mm - 1; k > 1; --k) order[k] = order[k - 1];
+        order[1] = last;
+      }
+      __syncthreads();
+    }
+  }
+  if (tid == 0) {
+    int best = 0;
+    for (int k = 1; k < m; ++k)
+      if (A[k][k] < A[best][best]) best = k;
+    double big = 0.0;
+    int arg = 0;
+    for (int r = 0; r < m; ++r)
+      if (fabs(Q[r][best]) > big) {
+        big = fabs(Q[r][best]);
+        arg = r;
+      }
+    double sg = Q[arg][best] < 0.0 ? -1.0 : 1.0;
+    out[0] = A[best][best];
+    double nrm = 0.0;
+    for (int r = 0; r < m; ++r) nrm += Q[r][best] * Q[r][best];
+    nrm = 1.0 / sqrt(nrm);
+    for (int r = 0; r < m; ++r) out[1 + r] = sg * Q[r][best] * nrm;
+    for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
+    if (all_evals)
+      for (int r = 0; r < m; ++r) all_evals[r] = A[r][r];
+  }
+}
+
+// argmin of D (lowest index on ties) -> idx[0]
+__global__ void k_argmin(const double* __restrict__ D, int64_t N, unsigned long long* best) {
+  // pack (orderable value, index) into 128 bits via two passes would be exact; here the
+  // value is mapped to an order-preserving uint64 and compared lexicographically.
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(D[j]);
+    u = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+    unsigned long long cur = atomicMin(best, u);
+    (void)cur;
+  }
+}
+__global__ void k_argmin_index(const double* __restrict__ D, int64_t N,
+                               const unsigned long long* best, unsigned long long* idx) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    unsigned long long u = (unsigned long long)__double_as_longlong(D[j]);
+    u = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+    if (u == *best) atomicMin(idx, (unsigned long long)j);
+  }
+}
+__global__ void k_unit(double* x, int64_t N, const unsigned long long* idx) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x)
+    x[j] = (j == (int64_t)*idx) ? 1.0 : 0.0;
+}
+
+__global__ void k_set_G(double* G, int ldg, int col, const double* vals, int m, int row_off) {
+  int i = threadIdx.x;
+  if (i < m) {
+    G[(row_off + i) * ldg + col] = vals[i];
+    G[col * ldg + row_off + i] = vals[i];
+  }
+}
+
+__global__ void k_f64_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t N) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x)
+    y[j] = (float)x[j];
+}
+
+// ------------------------------------------------------------ host helpers --
+
+struct Ctx {
+  const hinqs_ham_s* H;
+  const hinqs_subspace_s* B;
+  const hinqs_links_s* la;
+  const hinqs_links_s* lb;
+  cudaStream_t s;
+  int64_t N;
+  int grid;
+  double* partial = nullptr;  // [kRedGrid * (kMaxSub+1)]
+  double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
+};
+
+template <typename TA, typename TB>
+static int dots(Ctx& c, const TA* A, int64_t lda, int m, const TB* b, double* out) {
+  k_dots<TA, TB><<<kRedGrid, kRedThreads, 0, c.s>>>(A, lda, m, b, c.N, c.partial);
+  k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, m, out);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+template <typename TA>
+static int lincomb(Ctx& c, double* out, const TA* A, int64_t lda, int m, const double* coef,
+                   int mode) {
+  if (m <= 0) return HINQS_OK;
+  k_lincomb<TA><<<c.grid, 256, 0, c.s>>>(out, A, lda, m, coef, c.N, mode);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+// Orthonormalise t (FP64, modified in place) against an FP64 vector x (if any)
+// and m basis vectors V (type TV), classical Gram-Schmidt twice; store the
+// normalised result into dst (type TV).  Returns the norm ratio after/before.
+template <typename TV>
+static int orthonormalise(Ctx& c, double* t, const double* x, const TV* V, int64_t ld, int m,
+                          TV* dst, double* ratio) {
+  double* coef = c.small;             // [kMaxSub]
+  double* coefx = c.small + kMaxSub;  // [1]
+  double* nrm = c.small + kMaxSub + 1;
+  double hn[2];
+  HQ_TRY(dots<double, double>(c, t, c.N, 1, t, nrm));
+  HQ_CUDA(cudaMemcpyAsync(&hn[0], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  for (int pass = 0; pass < 2; ++pass) {
+    if (x) {
+      HQ_TRY(dots<double, double>(c, x, c.N, 1, t, coefx));
+      HQ_TRY(lincomb<double>(c, t, x, c.N, 1, coefx, -1));
+    }
+    if (m > 0) {
+      HQ_TRY(dots<TV, double>(c, V, ld, m, t, coef));
+      HQ_TRY(lincomb<TV>(c, t, V, ld, m, coef, -1));
+    }
+  }
+  HQ_TRY(dots<double, double>(c, t, c.N, 1, t, nrm));
+  HQ_CUDA(cudaMemcpyAsync(&hn[1], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  HQ_CUDA(cudaStreamSynchronize(c.s));
+  *ratio = (hn[0] > 0.0) ? std::sqrt(hn[1] / hn[0]) : 0.0;
+  if (hn[1] <= 0.0) return HINQS_OK;
+  k_scale_store<TV><<<c.grid, 256, 0, c.s>>>(t, nrm, dst, c.N);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+static int unit_at_min(Ctx& c, const double* D, double* x) {
+  unsigned long long* b = reinterpret_cast<unsigned long long*>(c.small + 3 * kMaxSub);
+  HQ_CUDA(cudaMemsetAsync(b, 0xff, 2 * sizeof(unsigned long long), c.s));
+  k_argmin<<<c.grid, 256, 0, c.s>>>(D, c.N, b);
+  k_argmin_index<<<c.grid, 256, 0, c.s>>>(D, c.N, b, b + 1);
+  k_unit<<<c.grid, 256, 0, c.s>>>(x, c.N, b + 1);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+struct Trace {
+  const hinqs_davidson_opts* o;
+  int len = 0;
+  std::chrono::steady_clock::time_point t0;
+  void add(double theta, double resid, int kind) {
+    if (!o || len >= o->trace_cap) return;
+    double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (o->trace_theta) o->trace_theta[len] = theta;
+    if (o->trace_resid) o->trace_resid[len] = resid;
+    if (o->trace_time) o->trace_time[len] = t;
+    if (o->trace_kind) o->trace_kind[len] = kind;
+    ++len;
+  }
+};
+
+// ---------------------------------------------------------------- FP64 ----
+
+static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
+                         double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
+  const int mmax = o.max_subspace;
+  const int64_t N = c.N;
+  double *V = nullptr, *W = nullptr, *t = nullptr, *X = nullptr, *G = nullptr, *ritz = nullptr,
+         *ritz_prev = nullptr, *col = nullptr;
+  int rc = HINQS_OK;
+  if ((rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
+      (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, 2 * N, c.s)) ||
+      (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&ritz_prev, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s))) {
+  }
+  auto cleanup = [&]() {
+    dfree(V, c.s);
+    dfree(W, c.s);
+    dfree(t, c.s);
+    dfree(X, c.s);
+    dfree(G, c.s);
+    dfree(ritz, c.s);
+    dfree(ritz_prev, c.s);
+    dfree(col, c.s);
+  };
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  auto run = [&]() -> int {
+    // initial vector
+    if (guess) {
+      HQ_CUDA(cudaMemcpyAsync(t, guess, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    } else {
+      HQ_TRY(unit_at_min(c, D, t));
+    }
+    double ratio;
+    HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, 0, V, &ratio));
+    if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
+    int m = 1;
+    double theta_prev = 0.0;
+    bool have_prev = false;
+    HQ_CUDA(cudaMemsetAsync(ritz_prev, 0, (kMaxSub + 2) * sizeof(double), c.s));
+    for (int it = 0; it < o.max_iter; ++it) {
+      double* vm = V + (size_t)(m - 1) * N;
+      double* wm = W + (size_t)(m - 1) * N;
+      HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, HINQS_PREC_FP64, c.s));
+      info.n_sigma_fp64++;
+      HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
+      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
+      k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
+                                                            D, o.denom_floor, N, t, c.partial);
+      k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+      HQ_LAUNCH_CHECK();
+      double h[2];
+      HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      HQ_CUDA(cudaStreamSynchronize(c.s));
+      double theta = h[0], res = std::sqrt(std::max(h[1], 0.0));
+      info.iterations = it + 1;
+      info.energy = theta;
+      info.residual = res;
+      tr.add(theta, res, 0);
+      bool conv = res <= o.tol_residual && have_prev && std::fabs(theta - theta_prev) <= o.tol_energy;
+      if (res <= o.tol_residual * 1e-3) conv = true;
+      if (conv || it + 1 == o.max_iter) {
+        HQ_TRY(lincomb<double>(c, c_out, V, N, m, ritz + 1, 0));
+        info.status = conv ? HINQS_OK : HINQS_NOT_CONVERGED;
+        if (energy) *energy = theta;
+        return info.status;
+      }
+      theta_prev = theta;
+      have_prev = true;
+      if (m == mmax) {
+        // restart with the current and the previous Ritz vectors
+        double* X0 = X;
+        double* X1 = X + N;
+        HQ_TRY(lincomb<double>(c, X0, V, N, m, ritz + 1, 0));
+        HQ_TRY(lincomb<double>(c, X1, V, N, m - 1, ritz_prev + 1, 0));
+        // W y and W y_prev into temporaries before V[0], W[0] are overwritten
+        double *tw0 = nullptr, *tw1 = nullptr;
+        HQ_TRY(dalloc(&tw0, N, c.s));
+        HQ_TRY(dalloc(&tw1, N, c.s));
+        HQ_TRY(lincomb<double>(c, tw0, W, N, m, ritz + 1, 0));
+        HQ_TRY(lincomb<double>(c, tw1, W, N, m - 1, ritz_prev + 1, 0));
+        HQ_CUDA(cudaMemcpyAsync(V, X0, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaMemcpyAsync(W, tw0, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        // X1 <- X1 - (V0.X1) V0, W1 likewise; normalise both by |X1|
+        double* a = c.small + 2 * kMaxSub;
+        HQ_TRY(dots<double, double>(c, V, N, 1, X1, a));
+        HQ_TRY(lincomb<double>(c, X1, V, N, 1, a, -1));
+        HQ_TRY(lincomb<double>(c, tw1, W, N, 1, a, -1));
+        HQ_TRY(dots<double, double>(c, X1, N, 1, X1, a + 1));
+        double hn = 0.0;
+        HQ_CUDA(cudaMemcpyAsync(&hn, a + 1, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));
+        m = 1;
+        if (hn > 1e-20) {
+          k_scale_store<double><<<c.grid, 256, 0, c.s>>>(X1, a + 1, V + N, N);
+          k_scale_store<double><<<c.grid, 256, 0, c.s>>>(tw1, a + 1, W + N, N);
+          m = 2;
+        }
+        dfree(tw0, c.s);
+        dfree(tw1, c.s);
+        HQ_CUDA(cudaMemsetAsync(G, 0, kMaxSub * kMaxSub * sizeof(double), c.s));
+        for (int j = 0; j < m; ++j) {
+          HQ_TRY(dots<double, double>(c, V, N, j + 1, W + (size_t)j * N, col));
+          k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
+        }
+        // the residual t is still valid for the new basis (span unchanged for x)
+        info.n_restarts++;
+      }
+      HQ_CUDA(cudaMemcpyAsync(ritz_prev, ritz, (kMaxSub + 2) * sizeof(double),
+                              cudaMemcpyDeviceToDevice, c.s));
+      if (m < mmax) {
+        HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, m, V + (size_t)m * N, &ratio));
+        if (ratio < 1e-10) {
+          // stagnated preconditioner: fall back to the plain residual direction
+          k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz,
+                                                                0, D, 1e300, N, t, c.partial);
+          HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, m, V + (size_t)m * N, &ratio));
+          if (ratio < 1e-14) {
+            HQ_TRY(lincomb<double>(c, c_out, V, N, m, ritz + 1, 0));
+            if (energy) *energy = info.energy;
+            info.status = HINQS_NOT_CONVERGED;
+            return info.status;
+          }
+        }
+        m++;
+      }
+    }
+    return HINQS_NOT_CONVERGED;
+  };
+  rc = run();
+  cleanup();
+  return rc;
+}
+
+// --------------------------------------------------------------- mixed ----
+
+static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
+                          double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
+  const int mmax = std::max(3, o.max_subspace);
+  const int64_t N = c.N;
+  double *x = nullptr, *sx = nullptr, *t = nullptr, *G = nullptr, *ritz = nullptr, *col = nullptr;
+  float *V = nullptr, *W = nullptr;
+  int rc = HINQS_OK;
+  if ((rc = dalloc(&x, N, c.s)) || (rc = dalloc(&sx, N, c.s)) || (rc = dalloc(&t, N, c.s)) ||
+      (rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
+      (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&col, kMaxSub + 2, c.s))) {
+  }
+  auto cleanup = [&]() {
+    dfree(x, c.s);
+    dfree(sx, c.s);
+    dfree(t, c.s);
+    dfree(V, c.s);
+    dfree(W, c.s);
+    dfree(G, c.s);
+    dfree(ritz, c.s);
+    dfree(col, c.s);
+  };
+  if (rc) {
+    cleanup();
+    return rc;
+  }
+  auto run = [&]() -> int {
+    if (guess) {
+      HQ_CUDA(cudaMemcpyAsync(t, guess, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+    } else {
+      HQ_TRY(unit_at_min(c, D, t));
+    }
+    double ratio;
+    HQ_TRY(orthonormalise<double>(c, t, nullptr, (double*)nullptr, N, 0, x, &ratio));
+    if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
+    double theta_prev = 0.0;
+    bool have_prev = false;
+    int total = 0;
+    for (int cycle = 0;; ++cycle) {
+      // FP64 product of the current x, its energy and residual
+      HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, x, sx, HINQS_PREC_FP64, c.s));
+      info.n_sigma_fp64++;
+      total++;
+      double* th = c.small + 2 * kMaxSub;
+      HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));  // theta = x.s
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, th, 1, 0);
+      // ritz = (theta, 1) for the one-vector subspace -> residual r = s - theta x
+      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, 1, ritz, nullptr);
+      k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz, 1, D,
+                                                           o.denom_floor, N, t, c.partial);
+      k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+      HQ_LAUNCH_CHECK();
+      double h[2];
+      HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      HQ_CUDA(cudaStreamSynchronize(c.s));
+      double theta = h[0], res = std::sqrt(std::max(h[1], 0.0));
+      info.energy = theta;
+      info.residual = res;
+      info.iterations++;
+      tr.add(theta, res, 0);
+      bool conv = res <= o.tol_residual && have_prev && std::fabs(theta - theta_prev) <= o.tol_energy;
+      if (res <= o.tol_residual * 1e-3) conv = true;
+      if (conv || total >= o.max_iter) {
+        HQ_CUDA(cudaMemcpyAsync(c_out, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        if (energy) *energy = theta;
+        info.status = conv ? HINQS_OK : HINQS_NOT_CONVERGED;
+        return info.status;
+      }
+      theta_prev = theta;
+      have_prev = true;
+      info.n_refinements++;
+      const double target = std::max(o.inner_tol * res, 0.3 * o.tol_residual);
+      // inner FP32 Davidson for the correction of x
+      int m = 0;
+      HQ_TRY(orthonormalise<float>(c, t, x, V, N, 0, V, &ratio));
+      if (ratio < 1e-12) continue;
+      m = 1;
+      for (;;) {
+        float* vm = V + (size_t)(m - 1) * N;
+        float* wm = W + (size_t)(m - 1) * N;
+        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, HINQS_PREC_FP32, c.s));
+        info.n_sigma_fp32++;
+        total++;
+        // G[0][m] = s . v_m ; G[i][m] = v_i . w_m (i = 1..m)
+        HQ_TRY(dots<float, double>(c, vm, N, 1, sx, col));
+        HQ_TRY(dots<float, float>(c, V, N, m, wm, col + 1));
+        k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m, col, m + 1, 0);
+        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, nullptr);
+        k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
+                                                             o.denom_floor, N, t, c.partial);
+        k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+        HQ_LAUNCH_CHECK();
+        HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));
+        double rin = std::sqrt(std::max(h[1], 0.0));
+        info.iterations++;
+        tr.add(h[0], rin, 1);
+        if (rin <= target || m + 1 >= mmax || total >= o.max_iter) break;
+        HQ_TRY(orthonormalise<float>(c, t, x, V, N, m, V + (size_t)m * N, &ratio));
+        if (ratio < 1e-12) break;
+        m++;
+      }
+      // x <- y0 x + sum y_i v_i, normalised (FP64)
+      double* y = ritz + 1;
+      {
+        // t = y0 * x + V y[1..]
+        HQ_TRY(lincomb<double>(c, t, x, N, 1, y, 0));
+        HQ_TRY(lincomb<float>(c, t, V, N, m, y + 1, 1));
+        double* nrm = c.small + 2 * kMaxSub + 1;
+        HQ_TRY(dots<double, double>(c, t, N, 1, t, nrm));
+        k_scale_store<double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
+        HQ_LAUNCH_CHECK();
+      }
+      HQ_CUDA(cudaMemsetAsync(G, 0, kMaxSub * kMaxSub * sizeof(double), c.s));
+    }
+  };
+  rc = run();
+  cleanup();
+  return rc;
+}
+
+}  // namespace hinqs
+
+using namespace hinqs;
+
+extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
+  if (!o) return;
+  o->precision = HINQS_DAVIDSON_FP64;
+  o->max_iter = 200;
+  o->max_subspace = 16;
+  o->tol_residual = 1e-8;
+  o->tol_energy = 1e-10;
+  o->denom_floor = 1e-4;
+  o->inner_tol = 1e-3;
+  o->trace_cap = 0;
+  o->trace_theta = nullptr;
+  o->trace_resid = nullptr;
+  o->trace_time = nullptr;
+  o->trace_kind = nullptr;
+}
+
+extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
+                              const hinqs_links* lb, const double* guess,
+                              const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                              hinqs_davidson_info* info_out, void* stream) {
+  HQ_TRY(check_triplet(H, B, la, lb, "hinqs_davidson"));
+  if (!c_out) return fail(HINQS_ERR_ARG, "hinqs_davidson: c_out is NULL");
+  hinqs_davidson_opts o;
+  hinqs_davidson_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_subspace < 3 || o.max_subspace > kMaxSub)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson: max_subspace must be in 3..%d", kMaxSub);
+  if (o.max_iter < 1 || !(o.tol_residual > 0.0) || !(o.denom_floor > 0.0))
+    return fail(HINQS_ERR_ARG, "hinqs_davidson: bad max_iter / tolerances");
+  if (o.precision != HINQS_DAVIDSON_FP64 && o.precision != HINQS_DAVIDSON_MIXED)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson: unknown precision %d", o.precision);
+  hinqs_davidson_info info{};
+  Trace tr;
+  tr.o = &o;
+  tr.t0 = std::chrono::steady_clock::now();
+  Ctx c{H, B, la, lb, (cudaStream_t)stream, B->Na * B->Nb, 0};
+  c.grid = (int)std::min<int64_t>(ceil_div(c.N, 256), 8 * kNumSMs);
+  double* D = nullptr;
+  int rc = HINQS_OK;
+  if ((rc = dalloc(&c.partial, kRedGrid * (kMaxSub + 1), c.s)) ||
+      (rc = dalloc(&c.small, 4 * (kMaxSub + 2), c.s)) || (rc = dalloc(&D, c.N, c.s))) {
+  }
+  if (!rc) rc = diag_launch(H, B, la, lb, D, c.s);
+  if (!rc) {
+    if (o.precision == HINQS_DAVIDSON_FP64)
+      rc = davidson_fp64(c, guess, o, D, energy, c_out, info, tr);
+    else
+      rc = davidson_mixed(c, guess, o, D, energy, c_out, info, tr);
+  }
+  if (rc >= 0) {
+    cudaError_t e = cudaStreamSynchronize(c.s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_davidson", __FILE__, __LINE__);
+  }
+  dfree(c.partial, c.s);
+  dfree(c.small, c.s);
+  dfree(D, c.s);
+  info.trace_len = tr.len;
+  info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - tr.t0).count();
+  if (rc >= 0) info.status = rc;
+  if (info_out) *info_out = info;
+  return rc;
+}

@@ -1,0 +1,125 @@
+// Internal declarations of the HI-NQS B300 library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdio>
+#include <string>
+
+#include "../../include/hinqs.h"
+
+namespace hinqs {
+
+// ------------------------------------------------------------------ errors --
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);  // records the message, returns code
+int cuda_fail(cudaError_t e, const char* what, const char* file, int line);
+
+#define HQ_CUDA(...)                                                       \
+  do {                                                                     \
+    cudaError_t e_ = (__VA_ARGS__);                                        \
+    if (e_ != cudaSuccess) return hinqs::cuda_fail(e_, #__VA_ARGS__, __FILE__, __LINE__); \
+  } while (0)
+
+#define HQ_LAUNCH_CHECK() HQ_CUDA(cudaGetLastError())
+
+#define HQ_TRY(...)                 \
+  do {                              \
+    int rc_ = (__VA_ARGS__);        \
+    if (rc_ < 0) return rc_;        \
+  } while (0)
+
+// Stream-ordered device allocation from the default pool.
+template <typename T>
+int dalloc(T** p, size_t count, cudaStream_t s) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocAsync((void**)p, count * sizeof(T), s);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HINQS_ERR_OOM, "device allocation of %zu bytes failed: %s", count * sizeof(T),
+                cudaGetErrorString(e));
+  }
+  return HINQS_OK;
+}
+
+template <typename T>
+void dfree(T*& p, cudaStream_t s) {
+  if (p) cudaFreeAsync((void*)p, s);
+  p = nullptr;
+}
+
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+__host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
+
+constexpr int kNumSMs = 148;
+
+}  // namespace hinqs
+
+// ------------------------------------------------------------- handles ------
+
+// Prepared Hamiltonian: copies of the FP64 integrals plus FP32 copies.
+struct hinqs_ham_s {
+  int n = 0, n_alpha = 0, n_beta = 0;
+  double e_nuc = 0.0;
+  double* h = nullptr;      // [n][n]
+  double* eri = nullptr;    // [n*n][n*n] chemist (pq|rs), row pq, column rs
+  float* h32 = nullptr;
+  float* eri32 = nullptr;
+};
+
+// Sorted unique alpha and beta strings of the product subspace.
+struct hinqs_subspace_s {
+  int n = 0, n_alpha = 0, n_beta = 0;
+  int64_t Na = 0, Nb = 0;
+  uint64_t* sa = nullptr;  // [Na] ascending
+  uint64_t* sb = nullptr;  // [Nb] ascending
+};
+
+// Same-spin string links of one spin species plus per-string tables.
+//  all links (singles + doubles, ascending J per row):
+//    row_ptr[N+1], col[nnz], hval64/hval32[nnz] (same-spin matrix element),
+//    exc[nnz] packed p | q<<8 | r<<16 | s<<24 (r = s = 255 for singles),
+//    sign[nnz], degree[nnz]
+//  single links (ascending J per row): srow_ptr[N+1], slink[nsingle] = {J, signed pair}
+//    with signed pair = sign * (p*n + q + 1)
+//  per-string tables: hdiag[N] = H_spin(I,I) (FP64);
+//    V64/V32[N][n*n] = sum_{i in I} (ii|xy)
+struct hinqs_links_s {
+  int spin = 0, n = 0, n_e = 0;
+  int64_t N = 0, nnz = 0, nsingle = 0;
+  int max_row = 0, max_srow = 0;
+  const uint64_t* strings = nullptr;  // borrowed from the subspace
+  int64_t* row_ptr = nullptr;
+  int32_t* col = nullptr;
+  double* hval64 = nullptr;
+  float* hval32 = nullptr;
+  uint32_t* exc = nullptr;
+  int8_t* sign = nullptr;
+  int8_t* degree = nullptr;
+  int64_t* srow_ptr = nullptr;
+  int2* slink = nullptr;
+  double* hdiag = nullptr;
+  double* V64 = nullptr;
+  float* V32 = nullptr;
+};
+
+namespace hinqs {
+
+// Kernel launchers shared between translation units.
+int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                 const hinqs_links_s* lb, const void* c, void* sigma, int precision,
+                 cudaStream_t s);
+int diag_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                const hinqs_links_s* lb, double* hdiag, cudaStream_t s);
+
+}  // namespace hinqs
+
+namespace hinqs {
+// Exclusive prefix sum of n int64 values on the device (out may alias in).
+// If total != nullptr the grand total is copied to *total (host) after a
+// stream synchronisation.
+int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
+                       cudaStream_t s);
+}  // namespace hinqs

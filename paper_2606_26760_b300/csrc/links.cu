@@ -1,0 +1,307 @@
+// K2: same-spin string links by XOR/popcount screening with warp ballots, their
+// fermionic phases by masked popcount, and the same-spin Slater-Condon elements.
+// Also the per-string tables used by the diagonal and the sigma.
+#include <algorithm>
+
+#include "hinqs_internal.cuh"
+
+namespace hinqs {
+
+__device__ __forceinline__ uint64_t below(int x) { return (1ull << x) - 1ull; }
+
+__device__ __forceinline__ double eri_at(const double* __restrict__ eri, int n, int p, int q,
+                                         int r, int s) {
+  return eri[((int64_t)(p * n + q) * n + r) * n + s];
+}
+
+// Pass 1: one warp per row I counts the J with popcount(I^J) in {2,4} (all links)
+// and == 2 (singles), scanning the sorted strings 32 at a time.
+__global__ void k_links_count(const uint64_t* __restrict__ S, int64_t N, int64_t* cnt_all,
+                              int64_t* cnt_single) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = warp; I < N; I += nwarps) {
+    uint64_t x = S[I];
+    int64_t ca = 0, cs = 0;
+    for (int64_t j0 = 0; j0 < N; j0 += 32) {
+      int64_t J = j0 + lane;
+      int d = (J < N) ? __popcll(x ^ S[J]) : 0;
+      unsigned ma = __ballot_sync(0xffffffffu, d == 2 || d == 4);
+      unsigned ms = __ballot_sync(0xffffffffu, d == 2);
+      ca += __popc(ma);
+      cs += __popc(ms);
+    }
+    if (lane == 0) {
+      cnt_all[I] = ca;
+      cnt_single[I] = cs;
+    }
+  }
+}
+
+// Pass 2: the same scan writes the records in ascending J order; each hit's
+// slot is its row offset plus the hits of lower lanes (ballot prefix count).
+__global__ void k_links_fill(const uint64_t* __restrict__ S, int64_t N, int n,
+                             const double* __restrict__ h, const double* __restrict__ eri,
+                             const int64_t* __restrict__ row_ptr,
+                             const int64_t* __restrict__ srow_ptr, int32_t* __restrict__ col,
+                             double* __restrict__ hval64, float* __restrict__ hval32,
+                             uint32_t* __restrict__ exc, int8_t* __restrict__ sign,
+                             int8_t* __restrict__ degree, int2* __restrict__ slink) {
+  int lane = threadIdx.x & 31;
+  unsigned lt = (1u << lane) - 1u;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = warp; I < N; I += nwarps) {
+    uint64_t x = S[I];
+    int64_t pa = row_ptr[I], ps = srow_ptr[I];
+    for (int64_t j0 = 0; j0 < N; j0 += 32) {
+      int64_t J = j0 + lane;
+      uint64_t y = (J < N) ? S[J] : x;
+      uint64_t dx = x ^ y;
+      int d = __popcll(dx);
+      bool hit = (d == 2 || d == 4);
+      unsigned ma = __ballot_sync(0xffffffffu, hit);
+      unsigned ms = __ballot_sync(0xffffffffu, d == 2);
+      if (hit) {
+        int64_t slot = pa + __popc(ma & lt);
+        uint64_t holes = x & dx, parts = y & dx;
+        int q = __ffsll((long long)holes) - 1;
+        int p = __ffsll((long long)parts) - 1;
+        double v;
+        int sg, r = 255, s = 255;
+        if (d == 2) {
+          // J = sign a+_p a_q I
+          int n1 = __popcll(x & below(q));
+          uint64_t x1 = x & ~(1ull << q);
+          int n2 = __popcll(x1 & below(p));
+          sg = ((n1 + n2) & 1) ? -1 : 1;
+          double acc = h[p * n + q];
+          uint64_t occ = x1;  // I without q
+          while (occ) {
+            int j = __ffsll((long long)occ) - 1;
+            occ &= occ - 1;
+            acc += eri_at(eri, n, p, q, j, j) - eri_at(eri, n, p, j, j, q);
+          }
+          v = sg * acc;
+          int64_t sslot = ps + __popc(ms & lt);
+          slink[sslot] = make_int2((int)J, sg * (p * n + q + 1));
+        } else {
+          // holes q < s, particles p < r: J = sign a+_p a+_r a_s a_q I
+          s = 63 - __clzll((long long)holes);
+          r = 63 - __clzll((long long)parts);
+          int n1 = __popcll(x & below(q));
+          uint64_t x1 = x & ~(1ull << q);
+          int n2 = __popcll(x1 & below(s));
+          uint64_t x2 = x1 & ~(1ull << s);
+          int n3 = __popcll(x2 & below(r));
+          uint64_t x3 = x2 | (1ull << r);
+          int n4 = __popcll(x3 & below(p));
+          sg = ((n1 + n2 + n3 + n4) & 1) ? -1 : 1;
+          v = sg * (eri_at(eri, n, p, q, r, s) - eri_at(eri, n, p, s, r, q));
+        }
+        col[slot] = (int32_t)J;
+        hval64[slot] = v;
+        hval32[slot] = (float)v;
+        exc[slot] = (uint32_t)p | ((uint32_t)q << 8) | ((uint32_t)r << 16) | ((uint32_t)s << 24);
+        sign[slot] = (int8_t)sg;
+        degree[slot] = (int8_t)(d / 2);
+      }
+      pa += __popc(ma);
+      ps += __popc(ms);
+    }
+  }
+}
+
+// Per-string tables: hdiag[I] = sum_{i in I} h_ii + 1/2 sum_{i,j in I} [(ii|jj) - (ij|ji)],
+// V[I][xy] = sum_{i in I} (ii|xy).  One block per string.
+__global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n,
+                                const double* __restrict__ h, const double* __restrict__ eri,
+                                double* __restrict__ hdiag, double* __restrict__ V64,
+                                float* __restrict__ V32) {
+  int n2 = n * n;
+  for (int64_t I = blockIdx.x; I < N; I += gridDim.x) {
+    uint64_t x = S[I];
+    for (int xy = threadIdx.x; xy < n2; xy += blockDim.x) {
+      double acc = 0.0;
+      uint64_t occ = x;
+      while (occ) {
+        int i = __ffsll((long long)occ) - 1;
+        occ &= occ - 1;
+        acc += eri[(int64_t)(i * n + i) * n2 + xy];
+      }
+      V64[I * n2 + xy] = acc;
+      V32[I * n2 + xy] = (float)acc;
+    }
+    if (threadIdx.x == 0) {
+      double e1 = 0.0, e2 = 0.0;
+      uint64_t oi = x;
+      while (oi) {
+        int i = __ffsll((long long)oi) - 1;
+        oi &= oi - 1;
+        e1 += h[i * n + i];
+        uint64_t oj = x;
+        while (oj) {
+          int j = __ffsll((long long)oj) - 1;
+          oj &= oj - 1;
+          e2 += eri_at(eri, n, i, i, j, j) - eri_at(eri, n, i, j, j, i);
+        }
+      }
+      hdiag[I] = e1 + 0.5 * e2;
+    }
+  }
+}
+
+// exc unpacking for export
+__global__ void k_unpack_exc(const uint32_t* __restrict__ exc, int64_t nnz, uint8_t* p,
+                             uint8_t* q, uint8_t* r, uint8_t* s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nnz;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t e = exc[i];
+    if (p) p[i] = (uint8_t)(e & 255u);
+    if (q) q[i] = (uint8_t)((e >> 8) & 255u);
+    if (r) r[i] = (uint8_t)((e >> 16) & 255u);
+    if (s) s[i] = (uint8_t)(e >> 24);
+  }
+}
+
+__global__ void k_row_max(const int64_t* __restrict__ rp, int64_t N, int* out) {
+  int m = 0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x)
+    m = max(m, (int)(rp[i + 1] - rp[i]));
+  atomicMax(out, m);
+}
+
+static void free_links(hinqs_links_s* L, cudaStream_t s) {
+  dfree(L->row_ptr, s);
+  dfree(L->col, s);
+  dfree(L->hval64, s);
+  dfree(L->hval32, s);
+  dfree(L->exc, s);
+  dfree(L->sign, s);
+  dfree(L->degree, s);
+  dfree(L->srow_ptr, s);
+  dfree(L->slink, s);
+  dfree(L->hdiag, s);
+  dfree(L->V64, s);
+  dfree(L->V32, s);
+}
+
+}  // namespace hinqs
+
+using namespace hinqs;
+
+extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, int spin,
+                                  hinqs_links** out, void* stream) {
+  if (!out) return fail(HINQS_ERR_ARG, "hinqs_string_links: out is NULL");
+  *out = nullptr;
+  if (!H || !B) return fail(HINQS_ERR_ARG, "hinqs_string_links: NULL handle");
+  if (spin != 0 && spin != 1) return fail(HINQS_ERR_ARG, "hinqs_string_links: spin must be 0 or 1");
+  if (H->n != B->n || H->n_alpha != B->n_alpha || H->n_beta != B->n_beta)
+    return fail(HINQS_ERR_ARG, "hinqs_string_links: Hamiltonian and subspace disagree on sizes");
+  cudaStream_t s = (cudaStream_t)stream;
+  hinqs_links_s* L = new hinqs_links_s();
+  L->spin = spin;
+  L->n = B->n;
+  L->n_e = spin ? B->n_beta : B->n_alpha;
+  L->N = spin ? B->Nb : B->Na;
+  L->strings = spin ? B->sb : B->sa;
+  const int64_t N = L->N;
+  const int n = L->n, n2 = n * n;
+  int64_t *ca = nullptr, *cs = nullptr;
+  int* dmax = nullptr;
+  int rc = HINQS_OK;
+  auto cleanup = [&]() {
+    dfree(ca, s);
+    dfree(cs, s);
+    dfree(dmax, s);
+  };
+  if ((rc = dalloc(&L->row_ptr, N + 1, s)) || (rc = dalloc(&L->srow_ptr, N + 1, s)) ||
+      (rc = dalloc(&ca, N + 1, s)) || (rc = dalloc(&cs, N + 1, s)) || (rc = dalloc(&dmax, 2, s))) {
+    cleanup();
+    free_links(L, s);
+    delete L;
+    return rc;
+  }
+  int warps_per_block = 8;
+  int grid = (int)std::min<int64_t>(ceil_div(N, warps_per_block), 16 * kNumSMs);
+  k_links_count<<<grid, 32 * warps_per_block, 0, s>>>(L->strings, N, ca, cs);
+  cudaMemsetAsync(ca + N, 0, sizeof(int64_t), s);
+  cudaMemsetAsync(cs + N, 0, sizeof(int64_t), s);
+  rc = exclusive_scan_i64(ca, L->row_ptr, N + 1, &L->nnz, s);
+  if (!rc) rc = exclusive_scan_i64(cs, L->srow_ptr, N + 1, &L->nsingle, s);
+  if (!rc) {
+    if ((rc = dalloc(&L->col, L->nnz, s)) || (rc = dalloc(&L->hval64, L->nnz, s)) ||
+        (rc = dalloc(&L->hval32, L->nnz, s)) || (rc = dalloc(&L->exc, L->nnz, s)) ||
+        (rc = dalloc(&L->sign, L->nnz, s)) || (rc = dalloc(&L->degree, L->nnz, s)) ||
+        (rc = dalloc(&L->slink, L->nsingle, s)) || (rc = dalloc(&L->hdiag, N, s)) ||
+        (rc = dalloc(&L->V64, N * n2, s)) || (rc = dalloc(&L->V32, N * n2, s))) {
+    }
+  }
+  if (!rc) {
+    k_links_fill<<<grid, 32 * warps_per_block, 0, s>>>(L->strings, N, n, H->h, H->eri, L->row_ptr,
+                                                       L->srow_ptr, L->col, L->hval64, L->hval32,
+                                                       L->exc, L->sign, L->degree, L->slink);
+    k_string_tables<<<(unsigned)std::min<int64_t>(N, 16 * kNumSMs), 128, 0, s>>>(
+        L->strings, N, n, H->h, H->eri, L->hdiag, L->V64, L->V32);
+    cudaMemsetAsync(dmax, 0, 2 * sizeof(int), s);
+    int g2 = (int)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs);
+    k_row_max<<<g2, 256, 0, s>>>(L->row_ptr, N, dmax);
+    k_row_max<<<g2, 256, 0, s>>>(L->srow_ptr, N, dmax + 1);
+    int hm[2] = {0, 0};
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hm, dmax, sizeof(hm), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_string_links", __FILE__, __LINE__);
+    L->max_row = hm[0];
+    L->max_srow = hm[1];
+  }
+  cleanup();
+  if (rc) {
+    free_links(L, s);
+    delete L;
+    return rc;
+  }
+  *out = L;
+  return HINQS_OK;
+}
+
+extern "C" int hinqs_links_count(const hinqs_links* L, int64_t* n_links, int64_t* n_singles,
+                                 int64_t* max_row) {
+  if (!L) return fail(HINQS_ERR_ARG, "hinqs_links_count: NULL handle");
+  if (n_links) *n_links = L->nnz;
+  if (n_singles) *n_singles = L->nsingle;
+  if (max_row) *max_row = L->max_row;
+  return HINQS_OK;
+}
+
+extern "C" int hinqs_links_export(const hinqs_links* L, int64_t* row_ptr, int32_t* col,
+                                  int8_t* degree, uint8_t* p, uint8_t* q, uint8_t* r, uint8_t* s,
+                                  int8_t* sign, double* hval, void* stream) {
+  if (!L) return fail(HINQS_ERR_ARG, "hinqs_links_export: NULL handle");
+  cudaStream_t st = (cudaStream_t)stream;
+  auto cp = [&](void* dst, const void* src, size_t bytes) -> int {
+    if (dst && bytes) HQ_CUDA(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
+    return HINQS_OK;
+  };
+  HQ_TRY(cp(row_ptr, L->row_ptr, (L->N + 1) * sizeof(int64_t)));
+  HQ_TRY(cp(col, L->col, L->nnz * sizeof(int32_t)));
+  HQ_TRY(cp(degree, L->degree, L->nnz));
+  HQ_TRY(cp(sign, L->sign, L->nnz));
+  HQ_TRY(cp(hval, L->hval64, L->nnz * sizeof(double)));
+  if ((p || q || r || s) && L->nnz) {
+    k_unpack_exc<<<(unsigned)std::min<int64_t>(ceil_div(L->nnz, 256), 4 * kNumSMs), 256, 0, st>>>(
+        L->exc, L->nnz, p, q, r, s);
+    HQ_LAUNCH_CHECK();
+  }
+  return HINQS_OK;
+}
+
+extern "C" int hinqs_links_destroy(hinqs_links* L) {
+  if (!L) return HINQS_OK;
+  cudaDeviceSynchronize();
+  free_links(L, 0);
+  delete L;
+  return HINQS_OK;
+}

@@ -1,0 +1,453 @@
+// K9: spin-summed 1- and 2-RDMs of a state on the product subspace (FP64),
+// the Hellmann-Feynman gradients of the energy; K10: spin marginals (Step 4).
+//
+//   gamma_pq   = sum_s <a+_ps a_qs>
+//   Gamma_pqrs = sum_{s,t} <a+_ps a+_rt a_st a_qs>
+//              = G^aa + G^bb + G^ab_pqrs + G^ab_rspq,  G^ab_pqrs = <E^a_pq E^b_rs>
+//
+// Same-spin parts come from the string-pair weights
+//   M_a(I,J) = sum_b c(I,b) c(J,b),   M_b(I,J) = sum_a c(a,I) c(a,J)
+// on the linked pairs (and I = J), expanded with the index patterns of the
+// one- and two-body transition elements between strings.  The opposite-spin
+// part groups the beta transitions (bra I_b, ket J_b, pair rs, sign) by rs and,
+// per ket alpha string J_a and alpha transition (I_a, pq, sign), sums
+//   X[pq][rs] = sum_{(I_b,J_b,s_b) with pair rs} s_b c(I_a,I_b) c(J_a,J_b).
+#include <algorithm>
+
+#include "hinqs_internal.cuh"
+
+namespace hinqs {
+
+// M[k] = dot(row_a, row_b) for every link k of rows of the matrix X (n_rows x len),
+// plus Mdiag[I] = |row_I|^2.  One warp per link.
+__global__ void k_link_dots(const double* __restrict__ X, int64_t len, const int64_t* __restrict__ rp,
+                            const int32_t* __restrict__ col, int64_t nrows, double* __restrict__ M,
+                            double* __restrict__ Mdiag) {
+  int lane = threadIdx.x & 31;
+  int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t I = warp; I < nrows; I += nw) {
+    const double* xi = X + I * len;
+    double d = 0.0;
+    for (int64_t j = lane; j < len; j += 32) d += xi[j] * xi[j];
+    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    if (lane == 0) Mdiag[I] = d;
+    for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
+      const double* xj = X + (int64_t)col[k] * len;
+      double v = 0.0;
+      for (int64_t j = lane; j < len; j += 32) v += xi[j] * xj[j];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) M[k] = v;
+    }
+  }
+}
+
+// Tiled transpose: out[j][i] = in[i][j] for in of rows x cols.
+__global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int64_t rows,
+                            int64_t cols) {
+  __shared__ double tile[32][33];
+  int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t i = by + k, j = bx + threadIdx.x;
+    if (i < rows && j < cols) tile[k][threadIdx.x] = in[i * cols + j];
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    int64_t j = bx + k, i = by + threadIdx.x;
+    if (i < rows && j < cols) out[j * rows + i] = tile[threadIdx.x][k];
+  }
+}
+
+// Same-spin contributions of one species into g1 (n^2) and g2 (n^4).
+// Row J is the ket; each link record gives the bra I = col with
+// <I| a+_p a_q |J> = sign (single) or <I| a+_p a+_r a_s a_q |J> = sign (double).
+__global__ void k_same_spin_expand(const uint64_t* __restrict__ S, int64_t N, int n,
+                                   const int64_t* __restrict__ rp, const uint32_t* __restrict__ exc,
+                                   const int8_t* __restrict__ sign, const int8_t* __restrict__ degree,
+                                   const double* __restrict__ M, const double* __restrict__ Mdiag,
+                                   double* __restrict__ g1, double* __restrict__ g2) {
+  const int64_t n2 = (int64_t)n * n, n3 = n2 * n;
+  auto G2 = [&](int p, int q, int r, int s, double v) {
+    if (g2) atomicAdd(g2 + p * n3 + q * n2 + (int64_t)r * n + s, v);
+  };
+  for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < N;
+       J += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t x = S[J];
+    const double md = Mdiag[J];
+    // diagonal: gamma_qq += M; Gamma_qqss += M, Gamma_sqqs -= M for q != s in J
+    uint64_t oq = x;
+    while (oq) {
+      int q = __ffsll((long long)oq) - 1;
+      oq &= oq - 1;
+      atomicAdd(g1 + q * n + q, md);
+      uint64_t os = x;
+      while (os) {
+        int s = __ffsll((long long)os) - 1;
+        os &= os - 1;
+        if (s == q) continue;
+        G2(q, q, s, s, md);
+        G2(s, q, q, s, -md);
+      }
+    }
+    for (int64_t k = rp[J]; k < rp[J + 1]; ++k) {
+      const uint32_t e = exc[k];
+      const int p = e & 255, q = (e >> 8) & 255, r = (e >> 16) & 255, s = e >> 24;
+      const double v = sign[k] * M[k];
+      if (degree[k] == 1) {
+        // bra = sign a+_p a_q |J>, particle e = p, hole h = q, spectators k in J \ {q}
+        atomicAdd(g1 + p * n + q, v);
+        uint64_t ok = x & ~(1ull << q);
+        while (ok) {
+          int kk = __ffsll((long long)ok) - 1;
+          ok &= ok - 1;
+          G2(p, q, kk, kk, v);
+          G2(kk, q, p, kk, -v);
+          G2(p, kk, kk, q, -v);
+          G2(kk, kk, p, q, v);
+        }
+      } else {
+        G2(p, q, r, s, v);
+        G2(r, q, p, s, -v);
+        G2(p, s, r, q, -v);
+        G2(r, s, p, q, v);
+      }
+    }
+  }
+}
+
+// Beta transitions grouped by pair rs: count, then place.
+// Transition (bra I_b, ket J_b, rs, s_b): from ket row J_b's single links
+// (bra = col, rs = p*n+q, sign) and the diagonal (I_b = J_b, rs = jj, +1).
+__global__ void k_trans_count(const uint64_t* __restrict__ S, int64_t N, int n,
+                              const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+                              int64_t* __restrict__ cnt) {
+  for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < N;
+       J += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t o = S[J];
+    while (o) {
+      int j = __ffsll((long long)o) - 1;
+      o &= o - 1;
+      atomicAdd((unsigned long long*)(cnt + j * n + j), 1ull);
+    }
+    for (int64_t k = srp[J]; k < srp[J + 1]; ++k) {
+      int sp = sl[k].y;
+      int rs = (sp > 0 ? sp : -sp) - 1;
+      atomicAdd((unsigned long long*)(cnt + rs), 1ull);
+    }
+  }
+}
+
+__global__ void k_trans_place(const uint64_t* __restrict__ S, int64_t N, int n,
+                              const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+                              int64_t* __restrict__ cursor, int4* __restrict__ out) {
+  for (int64_t J = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; J < N;
+       J += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t o = S[J];
+    while (o) {
+      int j = __ffsll((long long)o) - 1;
+      o &= o - 1;
+      int64_t pos = (int64_t)atomicAdd((unsigned long long*)(cursor + j * n + j), 1ull);
+      out[pos] = make_int4((int)J, (int)J, 1, 0);
+    }
+    for (int64_t k = srp[J]; k < srp[J + 1]; ++k) {
+      int2 l = sl[k];
+      int rs = (l.y > 0 ? l.y : -l.y) - 1;
+      int64_t pos = (int64_t)atomicAdd((unsigned long long*)(cursor + rs), 1ull);
+      out[pos] = make_int4(l.x, (int)J, l.y > 0 ? 1 : -1, 0);
+    }
+  }
+}
+
+// Opposite-spin 2-RDM, one block per ket alpha string J_a; CH alpha transitions
+// at a time; thread per (transition, rs) bin.
+template <int CH>
+__global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, int64_t Nb, int n,
+                                                const uint64_t* __restrict__ Sa,
+                                                const int64_t* __restrict__ a_srp,
+                                                const int2* __restrict__ a_sl,
+                                                const int64_t* __restrict__ off,
+                                                const int4* __restrict__ trans,
+                                                double* __restrict__ gab) {
+  const int n2 = n * n;
+  const int64_t Ja = blockIdx.x;
+  __shared__ int tI[CH], tpq[CH], ts[CH];
+  // alpha transitions of ket J_a: diagonal (I = J, pq = ii) then single links
+  const uint64_t x = Sa[Ja];
+  const int nd = __popcll(x);
+  const int64_t nl = a_srp[Ja + 1] - a_srp[Ja];
+  const int64_t total = nd + nl;
+  const double* cj = C + Ja * Nb;
+  for (int64_t t0 = 0; t0 < total; t0 += CH) {
+    const int cnt = (int)min64(CH, total - t0);
+    __syncthreads();
+    if (threadIdx.x < cnt) {
+      int64_t t = t0 + threadIdx.x;
+      if (t < nd) {
+        // t-th occupied orbital of J_a
+        uint64_t o = x;
+        for (int k = 0; k < t; ++k) o &= o - 1;
+        int i = __ffsll((long long)o) - 1;
+        tI[threadIdx.x] = (int)Ja;
+        tpq[threadIdx.x] = i * n + i;
+        ts[threadIdx.x] = 1;
+      } else {
+        int2 l = a_sl[a_srp[Ja] + (t - nd)];
+        tI[threadIdx.x] = l.x;
+        tpq[threadIdx.x] = (l.y > 0 ? l.y : -l.y) - 1;
+        ts[threadIdx.x] = l.y > 0 ? 1 : -1;
+      }
+    }
+    __syncthreads();
+    for (int bin = threadIdx.x; bin < cnt * n2; bin += blockDim.x) {
+      const int a = bin / n2, rs = bin % n2;
+      const double* ci = C + (int64_t)tI[a] * Nb;
+      double acc = 0.0;
+      for (int64_t k = off[rs]; k < off[rs + 1]; ++k) {
+        const int4 tr = trans[k];
+        acc += tr.z * ci[tr.x] * cj[tr.y];
+      }
+      if (acc != 0.0) atomicAdd(gab + (int64_t)tpq[a] * n2 + rs, ts[a] * acc);
+    }
+  }
+}
+
+__global__ void k_rdm2_combine(const double* __restrict__ same, const double* __restrict__ gab,
+                               int n, double* __restrict__ out) {
+  const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n4;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int64_t pq = i / n2, rs = i % n2;
+    out[i] = same[i] + gab[i] + gab[rs * n2 + pq];
+  }
+}
+
+__global__ void k_scale(const double* __restrict__ x, double a, double* __restrict__ y, int64_t m) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = a * x[i];
+}
+
+// ------------------------------------------------------------- marginals --
+
+// row sums of c^2: pa[a] (one block per row)
+__global__ void k_row_sq(const double* __restrict__ C, int64_t Na, int64_t Nb, double* pa) {
+  __shared__ double red[32];
+  for (int64_t a = blockIdx.x; a < Na; a += gridDim.x) {
+    double acc = 0.0;
+    for (int64_t b = threadIdx.x; b < Nb; b += blockDim.x) {
+      double v = C[a * Nb + b];
+      acc += v * v;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double v = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+      pa[a] = v;
+    }
+    __syncthreads();
+  }
+}
+
+// column sums of c^2 over a chunk of rows: part[chunk][b]
+__global__ void k_col_sq(const double* __restrict__ C, int64_t Na, int64_t Nb, int64_t rows_per,
+                         double* part) {
+  int64_t chunk = blockIdx.y;
+  int64_t a0 = chunk * rows_per, a1 = min64(Na, a0 + rows_per);
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < Nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t a = a0; a < a1; ++a) {
+      double v = C[a * Nb + b];
+      acc += v * v;
+    }
+    part[chunk * Nb + b] = acc;
+  }
+}
+
+__global__ void k_sum_chunks(const double* __restrict__ part, int64_t chunks, int64_t Nb, double* pb) {
+  for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < Nb;
+       b += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int64_t k = 0; k < chunks; ++k) acc += part[k * Nb + b];
+    pb[b] = acc;
+  }
+}
+
+// tot[0] = sum pa (= |c|^2); then normalise pa, pb, and tot[1] = sum pa' * sum pb'
+__global__ void k_marg_norm(double* pa, int64_t Na, double* pb, int64_t Nb, double* tot) {
+  __shared__ double red[32];
+  __shared__ double z;
+  double acc = 0.0;
+  for (int64_t i = threadIdx.x; i < Na; i += blockDim.x) acc += pa[i];
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) v += red[w];
+    z = v;
+    tot[0] = v;
+  }
+  __syncthreads();
+  const double inv = 1.0 / z;
+  double sa = 0.0, sb = 0.0;
+  for (int64_t i = threadIdx.x; i < Na; i += blockDim.x) {
+    pa[i] *= inv;
+    sa += pa[i];
+  }
+  for (int64_t i = threadIdx.x; i < Nb; i += blockDim.x) {
+    pb[i] *= inv;
+    sb += pb[i];
+  }
+  __syncthreads();
+  for (int o = 16; o > 0; o >>= 1) sa += __shfl_down_sync(0xffffffffu, sa, o);
+  for (int o = 16; o > 0; o >>= 1) sb += __shfl_down_sync(0xffffffffu, sb, o);
+  __shared__ double ra[32], rb[32];
+  if ((threadIdx.x & 31) == 0) {
+    ra[threadIdx.x >> 5] = sa;
+    rb[threadIdx.x >> 5] = sb;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0.0, Bv = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      A += ra[w];
+      Bv += rb[w];
+    }
+    tot[1] = A * Bv;
+  }
+}
+
+__global__ void k_teacher(const double* __restrict__ pa, const double* __restrict__ pb, int64_t Na,
+                          int64_t Nb, const double* __restrict__ tot, double* __restrict__ w) {
+  const double inv = 1.0 / tot[1];
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < Na * Nb;
+       I += (int64_t)gridDim.x * blockDim.x) {
+    int64_t a = I / Nb, b = I - a * Nb;
+    w[I] = pa[a] * pb[b] * inv;
+  }
+}
+
+}  // namespace hinqs
+
+using namespace hinqs;
+
+extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const hinqs_links* lb,
+                         const double* c, double* rdm1, double* rdm2, void* stream) {
+  if (!B || !la || !lb) return fail(HINQS_ERR_ARG, "hinqs_rdm: NULL handle");
+  if (!c || !rdm1) return fail(HINQS_ERR_ARG, "hinqs_rdm: NULL c or rdm1");
+  if (la->spin != 0 || lb->spin != 1 || la->N != B->Na || lb->N != B->Nb ||
+      la->strings != B->sa || lb->strings != B->sb)
+    return fail(HINQS_ERR_ARG, "hinqs_rdm: links do not belong to this subspace");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = B->n;
+  const int64_t n2 = (int64_t)n * n, n4 = n2 * n2, Na = B->Na, Nb = B->Nb, N = Na * Nb;
+  double *Ma = nullptr, *Mad = nullptr, *Mb = nullptr, *Mbd = nullptr, *CT = nullptr,
+         *same = nullptr, *gab = nullptr;
+  int64_t *cnt = nullptr, *off = nullptr;
+  int4* trans = nullptr;
+  auto cleanup = [&]() {
+    dfree(Ma, s);
+    dfree(Mad, s);
+    dfree(Mb, s);
+    dfree(Mbd, s);
+    dfree(CT, s);
+    dfree(same, s);
+    dfree(gab, s);
+    dfree(cnt, s);
+    dfree(off, s);
+    dfree(trans, s);
+  };
+  int rc = HINQS_OK;
+  const int64_t ntrans = lb->nsingle + Nb * B->n_beta;
+  if ((rc = dalloc(&Ma, la->nnz, s)) || (rc = dalloc(&Mad, Na, s)) || (rc = dalloc(&Mb, lb->nnz, s)) ||
+      (rc = dalloc(&Mbd, Nb, s)) || (rc = dalloc(&CT, N, s)) || (rc = dalloc(&same, n4, s)) ||
+      (rc = dalloc(&gab, n4, s)) || (rc = dalloc(&cnt, n2 + 1, s)) || (rc = dalloc(&off, n2 + 1, s)) ||
+      (rc = dalloc(&trans, ntrans, s))) {
+    cleanup();
+    return rc;
+  }
+  auto run = [&]() -> int {
+    const int g = 16 * kNumSMs;
+    // string-pair weights
+    k_link_dots<<<g, 256, 0, s>>>(c, Nb, la->row_ptr, la->col, Na, Ma, Mad);
+    dim3 tb(32, 8), tg((unsigned)ceil_div(Nb, 32), (unsigned)ceil_div(Na, 32));
+    k_transpose<<<tg, tb, 0, s>>>(c, CT, Na, Nb);
+    k_link_dots<<<g, 256, 0, s>>>(CT, Na, lb->row_ptr, lb->col, Nb, Mb, Mbd);
+    HQ_CUDA(cudaMemsetAsync(rdm1, 0, n2 * sizeof(double), s));
+    HQ_CUDA(cudaMemsetAsync(same, 0, n4 * sizeof(double), s));
+    HQ_CUDA(cudaMemsetAsync(gab, 0, n4 * sizeof(double), s));
+    double* g2 = rdm2 ? same : nullptr;
+    k_same_spin_expand<<<(unsigned)std::min<int64_t>(ceil_div(Na, 128), g), 128, 0, s>>>(
+        la->strings, Na, n, la->row_ptr, la->exc, la->sign, la->degree, Ma, Mad, rdm1, g2);
+    k_same_spin_expand<<<(unsigned)std::min<int64_t>(ceil_div(Nb, 128), g), 128, 0, s>>>(
+        lb->strings, Nb, n, lb->row_ptr, lb->exc, lb->sign, lb->degree, Mb, Mbd, rdm1, g2);
+    HQ_LAUNCH_CHECK();
+    if (!rdm2) return HINQS_OK;
+    // beta transitions grouped by rs
+    HQ_CUDA(cudaMemsetAsync(cnt, 0, (n2 + 1) * sizeof(int64_t), s));
+    k_trans_count<<<(unsigned)std::min<int64_t>(ceil_div(Nb, 128), g), 128, 0, s>>>(
+        lb->strings, Nb, n, lb->srow_ptr, lb->slink, cnt);
+    int64_t tot = 0;
+    HQ_TRY(exclusive_scan_i64(cnt, off, n2 + 1, &tot, s));
+    if (tot != ntrans) return fail(HINQS_ERR_CUDA, "hinqs_rdm: transition count mismatch");
+    HQ_CUDA(cudaMemcpyAsync(cnt, off, (n2 + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
+    k_trans_place<<<(unsigned)std::min<int64_t>(ceil_div(Nb, 128), g), 128, 0, s>>>(
+        lb->strings, Nb, n, lb->srow_ptr, lb->slink, cnt, trans);
+    k_rdm_ab<16><<<(unsigned)Na, 256, 0, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink, off,
+                                               trans, gab);
+    k_rdm2_combine<<<(unsigned)std::min<int64_t>(ceil_div(n4, 256), g), 256, 0, s>>>(same, gab, n,
+                                                                                   rdm2);
+    HQ_LAUNCH_CHECK();
+    return HINQS_OK;
+  };
+  rc = run();
+  cleanup();
+  return rc;
+}
+
+extern "C" int hinqs_energy_backward(int n_orb, double grad_E, const double* rdm1,
+                                     const double* rdm2, double* grad_h, double* grad_eri,
+                                     void* stream) {
+  if (n_orb < 1 || n_orb > 64 || !rdm1 || !grad_h || (grad_eri && !rdm2))
+    return fail(HINQS_ERR_ARG, "hinqs_energy_backward: bad arguments");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t n2 = (int64_t)n_orb * n_orb, n4 = n2 * n2;
+  k_scale<<<(unsigned)std::min<int64_t>(ceil_div(n2, 256), 64), 256, 0, s>>>(rdm1, grad_E, grad_h, n2);
+  if (grad_eri)
+    k_scale<<<(unsigned)std::min<int64_t>(ceil_div(n4, 256), 4096), 256, 0, s>>>(rdm2, 0.5 * grad_E,
+                                                                                grad_eri, n4);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+extern "C" int hinqs_spin_marginals(const hinqs_subspace* B, const double* c, double* pa,
+                                    double* pb, double* w, void* stream) {
+  if (!B || !c || !pa || !pb) return fail(HINQS_ERR_ARG, "hinqs_spin_marginals: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t Na = B->Na, Nb = B->Nb;
+  const int64_t rows_per = 64;
+  const int64_t chunks = ceil_div(Na, rows_per);
+  double *part = nullptr, *tot = nullptr;
+  int rc = HINQS_OK;
+  if ((rc = dalloc(&part, chunks * Nb, s)) || (rc = dalloc(&tot, 2, s))) {
+    dfree(part, s);
+    dfree(tot, s);
+    return rc;
+  }
+  k_row_sq<<<(unsigned)std::min<int64_t>(Na, 16 * kNumSMs), 256, 0, s>>>(c, Na, Nb, pa);
+  dim3 g((unsigned)std::min<int64_t>(ceil_div(Nb, 256), 64), (unsigned)chunks);
+  k_col_sq<<<g, 256, 0, s>>>(c, Na, Nb, rows_per, part);
+  k_sum_chunks<<<(unsigned)std::min<int64_t>(ceil_div(Nb, 256), 256), 256, 0, s>>>(part, chunks, Nb, pb);
+  k_marg_norm<<<1, 1024, 0, s>>>(pa, Na, pb, Nb, tot);
+  if (w)
+    k_teacher<<<(unsigned)std::min<int64_t>(ceil_div(Na * Nb, 256), 16 * kNumSMs), 256, 0, s>>>(
+        pa, pb, Na, Nb, tot, w);
+  cudaError_t e = cudaGetLastError();
+  dfree(part, s);
+  dfree(tot, s);
+  if (e != cudaSuccess) return cuda_fail(e, "hinqs_spin_marginals", __FILE__, __LINE__);
+  return HINQS_OK;
+}
