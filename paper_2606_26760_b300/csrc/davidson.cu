@@ -149,27 +149,77 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
   }
 }
 
-// Lowest eigenpair of the symmetric m x m matrix G (row-major, leading dim ldg)
-// by cyclic Jacobi with the round-robin parallel ordering; one block.
-// out[0] = theta, out[1..m] = unit eigenvector (sign: largest component > 0).
+// Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
+// ldg; S == NULL means S = I) by cyclic Jacobi with the round-robin parallel
+// ordering, in one block.  With S the pencil is reduced to C = L^-1 G L^-T by the
+// Cholesky factor S = L L^T and the eigenvector is mapped back, y = L^-T z, so
+// that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest |component| > 0).
 __global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __restrict__ out,
-                     double* __restrict__ all_evals) {
+                     const double* __restrict__ S) {
   __shared__ double A[kMaxSub][kMaxSub + 1];
   __shared__ double Q[kMaxSub][kMaxSub + 1];
+  __shared__ double L[kMaxSub][kMaxSub + 1];
+  __shared__ double X[kMaxSub][kMaxSub + 1];
   __shared__ double cs[kMaxSub / 2][2];
   __shared__ int pr[kMaxSub / 2][2];
   __shared__ int order[kMaxSub];
   __shared__ double offn;
+  __shared__ int use_s;
   const int tid = threadIdx.x;
   int mm = m + (m & 1);  // even size for the tournament; padded row/col is isolated
+  if (tid == 0) {
+    use_s = 0;
+    if (S) {
+      // Cholesky S = L L^T (S symmetrised)
+      use_s = 1;
+      for (int j = 0; j < m && use_s; ++j) {
+        double d = 0.5 * (S[j * ldg + j] + S[j * ldg + j]);
+        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+        if (!(d > 0.0)) {
+          use_s = 0;
+          break;
+        }
+        L[j][j] = sqrt(d);
+        for (int i = j + 1; i < m; ++i) {
+          double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
+          for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+          L[i][j] = v / L[j][j];
+        }
+      }
+    }
+  }
+  __syncthreads();
+  if (use_s) {
+    // X = L^-1 Gs (column j by forward substitution), then C = L^-1 X^T
+    if (tid < m) {
+      const int j = tid;
+      for (int i = 0; i < m; ++i) {
+        double v = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
+        for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][j];
+        X[i][j] = v / L[i][i];
+      }
+    }
+    __syncthreads();
+    if (tid < m) {
+      const int j = tid;
+      for (int i = 0; i < m; ++i) {
+        double v = X[j][i];
+        for (int k = 0; k < i; ++k) v -= L[i][k] * A[k][j];
+        A[i][j] = v / L[i][i];
+      }
+    }
+    __syncthreads();
+  }
   for (int i = tid; i < mm * mm; i += blockDim.x) {
     int r = i / mm, c = i % mm;
     double v = 0.0;
-    if (r < m && c < m) v = 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
+    if (r < m && c < m) v = use_s ? 0.5 * (A[r][c] + A[c][r]) : 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
     else if (r == c) v = 1e300;  // padding: never the lowest
-    A[r][c] = v;
+    X[r][c] = v;
     Q[r][c] = (r == c) ? 1.0 : 0.0;
   }
+  __syncthreads();
+  for (int i = tid; i < mm * mm; i += blockDim.x) A[i / mm][i % mm] = X[i / mm][i % mm];
   if (tid < mm) order[tid] = tid;
   __syncthreads();
   for (int sweep = 0; sweep < 30; ++sweep) {
@@ -241,22 +291,29 @@ __global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __res
     int best = 0;
     for (int k = 1; k < m; ++k)
       if (A[k][k] < A[best][best]) best = k;
-    double big = 0.0;
-    int arg = 0;
-    for (int r = 0; r < m; ++r)
-      if (fabs(Q[r][best]) > big) {
-        big = fabs(Q[r][best]);
-        arg = r;
-      }
-    double sg = Q[arg][best] < 0.0 ? -1.0 : 1.0;
-    out[0] = A[best][best];
+    double z[kMaxSub];
     double nrm = 0.0;
     for (int r = 0; r < m; ++r) nrm += Q[r][best] * Q[r][best];
     nrm = 1.0 / sqrt(nrm);
-    for (int r = 0; r < m; ++r) out[1 + r] = sg * Q[r][best] * nrm;
+    for (int r = 0; r < m; ++r) z[r] = Q[r][best] * nrm;
+    if (use_s) {  // y = L^-T z
+      for (int i = m - 1; i >= 0; --i) {
+        double v = z[i];
+        for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
+        z[i] = v / L[i][i];
+      }
+    }
+    double big = 0.0;
+    int arg = 0;
+    for (int r = 0; r < m; ++r)
+      if (fabs(z[r]) > big) {
+        big = fabs(z[r]);
+        arg = r;
+      }
+    double sg = z[arg] < 0.0 ? -1.0 : 1.0;
+    out[0] = A[best][best];
+    for (int r = 0; r < m; ++r) out[1 + r] = sg * z[r];
     for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
-    if (all_evals)
-      for (int r = 0; r < m; ++r) all_evals[r] = A[r][r];
   }
 }
 
@@ -391,34 +448,46 @@ struct Trace {
 
 // ---------------------------------------------------------------- FP64 ----
 
+__global__ void k_init_pencil(double* G, double* S, const double* theta) {
+  for (int i = threadIdx.x; i < kMaxSub * kMaxSub; i += blockDim.x) {
+    G[i] = 0.0;
+    if (S) S[i] = 0.0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    G[0] = theta ? theta[0] : 0.0;
+    if (S) S[0] = 1.0;
+  }
+}
+
 static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
                          double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
   const int mmax = o.max_subspace;
   const int64_t N = c.N;
-  double *V = nullptr, *W = nullptr, *t = nullptr, *X = nullptr, *G = nullptr, *ritz = nullptr,
-         *ritz_prev = nullptr, *col = nullptr;
+  double *V = nullptr, *W = nullptr, *t = nullptr, *X = nullptr, *WX = nullptr, *G = nullptr,
+         *ritz = nullptr, *col = nullptr, *ycoef = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
-      (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, 2 * N, c.s)) ||
+      (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, 2 * N, c.s)) || (rc = dalloc(&WX, 2 * N, c.s)) ||
       (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&ritz_prev, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s))) {
+      (rc = dalloc(&col, kMaxSub + 2, c.s)) || (rc = dalloc(&ycoef, 2 * (kMaxSub + 2), c.s))) {
   }
   auto cleanup = [&]() {
     dfree(V, c.s);
     dfree(W, c.s);
     dfree(t, c.s);
     dfree(X, c.s);
+    dfree(WX, c.s);
     dfree(G, c.s);
     dfree(ritz, c.s);
-    dfree(ritz_prev, c.s);
     dfree(col, c.s);
+    dfree(ycoef, c.s);
   };
   if (rc) {
     cleanup();
     return rc;
   }
   auto run = [&]() -> int {
-    // initial vector
     if (guess) {
       HQ_CUDA(cudaMemcpyAsync(t, guess, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
     } else {
@@ -427,10 +496,11 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
     double ratio;
     HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, 0, V, &ratio));
     if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
+    k_init_pencil<<<1, 256, 0, c.s>>>(G, nullptr, nullptr);
     int m = 1;
     double theta_prev = 0.0;
     bool have_prev = false;
-    HQ_CUDA(cudaMemsetAsync(ritz_prev, 0, (kMaxSub + 2) * sizeof(double), c.s));
+    double hr[kMaxSub + 2] = {0}, hr_prev[kMaxSub + 2] = {0};
     for (int it = 0; it < o.max_iter; ++it) {
       double* vm = V + (size_t)(m - 1) * N;
       double* wm = W + (size_t)(m - 1) * N;
@@ -443,11 +513,11 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
                                                             D, o.denom_floor, N, t, c.partial);
       k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
       HQ_LAUNCH_CHECK();
-      double h[2];
-      HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      double hres = 0.0;
+      HQ_CUDA(cudaMemcpyAsync(hr, ritz, (kMaxSub + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
+      HQ_CUDA(cudaMemcpyAsync(&hres, col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
       HQ_CUDA(cudaStreamSynchronize(c.s));
-      double theta = h[0], res = std::sqrt(std::max(h[1], 0.0));
+      double theta = hr[0], res = std::sqrt(std::max(hres, 0.0));
       info.iterations = it + 1;
       info.energy = theta;
       info.residual = res;
@@ -463,46 +533,50 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       theta_prev = theta;
       have_prev = true;
       if (m == mmax) {
-        // restart with the current and the previous Ritz vectors
-        double* X0 = X;
-        double* X1 = X + N;
-        HQ_TRY(lincomb<double>(c, X0, V, N, m, ritz + 1, 0));
-        HQ_TRY(lincomb<double>(c, X1, V, N, m - 1, ritz_prev + 1, 0));
-        // W y and W y_prev into temporaries before V[0], W[0] are overwritten
-        double *tw0 = nullptr, *tw1 = nullptr;
-        HQ_TRY(dalloc(&tw0, N, c.s));
-        HQ_TRY(dalloc(&tw1, N, c.s));
-        HQ_TRY(lincomb<double>(c, tw0, W, N, m, ritz + 1, 0));
-        HQ_TRY(lincomb<double>(c, tw1, W, N, m - 1, ritz_prev + 1, 0));
-        HQ_CUDA(cudaMemcpyAsync(V, X0, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-        HQ_CUDA(cudaMemcpyAsync(W, tw0, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-        // X1 <- X1 - (V0.X1) V0, W1 likewise; normalise both by |X1|
-        double* a = c.small + 2 * kMaxSub;
-        HQ_TRY(dots<double, double>(c, V, N, 1, X1, a));
-        HQ_TRY(lincomb<double>(c, X1, V, N, 1, a, -1));
-        HQ_TRY(lincomb<double>(c, tw1, W, N, 1, a, -1));
-        HQ_TRY(dots<double, double>(c, X1, N, 1, X1, a + 1));
-        double hn = 0.0;
-        HQ_CUDA(cudaMemcpyAsync(&hn, a + 1, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-        HQ_CUDA(cudaStreamSynchronize(c.s));
-        m = 1;
-        if (hn > 1e-20) {
-          k_scale_store<double><<<c.grid, 256, 0, c.s>>>(X1, a + 1, V + N, N);
-          k_scale_store<double><<<c.grid, 256, 0, c.s>>>(tw1, a + 1, W + N, N);
-          m = 2;
+        // Thick restart with the current Ritz vector x = V y and the previous one,
+        // orthonormalised against y in the m-dimensional coefficient space (the
+        // two are nearly parallel near convergence; doing it on the N-vectors
+        // would lose orthogonality).
+        double y[kMaxSub], yp[kMaxSub];
+        for (int i = 0; i < m; ++i) {
+          y[i] = hr[1 + i];
+          yp[i] = (i < m - 1) ? hr_prev[1 + i] : 0.0;
         }
-        dfree(tw0, c.s);
-        dfree(tw1, c.s);
-        HQ_CUDA(cudaMemsetAsync(G, 0, kMaxSub * kMaxSub * sizeof(double), c.s));
+        for (int pass = 0; pass < 2; ++pass) {
+          double d = 0.0;
+          for (int i = 0; i < m; ++i) d += y[i] * yp[i];
+          for (int i = 0; i < m; ++i) yp[i] -= d * y[i];
+        }
+        double nn = 0.0;
+        for (int i = 0; i < m; ++i) nn += yp[i] * yp[i];
+        const bool two = nn > 1e-24;
+        double hc[2 * (kMaxSub + 2)] = {0};
+        for (int i = 0; i < m; ++i) {
+          hc[i] = y[i];
+          hc[kMaxSub + 2 + i] = two ? yp[i] / std::sqrt(nn) : 0.0;
+        }
+        HQ_CUDA(cudaMemcpyAsync(ycoef, hc, sizeof(hc), cudaMemcpyHostToDevice, c.s));
+        double* yc1 = ycoef + kMaxSub + 2;
+        HQ_TRY(lincomb<double>(c, X, V, N, m, ycoef, 0));
+        HQ_TRY(lincomb<double>(c, WX, W, N, m, ycoef, 0));
+        if (two) {
+          HQ_TRY(lincomb<double>(c, X + N, V, N, m, yc1, 0));
+          HQ_TRY(lincomb<double>(c, WX + N, W, N, m, yc1, 0));
+        }
+        const int mnew = two ? 2 : 1;
+        HQ_CUDA(cudaMemcpyAsync(V, X, mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaMemcpyAsync(W, WX, mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));  // hc lives on the host stack
+        m = mnew;
+        k_init_pencil<<<1, 256, 0, c.s>>>(G, nullptr, nullptr);
         for (int j = 0; j < m; ++j) {
           HQ_TRY(dots<double, double>(c, V, N, j + 1, W + (size_t)j * N, col));
           k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
         }
-        // the residual t is still valid for the new basis (span unchanged for x)
+        // the residual t of the current Ritz vector (now V[0]) is still valid
         info.n_restarts++;
       }
-      HQ_CUDA(cudaMemcpyAsync(ritz_prev, ritz, (kMaxSub + 2) * sizeof(double),
-                              cudaMemcpyDeviceToDevice, c.s));
+      std::copy(hr, hr + kMaxSub + 1, hr_prev);
       if (m < mmax) {
         HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, m, V + (size_t)m * N, &ratio));
         if (ratio < 1e-10) {
@@ -533,13 +607,15 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
                           double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
   const int mmax = std::max(3, o.max_subspace);
   const int64_t N = c.N;
-  double *x = nullptr, *sx = nullptr, *t = nullptr, *G = nullptr, *ritz = nullptr, *col = nullptr;
+  double *x = nullptr, *sx = nullptr, *t = nullptr, *G = nullptr, *S = nullptr, *ritz = nullptr,
+         *col = nullptr, *scol = nullptr;
   float *V = nullptr, *W = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&x, N, c.s)) || (rc = dalloc(&sx, N, c.s)) || (rc = dalloc(&t, N, c.s)) ||
       (rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
-      (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&col, kMaxSub + 2, c.s))) {
+      (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&S, kMaxSub * kMaxSub, c.s)) ||
+      (rc = dalloc(&ritz, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&scol, kMaxSub + 2, c.s))) {
   }
   auto cleanup = [&]() {
     dfree(x, c.s);
@@ -548,8 +624,10 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     dfree(V, c.s);
     dfree(W, c.s);
     dfree(G, c.s);
+    dfree(S, c.s);
     dfree(ritz, c.s);
     dfree(col, c.s);
+    dfree(scol, c.s);
   };
   if (rc) {
     cleanup();
@@ -567,6 +645,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     double theta_prev = 0.0;
     bool have_prev = false;
     int total = 0;
+    double h[2];
     for (int cycle = 0;; ++cycle) {
       // FP64 product of the current x, its energy and residual
       HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, x, sx, HINQS_PREC_FP64, c.s));
@@ -574,14 +653,12 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       total++;
       double* th = c.small + 2 * kMaxSub;
       HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));  // theta = x.s
-      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, th, 1, 0);
-      // ritz = (theta, 1) for the one-vector subspace -> residual r = s - theta x
-      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, 1, ritz, nullptr);
+      k_init_pencil<<<1, 256, 0, c.s>>>(G, S, th);
+      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, 1, ritz, nullptr);  // (theta, 1)
       k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz, 1, D,
                                                            o.denom_floor, N, t, c.partial);
       k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
       HQ_LAUNCH_CHECK();
-      double h[2];
       HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
       HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
       HQ_CUDA(cudaStreamSynchronize(c.s));
@@ -602,7 +679,9 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       have_prev = true;
       info.n_refinements++;
       const double target = std::max(o.inner_tol * res, 0.3 * o.tol_residual);
-      // inner FP32 Davidson for the correction of x
+      // inner FP32 Davidson for the correction of x; the basis {x, v_1..v_m} is
+      // stored as FP64 x and FP32 v_i, so the projected pencil uses their exact
+      // FP64 overlap matrix S
       int m = 0;
       HQ_TRY(orthonormalise<float>(c, t, x, V, N, 0, V, &ratio));
       if (ratio < 1e-12) continue;
@@ -613,11 +692,14 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, HINQS_PREC_FP32, c.s));
         info.n_sigma_fp32++;
         total++;
-        // G[0][m] = s . v_m ; G[i][m] = v_i . w_m (i = 1..m)
+        // G[0][m] = s.v_m, G[i][m] = v_i.w_m; S[0][m] = x.v_m, S[i][m] = v_i.v_m
         HQ_TRY(dots<float, double>(c, vm, N, 1, sx, col));
         HQ_TRY(dots<float, float>(c, V, N, m, wm, col + 1));
+        HQ_TRY(dots<float, double>(c, vm, N, 1, x, scol));
+        HQ_TRY(dots<float, float>(c, V, N, m, vm, scol + 1));
         k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m, col, m + 1, 0);
-        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, nullptr);
+        k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, m, scol, m + 1, 0);
+        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S);
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -635,16 +717,12 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       }
       // x <- y0 x + sum y_i v_i, normalised (FP64)
       double* y = ritz + 1;
-      {
-        // t = y0 * x + V y[1..]
-        HQ_TRY(lincomb<double>(c, t, x, N, 1, y, 0));
-        HQ_TRY(lincomb<float>(c, t, V, N, m, y + 1, 1));
-        double* nrm = c.small + 2 * kMaxSub + 1;
-        HQ_TRY(dots<double, double>(c, t, N, 1, t, nrm));
-        k_scale_store<double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
-        HQ_LAUNCH_CHECK();
-      }
-      HQ_CUDA(cudaMemsetAsync(G, 0, kMaxSub * kMaxSub * sizeof(double), c.s));
+      HQ_TRY(lincomb<double>(c, t, x, N, 1, y, 0));
+      HQ_TRY(lincomb<float>(c, t, V, N, m, y + 1, 1));
+      double* nrm = c.small + 2 * kMaxSub + 1;
+      HQ_TRY(dots<double, double>(c, t, N, 1, t, nrm));
+      k_scale_store<double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
+      HQ_LAUNCH_CHECK();
     }
   };
   rc = run();
