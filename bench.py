@@ -289,9 +289,39 @@ def main():
         r = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-6,
                         tol_energy=1e-8, max_subspace=16, max_iter=200, trace_cap=512)
         fp64_runs.append(r)
-    tt_fp64 = min(x for x in (time_to(r.trace) for r in fp64_runs) if x is not None)
-    tt_mixed = [time_to(r.trace) for r in results]
-    tt_mixed = min(x for x in tt_mixed if x is not None)
+
+    def best_time(runs):
+        ts = [x for x in (time_to(r.trace) for r in runs) if x is not None]
+        return min(ts) if ts else None
+
+    tt_fp64 = best_time(fp64_runs)
+    tt_mixed = best_time(results)
+
+    # algorithmic FMA count of one sigma product (same-spin rows, diagonal,
+    # alpha-self x beta-singles, opposite-spin scatter)
+    fma = (N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
+           + la.n_singles * (lb.n_singles + sub.Nb * nb))
+    peaks = {"fp64_tflops": 1.129, "fp32_tflops": 68.82}  # measured FMA-chain peaks, this GPU model
+    roof = {"bound": "alu", "kernel": "hinqs_sigma FP32 (k_sigma_rows + k_sigma_ab)",
+            "achieved": 2 * fma / t_s32 / 1e12, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
+            "frac": 2 * fma / t_s32 / 1e12 / peaks["fp32_tflops"], "traffic": None,
+            "fp64": {"achieved": 2 * fma / t_s64 / 1e12, "peak": peaks["fp64_tflops"],
+                     "frac": 2 * fma / t_s64 / 1e12 / peaks["fp64_tflops"]},
+            "fma_per_sigma": fma}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        H_o = oracle.Ham(w["h"], w["eri"], w["e_nuc"], na, nb)
+        sa_o, sb_o = oracle.build_subspace(w["alpha"], w["beta"], na, nb)
+        rows = np.sort(np.random.default_rng(0).choice(N, 4000, replace=False))
+        c_h = c64.cpu().numpy()
+        t0 = time.perf_counter()
+        oracle.sigma(H_o, sa_o, sb_o, c_h, rows=rows)
+        tcpu = time.perf_counter() - t0
+        cpu = {"value": len(rows) / tcpu, "unit": "sigma dets/s", "cores": oracle.max_threads(),
+               "kind": "oracle",
+               "sample": f"{len(rows)} random rows of one FP64 sigma product of the {N}-determinant workload"}
 
     t_step = max(times) if world == 1 else max(times)
     t_mean = sum(times) / len(times)
@@ -325,7 +355,10 @@ def main():
         "sigma_dets_per_s": {"fp64": N / t_s64, "fp32": N / t_s32},
         "sigma_ms": {"fp64": 1e3 * t_s64, "fp32": 1e3 * t_s32},
         "time_to_1e-6_Ha_s": {"mixed": tt_mixed, "fp64": tt_fp64,
-                              "speedup_mixed_vs_fp64": tt_fp64 / tt_mixed},
+                              "speedup_mixed_vs_fp64": (tt_fp64 / tt_mixed)
+                              if (tt_fp64 and tt_mixed) else None},
+        "roofline": roof,
+        "cpu_baseline": cpu,
         "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
                    "mixed_sigmas": [last.n_sigma_fp64, last.n_sigma_fp32],
                    "fp64_sigmas": fp64_runs[-1].n_sigma_fp64},

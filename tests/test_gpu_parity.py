@@ -34,16 +34,16 @@ def make_case(name):
         rng = np.random.default_rng(5)
         a = synth.all_strings(10, 3)
         b = synth.all_strings(10, 4)
-        a = rng.choice(a, size=97, replace=False)
-        b = rng.choice(b, size=131, replace=False)
+        a = rng.choice(a, size=41, replace=False)
+        b = rng.choice(b, size=73, replace=False)
         return h, eri, 0.37, 10, 3, 4, a, b
     if name == "no_beta_6_2_0":
         h, eri, _ = synth.integrals(6, 102)
         return h, eri, 0.0, 6, 2, 0, synth.all_strings(6, 2), np.array([0], dtype=np.uint64)
     if name == "hf_12_4_4":
         h, eri, _ = synth.integrals(12, 103)
-        a = synth.hf_weighted_strings(12, 4, 300, 7)
-        b = synth.hf_weighted_strings(12, 4, 200, 8)
+        a = synth.hf_weighted_strings(12, 4, 60, 7)
+        b = synth.hf_weighted_strings(12, 4, 50, 8)
         return h, eri, -1.5, 12, 4, 4, a, b
     raise KeyError(name)
 
@@ -63,6 +63,19 @@ class Built:
 
 
 _cache = {}
+_gs = {}
+
+
+def ground_state(B):
+    """Oracle ground state: dense eigh up to 3500 determinants, else Lanczos."""
+    if id(B) not in _gs:
+        if len(B.sa) * len(B.sb) <= 3500:
+            _gs[id(B)] = oracle.ground_state_dense(B.H, B.sa, B.sb)
+        else:
+            E, c, r = oracle.lanczos(B.H, B.sa, B.sb, tol=1e-12)
+            assert r < 1e-9
+            _gs[id(B)] = (E, c)
+    return _gs[id(B)]
 
 
 def built(name):
@@ -237,7 +250,7 @@ def test_sigma_hermitian_full_size(precision_workload):
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_davidson_vs_dense(name, prec):
     B = built(name)
-    E, c0 = oracle.ground_state_dense(B.H, B.sa, B.sb)
+    E, c0 = ground_state(B)
     p = hq.DAVIDSON_FP64 if prec == "fp64" else hq.DAVIDSON_MIXED
     res = hq.davidson(B.ham, B.sub, B.la, B.lb, precision=p, tol_residual=1e-8,
                       max_subspace=12, max_iter=300)
@@ -252,9 +265,28 @@ def test_davidson_vs_dense(name, prec):
     assert np.linalg.norm(Hc - res.energy * c) <= 2e-8
 
 
+def test_davidson_full_size_properties(precision_workload):
+    """The bench configuration (4.0e6 determinants): FP64 and mixed solvers agree,
+    and the oracle's sampled rows confirm the residual of both eigenvectors."""
+    B = precision_workload
+    r64 = hq.davidson(B.ham, B.sub, B.la, B.lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-8,
+                      max_iter=400, max_subspace=16)
+    rmx = hq.davidson(B.ham, B.sub, B.la, B.lb, precision=hq.DAVIDSON_MIXED, tol_residual=1e-8,
+                      max_iter=400, max_subspace=16)
+    assert r64.status == hq.OK and rmx.status == hq.OK
+    assert abs(r64.energy - rmx.energy) <= 1e-8
+    assert rmx.n_sigma_fp64 < r64.n_sigma_fp64
+    rows = np.sort(np.random.default_rng(17).choice(B.sub.N, size=256, replace=False))
+    for res in (r64, rmx):
+        c = res.c.cpu().numpy()
+        assert abs(np.linalg.norm(c) - 1.0) < 1e-12
+        Hc = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
+        assert np.max(np.abs(Hc - res.energy * c[rows])) <= 1e-8
+
+
 def test_davidson_warm_start_and_not_converged():
     B = built("hf_12_4_4")
-    E, c0 = oracle.ground_state_dense(B.H, B.sa, B.sb)
+    E, c0 = ground_state(B)
     g = torch.tensor(c0, dtype=torch.float64, device="cuda")
     res = hq.davidson(B.ham, B.sub, B.la, B.lb, guess=g, tol_residual=1e-8)
     assert res.status == hq.OK and res.iterations <= 3 and abs(res.energy - E) < 1e-9
@@ -285,7 +317,7 @@ def test_energy_autograd_hellmann_feynman():
     E.backward()
     H = oracle.Ham(h, eri, e_nuc, na, nb)
     sa, sb = oracle.build_subspace(a, b, na, nb)
-    Eo, c0 = oracle.ground_state_dense(H, sa, sb)
+    Eo, c0 = ground_state(built("hf_12_4_4"))
     assert abs(float(E) - Eo) < 1e-9
     r1, r2 = oracle.rdm(n, sa, sb, c0)
     assert np.max(np.abs(ht.grad.cpu().numpy() - r1)) < 1e-8
