@@ -16,6 +16,7 @@
 // accuracy until the FP64 residual meets the tolerance.
 #include <algorithm>
 #include <chrono>
+#include <type_traits>
 #include <cmath>
 #include <vector>
 
@@ -32,51 +33,56 @@ constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------- kernels --
 
-// partial[b*m + i] = sum over this block's elements of A_i . bvec
+// partial[i*gridDim.x + b] = block b's share of A_i . bvec (grid.y = vector i).
+// FP32 x FP32 products are summed in FP32 over groups of four strided elements and
+// the group sums in FP64; every other combination is formed and summed in FP64.
 template <typename TA, typename TB>
-__global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, int64_t lda, int m,
+__global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, int64_t lda,
                                                       const TB* __restrict__ b, int64_t N,
                                                       double* __restrict__ partial) {
-  double acc[kMaxSub];
-#pragma unroll
-  for (int i = 0; i < kMaxSub; ++i) acc[i] = 0.0;
-  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
-       j += (int64_t)gridDim.x * blockDim.x) {
-    double bj = (double)b[j];
-#pragma unroll
-    for (int i = 0; i < kMaxSub; ++i)
-      if (i < m) acc[i] += (double)A[i * lda + j] * bj;
+  const int i = blockIdx.y;
+  const TA* __restrict__ a = A + (int64_t)i * lda;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc = 0.0;
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value) {
+    for (; j + 3 * stride < N; j += 4 * stride) {
+      float p = a[j] * b[j];
+      p = fmaf(a[j + stride], b[j + stride], p);
+      p = fmaf(a[j + 2 * stride], b[j + 2 * stride], p);
+      p = fmaf(a[j + 3 * stride], b[j + 3 * stride], p);
+      acc += (double)p;
+    }
   }
-  __shared__ double red[kRedThreads / 32][kMaxSub];
-  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (; j < N; j += stride) acc += (double)a[j] * (double)b[j];
+  __shared__ double red[kRedThreads / 32];
 #pragma unroll
-  for (int i = 0; i < kMaxSub; ++i) {
-    if (i >= m) break;
-    double v = acc[i];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) red[wid][i] = v;
-  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
-  if (threadIdx.x < m) {
+  if (threadIdx.x == 0) {
     double v = 0.0;
-    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w][threadIdx.x];
-    partial[blockIdx.x * m + threadIdx.x] = v;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[w];
+    partial[(int64_t)i * gridDim.x + blockIdx.x] = v;
   }
 }
 
-// out[i] = sum_b partial[b*m + i] (fixed order: deterministic)
+// out[i] = sum_b partial[i*nb + b] (fixed order: deterministic); one warp per i
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int m,
                                   double* __restrict__ out) {
-  int i = threadIdx.x;
-  if (i < m) {
+  const int lane = threadIdx.x & 31;
+  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
     double v = 0.0;
-    for (int b = 0; b < nb; ++b) v += partial[b * m + i];
-    out[i] = v;
+    for (int b = lane; b < nb; b += 32) v += partial[(int64_t)i * nb + b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[i] = v;
   }
 }
 
-// out (FP64) = alpha*out + sum_i coef[i] * A_i      (mode 0: set, 1: add, -1: subtract)
+// out (FP64) = (mode 0: 0, 1: out, -1: out) +/- sum_i coef[i] * A_i.  For FP32 A the
+// combination is formed in FP32 (it is a correction whose rounding is relative to
+// itself) and added to out in FP64.
 template <typename TA>
 __global__ void k_lincomb(double* __restrict__ out, const TA* __restrict__ A, int64_t lda, int m,
                           const double* __restrict__ coef, int64_t N, int mode) {
@@ -85,28 +91,58 @@ __global__ void k_lincomb(double* __restrict__ out, const TA* __restrict__ A, in
   __syncthreads();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * blockDim.x) {
-    double v = 0.0;
-    for (int i = 0; i < m; ++i) v += c[i] * (double)A[i * lda + j];
+    double v;
+    if constexpr (std::is_same<TA, float>::value) {
+      float f = 0.0f;
+      for (int i = 0; i < m; ++i) f = fmaf((float)c[i], A[i * lda + j], f);
+      v = (double)f;
+    } else {
+      v = 0.0;
+      for (int i = 0; i < m; ++i) v += c[i] * A[i * lda + j];
+    }
     if (mode == 0) out[j] = v;
     else if (mode > 0) out[j] += v;
     else out[j] -= v;
   }
 }
 
-// y = x / sqrt(nrm2[0]) with type conversion
-template <typename TO>
-__global__ void k_scale_store(const double* __restrict__ x, const double* __restrict__ nrm2,
-                              TO* __restrict__ y, int64_t N) {
-  double s = 1.0 / sqrt(nrm2[0]);
+// FP32 out = out - sum_i coef[i] * A_i (FP32 arithmetic)
+__global__ void k_lincomb_sub_f32(float* __restrict__ out, const float* __restrict__ A,
+                                  int64_t lda, int m, const double* __restrict__ coef, int64_t N) {
+  __shared__ float c[kMaxSub];
+  if (threadIdx.x < m) c[threadIdx.x] = (float)coef[threadIdx.x];
+  __syncthreads();
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
-       j += (int64_t)gridDim.x * blockDim.x)
-    y[j] = (TO)(x[j] * s);
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float f = out[j];
+    for (int i = 0; i < m; ++i) f = fmaf(-c[i], A[i * lda + j], f);
+    out[j] = f;
+  }
+}
+
+// y = x / sqrt(nrm2[0]) with type conversion
+template <typename TI, typename TO>
+__global__ void k_scale_store(const TI* __restrict__ x, const double* __restrict__ nrm2,
+                              TO* __restrict__ y, int64_t N) {
+  if constexpr (std::is_same<TI, float>::value) {
+    const float s = (float)(1.0 / sqrt(nrm2[0]));
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x)
+      y[j] = (TO)(x[j] * s);
+  } else {
+    const double s = 1.0 / sqrt(nrm2[0]);
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+         j += (int64_t)gridDim.x * blockDim.x)
+      y[j] = (TO)(x[j] * s);
+  }
 }
 
 // Residual and preconditioned correction.
 //   r = y0*s0 + sum_i y[i] W_i - theta*(y0*x0 + sum_i y[i] V_i)
 //   t = r / floor(D - theta);  partial ||r||^2 per block
-// (x0, s0 may be NULL; then y0 is ignored.)
+// (x0, s0 may be NULL; then y0 is ignored.)  For FP32 V, W the two sums over i
+// are formed in FP32: they carry the correction, whose rounding is relative to
+// itself, while the FP64 parts y0*s0 and y0*x0 stay FP64.
 template <typename TV>
 __global__ void __launch_bounds__(kRedThreads) k_residual(
     const double* __restrict__ x0, const double* __restrict__ s0, const TV* __restrict__ V,
@@ -118,19 +154,29 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
   if (threadIdx.x <= m + has_x0) y[threadIdx.x] = ritz[1 + threadIdx.x];
   __syncthreads();
   const double theta = ritz[0];
+  const int o = has_x0 ? 1 : 0;
   double acc = 0.0;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * blockDim.x) {
     double hx = 0.0, xx = 0.0;
-    int o = 0;
     if (has_x0) {
       hx = y[0] * s0[j];
       xx = y[0] * x0[j];
-      o = 1;
     }
-    for (int i = 0; i < m; ++i) {
-      hx += y[o + i] * (double)W[i * ld + j];
-      xx += y[o + i] * (double)V[i * ld + j];
+    if constexpr (std::is_same<TV, float>::value) {
+      float hf = 0.0f, xf = 0.0f;
+      for (int i = 0; i < m; ++i) {
+        const float yi = (float)y[o + i];
+        hf = fmaf(yi, W[i * ld + j], hf);
+        xf = fmaf(yi, V[i * ld + j], xf);
+      }
+      hx += (double)hf;
+      xx += (double)xf;
+    } else {
+      for (int i = 0; i < m; ++i) {
+        hx += y[o + i] * W[i * ld + j];
+        xx += y[o + i] * V[i * ld + j];
+      }
     }
     double r = hx - theta * xx;
     acc += r * r;
@@ -139,7 +185,7 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     t[j] = r / den;
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -368,14 +414,16 @@ struct Ctx {
   cudaStream_t s;
   int64_t N;
   int grid;
-  double* partial = nullptr;  // [kRedGrid * (kMaxSub+1)]
+  double* partial = nullptr;  // [(kMaxSub+1) * kRedGrid]
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
+  float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
 };
 
 template <typename TA, typename TB>
 static int dots(Ctx& c, const TA* A, int64_t lda, int m, const TB* b, double* out) {
-  k_dots<TA, TB><<<kRedGrid, kRedThreads, 0, c.s>>>(A, lda, m, b, c.N, c.partial);
-  k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, m, out);
+  if (m <= 0) return HINQS_OK;
+  k_dots<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b, c.N, c.partial);
+  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, m, out);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -389,34 +437,57 @@ static int lincomb(Ctx& c, double* out, const TA* A, int64_t lda, int m, const d
   return HINQS_OK;
 }
 
-// Orthonormalise t (FP64, modified in place) against an FP64 vector x (if any)
-// and m basis vectors V (type TV), classical Gram-Schmidt twice; store the
-// normalised result into dst (type TV).  Returns the norm ratio after/before.
-template <typename TV>
-static int orthonormalise(Ctx& c, double* t, const double* x, const TV* V, int64_t ld, int m,
-                          TV* dst, double* ratio) {
-  double* coef = c.small;             // [kMaxSub]
-  double* coefx = c.small + kMaxSub;  // [1]
+// Orthonormalise t (FP64, modified in place) against m FP64 basis vectors V,
+// classical Gram-Schmidt twice; store the normalised result into dst.
+// Returns the norm ratio after/before.
+static int orthonormalise(Ctx& c, double* t, const double* V, int64_t ld, int m, double* dst,
+                          double* ratio) {
+  double* coef = c.small;  // [kMaxSub]
   double* nrm = c.small + kMaxSub + 1;
   double hn[2];
   HQ_TRY(dots<double, double>(c, t, c.N, 1, t, nrm));
   HQ_CUDA(cudaMemcpyAsync(&hn[0], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-  for (int pass = 0; pass < 2; ++pass) {
-    if (x) {
-      HQ_TRY(dots<double, double>(c, x, c.N, 1, t, coefx));
-      HQ_TRY(lincomb<double>(c, t, x, c.N, 1, coefx, -1));
-    }
-    if (m > 0) {
-      HQ_TRY(dots<TV, double>(c, V, ld, m, t, coef));
-      HQ_TRY(lincomb<TV>(c, t, V, ld, m, coef, -1));
-    }
+  for (int pass = 0; pass < 2 && m > 0; ++pass) {
+    HQ_TRY(dots<double, double>(c, V, ld, m, t, coef));
+    HQ_TRY(lincomb<double>(c, t, V, ld, m, coef, -1));
   }
   HQ_TRY(dots<double, double>(c, t, c.N, 1, t, nrm));
   HQ_CUDA(cudaMemcpyAsync(&hn[1], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
   HQ_CUDA(cudaStreamSynchronize(c.s));
   *ratio = (hn[0] > 0.0) ? std::sqrt(hn[1] / hn[0]) : 0.0;
   if (hn[1] <= 0.0) return HINQS_OK;
-  k_scale_store<TV><<<c.grid, 256, 0, c.s>>>(t, nrm, dst, c.N);
+  k_scale_store<double, double><<<c.grid, 256, 0, c.s>>>(t, nrm, dst, c.N);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+// Mixed mode: remove the FP64 vector x from t in FP64 (twice), round t to FP32,
+// remove the m FP32 basis vectors V in FP32 arithmetic (twice) and store the
+// normalised FP32 result into dst.  The projected pencil carries the exact
+// overlap of the stored vectors, so FP32 orthogonality suffices here.
+static int orthonormalise_mixed(Ctx& c, double* t, const double* x, const float* V, int64_t ld,
+                                int m, float* dst, double* ratio) {
+  double* coef = c.small;
+  double* coefx = c.small + kMaxSub;
+  double* nrm = c.small + kMaxSub + 1;
+  double hn[2];
+  HQ_TRY(dots<double, double>(c, t, c.N, 1, t, nrm));
+  HQ_CUDA(cudaMemcpyAsync(&hn[0], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  for (int pass = 0; pass < 2; ++pass) {
+    HQ_TRY(dots<double, double>(c, x, c.N, 1, t, coefx));
+    HQ_TRY(lincomb<double>(c, t, x, c.N, 1, coefx, -1));
+  }
+  k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(t, c.t32, c.N);
+  for (int pass = 0; pass < 2 && m > 0; ++pass) {
+    HQ_TRY(dots<float, float>(c, V, ld, m, c.t32, coef));
+    k_lincomb_sub_f32<<<c.grid, 256, 0, c.s>>>(c.t32, V, ld, m, coef, c.N);
+  }
+  HQ_TRY(dots<float, float>(c, c.t32, c.N, 1, c.t32, nrm));
+  HQ_CUDA(cudaMemcpyAsync(&hn[1], nrm, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+  HQ_CUDA(cudaStreamSynchronize(c.s));
+  *ratio = (hn[0] > 0.0) ? std::sqrt(hn[1] / hn[0]) : 0.0;
+  if (hn[1] <= 0.0) return HINQS_OK;
+  k_scale_store<float, float><<<c.grid, 256, 0, c.s>>>(c.t32, nrm, dst, c.N);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -494,7 +565,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       HQ_TRY(unit_at_min(c, D, t));
     }
     double ratio;
-    HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, 0, V, &ratio));
+    HQ_TRY(orthonormalise(c, t, V, N, 0, V, &ratio));
     if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
     k_init_pencil<<<1, 256, 0, c.s>>>(G, nullptr, nullptr);
     int m = 1;
@@ -511,7 +582,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
       k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
                                                             D, o.denom_floor, N, t, c.partial);
-      k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
       HQ_LAUNCH_CHECK();
       double hres = 0.0;
       HQ_CUDA(cudaMemcpyAsync(hr, ritz, (kMaxSub + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -578,12 +649,12 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       }
       std::copy(hr, hr + kMaxSub + 1, hr_prev);
       if (m < mmax) {
-        HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, m, V + (size_t)m * N, &ratio));
+        HQ_TRY(orthonormalise(c, t, V, N, m, V + (size_t)m * N, &ratio));
         if (ratio < 1e-10) {
           // stagnated preconditioner: fall back to the plain residual direction
           k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz,
                                                                 0, D, 1e300, N, t, c.partial);
-          HQ_TRY(orthonormalise<double>(c, t, nullptr, V, N, m, V + (size_t)m * N, &ratio));
+          HQ_TRY(orthonormalise(c, t, V, N, m, V + (size_t)m * N, &ratio));
           if (ratio < 1e-14) {
             HQ_TRY(lincomb<double>(c, c_out, V, N, m, ritz + 1, 0));
             if (energy) *energy = info.energy;
@@ -615,7 +686,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       (rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
       (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&S, kMaxSub * kMaxSub, c.s)) ||
       (rc = dalloc(&ritz, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&scol, kMaxSub + 2, c.s))) {
+      (rc = dalloc(&scol, kMaxSub + 2, c.s)) || (rc = dalloc(&c.t32, N, c.s))) {
   }
   auto cleanup = [&]() {
     dfree(x, c.s);
@@ -628,6 +699,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     dfree(ritz, c.s);
     dfree(col, c.s);
     dfree(scol, c.s);
+    dfree(c.t32, c.s);
   };
   if (rc) {
     cleanup();
@@ -640,7 +712,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       HQ_TRY(unit_at_min(c, D, t));
     }
     double ratio;
-    HQ_TRY(orthonormalise<double>(c, t, nullptr, (double*)nullptr, N, 0, x, &ratio));
+    HQ_TRY(orthonormalise(c, t, nullptr, N, 0, x, &ratio));
     if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
     double theta_prev = 0.0;
     bool have_prev = false;
@@ -657,7 +729,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, 1, ritz, nullptr);  // (theta, 1)
       k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz, 1, D,
                                                            o.denom_floor, N, t, c.partial);
-      k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
       HQ_LAUNCH_CHECK();
       HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
       HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -683,7 +755,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       // stored as FP64 x and FP32 v_i, so the projected pencil uses their exact
       // FP64 overlap matrix S
       int m = 0;
-      HQ_TRY(orthonormalise<float>(c, t, x, V, N, 0, V, &ratio));
+      HQ_TRY(orthonormalise_mixed(c, t, x, V, N, 0, V, &ratio));
       if (ratio < 1e-12) continue;
       m = 1;
       for (;;) {
@@ -702,7 +774,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S);
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
-        k_reduce_partials<<<1, 64, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
         HQ_LAUNCH_CHECK();
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -711,7 +783,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         info.iterations++;
         tr.add(h[0], rin, 1);
         if (rin <= target || m + 1 >= mmax || total >= o.max_iter) break;
-        HQ_TRY(orthonormalise<float>(c, t, x, V, N, m, V + (size_t)m * N, &ratio));
+        HQ_TRY(orthonormalise_mixed(c, t, x, V, N, m, V + (size_t)m * N, &ratio));
         if (ratio < 1e-12) break;
         m++;
       }
@@ -721,7 +793,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       HQ_TRY(lincomb<float>(c, t, V, N, m, y + 1, 1));
       double* nrm = c.small + 2 * kMaxSub + 1;
       HQ_TRY(dots<double, double>(c, t, N, 1, t, nrm));
-      k_scale_store<double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
+      k_scale_store<double, double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
       HQ_LAUNCH_CHECK();
     }
   };
