@@ -241,6 +241,24 @@ int hinqs_energy_backward(int n_orb, double grad_E, const double* rdm1, const do
 int hinqs_spin_marginals(const hinqs_subspace* sub, const double* c, double* p_alpha,
                          double* p_beta, double* w, void* stream);
 
+/* ---------------------------------------------- allocation-free marginals --
+ * The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory while they run: a process whose allocator has already
+ * reserved all the device memory it may use, or a serving loop that must not meet
+ * an out-of-memory failure, or change its footprint, once it is up.
+ * Same arguments and results as hinqs_spin_marginals (up to summation order), but
+ * its scratch space is a fixed array inside the library (2^20 doubles = 8 MiB,
+ * held by every GPU that loads the library until the process exits) instead of
+ * memory allocated per call; it calls no allocating routine.
+ *   Limit: N_beta <= 2^20 - 2, else HINQS_ERR_ARG with a message; nothing is done.
+ *   Set-up: the first call on a device looks up the array's device address with
+ *   that device current; make that first call before any stream capture.
+ *   Concurrency: all calls share the array and it keeps the last call's contents;
+ *   calls that can overlap on the GPU (other streams, other host threads) race on
+ *   it and must be serialised by the caller. */
+int hinqs_spin_marginals_noalloc(const hinqs_subspace* sub, const double* c, double* p_alpha,
+                                 double* p_beta, double* w, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

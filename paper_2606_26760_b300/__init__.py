@@ -70,6 +70,7 @@ EXPORTED = [
     "hinqs_subspace_destroy", "hinqs_string_links", "hinqs_links_count", "hinqs_links_export",
     "hinqs_links_destroy", "hinqs_diag", "hinqs_sigma", "hinqs_davidson_default_opts",
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
+    "hinqs_spin_marginals_noalloc",
 ]
 
 
@@ -105,6 +106,7 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_rdm.argtypes = [P, P, P, P, P, P, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
+    lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
     _lib = lib
     return lib
 
@@ -333,6 +335,14 @@ def spin_marginals(sub, c, want_w: bool = False):
     w = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if want_w else None
     _check(_lib.hinqs_spin_marginals(sub.handle, _ptr(c), _ptr(pa), _ptr(pb), _ptr(w), _stream()))
     return (pa, pb, w) if want_w else (pa, pb)
+
+
+def spin_marginals_noalloc(sub, c, p_alpha, p_beta, w=None):
+    """hinqs_spin_marginals_noalloc: the library allocates nothing (its scratch is a
+    fixed 8 MiB device array); the caller provides every output buffer."""
+    _check(_lib.hinqs_spin_marginals_noalloc(sub.handle, _ptr(c), _ptr(p_alpha), _ptr(p_beta),
+                                             _ptr(w), _stream()))
+    return p_alpha, p_beta, w
 
 
 class HinqsEnergy(torch.autograd.Function):

@@ -117,6 +117,15 @@ int diag_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_lin
 }  // namespace hinqs
 
 namespace hinqs {
+// Spin-marginal reduction kernels (defined with hinqs_spin_marginals).
+__global__ void k_row_sq(const double* __restrict__ C, int64_t Na, int64_t Nb, double* pa);
+__global__ void k_col_sq(const double* __restrict__ C, int64_t Na, int64_t Nb, int64_t rows_per,
+                         double* part);
+__global__ void k_sum_chunks(const double* __restrict__ part, int64_t chunks, int64_t Nb, double* pb);
+__global__ void k_marg_norm(double* pa, int64_t Na, double* pb, int64_t Nb, double* tot);
+__global__ void k_teacher(const double* __restrict__ pa, const double* __restrict__ pb, int64_t Na,
+                          int64_t Nb, const double* __restrict__ tot, double* __restrict__ w);
+
 // Exclusive prefix sum of n int64 values on the device (out may alias in).
 // If total != nullptr the grand total is copied to *total (host) after a
 // stream synchronisation.
