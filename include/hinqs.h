@@ -65,6 +65,12 @@ extern "C" {
 /* sigma precision */
 #define HINQS_PREC_FP64 0   /* c, sigma: double; FP64 arithmetic */
 #define HINQS_PREC_FP32 1   /* c, sigma: float; FP32 arithmetic */
+/* c, sigma: float; same-spin and diagonal terms in FP32, the opposite-spin term as a
+ * gather into D and a tcgen05 GEMM against (pq|rs) with FP32 accumulation in tensor
+ * memory, operands BF16 (about 8 significant bits) ... */
+#define HINQS_PREC_FP32_BF16AB 2
+/* ... or operands split as hi + lo BF16 with hi*hi + hi*lo + lo*hi (about 16 bits) */
+#define HINQS_PREC_FP32_BF16X3AB 3
 
 /* Davidson precision */
 #define HINQS_DAVIDSON_FP64 0   /* every sigma in FP64 */
@@ -156,7 +162,9 @@ int hinqs_diag(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_link
  *   sigma = H_a C + C H_b^T + sum_{pq,rs} (pq|rs) E^a_pq C (E^b_rs)^T + E_nuc C
  * with C the N_a x N_b matrix of c.  c and sigma are device vectors of
  * N_a*N_b elements of the precision's type (double for HINQS_PREC_FP64, float
- * for HINQS_PREC_FP32); sigma is overwritten; c and sigma must not overlap.
+ * otherwise); sigma is overwritten; c and sigma must not overlap.  The tensor-core
+ * modes synchronise the stream to check the kernel's bounded waits
+ * (HINQS_ERR_TIMEOUT if one ran out).
  * la / lb are the alpha / beta links of this ham and subspace. */
 int hinqs_sigma(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
                 const hinqs_links* lb, const void* c, void* sigma, int precision, void* stream);
@@ -186,6 +194,8 @@ typedef struct hinqs_davidson_opts {
   double* trace_resid;  /* host [trace_cap] or NULL: residual norm estimate per iteration */
   double* trace_time;   /* host [trace_cap] or NULL: seconds since the call began */
   int* trace_kind;      /* host [trace_cap] or NULL: 0 = FP64 iterate, 1 = FP32 inner iterate */
+  int inner_precision;  /* mixed: sigma precision of the inner products: HINQS_PREC_FP32,
+                           HINQS_PREC_FP32_BF16AB or HINQS_PREC_FP32_BF16X3AB */
 } hinqs_davidson_opts;
 
 typedef struct hinqs_davidson_info {
@@ -201,7 +211,7 @@ typedef struct hinqs_davidson_info {
   double seconds;       /* wall time of the call */
 } hinqs_davidson_info;
 
-/* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace). */
+/* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace, FP32 inner). */
 void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
 
 /*   guess   device FP64 [N] or NULL (then e_k at argmin H_diag, lowest index on ties)

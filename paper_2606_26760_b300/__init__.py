@@ -32,7 +32,7 @@ ERR_ARG, ERR_PARTICLE_NUMBER, ERR_ASYMMETRIC, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ER
     -1, -2, -3, -4, -5, -6, -7)
 DROP_BAD, ERROR_BAD, FULL_SPACE = 0x0, 0x1, 0x2
 CHECK_SYMMETRY = 0x1
-PREC_FP64, PREC_FP32 = 0, 1
+PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB = 0, 1, 2, 3
 DAVIDSON_FP64, DAVIDSON_MIXED = 0, 1
 
 
@@ -53,7 +53,8 @@ class _Opts(ctypes.Structure):
                 ("trace_theta", ctypes.POINTER(ctypes.c_double)),
                 ("trace_resid", ctypes.POINTER(ctypes.c_double)),
                 ("trace_time", ctypes.POINTER(ctypes.c_double)),
-                ("trace_kind", ctypes.POINTER(ctypes.c_int))]
+                ("trace_kind", ctypes.POINTER(ctypes.c_int)),
+                ("inner_precision", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -248,7 +249,8 @@ def diag(ham, sub, la, lb, out=None):
 
 
 def sigma(ham, sub, la, lb, c, out=None, precision: int | None = None):
-    """sigma = H_B c; precision from c's dtype (float64 -> FP64, float32 -> FP32)."""
+    """sigma = H_B c; precision from c's dtype (float64 -> FP64, float32 -> FP32) unless
+    given (the tensor-core modes take float32 vectors)."""
     if precision is None:
         precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
     dt = torch.float64 if precision == PREC_FP64 else torch.float32
@@ -280,12 +282,13 @@ class DavidsonResult:
 def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
              max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
              denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
-             out=None) -> DavidsonResult:
+             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
     opts = _Opts()
     _lib.hinqs_davidson_default_opts(ctypes.byref(opts))
     opts.precision, opts.max_iter, opts.max_subspace = precision, max_iter, max_subspace
     opts.tol_residual, opts.tol_energy, opts.denom_floor = tol_residual, tol_energy, denom_floor
     opts.inner_tol = inner_tol
+    opts.inner_precision = inner_precision
     bufs = None
     if trace_cap > 0:
         bufs = ((ctypes.c_double * trace_cap)(), (ctypes.c_double * trace_cap)(),

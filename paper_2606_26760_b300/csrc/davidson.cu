@@ -761,7 +761,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       for (;;) {
         float* vm = V + (size_t)(m - 1) * N;
         float* wm = W + (size_t)(m - 1) * N;
-        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, HINQS_PREC_FP32, c.s));
+        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, o.inner_precision, c.s));
         info.n_sigma_fp32++;
         total++;
         // G[0][m] = s.v_m, G[i][m] = v_i.w_m; S[0][m] = x.v_m, S[i][m] = v_i.v_m
@@ -820,6 +820,7 @@ extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
   o->trace_resid = nullptr;
   o->trace_time = nullptr;
   o->trace_kind = nullptr;
+  o->inner_precision = HINQS_PREC_FP32;
 }
 
 extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
@@ -837,6 +838,9 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
     return fail(HINQS_ERR_ARG, "hinqs_davidson: bad max_iter / tolerances");
   if (o.precision != HINQS_DAVIDSON_FP64 && o.precision != HINQS_DAVIDSON_MIXED)
     return fail(HINQS_ERR_ARG, "hinqs_davidson: unknown precision %d", o.precision);
+  if (o.precision == HINQS_DAVIDSON_MIXED && o.inner_precision != HINQS_PREC_FP32 &&
+      o.inner_precision != HINQS_PREC_FP32_BF16AB && o.inner_precision != HINQS_PREC_FP32_BF16X3AB)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson: unknown inner precision %d", o.inner_precision);
   hinqs_davidson_info info{};
   Trace tr;
   tr.o = &o;
@@ -858,6 +862,10 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   if (rc >= 0) {
     cudaError_t e = cudaStreamSynchronize(c.s);
     if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_davidson", __FILE__, __LINE__);
+  }
+  if (rc >= 0 && o.precision == HINQS_DAVIDSON_MIXED && o.inner_precision != HINQS_PREC_FP32) {
+    int t = tc_error_check(c.s);
+    if (t < 0) rc = t;
   }
   dfree(c.partial, c.s);
   dfree(c.small, c.s);

@@ -85,7 +85,7 @@ struct hinqs_subspace_s {
 //  single links (ascending J per row): srow_ptr[N+1], slink[nsingle] = {J, signed pair}
 //    with signed pair = sign * (p*n + q + 1)
 //  per-string tables: hdiag[N] = H_spin(I,I) (FP64);
-//    V64/V32[N][n*n] = sum_{i in I} (ii|xy)
+//    V64/V32[N][n*n] = sum_{i in I} (ii|xy), VT64/VT32 its transpose [n*n][N]
 struct hinqs_links_s {
   int spin = 0, n = 0, n_e = 0;
   int64_t N = 0, nnz = 0, nsingle = 0;
@@ -103,6 +103,13 @@ struct hinqs_links_s {
   double* hdiag = nullptr;
   double* V64 = nullptr;
   float* V32 = nullptr;
+  double* VT64 = nullptr;  // [n*n][N], transpose of V
+  float* VT32 = nullptr;
+  // single links plus the n_e diagonal pseudo-links (J = I, pair jj, +1) of every
+  // row, slot-major: sell[slot * N + I] = {J, sign * (pair + 1)}, slot < scount[I]
+  int ell_width = 0;
+  int2* sell = nullptr;
+  int* scount = nullptr;
 };
 
 namespace hinqs {
@@ -113,6 +120,12 @@ int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_li
                  cudaStream_t s);
 int diag_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                 const hinqs_links_s* lb, double* hdiag, cudaStream_t s);
+// opposite-spin sigma term on the tensor cores (FP32 vectors; split = 1 or 3)
+int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                       const hinqs_links_s* lb, const float* c, float* sig, int split,
+                       cudaStream_t s);
+// HINQS_ERR_TIMEOUT (and clears the flag) if a tensor-core kernel's bounded wait ran out
+int tc_error_check(cudaStream_t s);
 
 }  // namespace hinqs
 

@@ -118,7 +118,8 @@ __global__ void k_links_fill(const uint64_t* __restrict__ S, int64_t N, int n,
 __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n,
                                 const double* __restrict__ h, const double* __restrict__ eri,
                                 double* __restrict__ hdiag, double* __restrict__ V64,
-                                float* __restrict__ V32) {
+                                float* __restrict__ V32, double* __restrict__ VT64,
+                                float* __restrict__ VT32) {
   int n2 = n * n;
   for (int64_t I = blockIdx.x; I < N; I += gridDim.x) {
     uint64_t x = S[I];
@@ -132,6 +133,8 @@ __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n
       }
       V64[I * n2 + xy] = acc;
       V32[I * n2 + xy] = (float)acc;
+      VT64[(int64_t)xy * N + I] = acc;
+      VT32[(int64_t)xy * N + I] = (float)acc;
     }
     if (threadIdx.x == 0) {
       double e1 = 0.0, e2 = 0.0;
@@ -149,6 +152,26 @@ __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n
       }
       hdiag[I] = e1 + 0.5 * e2;
     }
+  }
+}
+
+// Slot-major copy of the single links plus the diagonal pseudo-links of each row.
+__global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
+                            const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+                            int width, int2* __restrict__ ell, int* __restrict__ cnt) {
+  for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
+       I += (int64_t)gridDim.x * blockDim.x) {
+    int k = 0;
+    for (int64_t q = srp[I]; q < srp[I + 1]; ++q, ++k) ell[(int64_t)k * N + I] = sl[q];
+    uint64_t o = S[I];
+    while (o) {
+      int j = __ffsll((long long)o) - 1;
+      o &= o - 1;
+      ell[(int64_t)k * N + I] = make_int2((int)I, j * n + j + 1);
+      ++k;
+    }
+    cnt[I] = k;
+    for (; k < width; ++k) ell[(int64_t)k * N + I] = make_int2(0, 0);
   }
 }
 
@@ -186,6 +209,10 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->hdiag, s);
   dfree(L->V64, s);
   dfree(L->V32, s);
+  dfree(L->VT64, s);
+  dfree(L->VT32, s);
+  dfree(L->sell, s);
+  dfree(L->scount, s);
 }
 
 }  // namespace hinqs
@@ -236,7 +263,8 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
         (rc = dalloc(&L->hval32, L->nnz, s)) || (rc = dalloc(&L->exc, L->nnz, s)) ||
         (rc = dalloc(&L->sign, L->nnz, s)) || (rc = dalloc(&L->degree, L->nnz, s)) ||
         (rc = dalloc(&L->slink, L->nsingle, s)) || (rc = dalloc(&L->hdiag, N, s)) ||
-        (rc = dalloc(&L->V64, N * n2, s)) || (rc = dalloc(&L->V32, N * n2, s))) {
+        (rc = dalloc(&L->V64, N * n2, s)) || (rc = dalloc(&L->V32, N * n2, s)) ||
+        (rc = dalloc(&L->VT64, N * n2, s)) || (rc = dalloc(&L->VT32, N * n2, s))) {
     }
   }
   if (!rc) {
@@ -244,7 +272,7 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
                                                        L->srow_ptr, L->col, L->hval64, L->hval32,
                                                        L->exc, L->sign, L->degree, L->slink);
     k_string_tables<<<(unsigned)std::min<int64_t>(N, 16 * kNumSMs), 128, 0, s>>>(
-        L->strings, N, n, H->h, H->eri, L->hdiag, L->V64, L->V32);
+        L->strings, N, n, H->h, H->eri, L->hdiag, L->V64, L->V32, L->VT64, L->VT32);
     cudaMemsetAsync(dmax, 0, 2 * sizeof(int), s);
     int g2 = (int)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs);
     k_row_max<<<g2, 256, 0, s>>>(L->row_ptr, N, dmax);
@@ -256,6 +284,16 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
     if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_string_links", __FILE__, __LINE__);
     L->max_row = hm[0];
     L->max_srow = hm[1];
+  }
+  if (!rc) {
+    L->ell_width = L->max_srow + L->n_e;
+    if (!(rc = dalloc(&L->sell, (size_t)std::max(1, L->ell_width) * N, s)) &&
+        !(rc = dalloc(&L->scount, N, s))) {
+      k_build_ell<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs), 256, 0, s>>>(
+          L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->scount);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "k_build_ell", __FILE__, __LINE__);
+    }
   }
   cleanup();
   if (rc) {

@@ -214,6 +214,37 @@ def test_sigma_fp64_and_fp32(name):
         assert np.all(np.abs(s32 - ref) <= _sigma_tol(2e-5, hd, c, ref))
 
 
+@pytest.mark.parametrize("name", SMALL)
+def test_sigma_tensor_core_modes(name):
+    """Opposite-spin term on the tensor cores: operands rounded to BF16 (u = 2^-9)
+    bound the error by ~1e-2 of the term scale; the hi+lo split by ~1e-4."""
+    B = built(name)
+    N = len(B.sa) * len(B.sb)
+    c = synth.random_vector(N, 1)
+    ref = oracle.sigma(B.H, B.sa, B.sb, c)
+    hd = oracle.diag(B.H, B.sa, B.sb)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    for prec, rel in ((hq.PREC_FP32_BF16AB, 2e-2), (hq.PREC_FP32_BF16X3AB, 2e-4)):
+        s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=prec).double().cpu().numpy()
+        assert np.all(np.abs(s - ref) <= _sigma_tol(rel, hd, c, ref)), prec
+
+
+def test_sigma_tensor_core_full_size(precision_workload):
+    B = precision_workload
+    c = synth.random_vector(B.sub.N, 3)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(4).choice(B.sub.N, size=256, replace=False))
+    ref = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
+    hd = oracle.diag(B.H, B.sa, B.sb, rows=rows)
+    s32 = hq.sigma(B.ham, B.sub, B.la, B.lb, ct).double()
+    for prec, rel in ((hq.PREC_FP32_BF16AB, 2e-2), (hq.PREC_FP32_BF16X3AB, 2e-4)):
+        s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=prec).double()
+        sr = s.cpu().numpy()[rows]
+        assert np.all(np.abs(sr - ref) <= _sigma_tol(rel, hd, c[rows], ref)), prec
+        # and against the FP32 CUDA-core product everywhere (a property at full size)
+        assert float(torch.max(torch.abs(s - s32))) <= rel * float(torch.max(torch.abs(s32)))
+
+
 def test_sigma_full_size_sampled_rows(precision_workload):
     """The bench configuration (n=16, 5/5, 2000 x 2000): 512 sampled rows."""
     B = precision_workload
@@ -282,6 +313,20 @@ def test_davidson_full_size_properties(precision_workload):
         assert abs(np.linalg.norm(c) - 1.0) < 1e-12
         Hc = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
         assert np.max(np.abs(Hc - res.energy * c[rows])) <= 1e-8
+
+
+@pytest.mark.parametrize("inner", ["bf16", "bf16x3"])
+def test_davidson_mixed_tensor_core_inner(inner):
+    """Mixed Davidson whose inner products use the tensor-core term: the FP64
+    refinement still reaches the FP64 energy."""
+    B = built("hf_12_4_4")
+    E, c0 = ground_state(B)
+    p = hq.PREC_FP32_BF16AB if inner == "bf16" else hq.PREC_FP32_BF16X3AB
+    res = hq.davidson(B.ham, B.sub, B.la, B.lb, precision=hq.DAVIDSON_MIXED, inner_precision=p,
+                      tol_residual=1e-8, max_subspace=12, max_iter=400)
+    assert res.status == hq.OK
+    assert abs(res.energy - E) <= 1e-6
+    assert res.residual <= 1e-8
 
 
 def test_davidson_warm_start_and_not_converged():
