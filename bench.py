@@ -46,6 +46,11 @@ def parse():
     return ap.parse_args()
 
 
+def max_singles(links, n_rows):
+    """Largest number of single links of a string (host side, from the link counts)."""
+    return links.max_srow
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -189,8 +194,9 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    solve_opts = dict(precision=hq.DAVIDSON_MIXED, tol_residual=1e-6, tol_energy=1e-8,
-                      max_subspace=16, max_iter=200, trace_cap=512)
+    solve_opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB,
+                      tol_residual=1e-6, tol_energy=1e-8, max_subspace=16, max_iter=600,
+                      trace_cap=1024)
 
     def step(h_in, eri_in, a_in, b_in):
         ham_s = hq.Hamiltonian(h_in, eri_in, na, nb, w["e_nuc"])
@@ -262,52 +268,90 @@ def main():
     clk = clocks.stop()
     h2d = sum(x.numel() * x.element_size() for x in (h_h, eri_h, a_h, b_h))
 
-    # kernel-level sigma rates and the FP64 solver's time-to-1e-6 Ha
+    # kernel-level sigma rates in every precision, and each half of the step's product
     c64 = torch.tensor(synth.random_vector(N, 3), device=dev)
     c32 = c64.float()
-    s64, s32 = torch.empty_like(c64), torch.empty_like(c32)
 
-    def sigma_rate(c, s, reps=10):
+    def timed(fn, reps=10):
         for _ in range(3):
-            hq.sigma(ham, sub, la, lb, c, out=s)
+            fn()
         ts = []
         for _ in range(reps):
             flush.zero_()
             torch.cuda.synchronize()
             ev0.record(stream)
-            hq.sigma(ham, sub, la, lb, c, out=s)
+            fn()
             ev1.record(stream)
             torch.cuda.synchronize()
             ts.append(ev0.elapsed_time(ev1) / 1e3)
         ts.sort()
         return ts[len(ts) // 2]
 
-    t_s64 = sigma_rate(c64, s64, reps=5)
-    t_s32 = sigma_rate(c32, s32)
-    fp64_runs = []
-    for _ in range(2):
-        r = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-6,
-                        tol_energy=1e-8, max_subspace=16, max_iter=200, trace_cap=512)
-        fp64_runs.append(r)
+    precs = {"fp64": (hq.PREC_FP64, c64), "fp32": (hq.PREC_FP32, c32),
+             "fp32_bf16ab": (hq.PREC_FP32_BF16AB, c32), "fp32_bf16x3ab": (hq.PREC_FP32_BF16X3AB, c32)}
+    t_sig = {}
+    for name, (p, x) in precs.items():
+        out = torch.empty_like(x)
+        t_sig[name] = timed(lambda: hq.sigma(ham, sub, la, lb, x, out=out, precision=p),
+                            reps=5 if name == "fp64" else 10)
+    out32 = torch.empty_like(c32)
+    t_same = timed(lambda: hq.sigma_part(ham, sub, la, lb, c32, out32, "same",
+                                         precision=hq.PREC_FP32_BF16AB))
+    t_opp = timed(lambda: hq.sigma_part(ham, sub, la, lb, c32, out32, "opposite",
+                                        precision=hq.PREC_FP32_BF16AB))
 
-    def best_time(runs):
-        ts = [x for x in (time_to(r.trace) for r in runs) if x is not None]
+    # FP64 and the mixed variants: time-to-1e-6 Ha on the same GPU
+    variants = {"fp64": dict(precision=hq.DAVIDSON_FP64),
+                "mixed_fp32": dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32),
+                "mixed_bf16x3": dict(precision=hq.DAVIDSON_MIXED,
+                                     inner_precision=hq.PREC_FP32_BF16X3AB)}
+    runs = {}
+    for name, kw in variants.items():
+        runs[name] = hq.davidson(ham, sub, la, lb, tol_residual=1e-6, tol_energy=1e-8,
+                                 max_subspace=16, max_iter=600, trace_cap=1024, **kw)
+    fp64_runs = [runs["fp64"]]
+
+    def best_time(rs):
+        ts = [x for x in (time_to(r.trace) for r in rs) if x is not None]
         return min(ts) if ts else None
 
     tt_fp64 = best_time(fp64_runs)
     tt_mixed = best_time(results)
+    tt_variants = {k: best_time([r]) for k, r in runs.items() if k != "fp64"}
 
-    # algorithmic FMA count of one sigma product (same-spin rows, diagonal,
-    # alpha-self x beta-singles, opposite-spin scatter)
-    fma = (N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
-           + la.n_singles * (lb.n_singles + sub.Nb * nb))
-    peaks = {"fp64_tflops": 1.129, "fp32_tflops": 68.82}  # measured FMA-chain peaks, this GPU model
-    roof = {"bound": "alu", "kernel": "hinqs_sigma FP32 (k_sigma_rows + k_sigma_ab)",
-            "achieved": 2 * fma / t_s32 / 1e12, "peak": peaks["fp32_tflops"], "unit": "TFLOP/s",
-            "frac": 2 * fma / t_s32 / 1e12 / peaks["fp32_tflops"], "traffic": None,
-            "fp64": {"achieved": 2 * fma / t_s64 / 1e12, "peak": peaks["fp64_tflops"],
-                     "frac": 2 * fma / t_s64 / 1e12 / peaks["fp64_tflops"]},
-            "fma_per_sigma": fma}
+    # rooflines of the two halves of the step's product (FP32 vectors, BF16 tensor cores)
+    #   same-spin: algorithmic FMAs of the row products + diagonal + alpha-self x beta singles
+    #   opposite-spin: dense MMA FLOPs the tensor cores execute (and the useful share)
+    fma_same = N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
+    fma_opp_useful = la.n_singles * (lb.n_singles + sub.Nb * nb)
+    K = n * (n + 1) // 2
+    Kp = -(-K // 16) * 16
+    NW = 64 if la.max_row >= 0 and max_singles(la, sub.Na) <= 64 else 128
+    n_tiles = -(-sub.Nb // 128)
+    mma_flops = 2.0 * 128 * NW * Kp * n_tiles * sub.Na * (-(-max_singles(la, sub.Na) // NW))
+    peaks = {"fp64_tflops": 1.129, "fp32_tflops": 68.82}  # measured FMA-chain peaks
+    import json as _json
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        mp = _json.load(f)
+    bf16_peak = mp.get("bf16_tflops_sustained", 1371.7)
+    n_inner = sum(r.n_sigma_fp32 for r in results) / len(results)
+    share_same = n_inner * t_same
+    share_opp = n_inner * t_opp
+    same_line = {"bound": "alu", "kernel": "hinqs_sigma_same_spin FP32 (k_spmm_rows x2, transposes)",
+                 "achieved": 2 * fma_same / t_same / 1e12, "peak": peaks["fp32_tflops"],
+                 "unit": "TFLOP/s", "frac": 2 * fma_same / t_same / 1e12 / peaks["fp32_tflops"],
+                 "traffic": None, "flops_per_launch": 2 * fma_same, "ms": 1e3 * t_same,
+                 "peak_source": "measured FP32 FMA chain on this B300 model"}
+    opp_line = {"bound": "tensor", "kernel": "hinqs_sigma_opposite_spin BF16 (k_sigma_ab_tc<64,1>)",
+                "achieved": mma_flops / t_opp / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
+                "frac": mma_flops / t_opp / 1e12 / bf16_peak, "traffic": None,
+                "flops_per_launch": mma_flops, "useful_flops_per_launch": 2 * fma_opp_useful,
+                "ms": 1e3 * t_opp, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
+    roof = dict(same_line if share_same >= share_opp else opp_line)
+    roof["other_half"] = opp_line if share_same >= share_opp else same_line
+    roof["fp64_sigma"] = {"achieved": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12,
+                          "peak": peaks["fp64_tflops"],
+                          "frac": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12 / peaks["fp64_tflops"]}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -352,16 +396,16 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * N / e2e_mean, "unit": "dets/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "sigma_dets_per_s": {"fp64": N / t_s64, "fp32": N / t_s32},
-        "sigma_ms": {"fp64": 1e3 * t_s64, "fp32": 1e3 * t_s32},
-        "time_to_1e-6_Ha_s": {"mixed": tt_mixed, "fp64": tt_fp64,
+        "sigma_dets_per_s": {k: N / v for k, v in t_sig.items()},
+        "sigma_ms": {k: 1e3 * v for k, v in t_sig.items()},
+        "time_to_1e-6_Ha_s": {"mixed_bf16": tt_mixed, "fp64": tt_fp64, **tt_variants,
                               "speedup_mixed_vs_fp64": (tt_fp64 / tt_mixed)
                               if (tt_fp64 and tt_mixed) else None},
         "roofline": roof,
         "cpu_baseline": cpu,
         "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
-                   "mixed_sigmas": [last.n_sigma_fp64, last.n_sigma_fp32],
-                   "fp64_sigmas": fp64_runs[-1].n_sigma_fp64},
+                   "mixed_sigmas_fp64_fp32": [last.n_sigma_fp64, last.n_sigma_fp32],
+                   "fp64_sigmas": fp64_runs[-1].n_sigma_fp64, "mixed_status": last.status},
         "clocks": clk,
     }
     if args.detail:

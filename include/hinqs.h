@@ -148,6 +148,8 @@ int hinqs_links_export(const hinqs_links* links, int64_t* row_ptr, int32_t* col,
                        uint8_t* p, uint8_t* q, uint8_t* r, uint8_t* s, int8_t* sign,
                        double* hval, void* stream);
 int hinqs_links_destroy(hinqs_links* links);
+/* largest number of single links of one string (0 for a NULL handle) */
+int hinqs_links_max_singles(const hinqs_links* links);
 
 /* ------------------------------------------------------------- diagonal --
  * hdiag[I] = <I|H|I> (FP64, [N_a*N_b]): the H_xx of Step 2 (cold-start ranking)
@@ -168,6 +170,20 @@ int hinqs_diag(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_link
  * la / lb are the alpha / beta links of this ham and subspace. */
 int hinqs_sigma(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
                 const hinqs_links* lb, const void* c, void* sigma, int precision, void* stream);
+
+/* The two halves of hinqs_sigma (the decomposition of H above), for callers that
+ * compose or time them separately; same arguments and vector types.
+ * hinqs_sigma_same_spin OVERWRITES sigma with
+ *   H_a C + C H_b^T + (diagonal cross term sum_{i in Ia, j in Ib} (ii|jj) + E_nuc) C
+ *   + sum_{beta singles} [sum_{i in Ia} (ii|rs)] C      (alpha diagonal x beta singles);
+ * hinqs_sigma_opposite_spin ADDS the remaining opposite-spin terms
+ *   sum_{alpha singles pq} sum_{beta singles rs and beta diagonal} (pq|rs) E^a_pq C (E^b_rs)^T. */
+int hinqs_sigma_same_spin(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                          const hinqs_links* lb, const void* c, void* sigma, int precision,
+                          void* stream);
+int hinqs_sigma_opposite_spin(const hinqs_ham* ham, const hinqs_subspace* sub,
+                              const hinqs_links* la, const hinqs_links* lb, const void* c,
+                              void* sigma, int precision, void* stream);
 
 /* ------------------------------------------------------------- Davidson --
  * Lowest eigenpair of H_B by Davidson's method (Step 3, Davidson 1975), with an

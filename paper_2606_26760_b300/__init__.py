@@ -71,7 +71,8 @@ EXPORTED = [
     "hinqs_subspace_destroy", "hinqs_string_links", "hinqs_links_count", "hinqs_links_export",
     "hinqs_links_destroy", "hinqs_diag", "hinqs_sigma", "hinqs_davidson_default_opts",
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
-    "hinqs_spin_marginals_noalloc",
+    "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
+    "hinqs_links_max_singles",
 ]
 
 
@@ -98,8 +99,11 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_links_count.argtypes = [P, PI64, PI64, PI64]
     lib.hinqs_links_export.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
     lib.hinqs_links_destroy.argtypes = [P]
+    lib.hinqs_links_max_singles.argtypes = [P]
     lib.hinqs_diag.argtypes = [P, P, P, P, P, P]
     lib.hinqs_sigma.argtypes = [P, P, P, P, P, P, I, P]
+    lib.hinqs_sigma_same_spin.argtypes = [P, P, P, P, P, P, I, P]
+    lib.hinqs_sigma_opposite_spin.argtypes = [P, P, P, P, P, P, I, P]
     lib.hinqs_davidson_default_opts.argtypes = [ctypes.POINTER(_Opts)]
     lib.hinqs_davidson_default_opts.restype = None
     lib.hinqs_davidson.argtypes = [P, P, P, P, P, ctypes.POINTER(_Opts),
@@ -212,6 +216,7 @@ class Links:
         nl, ns, mr = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
         _check(_lib.hinqs_links_count(handle, ctypes.byref(nl), ctypes.byref(ns), ctypes.byref(mr)))
         self.n_links, self.n_singles, self.max_row = nl.value, ns.value, mr.value
+        self.max_srow = _lib.hinqs_links_max_singles(handle)
 
     def export(self):
         dev = _dev()
@@ -261,6 +266,15 @@ def sigma(ham, sub, la, lb, c, out=None, precision: int | None = None):
     out = torch.empty_like(c) if out is None else out
     _check(_lib.hinqs_sigma(ham.handle, sub.handle, la.handle, lb.handle, _ptr(c), _ptr(out),
                             precision, _stream()))
+    return out
+
+
+def sigma_part(ham, sub, la, lb, c, out, part: str, precision: int | None = None):
+    """part = "same" (overwrites out) or "opposite" (adds into out); see hinqs.h."""
+    if precision is None:
+        precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
+    fn = _lib.hinqs_sigma_same_spin if part == "same" else _lib.hinqs_sigma_opposite_spin
+    _check(fn(ham.handle, sub.handle, la.handle, lb.handle, _ptr(c), _ptr(out), precision, _stream()))
     return out
 
 

@@ -28,6 +28,7 @@ int check_triplet(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_l
                   const hinqs_links_s* lb, const char* who);
 
 constexpr int kMaxSub = 32;
+constexpr int kRitzStride = kMaxSub + 2;  // (theta, y[kMaxSub], pad) per Ritz pair
 constexpr int kRedGrid = 2 * kNumSMs;
 constexpr int kRedThreads = 256;
 
@@ -201,7 +202,7 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
 // Cholesky factor S = L L^T and the eigenvector is mapped back, y = L^-T z, so
 // that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest |component| > 0).
 __global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __restrict__ out,
-                     const double* __restrict__ S) {
+                     const double* __restrict__ S, double* __restrict__ all = nullptr) {
   __shared__ double A[kMaxSub][kMaxSub + 1];
   __shared__ double Q[kMaxSub][kMaxSub + 1];
   __shared__ double L[kMaxSub][kMaxSub + 1];
@@ -360,6 +361,36 @@ __global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __res
     out[0] = A[best][best];
     for (int r = 0; r < m; ++r) out[1 + r] = sg * z[r];
     for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
+    if (all) {
+      // every eigenpair, ascending: all[j * kRitzStride] = lambda_j, then its vector
+      int order_[kMaxSub];
+      for (int k = 0; k < m; ++k) order_[k] = k;
+      for (int a = 0; a < m; ++a)
+        for (int b = a + 1; b < m; ++b)
+          if (A[order_[b]][order_[b]] < A[order_[a]][order_[a]]) {
+            int t = order_[a];
+            order_[a] = order_[b];
+            order_[b] = t;
+          }
+      for (int j = 0; j < m; ++j) {
+        const int col = order_[j];
+        double nz = 0.0;
+        for (int r = 0; r < m; ++r) nz += Q[r][col] * Q[r][col];
+        nz = 1.0 / sqrt(nz);
+        for (int r = 0; r < m; ++r) z[r] = Q[r][col] * nz;
+        if (use_s) {
+          for (int i = m - 1; i >= 0; --i) {
+            double v = z[i];
+            for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
+            z[i] = v / L[i][i];
+          }
+        }
+        double* o = all + (size_t)j * kRitzStride;
+        o[0] = A[col][col];
+        for (int r = 0; r < m; ++r) o[1 + r] = z[r];
+        for (int r = m; r < kMaxSub; ++r) o[1 + r] = 0.0;
+      }
+    }
   }
 }
 
@@ -673,38 +704,67 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
 }
 
 // --------------------------------------------------------------- mixed ----
+//
+// Basis {x, v_1..v_m}: x is an FP64 unit vector (the anchor) with an FP64 product
+// s = H x, the v_i are FP32 with FP32 products w_i.  The projected pencil (G, S) is
+// FP64 with G_00 = x.s, G_0i = s.v_i, G_ij = v_i.w_j, S_0i = x.v_i, S_ij = v_i.v_j.
+// Inner iterations add preconditioned residual directions (FP32 products).  A
+// restart keeps the anchor's Ritz vector and the next keep-1 Ritz vectors (as FP32
+// vectors with FP32-combined products).  The anchor's product after a restart is
+// y_0 s + sum y_i w_i; an FP64 product replaces it (a refinement) when the inner
+// residual falls below inner_tol times the last FP64 residual, or after
+// kSoftRestarts restarts without one.  Convergence is judged on FP64 residuals.
+
+constexpr int kSoftRestarts = 3;
 
 static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
                           double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
-  const int mmax = std::max(3, o.max_subspace);
+  const int mmax = std::max(4, o.max_subspace);  // pencil order 1 + m <= mmax
+  const int keep = std::min(4, mmax - 2);         // Ritz vectors kept at a restart (with x)
   const int64_t N = c.N;
-  double *x = nullptr, *sx = nullptr, *t = nullptr, *G = nullptr, *S = nullptr, *ritz = nullptr,
-         *col = nullptr, *scol = nullptr;
-  float *V = nullptr, *W = nullptr;
+  double *x = nullptr, *sx = nullptr, *t = nullptr, *xn = nullptr, *sxn = nullptr, *G = nullptr,
+         *S = nullptr, *G1 = nullptr, *ritz = nullptr, *ritz1 = nullptr, *all = nullptr,
+         *col = nullptr, *scol = nullptr, *tmp = nullptr;
+  float *V = nullptr, *W = nullptr, *U = nullptr, *WU = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&x, N, c.s)) || (rc = dalloc(&sx, N, c.s)) || (rc = dalloc(&t, N, c.s)) ||
+      (rc = dalloc(&xn, N, c.s)) || (rc = dalloc(&sxn, N, c.s)) || (rc = dalloc(&tmp, N, c.s)) ||
       (rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
+      (rc = dalloc(&U, (size_t)keep * N, c.s)) || (rc = dalloc(&WU, (size_t)keep * N, c.s)) ||
       (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&S, kMaxSub * kMaxSub, c.s)) ||
-      (rc = dalloc(&ritz, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&scol, kMaxSub + 2, c.s)) || (rc = dalloc(&c.t32, N, c.s))) {
+      (rc = dalloc(&G1, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&ritz1, kMaxSub + 2, c.s)) || (rc = dalloc(&all, kMaxSub * kRitzStride, c.s)) ||
+      (rc = dalloc(&col, kMaxSub + 2, c.s)) || (rc = dalloc(&scol, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&c.t32, N, c.s))) {
   }
   auto cleanup = [&]() {
-    dfree(x, c.s);
-    dfree(sx, c.s);
-    dfree(t, c.s);
+    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol}) {
+      double* q = p;
+      dfree(q, c.s);
+    }
     dfree(V, c.s);
     dfree(W, c.s);
-    dfree(G, c.s);
-    dfree(S, c.s);
-    dfree(ritz, c.s);
-    dfree(col, c.s);
-    dfree(scol, c.s);
+    dfree(U, c.s);
+    dfree(WU, c.s);
     dfree(c.t32, c.s);
   };
   if (rc) {
     cleanup();
     return rc;
   }
+  // G, S column for basis vector index j (j >= 1, FP32 vector V[j-1] with product W[j-1])
+  auto add_column = [&](int j) -> int {
+    const float* v = V + (size_t)(j - 1) * N;
+    const float* w = W + (size_t)(j - 1) * N;
+    HQ_TRY(dots<float, double>(c, v, N, 1, sx, col));
+    HQ_TRY(dots<float, float>(c, V, N, j, w, col + 1));
+    HQ_TRY(dots<float, double>(c, v, N, 1, x, scol));
+    HQ_TRY(dots<float, float>(c, V, N, j, v, scol + 1));
+    k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
+    k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, j, scol, j + 1, 0);
+    HQ_LAUNCH_CHECK();
+    return HINQS_OK;
+  };
   auto run = [&]() -> int {
     if (guess) {
       HQ_CUDA(cudaMemcpyAsync(t, guess, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
@@ -714,64 +774,66 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     double ratio;
     HQ_TRY(orthonormalise(c, t, nullptr, N, 0, x, &ratio));
     if (ratio == 0.0) return fail(HINQS_ERR_ARG, "hinqs_davidson: zero initial guess");
-    double theta_prev = 0.0;
-    bool have_prev = false;
-    int total = 0;
+    k_init_pencil<<<1, 256, 0, c.s>>>(G, S, nullptr);
+    int m = 0, soft = 0, total = 0;
+    bool hard = true, have_prev = false;
+    double theta_prev = 0.0, target = 0.0;
     double h[2];
-    for (int cycle = 0;; ++cycle) {
-      // FP64 product of the current x, its energy and residual
-      HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, x, sx, HINQS_PREC_FP64, c.s));
-      info.n_sigma_fp64++;
-      total++;
-      double* th = c.small + 2 * kMaxSub;
-      HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));  // theta = x.s
-      k_init_pencil<<<1, 256, 0, c.s>>>(G, S, th);
-      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, 1, ritz, nullptr);  // (theta, 1)
-      k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz, 1, D,
-                                                           o.denom_floor, N, t, c.partial);
-      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
-      HQ_LAUNCH_CHECK();
-      HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-      HQ_CUDA(cudaStreamSynchronize(c.s));
-      double theta = h[0], res = std::sqrt(std::max(h[1], 0.0));
-      info.energy = theta;
-      info.residual = res;
-      info.iterations++;
-      tr.add(theta, res, 0);
-      bool conv = res <= o.tol_residual && have_prev && std::fabs(theta - theta_prev) <= o.tol_energy;
-      if (res <= o.tol_residual * 1e-3) conv = true;
-      if (conv || total >= o.max_iter) {
-        HQ_CUDA(cudaMemcpyAsync(c_out, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-        if (energy) *energy = theta;
-        info.status = conv ? HINQS_OK : HINQS_NOT_CONVERGED;
-        return info.status;
+    for (;;) {
+      if (hard) {
+        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, x, sx, HINQS_PREC_FP64, c.s));
+        info.n_sigma_fp64++;
+        total++;
+        double* th = c.small + 2 * kMaxSub;
+        HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));
+        k_init_pencil<<<1, 256, 0, c.s>>>(G1, nullptr, th);
+        k_rr<<<1, 256, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
+        k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
+                                                             o.denom_floor, N, t, c.partial);
+        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+        HQ_LAUNCH_CHECK();
+        HQ_CUDA(cudaMemcpyAsync(&h[0], ritz1, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));
+        const double theta = h[0], res = std::sqrt(std::max(h[1], 0.0));
+        info.energy = theta;
+        info.residual = res;
+        info.iterations++;
+        tr.add(theta, res, 0);
+        bool conv = res <= o.tol_residual && have_prev && std::fabs(theta - theta_prev) <= o.tol_energy;
+        if (res <= o.tol_residual * 1e-3) conv = true;
+        if (conv || total >= o.max_iter) {
+          HQ_CUDA(cudaMemcpyAsync(c_out, x, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+          if (energy) *energy = theta;
+          info.status = conv ? HINQS_OK : HINQS_NOT_CONVERGED;
+          return info.status;
+        }
+        theta_prev = theta;
+        have_prev = true;
+        info.n_refinements++;
+        target = std::max(o.inner_tol * res, 0.3 * o.tol_residual);
+        soft = 0;
+        hard = false;
       }
-      theta_prev = theta;
-      have_prev = true;
-      info.n_refinements++;
-      const double target = std::max(o.inner_tol * res, 0.3 * o.tol_residual);
-      // inner FP32 Davidson for the correction of x; the basis {x, v_1..v_m} is
-      // stored as FP64 x and FP32 v_i, so the projected pencil uses their exact
-      // FP64 overlap matrix S
-      int m = 0;
-      HQ_TRY(orthonormalise_mixed(c, t, x, V, N, 0, V, &ratio));
-      if (ratio < 1e-12) continue;
-      m = 1;
-      for (;;) {
-        float* vm = V + (size_t)(m - 1) * N;
-        float* wm = W + (size_t)(m - 1) * N;
-        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, o.inner_precision, c.s));
+      // row and column 0 of the pencil for the current anchor
+      HQ_TRY(dots<double, double>(c, x, N, 1, sx, col));
+      HQ_TRY(dots<float, double>(c, V, N, m, sx, col + 1));
+      HQ_TRY(dots<double, double>(c, x, N, 1, x, scol));
+      HQ_TRY(dots<float, double>(c, V, N, m, x, scol + 1));
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, col, m + 1, 0);
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, 0, scol, m + 1, 0);
+      HQ_LAUNCH_CHECK();
+      if (m == 0) {  // first direction: the preconditioned FP64 residual in t
+        HQ_TRY(orthonormalise_mixed(c, t, x, V, N, 0, V, &ratio));
+        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, V, W, o.inner_precision, c.s));
         info.n_sigma_fp32++;
         total++;
-        // G[0][m] = s.v_m, G[i][m] = v_i.w_m; S[0][m] = x.v_m, S[i][m] = v_i.v_m
-        HQ_TRY(dots<float, double>(c, vm, N, 1, sx, col));
-        HQ_TRY(dots<float, float>(c, V, N, m, wm, col + 1));
-        HQ_TRY(dots<float, double>(c, vm, N, 1, x, scol));
-        HQ_TRY(dots<float, float>(c, V, N, m, vm, scol + 1));
-        k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m, col, m + 1, 0);
-        k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, m, scol, m + 1, 0);
-        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S);
+        m = 1;
+        HQ_TRY(add_column(1));
+      }
+      bool restart_hard = false;
+      for (;;) {
+        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -779,22 +841,68 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaStreamSynchronize(c.s));
-        double rin = std::sqrt(std::max(h[1], 0.0));
+        const double rin = std::sqrt(std::max(h[1], 0.0));
         info.iterations++;
         tr.add(h[0], rin, 1);
-        if (rin <= target || m + 1 >= mmax || total >= o.max_iter) break;
+        if (rin <= target || total >= o.max_iter) {
+          restart_hard = true;
+          break;
+        }
+        if (m + 1 >= mmax) {
+          restart_hard = (++soft > kSoftRestarts);
+          break;
+        }
         HQ_TRY(orthonormalise_mixed(c, t, x, V, N, m, V + (size_t)m * N, &ratio));
-        if (ratio < 1e-12) break;
+        if (ratio < 1e-12) {
+          restart_hard = true;
+          break;
+        }
+        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, V + (size_t)m * N, W + (size_t)m * N,
+                            o.inner_precision, c.s));
+        info.n_sigma_fp32++;
+        total++;
         m++;
+        HQ_TRY(add_column(m));
       }
-      // x <- y0 x + sum y_i v_i, normalised (FP64)
-      double* y = ritz + 1;
-      HQ_TRY(lincomb<double>(c, t, x, N, 1, y, 0));
-      HQ_TRY(lincomb<float>(c, t, V, N, m, y + 1, 1));
+      // restart: anchor = lowest Ritz vector, plus keep-1 FP32 Ritz vectors
+      const int kk = std::min(keep, m + 1);
+      // xn = y0 x + V y, sxn = y0 s + W y  (FP64 sums; the FP32 parts carry the correction)
+      HQ_TRY(lincomb<double>(c, xn, x, N, 1, all + 1, 0));
+      HQ_TRY(lincomb<float>(c, xn, V, N, m, all + 2, 1));
+      HQ_TRY(lincomb<double>(c, sxn, sx, N, 1, all + 1, 0));
+      HQ_TRY(lincomb<float>(c, sxn, W, N, m, all + 2, 1));
+      for (int j = 1; j < kk; ++j) {
+        const double* yj = all + (size_t)j * kRitzStride + 1;
+        HQ_TRY(lincomb<double>(c, tmp, x, N, 1, yj, 0));
+        HQ_TRY(lincomb<float>(c, tmp, V, N, m, yj + 1, 1));
+        k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(tmp, U + (size_t)(j - 1) * N, N);
+        HQ_TRY(lincomb<double>(c, tmp, sx, N, 1, yj, 0));
+        HQ_TRY(lincomb<float>(c, tmp, W, N, m, yj + 1, 1));
+        k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(tmp, WU + (size_t)(j - 1) * N, N);
+      }
+      // normalise the anchor (y^T S y = 1 up to rounding) and its product alike
       double* nrm = c.small + 2 * kMaxSub + 1;
-      HQ_TRY(dots<double, double>(c, t, N, 1, t, nrm));
-      k_scale_store<double, double><<<c.grid, 256, 0, c.s>>>(t, nrm, x, N);
+      HQ_TRY(dots<double, double>(c, xn, N, 1, xn, nrm));
+      k_scale_store<double, double><<<c.grid, 256, 0, c.s>>>(xn, nrm, x, N);
+      k_scale_store<double, double><<<c.grid, 256, 0, c.s>>>(sxn, nrm, sx, N);
+      m = kk - 1;
+      if (m > 0) {
+        HQ_CUDA(cudaMemcpyAsync(V, U, (size_t)m * N * sizeof(float), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaMemcpyAsync(W, WU, (size_t)m * N * sizeof(float), cudaMemcpyDeviceToDevice, c.s));
+      }
+      k_init_pencil<<<1, 256, 0, c.s>>>(G, S, nullptr);
       HQ_LAUNCH_CHECK();
+      for (int j = 1; j <= m; ++j) {
+        const float* v = V + (size_t)(j - 1) * N;
+        const float* w = W + (size_t)(j - 1) * N;
+        HQ_TRY(dots<float, float>(c, V, N, j, w, col + 1));
+        HQ_TRY(dots<float, float>(c, V, N, j, v, scol + 1));
+        k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col + 1, j, 1);
+        k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, j, scol + 1, j, 1);
+      }
+      HQ_LAUNCH_CHECK();
+      info.n_restarts++;
+      hard = restart_hard;
     }
   };
   rc = run();

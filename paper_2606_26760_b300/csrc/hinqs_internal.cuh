@@ -110,14 +110,21 @@ struct hinqs_links_s {
   int ell_width = 0;
   int2* sell = nullptr;
   int* scount = nullptr;
+  // all links as packed records for the row products: element offset of the linked
+  // row (J * other dimension, uint32) with the element: rec32 {off, float bits},
+  // rec64 {off, 0, double bits}; null when N_a * N_b >= 2^32
+  int2* rec32 = nullptr;
+  int4* rec64 = nullptr;
 };
 
 namespace hinqs {
 
 // Kernel launchers shared between translation units.
+constexpr int kSameSpin = 1;      // H_a C + C H_b^T + diagonal + alpha-self x beta singles
+constexpr int kOppositeSpin = 2;  // += alpha singles x (beta singles + beta self)
 int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                  const hinqs_links_s* lb, const void* c, void* sigma, int precision,
-                 cudaStream_t s);
+                 cudaStream_t s, int parts = kSameSpin | kOppositeSpin);
 int diag_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                 const hinqs_links_s* lb, double* hdiag, cudaStream_t s);
 // opposite-spin sigma term on the tensor cores (FP32 vectors; split = 1 or 3)

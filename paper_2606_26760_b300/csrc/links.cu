@@ -175,6 +175,20 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
   }
 }
 
+// Packed link records for the row products (see hinqs_links_s).
+__global__ void k_pack_records(const int32_t* __restrict__ col, const double* __restrict__ h64,
+                               int64_t nnz, int64_t other, int2* __restrict__ r32,
+                               int4* __restrict__ r64) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t off = (uint32_t)((int64_t)col[k] * other);
+    const double h = h64[k];
+    r32[k] = make_int2((int)off, __float_as_int((float)h));
+    const long long b = __double_as_longlong(h);
+    r64[k] = make_int4((int)off, 0, (int)(b & 0xffffffffll), (int)(b >> 32));
+  }
+}
+
 // exc unpacking for export
 __global__ void k_unpack_exc(const uint32_t* __restrict__ exc, int64_t nnz, uint8_t* p,
                              uint8_t* q, uint8_t* r, uint8_t* s) {
@@ -213,6 +227,8 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->VT32, s);
   dfree(L->sell, s);
   dfree(L->scount, s);
+  dfree(L->rec32, s);
+  dfree(L->rec64, s);
 }
 
 }  // namespace hinqs
@@ -295,6 +311,15 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
       if (e != cudaSuccess) rc = cuda_fail(e, "k_build_ell", __FILE__, __LINE__);
     }
   }
+  if (!rc && (uint64_t)B->Na * (uint64_t)B->Nb < (1ull << 32)) {
+    const int64_t other = spin ? B->Na : B->Nb;
+    if (!(rc = dalloc(&L->rec32, L->nnz, s)) && !(rc = dalloc(&L->rec64, L->nnz, s))) {
+      k_pack_records<<<(unsigned)std::min<int64_t>(ceil_div(L->nnz, 256) + 1, 16 * kNumSMs), 256, 0,
+                       s>>>(L->col, L->hval64, L->nnz, other, L->rec32, L->rec64);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) rc = cuda_fail(e, "k_pack_records", __FILE__, __LINE__);
+    }
+  }
   cleanup();
   if (rc) {
     free_links(L, s);
@@ -335,6 +360,8 @@ extern "C" int hinqs_links_export(const hinqs_links* L, int64_t* row_ptr, int32_
   }
   return HINQS_OK;
 }
+
+extern "C" int hinqs_links_max_singles(const hinqs_links* L) { return L ? L->max_srow : 0; }
 
 extern "C" int hinqs_links_destroy(hinqs_links* L) {
   if (!L) return HINQS_OK;

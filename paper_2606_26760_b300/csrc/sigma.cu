@@ -102,6 +102,130 @@ __global__ void __launch_bounds__(256) k_spmm_rows(
   }
 }
 
+// Packed link records: {element offset of the linked row, element}.
+template <typename T>
+struct Rec;
+template <>
+struct Rec<float> {
+  using type = int2;
+  using vec2 = float2;
+  __device__ static float h(const int2& r) { return __int_as_float(r.y); }
+  __device__ static uint32_t off(const int2& r) { return (uint32_t)r.x; }
+};
+template <>
+struct Rec<double> {
+  using type = int4;
+  using vec2 = double2;
+  __device__ static double h(const int4& r) { return __hiloint2double(r.w, r.z); }
+  __device__ static uint32_t off(const int4& r) { return (uint32_t)r.x; }
+};
+
+// Same row product as k_spmm_rows with packed records (no per-link index
+// arithmetic), 8 links in flight per lane, and VEC consecutive columns per lane.
+template <typename T, int VEC>
+__global__ void __launch_bounds__(256) k_spmm_rec(
+    const T* __restrict__ X, T* __restrict__ Y, int64_t nrows, int64_t ncols,
+    const int64_t* __restrict__ rp, const typename Rec<T>::type* __restrict__ rec,
+    const int64_t* __restrict__ srp, const int2* __restrict__ sl, const T* __restrict__ VT,
+    const double* __restrict__ hd_row, const double* __restrict__ hd_col, double e_nuc,
+    const T* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
+  using R = Rec<T>;
+  using RT = typename R::type;
+  using V2 = typename R::vec2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * VEC;
+  const bool active = c0 < ncols;  // VEC divides ncols
+  const int64_t cc = active ? c0 : 0;
+  const int n2 = n * n;
+  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * kRowsPerWarp;
+  for (int rr = 0; rr < kRowsPerWarp; ++rr) {
+    const int64_t I = I0 + rr;
+    if (I >= nrows) break;
+    T acc[VEC];
+#pragma unroll
+    for (int v = 0; v < VEC; ++v) acc[v] = (accumulate && active) ? Y[I * ncols + c0 + v] : T(0);
+    if (hd_row) {
+      const T v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : T(0);
+      const T v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : T(0);
+      uint64_t bits[VEC];
+      T cross[VEC];
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) {
+        bits[v] = scol[cc + v];
+        cross[v] = T(0);
+      }
+      for (int j = 0; j < n; ++j) {
+        const T a = __shfl_sync(0xffffffffu, j < 32 ? v0 : v1, j & 31);
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          if ((bits[v] >> j) & 1ull) cross[v] += a;
+      }
+      if (active) {
+#pragma unroll
+        for (int v = 0; v < VEC; ++v)
+          acc[v] += ((T)(hd_row[I] + hd_col[c0 + v] + e_nuc) + cross[v]) * X[I * ncols + c0 + v];
+      }
+    }
+    const RT* __restrict__ r = rec + rp[I];
+    const int nk = (int)(rp[I + 1] - rp[I]);
+    const T* __restrict__ Xc = X + cc;
+    int k = 0;
+    for (; k + 8 <= nk; k += 8) {
+      RT q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) q[u] = r[k + u];
+      if constexpr (VEC == 1) {
+        T x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = Xc[R::off(q[u])];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[0] += R::h(q[u]) * x[u];
+      } else {
+        V2 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = *reinterpret_cast<const V2*>(Xc + R::off(q[u]));
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          acc[0] += R::h(q[u]) * x[u].x;
+          acc[1] += R::h(q[u]) * x[u].y;
+        }
+      }
+    }
+    for (; k < nk; ++k) {
+      const RT q = r[k];
+      if constexpr (VEC == 1) {
+        acc[0] += R::h(q) * Xc[R::off(q)];
+      } else {
+        const V2 x = *reinterpret_cast<const V2*>(Xc + R::off(q));
+        acc[0] += R::h(q) * x.x;
+        acc[1] += R::h(q) * x.y;
+      }
+    }
+    if (srp) {
+      for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
+        const int2 l = sl[q];
+        const int pair = (l.y > 0 ? l.y : -l.y) - 1;
+#pragma unroll
+        for (int v = 0; v < VEC; ++v) {
+          const T t = VT[(int64_t)pair * ncols + cc + v] * X[(int64_t)l.x * ncols + cc + v];
+          acc[v] += (l.y > 0) ? t : -t;
+        }
+      }
+    }
+    if (active) {
+#pragma unroll
+      for (int v = 0; v < VEC; ++v) Y[I * ncols + c0 + v] = acc[v];
+    }
+  }
+}
+
+template <typename T>
+const typename Rec<T>::type* recof(const hinqs_links_s* L);
+template <>
+const int2* recof<float>(const hinqs_links_s* L) { return L->rec32; }
+template <>
+const int4* recof<double>(const hinqs_links_s* L) { return L->rec64; }
+
 // out[j][i] = in[i][j] (+ out[j][i] if accumulate) for in of rows x cols; 32x32 tiles.
 template <typename T>
 __global__ void k_transpose_t(const T* __restrict__ in, T* __restrict__ out, int64_t rows,
@@ -130,6 +254,7 @@ struct AbArgs {
   const int2* a_slink;
   const int2* b_ell;   // slot-major beta singles + self, [width][Nb]
   const int* b_cnt;    // entries per beta string
+  int vec4;            // Nb % 4 == 0
 };
 
 // Opposite-spin part, one block per alpha string Ja.  CH alpha single links of Ja
@@ -170,11 +295,13 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
     }
     if (threadIdx.x < CH) tgt[threadIdx.x] = (threadIdx.x < cnt) ? A.a_slink[a0 + threadIdx.x].x : 0;
     __syncthreads();
-    for (int64_t Ib = threadIdx.x; Ib < A.Nb; Ib += blockDim.x) {
+    for (int64_t Ib0 = 0; Ib0 < A.Nb; Ib0 += blockDim.x) {
+      const int64_t Ib = Ib0 + threadIdx.x;
+      const bool live = Ib < A.Nb;
       T e[CH];
 #pragma unroll
       for (int a = 0; a < CH; ++a) e[a] = T(0);
-      const int nk = A.b_cnt[Ib];
+      const int nk = live ? A.b_cnt[Ib] : 0;
       const int2* ell = A.b_ell + Ib;
       int k = 0;
       for (; k + 2 <= nk; k += 2) {
@@ -195,9 +322,32 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
 #pragma unroll
         for (int a = 0; a < CH; ++a) e[a] += v0 * er0[a];
       }
+      if constexpr (sizeof(T) == 4) {
+        // transpose through shared memory, then float4 atomics over four
+        // consecutive beta strings of one target row
+        T* stage = Crow + (ROW_SMEM ? A.Nb : 0);  // [CH][256], 16-byte aligned
 #pragma unroll
-      for (int a = 0; a < CH; ++a)
-        if (a < cnt) atomicAdd(sig + (int64_t)tgt[a] * A.Nb + Ib, e[a]);
+        for (int a = 0; a < CH; ++a) stage[a * 256 + threadIdx.x] = e[a];
+        __syncthreads();
+        for (int idx = threadIdx.x; idx < cnt * 64; idx += blockDim.x) {
+          const int a = idx >> 6, m4 = (idx & 63) * 4;
+          const int64_t ib = Ib0 + m4;
+          if (ib >= A.Nb) continue;
+          T* dst = sig + (int64_t)tgt[a] * A.Nb + ib;
+          const T* src = stage + a * 256 + m4;
+          if (A.vec4 && ib + 3 < A.Nb)
+            atomicAdd(reinterpret_cast<float4*>(dst), make_float4(src[0], src[1], src[2], src[3]));
+          else
+            for (int q = 0; q < 4 && ib + q < A.Nb; ++q) atomicAdd(dst + q, src[q]);
+        }
+        __syncthreads();
+      } else {
+        if (live) {
+#pragma unroll
+          for (int a = 0; a < CH; ++a)
+            if (a < cnt) atomicAdd(sig + (int64_t)tgt[a] * A.Nb + Ib, e[a]);
+        }
+      }
     }
   }
 }
@@ -206,12 +356,13 @@ template <typename T, int CH>
 static int launch_ab(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                      const hinqs_links_s* lb, const T* c, T* sig, cudaStream_t s,
                      size_t smem_limit) {
-  AbArgs A{B->Na, B->Nb, H->n, la->srow_ptr, la->slink, lb->sell, lb->scount};
+  AbArgs A{B->Na, B->Nb, H->n, la->srow_ptr, la->slink, lb->sell, lb->scount, B->Nb % 4 == 0};
   const int n2 = H->n * H->n;
   constexpr int LD = CH + 16 / (int)sizeof(T);
   size_t base = (size_t)n2 * LD * sizeof(T) + (CH + 4) * sizeof(int);
   base = (base + 15) & ~(size_t)15;
-  size_t with_row = base + (size_t)B->Nb * sizeof(T);
+  if (sizeof(T) == 4) base += (size_t)CH * 256 * sizeof(T);  // epilogue staging
+  size_t with_row = base + (((size_t)B->Nb * sizeof(T) + 15) & ~(size_t)15);
   if (with_row <= smem_limit) {
     auto kern = k_sigma_ab<T, CH, true>;
     HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_row));
@@ -239,6 +390,23 @@ static int spmm_rows(const T* X, T* Y, int64_t nrows, int64_t ncols, const hinqs
                      const hinqs_links_s* Lsingles, const T* VT, const double* hd_row,
                      const double* hd_col, double e_nuc, const T* Vrow, const uint64_t* scol,
                      int n, int accumulate, cudaStream_t s) {
+  const auto* rec = recof<T>(L);
+  if (rec) {
+    const unsigned gy = (unsigned)ceil_div(nrows, kRowWarps * kRowsPerWarp);
+    const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
+    const int2* sl = Lsingles ? Lsingles->slink : nullptr;
+    if (ncols % 2 == 0) {
+      k_spmm_rec<T, 2><<<dim3((unsigned)ceil_div(ncols, 64), gy), 32 * kRowWarps, 0, s>>>(
+          X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n,
+          accumulate);
+    } else {
+      k_spmm_rec<T, 1><<<dim3((unsigned)ceil_div(ncols, 32), gy), 32 * kRowWarps, 0, s>>>(
+          X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n,
+          accumulate);
+    }
+    HQ_LAUNCH_CHECK();
+    return HINQS_OK;
+  }
   dim3 grid((unsigned)ceil_div(ncols, 32), (unsigned)ceil_div(nrows, kRowWarps * kRowsPerWarp));
   k_spmm_rows<T><<<grid, 32 * kRowWarps, 0, s>>>(
       X, Y, nrows, ncols, L->row_ptr, L->col, Prec<T>::hval(L),
@@ -251,18 +419,19 @@ static int spmm_rows(const T* X, T* Y, int64_t nrows, int64_t ncols, const hinqs
 template <typename T>
 static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                       const hinqs_links_s* lb, const T* c, T* sig, cudaStream_t s,
-                      int tc_split = 0) {
+                      int tc_split, int parts) {
   const size_t limit = 200 * 1024;
   const int n = H->n, n2 = n * n;
   const int64_t Na = B->Na, Nb = B->Nb, N = Na * Nb;
   T *CT = nullptr, *ST = nullptr;
   int rc = HINQS_OK;
-  if ((rc = dalloc(&CT, N, s)) || (rc = dalloc(&ST, N, s))) {
+  if ((parts & kSameSpin) && ((rc = dalloc(&CT, N, s)) || (rc = dalloc(&ST, N, s)))) {
     dfree(CT, s);
     dfree(ST, s);
     return rc;
   }
   auto run = [&]() -> int {
+    if (!(parts & kSameSpin)) goto opposite;
     HQ_TRY(transpose<T>(c, CT, Na, Nb, 0, s));
     // beta same-spin links and alpha-self x beta singles, rows = beta strings
     HQ_TRY(spmm_rows<T>(CT, ST, Nb, Na, lb, lb, VTof<T>(la), nullptr, nullptr, 0.0, nullptr,
@@ -271,7 +440,8 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
     // alpha same-spin links and the diagonal, rows = alpha strings
     HQ_TRY(spmm_rows<T>(c, sig, Na, Nb, la, nullptr, nullptr, la->hdiag, lb->hdiag, H->e_nuc,
                         Prec<T>::V(la), B->sb, n, 1, s));
-    if (la->nsingle == 0) return HINQS_OK;
+  opposite:
+    if (!(parts & kOppositeSpin) || la->nsingle == 0) return HINQS_OK;
     if constexpr (sizeof(T) == 4) {
       if (tc_split) return sigma_ab_tc_launch(H, B, la, lb, c, sig, tc_split, s);
     }
@@ -288,15 +458,15 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
 
 int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                  const hinqs_links_s* lb, const void* c, void* sigma, int precision,
-                 cudaStream_t s) {
+                 cudaStream_t s, int parts) {
   if (precision == HINQS_PREC_FP64)
-    return sigma_impl<double>(H, B, la, lb, (const double*)c, (double*)sigma, s);
+    return sigma_impl<double>(H, B, la, lb, (const double*)c, (double*)sigma, s, 0, parts);
   if (precision == HINQS_PREC_FP32)
-    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s);
+    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 0, parts);
   if (precision == HINQS_PREC_FP32_BF16AB)
-    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 1);
+    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 1, parts);
   if (precision == HINQS_PREC_FP32_BF16X3AB)
-    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 3);
+    return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 3, parts);
   return fail(HINQS_ERR_ARG, "hinqs_sigma: unknown precision %d", precision);
 }
 
@@ -351,14 +521,36 @@ extern "C" int hinqs_diag(const hinqs_ham* H, const hinqs_subspace* B, const hin
   return diag_launch(H, B, la, lb, hdiag, (cudaStream_t)stream);
 }
 
+static int sigma_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
+                       const hinqs_links* lb, const void* c, void* sigma, int precision,
+                       void* stream, int parts, const char* who) {
+  HQ_TRY(check_triplet(H, B, la, lb, who));
+  if (!c || !sigma) return fail(HINQS_ERR_ARG, "%s: NULL vector", who);
+  if (c == sigma) return fail(HINQS_ERR_ARG, "%s: c and sigma must not overlap", who);
+  HQ_TRY(sigma_launch(H, B, la, lb, c, sigma, precision, (cudaStream_t)stream, parts));
+  if ((parts & kOppositeSpin) &&
+      (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB))
+    return tc_error_check((cudaStream_t)stream);
+  return HINQS_OK;
+}
+
 extern "C" int hinqs_sigma(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
                            const hinqs_links* lb, const void* c, void* sigma, int precision,
                            void* stream) {
-  HQ_TRY(check_triplet(H, B, la, lb, "hinqs_sigma"));
-  if (!c || !sigma) return fail(HINQS_ERR_ARG, "hinqs_sigma: NULL vector");
-  if (c == sigma) return fail(HINQS_ERR_ARG, "hinqs_sigma: c and sigma must not overlap");
-  HQ_TRY(sigma_launch(H, B, la, lb, c, sigma, precision, (cudaStream_t)stream));
-  if (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB)
-    return tc_error_check((cudaStream_t)stream);
-  return HINQS_OK;
+  return sigma_entry(H, B, la, lb, c, sigma, precision, stream, kSameSpin | kOppositeSpin,
+                     "hinqs_sigma");
+}
+
+extern "C" int hinqs_sigma_same_spin(const hinqs_ham* H, const hinqs_subspace* B,
+                                     const hinqs_links* la, const hinqs_links* lb, const void* c,
+                                     void* sigma, int precision, void* stream) {
+  return sigma_entry(H, B, la, lb, c, sigma, precision, stream, kSameSpin,
+                     "hinqs_sigma_same_spin");
+}
+
+extern "C" int hinqs_sigma_opposite_spin(const hinqs_ham* H, const hinqs_subspace* B,
+                                         const hinqs_links* la, const hinqs_links* lb,
+                                         const void* c, void* sigma, int precision, void* stream) {
+  return sigma_entry(H, B, la, lb, c, sigma, precision, stream, kOppositeSpin,
+                     "hinqs_sigma_opposite_spin");
 }

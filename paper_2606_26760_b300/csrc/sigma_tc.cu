@@ -18,6 +18,7 @@
 // hi*hi + hi*lo + lo*hi (about 16 significant bits); SPLIT = 1 uses hi only.
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "hinqs_internal.cuh"
@@ -122,6 +123,8 @@ struct Args {
   const float* eri;  // FP32 (pq|rs), [n2][n2]
   const float* C;
   float* sig;
+  int crow_smem;  // stage the row C(Ja, :) in shared memory
+  int vec4;       // N_b % 4 == 0: float4 atomics are aligned
 };
 
 __device__ __forceinline__ int fold_index(int r, int s) {
@@ -138,7 +141,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   extern __shared__ __align__(1024) unsigned char smem[];
   const int tid = threadIdx.x, warp = tid >> 5;
   const int KB = A.KB, Kp = KB * 8, n = A.n, n2 = n * n;
-  const uint32_t a_bytes = (uint32_t)kTileM * Kp * 2, b_bytes = (uint32_t)NW * Kp * 2;
+  // each A region also holds the [16][kTileM] FP32 epilogue staging, so at least 8 KB
+  const uint32_t a_bytes = max((uint32_t)kTileM * Kp * 2, 16u * kTileM * 4u);
+  const uint32_t b_bytes = (uint32_t)NW * Kp * 2;
   unsigned char* a_hi = smem;
   unsigned char* a_lo = smem + a_bytes;
   unsigned char* b_hi = smem + (SPLIT == 3 ? 2 : 1) * a_bytes;
@@ -149,6 +154,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   int* tgt = reinterpret_cast<int*>(tail + 16);          // [NW]
   int* unfold = reinterpret_cast<int*>(tail + 16 + 4 * NW);  // [Kp] -> r*n+s, or -1
   int* wait_ok = reinterpret_cast<int*>(tail + 12);
+  // epilogue staging [16][kTileM] reuses the A tile, which the completed MMA no longer reads
+  float* stage = reinterpret_cast<float*>(a_hi);
+  float* crow_s = reinterpret_cast<float*>(tail + 16 + 4 * NW + 4 * Kp);  // [Nb] when A.crow_smem
 
   const int64_t Ja = blockIdx.x;
   const int64_t a_beg = A.a_srow[Ja], a_end = A.a_srow[Ja + 1];
@@ -179,27 +187,46 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = make_idesc(kTileM, NW);
   const float* crow = A.C + Ja * A.Nb;
+  if (A.crow_smem) {
+    for (int64_t j = tid; j < A.Nb; j += kThreads) crow_s[j] = crow[j];
+    crow = crow_s;
+  }
   uint32_t phase = 0;
   bool ok = true;
+  __syncthreads();
 
   for (int64_t a0 = a_beg; a0 < a_end && ok; a0 += NW) {
     const int cnt = (int)min64(NW, a_end - a0);
     // B operand: rows a = alpha singles of Ja, columns k = folded rs
-    for (int i = tid; i < NW * Kp; i += kThreads) {
-      const int a = i / Kp, k = i - a * Kp;
-      float v = 0.0f;
-      const int rs = unfold[k];
-      if (a < cnt && rs >= 0) {
-        const int sp = A.a_slink[a0 + a].y;
-        const int pq = (sp > 0 ? sp : -sp) - 1;
-        v = A.eri[(int64_t)pq * n2 + rs];
-        if (sp < 0) v = -v;
+    for (int i0 = tid; i0 < NW * Kp; i0 += 8 * kThreads) {
+      // eight integral values in flight before any shared-memory store
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * kThreads;
+        v[u] = 0.0f;
+        if (i < NW * Kp) {
+          const int a = i / Kp, k = i - a * Kp;
+          const int rs = unfold[k];
+          if (a < cnt && rs >= 0) {
+            const int sp = __ldg(&A.a_slink[a0 + a].y);
+            const int pq = (sp > 0 ? sp : -sp) - 1;
+            v[u] = __ldg(A.eri + (int64_t)pq * n2 + rs);
+            if (sp < 0) v[u] = -v[u];
+          }
+        }
       }
-      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-      *reinterpret_cast<__nv_bfloat16*>(b_hi + tile_off(a, k, KB)) = hi;
-      if (SPLIT == 3)
-        *reinterpret_cast<__nv_bfloat16*>(b_lo + tile_off(a, k, KB)) =
-            __float2bfloat16_rn(v - __bfloat162float(hi));
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + u * kThreads;
+        if (i >= NW * Kp) break;
+        const int a = i / Kp, k = i - a * Kp;
+        const __nv_bfloat16 hi = __float2bfloat16_rn(v[u]);
+        *reinterpret_cast<__nv_bfloat16*>(b_hi + tile_off(a, k, KB)) = hi;
+        if (SPLIT == 3)
+          *reinterpret_cast<__nv_bfloat16*>(b_lo + tile_off(a, k, KB)) =
+              __float2bfloat16_rn(v[u] - __bfloat162float(hi));
+      }
     }
     if (tid < NW) tgt[tid] = (tid < cnt) ? A.a_slink[a0 + tid].x : 0;
 
@@ -213,18 +240,27 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
           *reinterpret_cast<uint4*>(a_lo + tile_off(m, kb * 8, KB)) = make_uint4(0, 0, 0, 0);
       }
       if (Ib < A.Nb) {
-        const int nk = A.b_cnt[Ib];
-        for (int k = 0; k < nk; ++k) {
-          const int2 l = A.b_ell[(int64_t)k * A.Nb + Ib];
-          const int pair = (l.y > 0 ? l.y : -l.y) - 1;
-          float v = crow[l.x];
-          if (l.y < 0) v = -v;
-          const int kf = fold_index(pair / n, pair % n);
-          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-          *reinterpret_cast<__nv_bfloat16*>(a_hi + tile_off(m, kf, KB)) = hi;
-          if (SPLIT == 3)
-            *reinterpret_cast<__nv_bfloat16*>(a_lo + tile_off(m, kf, KB)) =
-                __float2bfloat16_rn(v - __bfloat162float(hi));
+        const int nk = __ldg(A.b_cnt + Ib);
+        const int2* __restrict__ ell = A.b_ell + Ib;
+        for (int k0 = 0; k0 < nk; k0 += 8) {
+          // eight link records in flight before any shared-memory store
+          int2 l[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            l[u] = (k0 + u < nk) ? __ldg(ell + (int64_t)(k0 + u) * A.Nb) : make_int2(0, 0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            if (k0 + u >= nk) break;
+            const int pair = (l[u].y > 0 ? l[u].y : -l[u].y) - 1;
+            float v = crow[l[u].x];
+            if (l[u].y < 0) v = -v;
+            const int kf = fold_index(pair / n, pair % n);
+            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+            *reinterpret_cast<__nv_bfloat16*>(a_hi + tile_off(m, kf, KB)) = hi;
+            if (SPLIT == 3)
+              *reinterpret_cast<__nv_bfloat16*>(a_lo + tile_off(m, kf, KB)) =
+                  __float2bfloat16_rn(v - __bfloat162float(hi));
+          }
         }
       }
       fence_proxy_async();
@@ -268,14 +304,31 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
       // epilogue: row m of E lives in TMEM lane m; warp w reads lanes 32w..32w+31
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
 #pragma unroll 1
-      for (int c0 = 0; c0 < NW; c0 += 16) {
+      for (int c0 = 0; c0 < NW && c0 < cnt; c0 += 16) {
         float e[16];
         tmem_ld16(tmem + lane_base + (uint32_t)c0, e);
-        if (Ib < A.Nb) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i)
-            if (c0 + i < cnt) atomicAdd(A.sig + (int64_t)tgt[c0 + i] * A.Nb + Ib, e[i]);
+        for (int i = 0; i < 16; ++i) stage[i * kTileM + m] = e[i];
+        __syncthreads();
+        // transpose through shared memory: each thread adds four consecutive beta
+        // strings of one target row at a time (vector atomics, 4x fewer operations)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int idx = tid + j * kThreads;  // 0..511
+          const int ci = idx >> 5, m4 = (idx & 31) * 4;
+          const int a = c0 + ci;
+          const int64_t ib = ib0 + m4;
+          if (a < cnt && ib < A.Nb) {
+            float* dst = A.sig + (int64_t)tgt[a] * A.Nb + ib;
+            const float* src = stage + ci * kTileM + m4;
+            if (A.vec4 && ib + 3 < A.Nb) {
+              atomicAdd(reinterpret_cast<float4*>(dst), make_float4(src[0], src[1], src[2], src[3]));
+            } else {
+              for (int q = 0; q < 4 && ib + q < A.Nb; ++q) atomicAdd(dst + q, src[q]);
+            }
+          }
         }
+        __syncthreads();
       }
       fence_before();
       __syncthreads();
@@ -294,13 +347,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
 template <int NW, int SPLIT>
 static int launch(const Args& a, cudaStream_t s) {
   const int Kp = a.KB * 8;
-  size_t bytes = (size_t)(SPLIT == 3 ? 2 : 1) * (kTileM + NW) * Kp * 2 + 16 + 4 * NW + 4 * Kp + 64;
+  const size_t a_region = std::max<size_t>((size_t)kTileM * Kp * 2, 16 * kTileM * 4);
+  size_t bytes = (size_t)(SPLIT == 3 ? 2 : 1) * (a_region + (size_t)NW * Kp * 2) + 16 + 4 * NW +
+                 4 * Kp + 64;
+  Args b = a;
+  b.crow_smem = (bytes + 4 * a.Nb <= 200 * 1024) ? 1 : 0;
+  if (b.crow_smem) bytes += 4 * a.Nb;
   if (bytes > 220 * 1024)
     return fail(HINQS_ERR_ARG, "tensor-core sigma: tile of %zu bytes exceeds shared memory (n_orb=%d)",
                 bytes, a.n);
   auto kern = k_sigma_ab_tc<NW, SPLIT>;
   HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-  kern<<<(unsigned)a.Na, kThreads, bytes, s>>>(a);
+  kern<<<(unsigned)a.Na, kThreads, bytes, s>>>(b);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -323,6 +381,8 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   a.eri = H->eri32;
   a.C = c;
   a.sig = sig;
+  a.crow_smem = 0;
+  a.vec4 = (B->Nb % 4 == 0) ? 1 : 0;
   const bool wide = la->max_srow > 64;
   if (split == 3) return wide ? tc::launch<128, 3>(a, s) : tc::launch<64, 3>(a, s);
   return wide ? tc::launch<128, 1>(a, s) : tc::launch<64, 1>(a, s);

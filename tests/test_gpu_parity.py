@@ -245,6 +245,20 @@ def test_sigma_tensor_core_full_size(precision_workload):
         assert float(torch.max(torch.abs(s - s32))) <= rel * float(torch.max(torch.abs(s32)))
 
 
+def test_sigma_halves_sum_to_sigma(precision_workload):
+    """hinqs_sigma_same_spin + hinqs_sigma_opposite_spin == hinqs_sigma in every mode."""
+    B = precision_workload
+    c = torch.tensor(synth.random_vector(B.sub.N, 7), device="cuda")
+    for prec, x in ((hq.PREC_FP64, c), (hq.PREC_FP32, c.float()),
+                    (hq.PREC_FP32_BF16AB, c.float()), (hq.PREC_FP32_BF16X3AB, c.float())):
+        full = hq.sigma(B.ham, B.sub, B.la, B.lb, x, precision=prec)
+        part = torch.empty_like(x)
+        hq.sigma_part(B.ham, B.sub, B.la, B.lb, x, part, "same", precision=prec)
+        hq.sigma_part(B.ham, B.sub, B.la, B.lb, x, part, "opposite", precision=prec)
+        tol = (1e-12 if prec == hq.PREC_FP64 else 1e-5) * float(torch.max(torch.abs(full)))
+        assert float(torch.max(torch.abs(full - part))) <= tol
+
+
 def test_sigma_full_size_sampled_rows(precision_workload):
     """The bench configuration (n=16, 5/5, 2000 x 2000): 512 sampled rows."""
     B = precision_workload
