@@ -179,11 +179,13 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
         xx += y[o + i] * V[i * ld + j];
       }
     }
-    double r = hx - theta * xx;
+    const double r = hx - theta * xx;
     acc += r * r;
-    double den = D[j] - theta;
-    if (fabs(den) < floor_) den = (den < 0.0) ? -floor_ : floor_;
-    t[j] = r / den;
+    // the correction only steers the search: divide in FP32
+    float den = (float)(D[j] - theta);
+    const float fl = (float)floor_;
+    if (fabsf(den) < fl) den = (den < 0.0f) ? -fl : fl;
+    t[j] = (double)__fdividef((float)r, den);
   }
 #pragma unroll
   for (int o2 = 16; o2 > 0; o2 >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o2);
@@ -198,11 +200,15 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
 
 // Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
 // ldg; S == NULL means S = I) by cyclic Jacobi with the round-robin parallel
-// ordering, in one block.  With S the pencil is reduced to C = L^-1 G L^-T by the
-// Cholesky factor S = L L^T and the eigenvector is mapped back, y = L^-T z, so
-// that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest |component| > 0).
-__global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __restrict__ out,
-                     const double* __restrict__ S, double* __restrict__ all = nullptr) {
+// ordering, in ONE WARP (warp-synchronous: m <= 32).  With S the pencil is reduced
+// to C = L^-1 G L^-T by the Cholesky factor S = L L^T and eigenvectors are mapped
+// back, y = L^-T z, so that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest
+// |component| > 0).  If all != NULL every eigenpair is written in ascending order,
+// all[j * kRitzStride] = lambda_j, all[j * kRitzStride + 1 ..] = y_j.
+__global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg, int m,
+                                           double* __restrict__ out,
+                                           const double* __restrict__ S,
+                                           double* __restrict__ all = nullptr) {
   __shared__ double A[kMaxSub][kMaxSub + 1];
   __shared__ double Q[kMaxSub][kMaxSub + 1];
   __shared__ double L[kMaxSub][kMaxSub + 1];
@@ -210,182 +216,169 @@ __global__ void k_rr(const double* __restrict__ G, int ldg, int m, double* __res
   __shared__ double cs[kMaxSub / 2][2];
   __shared__ int pr[kMaxSub / 2][2];
   __shared__ int order[kMaxSub];
-  __shared__ double offn;
-  __shared__ int use_s;
-  const int tid = threadIdx.x;
-  int mm = m + (m & 1);  // even size for the tournament; padded row/col is isolated
-  if (tid == 0) {
-    use_s = 0;
-    if (S) {
-      // Cholesky S = L L^T (S symmetrised)
-      use_s = 1;
-      for (int j = 0; j < m && use_s; ++j) {
-        double d = 0.5 * (S[j * ldg + j] + S[j * ldg + j]);
-        for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
-        if (!(d > 0.0)) {
-          use_s = 0;
-          break;
-        }
-        L[j][j] = sqrt(d);
-        for (int i = j + 1; i < m; ++i) {
-          double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
-          for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-          L[i][j] = v / L[j][j];
-        }
+  __shared__ int rank_of[kMaxSub];
+  const int lane = threadIdx.x;
+  const unsigned full = 0xffffffffu;
+  const int mm = m + (m & 1);  // even size for the tournament; the pad row/col is isolated
+  bool use_s = false;
+  if (S) {
+    // Cholesky S = L L^T, column by column; lanes take the rows below the pivot
+    use_s = true;
+    for (int j = 0; j < m; ++j) {
+      // every lane forms the pivot from values stored before the last barrier
+      double d = S[j * ldg + j];
+      for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+      if (!(d > 0.0)) {
+        use_s = false;
+        break;
       }
+      const double ljj = sqrt(d);
+      for (int i = j + 1 + lane; i < m; i += 32) {
+        double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
+        for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
+        L[i][j] = v / ljj;
+      }
+      if (lane == 0) L[j][j] = ljj;
+      __syncwarp();
     }
   }
-  __syncthreads();
   if (use_s) {
-    // X = L^-1 Gs (column j by forward substitution), then C = L^-1 X^T
-    if (tid < m) {
-      const int j = tid;
+    // X = L^-1 Gs (lane = column), then C = L^-1 X^T (lane = column)
+    if (lane < m) {
       for (int i = 0; i < m; ++i) {
-        double v = 0.5 * (G[i * ldg + j] + G[j * ldg + i]);
-        for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][j];
-        X[i][j] = v / L[i][i];
+        double v = 0.5 * (G[i * ldg + lane] + G[lane * ldg + i]);
+        for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][lane];
+        X[i][lane] = v / L[i][i];
       }
     }
-    __syncthreads();
-    if (tid < m) {
-      const int j = tid;
+    __syncwarp();
+    if (lane < m) {
       for (int i = 0; i < m; ++i) {
-        double v = X[j][i];
-        for (int k = 0; k < i; ++k) v -= L[i][k] * A[k][j];
-        A[i][j] = v / L[i][i];
+        double v = X[lane][i];
+        for (int k = 0; k < i; ++k) v -= L[i][k] * A[k][lane];
+        A[i][lane] = v / L[i][i];
       }
     }
-    __syncthreads();
+    __syncwarp();
+    for (int i = lane; i < m * m; i += 32) X[i / m][i % m] = 0.5 * (A[i / m][i % m] + A[i % m][i / m]);
+    __syncwarp();
   }
-  for (int i = tid; i < mm * mm; i += blockDim.x) {
-    int r = i / mm, c = i % mm;
+  for (int i = lane; i < mm * mm; i += 32) {
+    const int r = i / mm, c = i % mm;
     double v = 0.0;
-    if (r < m && c < m) v = use_s ? 0.5 * (A[r][c] + A[c][r]) : 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
+    if (r < m && c < m) v = use_s ? X[r][c] : 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
     else if (r == c) v = 1e300;  // padding: never the lowest
-    X[r][c] = v;
+    A[r][c] = v;
     Q[r][c] = (r == c) ? 1.0 : 0.0;
   }
-  __syncthreads();
-  for (int i = tid; i < mm * mm; i += blockDim.x) A[i / mm][i % mm] = X[i / mm][i % mm];
-  if (tid < mm) order[tid] = tid;
-  __syncthreads();
+  if (lane < mm) order[lane] = lane;
+  __syncwarp();
   for (int sweep = 0; sweep < 30; ++sweep) {
-    if (tid == 0) {
-      double s = 0.0, d = 0.0;
-      for (int r = 0; r < m; ++r)
-        for (int c = 0; c < m; ++c) {
-          if (r != c) s += A[r][c] * A[r][c];
-          else d += A[r][c] * A[r][c];
-        }
-      offn = (s <= 1e-30 * d || s == 0.0) ? 1.0 : 0.0;
+    double off = 0.0, dia = 0.0;
+    for (int i = lane; i < m * m; i += 32) {
+      const double v = A[i / m][i % m];
+      if (i / m != i % m) off += v * v;
+      else dia += v * v;
     }
-    __syncthreads();
-    if (offn > 0.5) break;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(full, off, o);
+      dia += __shfl_xor_sync(full, dia, o);
+    }
+    if (off <= 1e-30 * dia || off == 0.0) break;
     for (int step = 0; step < mm - 1; ++step) {
-      // pairs of the round-robin schedule
-      if (tid < mm / 2) {
-        int p = order[tid], q = order[mm - 1 - tid];
+      if (lane < mm / 2) {
+        int p = order[lane], q = order[mm - 1 - lane];
         if (p > q) {
-          int t = p;
+          const int t = p;
           p = q;
           q = t;
         }
-        pr[tid][0] = p;
-        pr[tid][1] = q;
-        double apq = A[p][q], c = 1.0, s = 0.0;
+        pr[lane][0] = p;
+        pr[lane][1] = q;
+        const double apq = A[p][q];
+        double c = 1.0, sn = 0.0;
         if (apq != 0.0 && p < m && q < m) {
-          double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-          double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
           c = 1.0 / sqrt(1.0 + t * t);
-          s = t * c;
+          sn = t * c;
         }
-        cs[tid][0] = c;
-        cs[tid][1] = s;
+        cs[lane][0] = c;
+        cs[lane][1] = sn;
       }
-      __syncthreads();
-      // A <- J^T A (rows p, q)
-      for (int i = tid; i < (mm / 2) * mm; i += blockDim.x) {
-        int k = i / mm, col = i % mm;
-        int p = pr[k][0], q = pr[k][1];
-        double c = cs[k][0], s = cs[k][1];
-        double ap = A[p][col], aq = A[q][col];
-        A[p][col] = c * ap - s * aq;
-        A[q][col] = s * ap + c * aq;
+      __syncwarp();
+      for (int i = lane; i < (mm / 2) * mm; i += 32) {  // A <- J^T A (rows p, q)
+        const int k = i / mm, col = i % mm;
+        const int p = pr[k][0], q = pr[k][1];
+        const double c = cs[k][0], sn = cs[k][1];
+        const double ap = A[p][col], aq = A[q][col];
+        A[p][col] = c * ap - sn * aq;
+        A[q][col] = sn * ap + c * aq;
       }
-      __syncthreads();
-      // A <- A J (cols p, q), Q <- Q J
-      for (int i = tid; i < (mm / 2) * mm; i += blockDim.x) {
-        int k = i / mm, row = i % mm;
-        int p = pr[k][0], q = pr[k][1];
-        double c = cs[k][0], s = cs[k][1];
-        double ap = A[row][p], aq = A[row][q];
-        A[row][p] = c * ap - s * aq;
-        A[row][q] = s * ap + c * aq;
-        double qp = Q[row][p], qq = Q[row][q];
-        Q[row][p] = c * qp - s * qq;
-        Q[row][q] = s * qp + c * qq;
+      __syncwarp();
+      for (int i = lane; i < (mm / 2) * mm; i += 32) {  // A <- A J, Q <- Q J (cols p, q)
+        const int k = i / mm, row = i % mm;
+        const int p = pr[k][0], q = pr[k][1];
+        const double c = cs[k][0], sn = cs[k][1];
+        const double ap = A[row][p], aq = A[row][q];
+        A[row][p] = c * ap - sn * aq;
+        A[row][q] = sn * ap + c * aq;
+        const double qp = Q[row][p], qq = Q[row][q];
+        Q[row][p] = c * qp - sn * qq;
+        Q[row][q] = sn * qp + c * qq;
       }
-      __syncthreads();
-      if (tid == 0) {  // rotate the tournament, order[0] fixed
-        int last = order[mm - 1];
+      __syncwarp();
+      if (lane == 0) {  // rotate the tournament, order[0] fixed
+        const int last = order[mm - 1];
         for (int k = mm - 1; k > 1; --k) order[k] = order[k - 1];
         order[1] = last;
       }
-      __syncthreads();
+      __syncwarp();
     }
   }
-  if (tid == 0) {
-    int best = 0;
-    for (int k = 1; k < m; ++k)
-      if (A[k][k] < A[best][best]) best = k;
-    double z[kMaxSub];
-    double nrm = 0.0;
-    for (int r = 0; r < m; ++r) nrm += Q[r][best] * Q[r][best];
-    nrm = 1.0 / sqrt(nrm);
-    for (int r = 0; r < m; ++r) z[r] = Q[r][best] * nrm;
-    if (use_s) {  // y = L^-T z
-      for (int i = m - 1; i >= 0; --i) {
-        double v = z[i];
-        for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
-        z[i] = v / L[i][i];
-      }
+  // rank of each eigenvalue (ascending, ties by index)
+  if (lane < m) {
+    const double lj = A[lane][lane];
+    int r = 0;
+    for (int k = 0; k < m; ++k) {
+      const double lk = A[k][k];
+      if (lk < lj || (lk == lj && k < lane)) ++r;
     }
-    double big = 0.0;
-    int arg = 0;
-    for (int r = 0; r < m; ++r)
-      if (fabs(z[r]) > big) {
-        big = fabs(z[r]);
-        arg = r;
-      }
-    double sg = z[arg] < 0.0 ? -1.0 : 1.0;
-    out[0] = A[best][best];
-    for (int r = 0; r < m; ++r) out[1 + r] = sg * z[r];
-    for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
-    if (all) {
-      // every eigenpair, ascending: all[j * kRitzStride] = lambda_j, then its vector
-      int order_[kMaxSub];
-      for (int k = 0; k < m; ++k) order_[k] = k;
-      for (int a = 0; a < m; ++a)
-        for (int b = a + 1; b < m; ++b)
-          if (A[order_[b]][order_[b]] < A[order_[a]][order_[a]]) {
-            int t = order_[a];
-            order_[a] = order_[b];
-            order_[b] = t;
-          }
-      for (int j = 0; j < m; ++j) {
-        const int col = order_[j];
-        double nz = 0.0;
-        for (int r = 0; r < m; ++r) nz += Q[r][col] * Q[r][col];
-        nz = 1.0 / sqrt(nz);
-        for (int r = 0; r < m; ++r) z[r] = Q[r][col] * nz;
-        if (use_s) {
-          for (int i = m - 1; i >= 0; --i) {
-            double v = z[i];
-            for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
-            z[i] = v / L[i][i];
-          }
+    rank_of[lane] = r;
+  }
+  __syncwarp();
+  // lane j maps eigenvector j back (z -> y) and writes it where its rank says
+  if (lane < m) {
+    const int col = lane, rank = rank_of[lane];
+    if (all || rank == 0) {
+      double z[kMaxSub];
+      double nz = 0.0;
+      for (int r = 0; r < m; ++r) nz += Q[r][col] * Q[r][col];
+      nz = 1.0 / sqrt(nz);
+      for (int r = 0; r < m; ++r) z[r] = Q[r][col] * nz;
+      if (use_s) {
+        for (int i = m - 1; i >= 0; --i) {
+          double v = z[i];
+          for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
+          z[i] = v / L[i][i];
         }
-        double* o = all + (size_t)j * kRitzStride;
+      }
+      if (rank == 0) {
+        double big = 0.0;
+        int arg = 0;
+        for (int r = 0; r < m; ++r)
+          if (fabs(z[r]) > big) {
+            big = fabs(z[r]);
+            arg = r;
+          }
+        const double sg = z[arg] < 0.0 ? -1.0 : 1.0;
+        out[0] = A[col][col];
+        for (int r = 0; r < m; ++r) out[1 + r] = sg * z[r];
+        for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
+      }
+      if (all) {
+        double* o = all + (size_t)rank * kRitzStride;
         o[0] = A[col][col];
         for (int r = 0; r < m; ++r) o[1 + r] = z[r];
         for (int r = m; r < kMaxSub; ++r) o[1 + r] = 0.0;
@@ -610,7 +603,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       info.n_sigma_fp64++;
       HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
-      k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
+      k_rr<<<1, 32, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
       k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
                                                             D, o.denom_floor, N, t, c.partial);
       k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -787,7 +780,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         double* th = c.small + 2 * kMaxSub;
         HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));
         k_init_pencil<<<1, 256, 0, c.s>>>(G1, nullptr, th);
-        k_rr<<<1, 256, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
+        k_rr<<<1, 32, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -833,7 +826,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       }
       bool restart_hard = false;
       for (;;) {
-        k_rr<<<1, 256, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
+        k_rr<<<1, 32, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
