@@ -86,8 +86,8 @@ const char* hinqs_last_error_message(void);
 const char* hinqs_version(void);
 
 /* ---------------------------------------------------------- Hamiltonian --
- * Prepare the second-quantised Hamiltonian of Sec. 2.2 ("Given a
- * second-quantized molecular Hamiltonian ... in an orthonormal orbital basis").
+ * Prepare the second-quantised Hamiltonian of Sec. 2.2: one- and two-electron
+ * integrals over an orthonormal set of spatial orbitals.
  *   h      device, FP64 [n_orb*n_orb], copied
  *   eri    device, FP64 [n_orb^4] chemist (pq|rs), copied
  *   n_alpha, n_beta  electron counts of the fixed (n_alpha, n_beta) sector
@@ -239,6 +239,50 @@ void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
 int hinqs_davidson(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
                    const hinqs_links* lb, const double* guess, const hinqs_davidson_opts* opts,
                    double* energy, double* c_out, hinqs_davidson_info* info, void* stream);
+
+/* ------------------------------------------------------------- autotune --
+ * Not in the paper (its benchmarks use one geometry each; potential-energy scans
+ * are named as future work in the Conclusion, item iii).  Times the sigma product
+ * of `precision` on this problem for each candidate tile configuration -- rows per
+ * warp of the same-spin row products (2, 4, 8) and, for the CUDA-core
+ * opposite-spin kernel (HINQS_PREC_FP64, HINQS_PREC_FP32), the alpha-single chunk
+ * width (16, 32) -- and stores the fastest in la and lb; every later sigma,
+ * Davidson and batch call on these links uses it.  Choices are cached per
+ * (n_orb, n_alpha, n_beta, precision, N_alpha and N_beta in quarter-octave
+ * buckets) for the life of the process, so similar problems are timed once.
+ *   best_ms  host double or NULL: time of one sigma with the chosen tiles
+ * Allocates two vectors of N elements for the trial products and synchronises
+ * the stream.  Results of sigma do not depend on the choice beyond summation
+ * order.  Errors: HINQS_ERR_ARG, HINQS_ERR_OOM, HINQS_ERR_CUDA, HINQS_ERR_TIMEOUT. */
+int hinqs_autotune(const hinqs_ham* ham, const hinqs_subspace* sub, hinqs_links* la,
+                   hinqs_links* lb, int precision, double* best_ms, void* stream);
+
+/* ------------------------------------------------------- batched solve --
+ * Not in the paper (see hinqs_autotune): lowest eigenpairs of n_geom independent
+ * problems, e.g. the geometries of a bond scan, each exactly as hinqs_davidson
+ * would solve it with `opts` (NULL = defaults).  The problems are ordered by an
+ * estimate of their sigma cost, longest first, and taken from a shared queue by
+ * n_streams host workers (<= 0: 4), each running its solves on a CUDA stream of
+ * its own, so solves of different geometries overlap on the GPU.  The worker
+ * streams start after the work already queued on `stream`, and `stream` waits for
+ * all of them before later work; the call itself returns when every solve is done.
+ *   hams, subs, las, lbs  arrays of n_geom handles (la/lb: alpha/beta links of subs[g])
+ *   guesses   NULL or array of n_geom device FP64 pointers (each may be NULL)
+ *   autotune  nonzero: run hinqs_autotune on each problem first, for the sigma
+ *             precision the solve uses most (the inner precision when mixed)
+ *   energies  host double [n_geom];  c_outs: n_geom device FP64 [N_g] pointers
+ *   infos     host [n_geom] or NULL
+ * Returns the first error of any geometry (with its index in the message), else
+ * HINQS_NOT_CONVERGED if any geometry did not converge, else HINQS_OK.
+ * The trace arrays of opts are ignored.
+ * Concurrency: the tensor-core wait-timeout flag is shared by the library, so a
+ * timeout in one geometry's tensor-core sigma may be reported by another's. */
+int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
+                         const hinqs_subspace* const* subs, hinqs_links* const* las,
+                         hinqs_links* const* lbs, const double* const* guesses,
+                         const hinqs_davidson_opts* opts, int n_streams, int autotune,
+                         double* energies, double* const* c_outs, hinqs_davidson_info* infos,
+                         void* stream);
 
 /* ------------------------------------------------------------------ RDMs --
  * Spin-summed reduced density matrices of the state c (FP64 [N], used as given):

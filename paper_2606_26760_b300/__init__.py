@@ -72,7 +72,7 @@ EXPORTED = [
     "hinqs_links_destroy", "hinqs_diag", "hinqs_sigma", "hinqs_davidson_default_opts",
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
     "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
-    "hinqs_links_max_singles",
+    "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch",
 ]
 
 
@@ -108,6 +108,9 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_davidson_default_opts.restype = None
     lib.hinqs_davidson.argtypes = [P, P, P, P, P, ctypes.POINTER(_Opts),
                                    ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(_Info), P]
+    lib.hinqs_autotune.argtypes = [P, P, P, P, I, ctypes.POINTER(ctypes.c_double), P]
+    lib.hinqs_davidson_batch.argtypes = [I, P, P, P, P, P, ctypes.POINTER(_Opts), I, I, P, P,
+                                         P, P]
     lib.hinqs_rdm.argtypes = [P, P, P, P, P, P, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
@@ -293,16 +296,23 @@ class DavidsonResult:
     trace: dict = field(default_factory=dict)
 
 
-def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
-             max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
-             denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
-             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
+def _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor, inner_tol,
+               inner_precision):
     opts = _Opts()
     _lib.hinqs_davidson_default_opts(ctypes.byref(opts))
     opts.precision, opts.max_iter, opts.max_subspace = precision, max_iter, max_subspace
     opts.tol_residual, opts.tol_energy, opts.denom_floor = tol_residual, tol_energy, denom_floor
     opts.inner_tol = inner_tol
     opts.inner_precision = inner_precision
+    return opts
+
+
+def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
+             max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
+             denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
+             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
+    opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
+                      inner_tol, inner_precision)
     bufs = None
     if trace_cap > 0:
         bufs = ((ctypes.c_double * trace_cap)(), (ctypes.c_double * trace_cap)(),
@@ -328,6 +338,53 @@ def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_i
                   kind=list(bufs[3][:n]))
     return DavidsonResult(e.value, c, rc, info.iterations, info.n_sigma_fp64, info.n_sigma_fp32,
                           info.n_restarts, info.n_refinements, info.residual, info.seconds, tr)
+
+
+def autotune(ham, sub, la, lb, precision: int = PREC_FP32) -> float:
+    """hinqs_autotune: time the sigma tile candidates on this problem, keep the
+    fastest in la/lb; returns the milliseconds of one sigma with the choice."""
+    ms = ctypes.c_double()
+    _check(_lib.hinqs_autotune(ham.handle, sub.handle, la.handle, lb.handle, precision,
+                               ctypes.byref(ms), _stream()))
+    return ms.value
+
+
+def davidson_batch(problems, guesses=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
+                   max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
+                   denom_floor: float = 1e-4, inner_tol: float = 1e-3,
+                   inner_precision: int = PREC_FP32, n_streams: int = 4, autotune: bool = False,
+                   outs=None):
+    """hinqs_davidson_batch over `problems` = [(ham, sub, la, lb), ...]: every
+    geometry solved as davidson() would, several at a time on their own streams.
+    Returns a list of DavidsonResult (no trace), in the order of `problems`."""
+    G = len(problems)
+    if G == 0:
+        return []
+    opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
+                      inner_tol, inner_precision)
+    dev = _dev()
+    cs = outs if outs is not None else [torch.empty(p[1].N, dtype=torch.float64, device=dev)
+                                        for p in problems]
+    if guesses is not None:
+        for g, p in zip(guesses, problems):
+            if g is not None and (g.dtype != torch.float64 or g.numel() != p[1].N):
+                raise ValueError("each guess must be a float64 tensor of its subspace size")
+    VP = ctypes.c_void_p * G
+    hams = VP(*[p[0].handle for p in problems])
+    subs = VP(*[p[1].handle for p in problems])
+    las = VP(*[p[2].handle for p in problems])
+    lbs = VP(*[p[3].handle for p in problems])
+    gp = VP(*[(g.data_ptr() if g is not None else None) for g in guesses]) if guesses else None
+    cp = VP(*[c.data_ptr() for c in cs])
+    energies = (ctypes.c_double * G)()
+    infos = (_Info * G)()
+    rc = _lib.hinqs_davidson_batch(G, hams, subs, las, lbs, gp, ctypes.byref(opts), n_streams,
+                                   1 if autotune else 0, energies, cp, infos, _stream())
+    _check(rc, allow_warning=True)
+    return [DavidsonResult(energies[g], cs[g], infos[g].status, infos[g].iterations,
+                           infos[g].n_sigma_fp64, infos[g].n_sigma_fp32, infos[g].n_restarts,
+                           infos[g].n_refinements, infos[g].residual, infos[g].seconds, {})
+            for g in range(G)]
 
 
 def rdm(sub, la, lb, c, want2: bool = True):

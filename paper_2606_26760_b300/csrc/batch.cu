@@ -1,0 +1,224 @@
+// Sigma tile autotuner and the batched multi-geometry Davidson solve.
+//
+// Autotuner: for one (Hamiltonian, subspace, links) it times the sigma product for
+// each candidate tile configuration -- rows per warp of the same-spin row products
+// and, for the CUDA-core opposite-spin kernel, the width of its alpha-single chunk --
+// and stores the fastest in the links handles.  Results are cached per problem
+// class (orbitals, electrons, precision, and the string counts in quarter-octave
+// buckets), so geometries of a scan with similar sizes are tuned once.
+//
+// Batched solve: the geometries of a scan are independent eigenproblems of uneven
+// size.  They are ordered by estimated cost (longest first) and handed out from a
+// shared counter to worker threads, each driving the single-geometry Davidson on a
+// stream of its own, so several solves -- each a chain of dependent launches with a
+// host decision per iteration -- run on the GPU at the same time.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "hinqs_internal.cuh"
+
+namespace hinqs {
+
+int check_triplet(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                  const hinqs_links_s* lb, const char* who);
+
+namespace {
+
+using TuneKey = std::tuple<int, int, int, int, int, int>;
+struct TuneVal {
+  int rows, ch;
+  double ms;
+};
+std::mutex g_tune_mutex;
+std::map<TuneKey, TuneVal> g_tune_cache;
+
+int bucket(int64_t n) { return (int)std::floor(4.0 * std::log2((double)std::max<int64_t>(n, 1))); }
+
+__global__ void k_fill_pattern(void* x, int64_t N, int is_double) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = 1.0 / (1.0 + (double)(i % 97));
+    if (is_double) static_cast<double*>(x)[i] = v;
+    else static_cast<float*>(x)[i] = (float)v;
+  }
+}
+
+}  // namespace
+
+int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s* la,
+                  hinqs_links_s* lb, int precision, double* best_ms, cudaStream_t s) {
+  const TuneKey key{H->n, H->n_alpha, H->n_beta, precision, bucket(B->Na), bucket(B->Nb)};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      la->tune_rows = lb->tune_rows = it->second.rows;
+      la->tune_ch = it->second.ch;
+      if (best_ms) *best_ms = it->second.ms;
+      return HINQS_OK;
+    }
+  }
+  const int64_t N = B->Na * B->Nb;
+  const bool dbl = precision == HINQS_PREC_FP64;
+  const size_t esz = dbl ? sizeof(double) : sizeof(float);
+  void *c = nullptr, *sg = nullptr;
+  if (cudaMallocAsync(&c, N * esz, s) != cudaSuccess || cudaMallocAsync(&sg, N * esz, s) != cudaSuccess) {
+    cudaGetLastError();
+    if (c) cudaFreeAsync(c, s);
+    return fail(HINQS_ERR_OOM, "hinqs_autotune: no room for two test vectors");
+  }
+  k_fill_pattern<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 8 * kNumSMs), 256, 0, s>>>(c, N, dbl);
+  const bool cuda_core_ab = precision == HINQS_PREC_FP64 || precision == HINQS_PREC_FP32;
+  std::vector<std::pair<int, int>> cands;
+  for (int r : {2, 4, 8})
+    for (int ch : (cuda_core_ab ? std::vector<int>{16, 32} : std::vector<int>{0}))
+      cands.push_back({r, ch});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  double best = 1e300;
+  TuneVal bestv{0, 0, 0.0};
+  int rc = HINQS_OK;
+  for (auto [r, ch] : cands) {
+    la->tune_rows = lb->tune_rows = r;
+    la->tune_ch = ch;
+    if ((rc = sigma_launch(H, B, la, lb, c, sg, precision, s)) < 0) break;  // warm-up
+    cudaEventRecord(e0, s);
+    const int reps = 3;
+    for (int k = 0; k < reps && rc >= 0; ++k) rc = sigma_launch(H, B, la, lb, c, sg, precision, s);
+    if (rc < 0) break;
+    cudaEventRecord(e1, s);
+    cudaEventSynchronize(e1);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    const double t = ms / reps;
+    if (t < best) {
+      best = t;
+      bestv = TuneVal{r, ch, t};
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(c, s);
+  cudaFreeAsync(sg, s);
+  if (rc < 0) return rc;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "hinqs_autotune", __FILE__, __LINE__);
+  la->tune_rows = lb->tune_rows = bestv.rows;
+  la->tune_ch = bestv.ch;
+  if (best_ms) *best_ms = bestv.ms;
+  std::lock_guard<std::mutex> lock(g_tune_mutex);
+  g_tune_cache[key] = bestv;
+  return HINQS_OK;
+}
+
+}  // namespace hinqs
+
+using namespace hinqs;
+
+extern "C" int hinqs_autotune(const hinqs_ham* H, const hinqs_subspace* B, hinqs_links* la,
+                              hinqs_links* lb, int precision, double* best_ms, void* stream) {
+  HQ_TRY(check_triplet(H, B, la, lb, "hinqs_autotune"));
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+    return fail(HINQS_ERR_ARG, "hinqs_autotune: unknown precision %d", precision);
+  return autotune_impl(H, B, la, lb, precision, best_ms, (cudaStream_t)stream);
+}
+
+extern "C" int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
+                                    const hinqs_subspace* const* subs, hinqs_links* const* las,
+                                    hinqs_links* const* lbs, const double* const* guesses,
+                                    const hinqs_davidson_opts* opts, int n_streams, int autotune,
+                                    double* energies, double* const* c_outs,
+                                    hinqs_davidson_info* infos, void* stream) {
+  if (n_geom < 0 || (n_geom > 0 && (!hams || !subs || !las || !lbs || !c_outs || !energies)))
+    return fail(HINQS_ERR_ARG, "hinqs_davidson_batch: NULL arrays");
+  if (n_geom == 0) return HINQS_OK;
+  for (int g = 0; g < n_geom; ++g) {
+    HQ_TRY(check_triplet(hams[g], subs[g], las[g], lbs[g], "hinqs_davidson_batch"));
+    if (!c_outs[g]) return fail(HINQS_ERR_ARG, "hinqs_davidson_batch: c_out[%d] is NULL", g);
+  }
+  hinqs_davidson_opts o;
+  hinqs_davidson_default_opts(&o);
+  if (opts) o = *opts;
+  // the host trace arrays would be shared by the concurrent solves
+  o.trace_cap = 0;
+  o.trace_theta = o.trace_resid = o.trace_time = nullptr;
+  o.trace_kind = nullptr;
+  cudaStream_t s = (cudaStream_t)stream;
+  // autotune the sigma the solve uses most (inner products of the mixed solver)
+  if (autotune) {
+    const int p = o.precision == HINQS_DAVIDSON_MIXED ? o.inner_precision : HINQS_PREC_FP64;
+    for (int g = 0; g < n_geom; ++g) HQ_TRY(autotune_impl(hams[g], subs[g], las[g], lbs[g], p, nullptr, s));
+  }
+  // longest first: cost ~ N * (links per alpha string + links per beta string + singles product)
+  std::vector<std::pair<double, int>> order;
+  for (int g = 0; g < n_geom; ++g) {
+    const double Na = (double)subs[g]->Na, Nb = (double)subs[g]->Nb;
+    const double cost = Na * Nb *
+                        ((double)las[g]->nnz / Na + (double)lbs[g]->nnz / Nb +
+                         ((double)las[g]->nsingle / Na) * ((double)lbs[g]->nsingle / Nb + 1.0));
+    order.push_back({cost, g});
+  }
+  std::sort(order.begin(), order.end(), [](auto& a, auto& b) { return a.first > b.first; });
+  int nw = n_streams > 0 ? n_streams : 4;
+  nw = std::max(1, std::min(nw, n_geom));
+  // worker streams start after the caller's stream reaches this point
+  cudaEvent_t start;
+  HQ_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+  HQ_CUDA(cudaEventRecord(start, s));
+  std::vector<cudaStream_t> ws(nw);
+  for (int w = 0; w < nw; ++w) {
+    HQ_CUDA(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
+    HQ_CUDA(cudaStreamWaitEvent(ws[w], start, 0));
+  }
+  std::atomic<int> next{0};
+  std::vector<int> status(n_geom, HINQS_OK);
+  std::vector<std::string> msg(n_geom);
+  std::vector<hinqs_davidson_info> inf(n_geom);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  auto worker = [&](int w) {
+    cudaSetDevice(dev);
+    for (;;) {
+      const int k = next.fetch_add(1);
+      if (k >= n_geom) break;
+      const int g = order[k].second;
+      double e = 0.0;
+      status[g] = hinqs_davidson(hams[g], subs[g], las[g], lbs[g], guesses ? guesses[g] : nullptr,
+                                 &o, &e, c_outs[g], &inf[g], (void*)ws[w]);
+      energies[g] = e;
+      if (status[g] < 0) msg[g] = hinqs_last_error_message();
+    }
+  };
+  std::vector<std::thread> threads;
+  for (int w = 0; w < nw; ++w) threads.emplace_back(worker, w);
+  for (auto& t : threads) t.join();
+  // the caller's stream continues after every worker stream
+  for (int w = 0; w < nw; ++w) {
+    cudaEvent_t done;
+    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    cudaEventRecord(done, ws[w]);
+    cudaStreamWaitEvent(s, done, 0);
+    cudaEventDestroy(done);
+    cudaStreamDestroy(ws[w]);
+  }
+  cudaEventDestroy(start);
+  int rc = HINQS_OK;
+  for (int g = 0; g < n_geom; ++g) {
+    if (infos) infos[g] = inf[g];
+    if (status[g] < 0 && rc >= 0) {
+      rc = status[g];
+      set_error("hinqs_davidson_batch: geometry %d: %s", g, msg[g].c_str());
+    } else if (status[g] > 0 && rc == HINQS_OK) {
+      rc = status[g];
+    }
+  }
+  return rc;
+}

@@ -115,6 +115,11 @@ struct hinqs_links_s {
   // rec64 {off, 0, double bits}; null when N_a * N_b >= 2^32
   int2* rec32 = nullptr;
   int4* rec64 = nullptr;
+  // sigma tiles chosen by hinqs_autotune (0 = built-in default): rows per warp of
+  // the row products that use these links, and the alpha-single chunk width of the
+  // CUDA-core opposite-spin kernel (read from the alpha links)
+  int tune_rows = 0;
+  int tune_ch = 0;
 };
 
 namespace hinqs {

@@ -122,7 +122,7 @@ struct Rec<double> {
 
 // Same row product as k_spmm_rows with packed records (no per-link index
 // arithmetic), 8 links in flight per lane, and VEC consecutive columns per lane.
-template <typename T, int VEC>
+template <typename T, int VEC, int RPW>
 __global__ void __launch_bounds__(256) k_spmm_rec(
     const T* __restrict__ X, T* __restrict__ Y, int64_t nrows, int64_t ncols,
     const int64_t* __restrict__ rp, const typename Rec<T>::type* __restrict__ rec,
@@ -137,8 +137,8 @@ __global__ void __launch_bounds__(256) k_spmm_rec(
   const bool active = c0 < ncols;  // VEC divides ncols
   const int64_t cc = active ? c0 : 0;
   const int n2 = n * n;
-  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * kRowsPerWarp;
-  for (int rr = 0; rr < kRowsPerWarp; ++rr) {
+  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  for (int rr = 0; rr < RPW; ++rr) {
     const int64_t I = I0 + rr;
     if (I >= nrows) break;
     T acc[VEC];
@@ -392,17 +392,23 @@ static int spmm_rows(const T* X, T* Y, int64_t nrows, int64_t ncols, const hinqs
                      int n, int accumulate, cudaStream_t s) {
   const auto* rec = recof<T>(L);
   if (rec) {
-    const unsigned gy = (unsigned)ceil_div(nrows, kRowWarps * kRowsPerWarp);
     const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
     const int2* sl = Lsingles ? Lsingles->slink : nullptr;
+    const int rpw = L->tune_rows ? L->tune_rows : kRowsPerWarp;
+    auto go = [&](auto kern, int vec, int r) {
+      const unsigned gy = (unsigned)ceil_div(nrows, kRowWarps * r);
+      kern<<<dim3((unsigned)ceil_div(ncols, 32 * vec), gy), 32 * kRowWarps, 0, s>>>(
+          X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n,
+          accumulate);
+    };
     if (ncols % 2 == 0) {
-      k_spmm_rec<T, 2><<<dim3((unsigned)ceil_div(ncols, 64), gy), 32 * kRowWarps, 0, s>>>(
-          X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n,
-          accumulate);
+      if (rpw == 2) go(k_spmm_rec<T, 2, 2>, 2, 2);
+      else if (rpw == 8) go(k_spmm_rec<T, 2, 8>, 2, 8);
+      else go(k_spmm_rec<T, 2, 4>, 2, 4);
     } else {
-      k_spmm_rec<T, 1><<<dim3((unsigned)ceil_div(ncols, 32), gy), 32 * kRowWarps, 0, s>>>(
-          X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n,
-          accumulate);
+      if (rpw == 2) go(k_spmm_rec<T, 1, 2>, 1, 2);
+      else if (rpw == 8) go(k_spmm_rec<T, 1, 8>, 1, 8);
+      else go(k_spmm_rec<T, 1, 4>, 1, 4);
     }
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
@@ -446,8 +452,11 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
       if (tc_split) return sigma_ab_tc_launch(H, B, la, lb, c, sig, tc_split, s);
     }
     auto need = [&](int ch) { return (size_t)n2 * (ch + 16 / sizeof(T)) * sizeof(T) + 256; };
-    if (sizeof(T) == 4 && need(32) <= limit / 2) return launch_ab<T, 32>(H, B, la, lb, c, sig, s, limit);
-    if (need(16) <= limit / 2) return launch_ab<T, 16>(H, B, la, lb, c, sig, s, limit);
+    int ch = la->tune_ch ? la->tune_ch : (sizeof(T) == 4 ? 32 : 16);
+    if (ch == 32 && !(need(32) <= limit / 2)) ch = 16;
+    if (ch == 16 && !(need(16) <= limit / 2)) ch = 8;
+    if (ch == 32) return launch_ab<T, 32>(H, B, la, lb, c, sig, s, limit);
+    if (ch == 16) return launch_ab<T, 16>(H, B, la, lb, c, sig, s, limit);
     return launch_ab<T, 8>(H, B, la, lb, c, sig, s, limit);
   };
   rc = run();
