@@ -28,6 +28,20 @@ int cuda_fail(cudaError_t e, const char* what, const char* file, int line) {
   return HINQS_ERR_CUDA;
 }
 
+int smem_optin_limit() {
+  static int cached[64] = {0};  // per device; a racing first fill writes the same value
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (cached[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess || v <= 0)
+      v = 227 * 1024;
+    cached[dev] = v;
+  }
+  return cached[dev];
+}
+
 // FP64 -> FP32 copy (round to nearest).
 __global__ void k_to_f32(const double* __restrict__ x, float* __restrict__ y, int64_t n) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;

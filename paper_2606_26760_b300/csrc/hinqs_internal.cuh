@@ -139,6 +139,18 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
 // HINQS_ERR_TIMEOUT (and clears the flag) if a tensor-core kernel's bounded wait ran out
 int tc_error_check(cudaStream_t s);
 
+// Opt-in shared-memory limit of the current device (bytes per block).
+int smem_optin_limit();
+// Raise a kernel's dynamic shared-memory cap to the device's opt-in limit.  The cap
+// is a property of the kernel shared by every host thread, so it is always set to
+// the same value: a per-launch value would race between concurrent solves.
+template <typename K>
+int allow_max_smem(K kern) {
+  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             smem_optin_limit());
+  return e == cudaSuccess ? HINQS_OK : cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
+}
+
 }  // namespace hinqs
 
 namespace hinqs {

@@ -365,11 +365,11 @@ static int launch_ab(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinq
   size_t with_row = base + (((size_t)B->Nb * sizeof(T) + 15) & ~(size_t)15);
   if (with_row <= smem_limit) {
     auto kern = k_sigma_ab<T, CH, true>;
-    HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)with_row));
+    HQ_TRY(allow_max_smem(kern));
     kern<<<(unsigned)B->Na, 256, with_row, s>>>(c, sig, A, Prec<T>::eri(H));
   } else {
     auto kern = k_sigma_ab<T, CH, false>;
-    HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)base));
+    HQ_TRY(allow_max_smem(kern));
     kern<<<(unsigned)B->Na, 256, base, s>>>(c, sig, A, Prec<T>::eri(H));
   }
   HQ_LAUNCH_CHECK();

@@ -357,7 +357,7 @@ static int launch(const Args& a, cudaStream_t s) {
     return fail(HINQS_ERR_ARG, "tensor-core sigma: tile of %zu bytes exceeds shared memory (n_orb=%d)",
                 bytes, a.n);
   auto kern = k_sigma_ab_tc<NW, SPLIT>;
-  HQ_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  HQ_TRY(allow_max_smem(kern));
   kern<<<(unsigned)a.Na, kThreads, bytes, s>>>(b);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
