@@ -117,6 +117,10 @@ extern "C" int hinqs_ham_create(const double* h, const double* eri, int n_orb, i
   cudaMemcpyAsync(H->eri, eri, n4 * sizeof(double), cudaMemcpyDeviceToDevice, s);
   k_to_f32<<<(int)std::min<int64_t>(ceil_div(n2, 256), 1024), 256, 0, s>>>(H->h, H->h32, n2);
   k_to_f32<<<(int)std::min<int64_t>(ceil_div(n4, 256), 4096), 256, 0, s>>>(H->eri, H->eri32, n4);
+  if ((rc = tc_tables_build(H, s)) < 0) {
+    hinqs_ham_destroy(H);
+    return rc;
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     hinqs_ham_destroy(H);
@@ -134,6 +138,8 @@ extern "C" int hinqs_ham_destroy(hinqs_ham* H) {
   dfree(H->eri, s);
   dfree(H->h32, s);
   dfree(H->eri32, s);
+  dfree(H->tc_bhi, s);
+  dfree(H->tc_blo, s);
   delete H;
   return HINQS_OK;
 }

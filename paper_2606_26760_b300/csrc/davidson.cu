@@ -28,6 +28,7 @@ int check_triplet(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_l
                   const hinqs_links_s* lb, const char* who);
 
 constexpr int kMaxSub = 32;
+constexpr int kRRThreads = 128;  // threads of the projected eigensolver
 constexpr int kRitzStride = kMaxSub + 2;  // (theta, y[kMaxSub], pad) per Ritz pair
 constexpr int kRedGrid = 2 * kNumSMs;
 constexpr int kRedThreads = 256;
@@ -200,12 +201,19 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
 
 // Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
 // ldg; S == NULL means S = I) by cyclic Jacobi with the round-robin parallel
-// ordering, in ONE WARP (warp-synchronous: m <= 32).  With S the pencil is reduced
+// ordering, in one block of kRRThreads threads (m <= kMaxSub).  FP64 runs at a small
+// fraction of the FP32 rate on this part and one warp issues to one sub-partition's
+// FP64 unit, so the rotation updates are spread over four warps; each rotation's
+// tangent is solved in FP32 and its cosine refined to FP64 accuracy by Newton steps
+// on 1/sqrt(1 + t^2), which keeps every rotation orthogonal to FP64 rounding while
+// avoiding FP64 division and square root in the serial part of each step (a rotation
+// that zeroes A_pq only to FP32 accuracy is still a valid Jacobi rotation; the
+// remainder is removed by later sweeps).  With S the pencil is reduced
 // to C = L^-1 G L^-T by the Cholesky factor S = L L^T and eigenvectors are mapped
 // back, y = L^-T z, so that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest
 // |component| > 0).  If all != NULL every eigenpair is written in ascending order,
 // all[j * kRitzStride] = lambda_j, all[j * kRitzStride + 1 ..] = y_j.
-__global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg, int m,
+__global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G, int ldg, int m,
                                            double* __restrict__ out,
                                            const double* __restrict__ S,
                                            double* __restrict__ all = nullptr) {
@@ -217,8 +225,9 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
   __shared__ int pr[kMaxSub / 2][2];
   __shared__ int order[kMaxSub];
   __shared__ int rank_of[kMaxSub];
-  const int lane = threadIdx.x;
+  const int lane = threadIdx.x;  // thread index in the block
   const unsigned full = 0xffffffffu;
+  __shared__ double red2[kRRThreads / 32][2];
   const int mm = m + (m & 1);  // even size for the tournament; the pad row/col is isolated
   bool use_s = false;
   if (S) {
@@ -233,13 +242,13 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         break;
       }
       const double ljj = sqrt(d);
-      for (int i = j + 1 + lane; i < m; i += 32) {
+      for (int i = j + 1 + lane; i < m; i += kRRThreads) {
         double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
         for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
         L[i][j] = v / ljj;
       }
       if (lane == 0) L[j][j] = ljj;
-      __syncwarp();
+      __syncthreads();
     }
   }
   if (use_s) {
@@ -251,7 +260,7 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         X[i][lane] = v / L[i][i];
       }
     }
-    __syncwarp();
+    __syncthreads();
     if (lane < m) {
       for (int i = 0; i < m; ++i) {
         double v = X[lane][i];
@@ -259,11 +268,11 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         A[i][lane] = v / L[i][i];
       }
     }
-    __syncwarp();
-    for (int i = lane; i < m * m; i += 32) X[i / m][i % m] = 0.5 * (A[i / m][i % m] + A[i % m][i / m]);
-    __syncwarp();
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) X[i / m][i % m] = 0.5 * (A[i / m][i % m] + A[i % m][i / m]);
+    __syncthreads();
   }
-  for (int i = lane; i < mm * mm; i += 32) {
+  for (int i = lane; i < mm * mm; i += kRRThreads) {
     const int r = i / mm, c = i % mm;
     double v = 0.0;
     if (r < m && c < m) v = use_s ? X[r][c] : 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
@@ -272,10 +281,10 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
     Q[r][c] = (r == c) ? 1.0 : 0.0;
   }
   if (lane < mm) order[lane] = lane;
-  __syncwarp();
+  __syncthreads();
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, dia = 0.0;
-    for (int i = lane; i < m * m; i += 32) {
+    for (int i = lane; i < m * m; i += kRRThreads) {
       const double v = A[i / m][i % m];
       if (i / m != i % m) off += v * v;
       else dia += v * v;
@@ -285,6 +294,18 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
       off += __shfl_xor_sync(full, off, o);
       dia += __shfl_xor_sync(full, dia, o);
     }
+    if ((lane & 31) == 0) {
+      red2[lane >> 5][0] = off;
+      red2[lane >> 5][1] = dia;
+    }
+    __syncthreads();
+    off = 0.0;
+    dia = 0.0;
+    for (int w = 0; w < kRRThreads / 32; ++w) {
+      off += red2[w][0];
+      dia += red2[w][1];
+    }
+    __syncthreads();
     if (off <= 1e-30 * dia || off == 0.0) break;
     for (int step = 0; step < mm - 1; ++step) {
       if (lane < mm / 2) {
@@ -299,16 +320,22 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         const double apq = A[p][q];
         double c = 1.0, sn = 0.0;
         if (apq != 0.0 && p < m && q < m) {
-          const double tau = (A[q][q] - A[p][p]) / (2.0 * apq);
-          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
-          c = 1.0 / sqrt(1.0 + t * t);
-          sn = t * c;
+          const float tau = (float)(A[q][q] - A[p][p]) / (2.0f * (float)apq);
+          float tf = 0.0f;  // tau overflowing FP32: A_pq is negligible, no rotation
+          if (isfinite(tau))
+            tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+          const double t = (double)tf, x = fma(t, t, 1.0);
+          double y = (double)rsqrtf((float)x);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          y = y * fma(-0.5 * x * y, y, 1.5);
+          c = y;
+          sn = t * y;
         }
         cs[lane][0] = c;
         cs[lane][1] = sn;
       }
-      __syncwarp();
-      for (int i = lane; i < (mm / 2) * mm; i += 32) {  // A <- J^T A (rows p, q)
+      __syncthreads();
+      for (int i = lane; i < (mm / 2) * mm; i += kRRThreads) {  // A <- J^T A (rows p, q)
         const int k = i / mm, col = i % mm;
         const int p = pr[k][0], q = pr[k][1];
         const double c = cs[k][0], sn = cs[k][1];
@@ -316,8 +343,8 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         A[p][col] = c * ap - sn * aq;
         A[q][col] = sn * ap + c * aq;
       }
-      __syncwarp();
-      for (int i = lane; i < (mm / 2) * mm; i += 32) {  // A <- A J, Q <- Q J (cols p, q)
+      __syncthreads();
+      for (int i = lane; i < (mm / 2) * mm; i += kRRThreads) {  // A <- A J, Q <- Q J (cols p, q)
         const int k = i / mm, row = i % mm;
         const int p = pr[k][0], q = pr[k][1];
         const double c = cs[k][0], sn = cs[k][1];
@@ -328,13 +355,13 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
         Q[row][p] = c * qp - sn * qq;
         Q[row][q] = sn * qp + c * qq;
       }
-      __syncwarp();
+      __syncthreads();
       if (lane == 0) {  // rotate the tournament, order[0] fixed
         const int last = order[mm - 1];
         for (int k = mm - 1; k > 1; --k) order[k] = order[k - 1];
         order[1] = last;
       }
-      __syncwarp();
+      __syncthreads();
     }
   }
   // rank of each eigenvalue (ascending, ties by index)
@@ -347,7 +374,7 @@ __global__ void __launch_bounds__(32) k_rr(const double* __restrict__ G, int ldg
     }
     rank_of[lane] = r;
   }
-  __syncwarp();
+  __syncthreads();
   // lane j maps eigenvector j back (z -> y) and writes it where its rank says
   if (lane < m) {
     const int col = lane, rank = rank_of[lane];
@@ -603,7 +630,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       info.n_sigma_fp64++;
       HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
-      k_rr<<<1, 32, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
+      k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
       k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
                                                             D, o.denom_floor, N, t, c.partial);
       k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -780,7 +807,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         double* th = c.small + 2 * kMaxSub;
         HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));
         k_init_pencil<<<1, 256, 0, c.s>>>(G1, nullptr, th);
-        k_rr<<<1, 32, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
+        k_rr<<<1, kRRThreads, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
@@ -826,7 +853,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       }
       bool restart_hard = false;
       for (;;) {
-        k_rr<<<1, 32, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
+        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
         k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
         k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);

@@ -67,7 +67,14 @@ struct hinqs_ham_s {
   double* eri = nullptr;    // [n*n][n*n] chemist (pq|rs), row pq, column rs
   float* h32 = nullptr;
   float* eri32 = nullptr;
+  // tensor-core operand rows (n <= kTcMaxOrb): BF16 hi/lo of (pq|rs) over the folded
+  // pairs r >= s, [n*n][8*tc_KB], zero-padded
+  uint16_t* tc_bhi = nullptr;
+  uint16_t* tc_blo = nullptr;
+  int tc_KB = 0;
 };
+
+constexpr int kTcMaxOrb = 32;
 
 // Sorted unique alpha and beta strings of the product subspace.
 struct hinqs_subspace_s {
@@ -110,6 +117,10 @@ struct hinqs_links_s {
   int ell_width = 0;
   int2* sell = nullptr;
   int* scount = nullptr;
+  // the same slots for the tensor-core gather: {J, sign * (kpart + 1)} with kpart the
+  // byte offset of the folded pair kf = max(p,q)(max(p,q)+1)/2 + min(p,q) inside a
+  // K-major core-matrix row, (kf / 8) * 128 + (kf % 8) * 2
+  int2* tcell = nullptr;
   // all links as packed records for the row products: element offset of the linked
   // row (J * other dimension, uint32) with the element: rec32 {off, float bits},
   // rec64 {off, 0, double bits}; null when N_a * N_b >= 2^32
@@ -138,16 +149,22 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
                        cudaStream_t s);
 // HINQS_ERR_TIMEOUT (and clears the flag) if a tensor-core kernel's bounded wait ran out
 int tc_error_check(cudaStream_t s);
+int tc_tables_build(hinqs_ham_s* H, cudaStream_t s);
 
 // Opt-in shared-memory limit of the current device (bytes per block).
 int smem_optin_limit();
 // Raise a kernel's dynamic shared-memory cap to the device's opt-in limit.  The cap
 // is a property of the kernel shared by every host thread, so it is always set to
 // the same value: a per-launch value would race between concurrent solves.
+// The carveout preference asks for the largest shared-memory split of the unified
+// L1/shared storage, so that several large-tile CTAs can be resident on one SM.
 template <typename K>
 int allow_max_smem(K kern) {
-  const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             smem_optin_limit());
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_optin_limit());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
   return e == cudaSuccess ? HINQS_OK : cuda_fail(e, "cudaFuncSetAttribute", __FILE__, __LINE__);
 }
 

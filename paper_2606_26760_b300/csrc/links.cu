@@ -155,23 +155,40 @@ __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n
   }
 }
 
-// Slot-major copy of the single links plus the diagonal pseudo-links of each row.
+// Slot-major copy of the single links plus the diagonal pseudo-links of each row,
+// and the same slots with the pair replaced by its tensor-core operand offset.
+__device__ __forceinline__ int tc_kpart(int pair, int n) {
+  const int p = pair / n, q = pair % n;
+  const int kf = p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p;
+  return (kf >> 3) * 128 + (kf & 7) * 2;
+}
+
 __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
                             const int64_t* __restrict__ srp, const int2* __restrict__ sl,
-                            int width, int2* __restrict__ ell, int* __restrict__ cnt) {
+                            int width, int2* __restrict__ ell, int2* __restrict__ tcell,
+                            int* __restrict__ cnt) {
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
        I += (int64_t)gridDim.x * blockDim.x) {
     int k = 0;
-    for (int64_t q = srp[I]; q < srp[I + 1]; ++q, ++k) ell[(int64_t)k * N + I] = sl[q];
+    for (int64_t q = srp[I]; q < srp[I + 1]; ++q, ++k) {
+      const int2 l = sl[q];
+      ell[(int64_t)k * N + I] = l;
+      const int kp = tc_kpart((l.y > 0 ? l.y : -l.y) - 1, n) + 1;
+      tcell[(int64_t)k * N + I] = make_int2(l.x, l.y > 0 ? kp : -kp);
+    }
     uint64_t o = S[I];
     while (o) {
       int j = __ffsll((long long)o) - 1;
       o &= o - 1;
       ell[(int64_t)k * N + I] = make_int2((int)I, j * n + j + 1);
+      tcell[(int64_t)k * N + I] = make_int2((int)I, tc_kpart(j * n + j, n) + 1);
       ++k;
     }
     cnt[I] = k;
-    for (; k < width; ++k) ell[(int64_t)k * N + I] = make_int2(0, 0);
+    for (; k < width; ++k) {
+      ell[(int64_t)k * N + I] = make_int2(0, 0);
+      tcell[(int64_t)k * N + I] = make_int2(0, 0);
+    }
   }
 }
 
@@ -226,6 +243,7 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->VT64, s);
   dfree(L->VT32, s);
   dfree(L->sell, s);
+  dfree(L->tcell, s);
   dfree(L->scount, s);
   dfree(L->rec32, s);
   dfree(L->rec64, s);
@@ -304,9 +322,10 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
   if (!rc) {
     L->ell_width = L->max_srow + L->n_e;
     if (!(rc = dalloc(&L->sell, (size_t)std::max(1, L->ell_width) * N, s)) &&
+        !(rc = dalloc(&L->tcell, (size_t)std::max(1, L->ell_width) * N, s)) &&
         !(rc = dalloc(&L->scount, N, s))) {
       k_build_ell<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs), 256, 0, s>>>(
-          L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->scount);
+          L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->tcell, L->scount);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "k_build_ell", __FILE__, __LINE__);
     }

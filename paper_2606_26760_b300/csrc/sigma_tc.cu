@@ -6,16 +6,21 @@
 //   D(Ja,Ib;rs)   = sum_{beta singles Ib -> Jb with pair rs} s_b C(Ja,Jb)
 //                   + [rs = jj, j in Ib] C(Ja,Ib).
 //
-// One CTA per alpha string Ja.  The (pq|rs) columns of Ja's alpha singles form
-// the B operand [NW x K] and each tile of 128 beta strings forms the A operand
-// D [128 x K], both BF16 in shared memory (K-major, canonical no-swizzle layout of
-// 8x16-byte core matrices); K runs over the folded pairs r >= s (the integral is
-// symmetric in r,s and a beta string contributes at most one of rs, sr), padded
-// to a multiple of 16.  One thread issues the tcgen05.mma chain into an FP32
-// accumulator in tensor memory; the four warps read their 32 lanes back with
-// tcgen05.ld and add s_a E into sigma with coalesced atomics.
-// SPLIT = 3 represents each operand as hi + lo BF16 terms and accumulates
-// hi*hi + hi*lo + lo*hi (about 16 significant bits); SPLIT = 1 uses hi only.
+// Work unit: one alpha string Ja and a chunk of at most NW of its alpha singles.
+// The (pq|.) rows of those singles form the B operand [NW x K], copied from a
+// BF16 table prepared with the Hamiltonian (the sign of the single flips the BF16
+// sign bits); each tile of 128 beta strings forms the A operand D [128 x K],
+// gathered from the row C(Ja, :).  Both are BF16 in shared memory (K-major,
+// canonical no-swizzle layout of 8x16-byte core matrices); K runs over the folded
+// pairs r >= s (the integral is symmetric in r,s and a beta string contributes at
+// most one of rs, sr), padded to a multiple of 16.  One thread issues the
+// tcgen05.mma chain into an FP32 accumulator in tensor memory.  With two stages the
+// gather of tile t+1 overlaps the MMA of tile t, each stage with its own A buffer,
+// tensor-memory columns and mbarrier.  The accumulator is read back with tcgen05.ld
+// (lane = beta string) and added into sigma with coalesced reductions.  CTAs are
+// persistent (at most what shared and tensor memory hold per SM) and stride over
+// the alpha strings.  SPLIT = 3 represents each operand as hi + lo BF16 terms and
+// accumulates hi*hi + hi*lo + lo*hi (about 16 significant bits); SPLIT = 1 uses hi.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -29,7 +34,7 @@ __device__ int g_tc_error = 0;  // set by a CTA whose bounded wait ran out
 
 namespace tc {
 
-constexpr int kThreads = 128;
+constexpr int kThreads = 256;
 constexpr int kTileM = 128;
 constexpr long long kWaitLimit = 1ll << 26;  // try_wait polls before giving up
 
@@ -115,70 +120,60 @@ __device__ __forceinline__ void fence_proxy_async() {
 
 struct Args {
   int64_t Na, Nb;
-  int n, K, KB;  // folded pairs, padded K / 8
+  int n, KB;  // KB = padded folded K / 8 (16-byte chunks per operand row)
   const int64_t* a_srow;
   const int2* a_slink;
-  const int2* b_ell;
+  const int2* b_ell;  // slot-major {Jb, sign * (kpart + 1)} (tensor-core gather slots)
   const int* b_cnt;
-  const float* eri;  // FP32 (pq|rs), [n2][n2]
+  const uint4* Bhi;  // [n*n][KB] BF16 rows of (pq|.) over the folded pairs
+  const uint4* Blo;  // low parts (SPLIT = 3)
   const float* C;
   float* sig;
   int crow_smem;  // stage the row C(Ja, :) in shared memory
-  int vec4;       // N_b % 4 == 0: float4 atomics are aligned
 };
 
-__device__ __forceinline__ int fold_index(int r, int s) {
-  if (r < s) {
-    int t = r;
-    r = s;
-    s = t;
-  }
-  return r * (r + 1) / 2 + s;
+// Shared-memory bytes of one CTA (the layout of the kernel below).
+__host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int KB, int64_t Nb,
+                                             bool crow) {
+  const size_t np = SPLIT == 3 ? 2 : 1;
+  size_t x = STAGES * np * (size_t)kTileM * KB * 16 + np * (size_t)NW * KB * 16 + 32 + 4 * NW;
+  x = (x + 15) & ~(size_t)15;
+  if (crow) x += 4 * (size_t)Nb;
+  return x;
 }
 
-template <int NW, int SPLIT>
+// Persistent CTAs of 8 warps; each takes alpha strings Ja = blockIdx.x, +gridDim.x, ...
+// and, per chunk of at most NW alpha singles of Ja, runs the beta tiles through a
+// STAGES-deep pipeline: while the MMA of tile t runs, the warps gather D for tile
+// t+1 into the other A buffer; then they read tile t's accumulator (its own TMEM
+// columns) and add it into sigma with coalesced reductions (lane = beta string).
+template <int NW, int SPLIT, int STAGES>
 __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const int KB = A.KB, Kp = KB * 8, n = A.n, n2 = n * n;
-  // each A region also holds the [16][kTileM] FP32 epilogue staging, so at least 8 KB
-  const uint32_t a_bytes = max((uint32_t)kTileM * Kp * 2, 16u * kTileM * 4u);
-  const uint32_t b_bytes = (uint32_t)NW * Kp * 2;
-  unsigned char* a_hi = smem;
-  unsigned char* a_lo = smem + a_bytes;
-  unsigned char* b_hi = smem + (SPLIT == 3 ? 2 : 1) * a_bytes;
-  unsigned char* b_lo = b_hi + b_bytes;
-  unsigned char* tail = b_hi + (SPLIT == 3 ? 2 : 1) * b_bytes;
-  uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 8);
-  int* tgt = reinterpret_cast<int*>(tail + 16);          // [NW]
-  int* unfold = reinterpret_cast<int*>(tail + 16 + 4 * NW);  // [Kp] -> r*n+s, or -1
-  int* wait_ok = reinterpret_cast<int*>(tail + 12);
-  // epilogue staging [16][kTileM] reuses the A tile, which the completed MMA no longer reads
-  float* stage = reinterpret_cast<float*>(a_hi);
-  float* crow_s = reinterpret_cast<float*>(tail + 16 + 4 * NW + 4 * Kp);  // [Nb] when A.crow_smem
-
-  const int64_t Ja = blockIdx.x;
-  const int64_t a_beg = A.a_srow[Ja], a_end = A.a_srow[Ja + 1];
-  if (a_beg == a_end) return;
+  constexpr int NP = SPLIT == 3 ? 2 : 1;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KB = A.KB;
+  const int64_t Nb = A.Nb;
+  const uint32_t a_bytes = (uint32_t)kTileM * KB * 16;
+  const uint32_t b_bytes = (uint32_t)NW * KB * 16;
+  unsigned char* a_buf = smem;                              // [STAGES][NP][a_bytes]
+  unsigned char* b_buf = smem + STAGES * NP * a_bytes;      // [NP][b_bytes]
+  unsigned char* tail = b_buf + NP * b_bytes;
+  uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);       // [2]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 16);
+  int* tgt = reinterpret_cast<int*>(tail + 32);             // [NW]
+  float* crow_s = reinterpret_cast<float*>(
+      smem + ((STAGES * NP * a_bytes + NP * b_bytes + 32 + 4 * NW + 15) & ~15u));
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar + 1)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  for (int k = tid; k < Kp; k += kThreads) {
-    int v = -1;
-    if (k < A.K) {
-      int r = 0;
-      while ((r + 1) * (r + 2) / 2 <= k) ++r;
-      v = r * n + (k - r * (r + 1) / 2);
-    }
-    unfold[k] = v;
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(NW));
+                 "r"(STAGES * NW));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   fence_before();
@@ -186,206 +181,268 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t idesc = make_idesc(kTileM, NW);
-  const float* crow = A.C + Ja * A.Nb;
-  if (A.crow_smem) {
-    for (int64_t j = tid; j < A.Nb; j += kThreads) crow_s[j] = crow[j];
-    crow = crow_s;
-  }
-  uint32_t phase = 0;
+  const uint32_t sbo = (uint32_t)KB * 128;
+  uint32_t ph0 = 0, ph1 = 0;
   bool ok = true;
-  __syncthreads();
+  const int T = (int)((Nb + kTileM - 1) / kTileM);
 
-  for (int64_t a0 = a_beg; a0 < a_end && ok; a0 += NW) {
-    const int cnt = (int)min64(NW, a_end - a0);
-    // B operand: rows a = alpha singles of Ja, columns k = folded rs
-    for (int i0 = tid; i0 < NW * Kp; i0 += 8 * kThreads) {
-      // eight integral values in flight before any shared-memory store
-      float v[8];
+  // zero one A stage (both planes)
+  auto zero_stage = [&](int st) {
+    uint4* z = reinterpret_cast<uint4*>(a_buf + (size_t)st * NP * a_bytes);
+    const int cnt16 = (int)(NP * a_bytes / 16);
+    for (int i = tid; i < cnt16; i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+  };
+  // gather D for beta tile t into stage st: row m = beta string, two threads per row
+  auto build_d = [&](int t, int st, const float* crow) {
+    const int m = tid & (kTileM - 1), hh = tid >> 7;
+    unsigned char* ah = a_buf + (size_t)st * NP * a_bytes + (m >> 3) * (KB * 128) + (m & 7) * 16;
+    const int64_t Ib = (int64_t)t * kTileM + m;
+    if (Ib < Nb) {
+      const int nk = __ldg(A.b_cnt + Ib);
+      const int2* __restrict__ ell = A.b_ell + Ib;
+      for (int k0 = hh; k0 < nk; k0 += 16) {
+        int2 l[8];  // eight link records in flight before any shared-memory store
 #pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = i0 + u * kThreads;
-        v[u] = 0.0f;
-        if (i < NW * Kp) {
-          const int a = i / Kp, k = i - a * Kp;
-          const int rs = unfold[k];
-          if (a < cnt && rs >= 0) {
-            const int sp = __ldg(&A.a_slink[a0 + a].y);
-            const int pq = (sp > 0 ? sp : -sp) - 1;
-            v[u] = __ldg(A.eri + (int64_t)pq * n2 + rs);
-            if (sp < 0) v[u] = -v[u];
-          }
+        for (int u = 0; u < 8; ++u)
+          l[u] = (k0 + 2 * u < nk) ? __ldg(ell + (int64_t)(k0 + 2 * u) * Nb) : make_int2(0, 0);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (k0 + 2 * u >= nk) break;
+          const int y = l[u].y;
+          float v = crow[l[u].x];
+          if (y < 0) v = -v;
+          const int off = (y > 0 ? y : -y) - 1;  // kpart of the folded pair
+          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+          *reinterpret_cast<__nv_bfloat16*>(ah + off) = hi;
+          if (SPLIT == 3)
+            *reinterpret_cast<__nv_bfloat16*>(ah + a_bytes + off) =
+                __float2bfloat16_rn(v - __bfloat162float(hi));
         }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int i = i0 + u * kThreads;
-        if (i >= NW * Kp) break;
-        const int a = i / Kp, k = i - a * Kp;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(v[u]);
-        *reinterpret_cast<__nv_bfloat16*>(b_hi + tile_off(a, k, KB)) = hi;
-        if (SPLIT == 3)
-          *reinterpret_cast<__nv_bfloat16*>(b_lo + tile_off(a, k, KB)) =
-              __float2bfloat16_rn(v[u] - __bfloat162float(hi));
       }
     }
-    if (tid < NW) tgt[tid] = (tid < cnt) ? A.a_slink[a0 + tid].x : 0;
-
-    for (int64_t ib0 = 0; ib0 < A.Nb && ok; ib0 += kTileM) {
-      // A operand: row m = beta string ib0 + m, zero then scatter D entries
-      const int m = tid;
-      const int64_t Ib = ib0 + m;
-      for (int kb = 0; kb < KB; ++kb) {
-        *reinterpret_cast<uint4*>(a_hi + tile_off(m, kb * 8, KB)) = make_uint4(0, 0, 0, 0);
-        if (SPLIT == 3)
-          *reinterpret_cast<uint4*>(a_lo + tile_off(m, kb * 8, KB)) = make_uint4(0, 0, 0, 0);
+    fence_proxy_async();  // generic-proxy writes (zeroing and gather) -> tensor-core reads
+  };
+  // one thread issues the MMA chain of stage st and commits it to mbar[st]
+  auto issue = [&](int st) {
+    const uint32_t ah = smem_u32(a_buf + (size_t)st * NP * a_bytes), al = ah + a_bytes;
+    const uint32_t bh = smem_u32(b_buf), bl = bh + b_bytes;
+    const uint32_t d = tmem + (uint32_t)(st * NW);
+    for (int kk = 0; kk < KB / 2; ++kk) {
+      const uint32_t off = (uint32_t)kk * 256;  // 16 K-elements = two core matrices
+      mma_bf16(d, make_desc(ah + off, 128, sbo), make_desc(bh + off, 128, sbo), idesc,
+               kk > 0 ? 1u : 0u);
+      if (SPLIT == 3) {
+        mma_bf16(d, make_desc(ah + off, 128, sbo), make_desc(bl + off, 128, sbo), idesc, 1u);
+        mma_bf16(d, make_desc(al + off, 128, sbo), make_desc(bh + off, 128, sbo), idesc, 1u);
       }
-      if (Ib < A.Nb) {
-        const int nk = __ldg(A.b_cnt + Ib);
-        const int2* __restrict__ ell = A.b_ell + Ib;
-        for (int k0 = 0; k0 < nk; k0 += 8) {
-          // eight link records in flight before any shared-memory store
-          int2 l[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u)
-            l[u] = (k0 + u < nk) ? __ldg(ell + (int64_t)(k0 + u) * A.Nb) : make_int2(0, 0);
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            if (k0 + u >= nk) break;
-            const int pair = (l[u].y > 0 ? l[u].y : -l[u].y) - 1;
-            float v = crow[l[u].x];
-            if (l[u].y < 0) v = -v;
-            const int kf = fold_index(pair / n, pair % n);
-            const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-            *reinterpret_cast<__nv_bfloat16*>(a_hi + tile_off(m, kf, KB)) = hi;
-            if (SPLIT == 3)
-              *reinterpret_cast<__nv_bfloat16*>(a_lo + tile_off(m, kf, KB)) =
-                  __float2bfloat16_rn(v - __bfloat162float(hi));
+    }
+    mma_commit(smem_u32(mbar + st));
+  };
+
+  for (int64_t Ja = blockIdx.x; Ja < A.Na && ok; Ja += gridDim.x) {
+    const int64_t a_beg = A.a_srow[Ja], a_end = A.a_srow[Ja + 1];
+    if (a_beg == a_end) continue;
+    const float* crow = A.C + Ja * Nb;
+    __syncthreads();  // the previous string's readers of crow_s, b_buf and tgt are done
+    if (A.crow_smem) {
+      for (int64_t j = tid; j < Nb; j += kThreads) crow_s[j] = crow[j];
+      crow = crow_s;
+    }
+    for (int64_t a0 = a_beg; a0 < a_end && ok; a0 += NW) {
+      const int cnt = (int)min64(NW, a_end - a0);
+      // B operand: the (pq|.) rows of the alpha singles, sign folded into the BF16 sign bits
+      for (int i = tid; i < NW * KB; i += kThreads) {
+        const int a = i / KB, kb = i - a * KB;
+        uint4 vh = make_uint4(0, 0, 0, 0), vl = make_uint4(0, 0, 0, 0);
+        if (a < cnt) {
+          const int sp = __ldg(&A.a_slink[a0 + a].y);
+          const int64_t row = (int64_t)((sp > 0 ? sp : -sp) - 1) * KB + kb;
+          vh = __ldg(A.Bhi + row);
+          if (SPLIT == 3) vl = __ldg(A.Blo + row);
+          if (sp < 0) {
+            vh.x ^= 0x80008000u, vh.y ^= 0x80008000u, vh.z ^= 0x80008000u, vh.w ^= 0x80008000u;
+            vl.x ^= 0x80008000u, vl.y ^= 0x80008000u, vl.z ^= 0x80008000u, vl.w ^= 0x80008000u;
           }
         }
+        *reinterpret_cast<uint4*>(b_buf + tile_off(a, kb * 8, KB)) = vh;
+        if (SPLIT == 3) *reinterpret_cast<uint4*>(b_buf + b_bytes + tile_off(a, kb * 8, KB)) = vl;
       }
-      fence_proxy_async();
+      if (tid < NW) tgt[tid] = (tid < cnt) ? A.a_slink[a0 + tid].x : 0;
+      for (int st = 0; st < STAGES; ++st) zero_stage(st);
+      __syncthreads();
+      build_d(0, 0, crow);
       fence_before();
       __syncthreads();
       fence_after();
-      if (tid == 0) {
-        const uint32_t sbo_a = (uint32_t)KB * 128, sbo_b = (uint32_t)KB * 128;
-        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi),
-                       bl = smem_u32(b_lo);
-        uint32_t acc = 0;
-        for (int kk = 0; kk < KB / 2; ++kk) {
-          const uint32_t off = (uint32_t)kk * 256;  // 16 K-elements = two core matrices
-          mma_bf16(tmem, make_desc(ah + off, 128, sbo_a), make_desc(bh + off, 128, sbo_b), idesc,
-                   acc);
-          acc = 1;
-          if (SPLIT == 3) {
-            mma_bf16(tmem, make_desc(ah + off, 128, sbo_a), make_desc(bl + off, 128, sbo_b),
-                     idesc, 1);
-            mma_bf16(tmem, make_desc(al + off, 128, sbo_a), make_desc(bh + off, 128, sbo_b),
-                     idesc, 1);
-          }
+      if (tid == 0) issue(0);
+
+      for (int t = 0; t < T; ++t) {
+        const int st = STAGES == 2 ? (t & 1) : 0;
+        if (STAGES == 2 && t + 1 < T) {
+          build_d(t + 1, st ^ 1, crow);  // overlaps the MMA of tile t
+          fence_before();
+          __syncthreads();
+          fence_after();
+          if (tid == 0) issue(st ^ 1);
         }
-        mma_commit(smem_u32(mbar));
-        // one thread polls the barrier (bounded) and tells the block
-        bool done = mbar_wait(smem_u32(mbar), phase);
-        if (!done) {
-          atomicExch(&g_tc_error, 1);
-          // a second bounded chance for the MMAs in flight before TMEM is freed
-          mbar_wait(smem_u32(mbar), phase);
-        }
-        *wait_ok = done ? 1 : 0;
-      }
-      __syncthreads();
-      if (!*wait_ok) {
-        ok = false;
-        break;
-      }
-      phase ^= 1u;
-      fence_after();
-      // epilogue: row m of E lives in TMEM lane m; warp w reads lanes 32w..32w+31
-      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+        // every thread waits (bounded) for tile t's MMA chain
+        // (warp-uniform, so that a warp reads tensor memory converged or not at all)
+        const bool done =
+            __all_sync(0xffffffffu, mbar_wait(smem_u32(mbar + st), st == 0 ? ph0 : ph1));
+        if (st == 0) ph0 ^= 1u;
+        else ph1 ^= 1u;
+        if (done) {
+          fence_after();
+          // epilogue: warp w reads TMEM lanes 32 (w % 4) .. +31 (beta strings) and the
+          // 16-column groups of its half; lane = beta string, so each reduction of one
+          // alpha target row is a coalesced 128-byte access
+          const int q = warp & 3;
+          const int64_t ib = (int64_t)t * kTileM + 32 * q + lane;
+          const uint32_t lane_base = (uint32_t)(32 * q) << 16;
 #pragma unroll 1
-      for (int c0 = 0; c0 < NW && c0 < cnt; c0 += 16) {
-        float e[16];
-        tmem_ld16(tmem + lane_base + (uint32_t)c0, e);
+          for (int c0 = 16 * (warp >> 2); c0 < cnt; c0 += 32) {
+            float e[16];
+            tmem_ld16(tmem + lane_base + (uint32_t)(st * NW + c0), e);
+            if (ib < Nb) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i) stage[i * kTileM + m] = e[i];
-        __syncthreads();
-        // transpose through shared memory: each thread adds four consecutive beta
-        // strings of one target row at a time (vector atomics, 4x fewer operations)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int idx = tid + j * kThreads;  // 0..511
-          const int ci = idx >> 5, m4 = (idx & 31) * 4;
-          const int a = c0 + ci;
-          const int64_t ib = ib0 + m4;
-          if (a < cnt && ib < A.Nb) {
-            float* dst = A.sig + (int64_t)tgt[a] * A.Nb + ib;
-            const float* src = stage + ci * kTileM + m4;
-            if (A.vec4 && ib + 3 < A.Nb) {
-              atomicAdd(reinterpret_cast<float4*>(dst), make_float4(src[0], src[1], src[2], src[3]));
-            } else {
-              for (int q = 0; q < 4 && ib + q < A.Nb; ++q) atomicAdd(dst + q, src[q]);
+              for (int i = 0; i < 16; ++i)
+                if (c0 + i < cnt) atomicAdd(A.sig + (int64_t)tgt[c0 + i] * Nb + ib, e[i]);
             }
           }
+          zero_stage(st);  // ready for the gather of tile t + STAGES
         }
-        __syncthreads();
+        fence_before();
+        if (__syncthreads_or(done ? 0 : 1)) {
+          ok = false;
+          if (tid == 0) {
+            atomicExch(&g_tc_error, 1);
+            // a second bounded chance for the MMAs in flight before TMEM is freed
+            mbar_wait(smem_u32(mbar + st), st == 0 ? ph0 ^ 1u : ph1 ^ 1u);
+            if (STAGES == 2 && t + 1 < T)
+              mbar_wait(smem_u32(mbar + (st ^ 1)), st == 0 ? ph1 : ph0);
+          }
+          __syncthreads();
+          break;
+        }
+        fence_after();
+        if (STAGES == 1 && t + 1 < T) {
+          build_d(t + 1, 0, crow);
+          fence_before();
+          __syncthreads();
+          fence_after();
+          if (tid == 0) issue(0);
+        }
       }
-      fence_before();
-      __syncthreads();
-      fence_after();
     }
-    __syncthreads();
   }
   fence_before();
   __syncthreads();
   if (warp == 0) {
     fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NW));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(STAGES * NW));
   }
 }
 
-template <int NW, int SPLIT>
-static int launch(const Args& a, cudaStream_t s) {
-  const int Kp = a.KB * 8;
-  const size_t a_region = std::max<size_t>((size_t)kTileM * Kp * 2, 16 * kTileM * 4);
-  size_t bytes = (size_t)(SPLIT == 3 ? 2 : 1) * (a_region + (size_t)NW * Kp * 2) + 16 + 4 * NW +
-                 4 * Kp + 64;
+// BF16 (hi, lo) rows of the folded integral matrix: row pq, column k < K holds
+// (pq|rs) for the k-th folded pair (r >= s), columns K..8KB-1 are zero.
+__global__ void k_btable(const float* __restrict__ eri32, int n, int K, int KB,
+                         __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int n2 = n * n, Kp = KB * 8;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n2 * Kp;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int pq = (int)(i / Kp), k = (int)(i % Kp);
+    float v = 0.0f;
+    if (k < K) {
+      int r = 0;
+      while ((r + 1) * (r + 2) / 2 <= k) ++r;
+      v = eri32[(int64_t)pq * n2 + r * n + (k - r * (r + 1) / 2)];
+    }
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+template <int NW, int SPLIT, int STAGES>
+static int launch(const Args& a, bool crow, cudaStream_t s) {
   Args b = a;
-  b.crow_smem = (bytes + 4 * a.Nb <= 200 * 1024) ? 1 : 0;
-  if (b.crow_smem) bytes += 4 * a.Nb;
-  if (bytes > 220 * 1024)
-    return fail(HINQS_ERR_ARG, "tensor-core sigma: tile of %zu bytes exceeds shared memory (n_orb=%d)",
-                bytes, a.n);
-  auto kern = k_sigma_ab_tc<NW, SPLIT>;
+  b.crow_smem = crow ? 1 : 0;
+  const size_t bytes = smem_bytes(NW, SPLIT, STAGES, a.KB, a.Nb, crow);
+  auto kern = k_sigma_ab_tc<NW, SPLIT, STAGES>;
   HQ_TRY(allow_max_smem(kern));
-  kern<<<(unsigned)a.Na, kThreads, bytes, s>>>(b);
+  // resident CTAs per SM: as many as shared memory, registers and threads allow, but
+  // never more than the 512 tensor-memory columns hold (padding the shared-memory
+  // request keeps the scheduler there, so that no CTA waits in tcgen05.alloc for
+  // another to finish).  228 KB of shared memory per SM, 1 KB reserved per CTA.
+  const int cap = 512 / (STAGES * NW);
+  cudaFuncAttributes fa;
+  HQ_CUDA(cudaFuncGetAttributes(&fa, kern));
+  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = 65536 / (warp_regs * (kThreads / 32));
+  const int by_threads = 2048 / kThreads;
+  size_t req = bytes;
+  if ((int)(233472 / (req + 1024)) > cap) req = 233472 / (cap + 1);  // 1 KB margin
+  const int per_sm = std::min(std::min(cap, (int)(233472 / (req + 1024))), std::min(by_regs, by_threads));
+  if (per_sm < 1)
+    return fail(HINQS_ERR_ARG, "tensor-core sigma: a CTA of %zu bytes does not fit an SM", bytes);
+  const int grid = (int)std::min<int64_t>(a.Na, (int64_t)per_sm * kNumSMs);
+  kern<<<grid, kThreads, req, s>>>(b);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
 
+// Largest configuration that fits: two stages with the C row in shared memory, then
+// without the row, then one stage.
+template <int NW, int SPLIT>
+static int launch_fit(const Args& a, cudaStream_t s) {
+  const size_t lim = (size_t)smem_optin_limit();
+  if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 2>(a, true, s);
+  if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 2>(a, false, s);
+  if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 1>(a, true, s);
+  if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 1>(a, false, s);
+  return fail(HINQS_ERR_ARG, "tensor-core sigma: operand tiles exceed shared memory (n_orb=%d)", a.n);
+}
+
 }  // namespace tc
+
+int tc_tables_build(hinqs_ham_s* H, cudaStream_t s) {
+  const int n = H->n;
+  if (n > kTcMaxOrb) return HINQS_OK;  // the tensor-core path is not offered
+  const int K = n * (n + 1) / 2;
+  H->tc_KB = (int)ceil_div(K, 16) * 2;
+  const int64_t cnt = (int64_t)n * n * H->tc_KB * 8;
+  HQ_TRY(dalloc(&H->tc_bhi, cnt, s));
+  HQ_TRY(dalloc(&H->tc_blo, cnt, s));
+  tc::k_btable<<<(unsigned)std::min<int64_t>(ceil_div(cnt, 256), 1024), 256, 0, s>>>(
+      H->eri32, n, K, H->tc_KB, reinterpret_cast<__nv_bfloat16*>(H->tc_bhi),
+      reinterpret_cast<__nv_bfloat16*>(H->tc_blo));
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
 
 int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                        const hinqs_links_s* lb, const float* c, float* sig, int split,
                        cudaStream_t s) {
+  if (!H->tc_bhi)
+    return fail(HINQS_ERR_ARG, "tensor-core sigma: n_orb=%d above %d", H->n, kTcMaxOrb);
   tc::Args a;
   a.Na = B->Na;
   a.Nb = B->Nb;
   a.n = H->n;
-  a.K = H->n * (H->n + 1) / 2;
-  a.KB = (int)ceil_div(a.K, 16) * 2;
+  a.KB = H->tc_KB;
   a.a_srow = la->srow_ptr;
   a.a_slink = la->slink;
-  a.b_ell = lb->sell;
+  a.b_ell = lb->tcell;
   a.b_cnt = lb->scount;
-  a.eri = H->eri32;
+  a.Bhi = reinterpret_cast<const uint4*>(H->tc_bhi);
+  a.Blo = reinterpret_cast<const uint4*>(H->tc_blo);
   a.C = c;
   a.sig = sig;
   a.crow_smem = 0;
-  a.vec4 = (B->Nb % 4 == 0) ? 1 : 0;
   const bool wide = la->max_srow > 64;
-  if (split == 3) return wide ? tc::launch<128, 3>(a, s) : tc::launch<64, 3>(a, s);
-  return wide ? tc::launch<128, 1>(a, s) : tc::launch<64, 1>(a, s);
+  if (split == 3) return wide ? tc::launch_fit<128, 3>(a, s) : tc::launch_fit<64, 3>(a, s);
+  return wide ? tc::launch_fit<128, 1>(a, s) : tc::launch_fit<64, 1>(a, s);
 }
 
 int tc_error_check(cudaStream_t s) {

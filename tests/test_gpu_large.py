@@ -1,0 +1,165 @@
+"""The differentiation (n=20, 7/7, 5000 x 5000 strings, 2.5e7 determinants) and
+large (n=26, 7/7, 20000 x 20000 strings, 4e8 determinants) workloads at full size.
+
+Exact oracle solves are out of reach at these sizes, so parity is checked on what
+the oracle computes one output at a time (sampled sigma rows), and on properties
+that hold at any size: RDM traces, partial traces and symmetries, the energy
+identity E = sum h gamma + 1/2 sum (pq|rs) Gamma + E_nuc, spin marginals that sum
+to one, and central finite differences of the energy against the Hellmann-Feynman
+gradient (1-RDM for h, 2-RDM / 2 summed over the symmetry orbit for (pq|rs)).
+
+Tolerances.  Sampled FP64 sigma rows: 1e-11 relative to max|sigma| (as in the
+small parity tests).  Energy identity: 1e-9 Ha.  Finite differences with step
+eps = 1e-5: the warm-started solves stop at a residual r <= 1e-8, so each energy is
+within r^2 / gap ~ 1e-15 Ha of the eigenvalue, and its FP64 rounding is ~1e-13 Ha;
+(E+ - E-) / (2 eps) is then within ~1e-8 of the derivative, truncation O(eps^2)
+is smaller still, and the test allows 2e-6 + 2e-6 |g|."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+hq = pytest.importorskip("paper_2606_26760_b300")
+
+
+def _setup(w, h=None, eri=None):
+    h = torch.tensor(w["h"], device="cuda") if h is None else h
+    eri = torch.tensor(w["eri"], device="cuda") if eri is None else eri
+    ham = hq.Hamiltonian(h, eri, w["n_alpha"], w["n_beta"], w["e_nuc"])
+    return ham
+
+
+@pytest.fixture(scope="module")
+def diff_case():
+    w = synth.workload("differentiation")
+    ham = _setup(w)
+    sub = hq.build_subspace(w["alpha"], w["beta"], w["n_orb"], w["n_alpha"], w["n_beta"])
+    la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
+    res = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_MIXED,
+                      inner_precision=hq.PREC_FP32_BF16AB, tol_residual=1e-8, tol_energy=1e-11,
+                      max_iter=1000)
+    assert res.status == hq.OK
+    g1, g2 = hq.rdm(sub, la, lb, res.c)
+    return w, ham, sub, la, lb, res, g1, g2
+
+
+def test_differentiation_sampled_sigma_rows(diff_case):
+    w, ham, sub, la, lb, res, _, _ = diff_case
+    H = oracle.Ham(w["h"], w["eri"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    sa, sb = oracle.build_subspace(w["alpha"], w["beta"], w["n_alpha"], w["n_beta"])
+    c = synth.random_vector(sub.N, 21)
+    got = hq.sigma(ham, sub, la, lb, torch.tensor(c, device="cuda")).cpu().numpy()
+    rng = np.random.default_rng(7)
+    rows = np.sort(np.concatenate([rng.choice(sub.N, 48, replace=False),
+                                   [0, sub.N - 1, sub.Nb - 1, sub.Nb]]))
+    ref = oracle.sigma(H, sa, sb, c, rows=rows)
+    scale = np.max(np.abs(got))
+    assert np.max(np.abs(got[rows] - ref)) <= 1e-11 * scale
+
+
+def test_differentiation_rdm_properties(diff_case):
+    w, ham, sub, la, lb, res, g1, g2 = diff_case
+    n, ne = w["n_orb"], w["n_alpha"] + w["n_beta"]
+    h = torch.tensor(w["h"], device="cuda")
+    eri = torch.tensor(w["eri"], device="cuda")
+    e_id = float((h * g1).sum() + 0.5 * (eri * g2).sum()) + w["e_nuc"]
+    assert abs(e_id - res.energy) < 1e-9
+    assert abs(float(torch.trace(g1)) - ne) < 1e-10
+    # sum_r Gamma_pqrr = <E_pq (N - 1)> = (N - 1) gamma_pq
+    part = torch.einsum("pqrr->pq", g2)
+    assert float((part - (ne - 1) * g1).abs().max()) < 1e-9
+    assert float((g1 - g1.T).abs().max()) < 1e-12
+    assert float((g2 - g2.permute(2, 3, 0, 1)).abs().max()) < 1e-11
+    assert float((g2 - g2.permute(1, 0, 3, 2)).abs().max()) < 1e-11
+    # spin marginals of the eigenvector and the teacher weights
+    pa, pb, wt = hq.spin_marginals(sub, res.c, want_w=True)
+    C2 = (res.c * res.c).reshape(sub.Na, sub.Nb)
+    assert float((pa - C2.sum(1) / C2.sum()).abs().max()) < 1e-14
+    assert float((pb - C2.sum(0) / C2.sum()).abs().max()) < 1e-14
+    assert abs(float(pa.sum()) - 1.0) < 1e-12 and abs(float(wt.sum()) - 1.0) < 1e-12
+
+
+def _orbit(p, q, r, s):
+    return {(p, q, r, s), (q, p, r, s), (p, q, s, r), (q, p, s, r),
+            (r, s, p, q), (s, r, p, q), (r, s, q, p), (s, r, q, p)}
+
+
+def test_differentiation_finite_differences(diff_case):
+    """Central differences (step 1e-5) of E on 50 random integral entries: 25 of h
+    (moving h_pq and h_qp together) and 25 of (pq|rs) (moving the 8-fold orbit)."""
+    w, ham, sub, la, lb, res, g1, g2 = diff_case
+    n = w["n_orb"]
+    eps = 1e-5
+    rng = np.random.default_rng(2606)
+    h0 = torch.tensor(w["h"], device="cuda")
+    e0 = torch.tensor(w["eri"], device="cuda")
+    g1h, g2h = g1.cpu().numpy(), g2.cpu().numpy()
+
+    def energy(h, eri):
+        hm = _setup(w, h, eri)
+        a, b = hq.string_links(hm, sub, 0), hq.string_links(hm, sub, 1)
+        r = hq.davidson(hm, sub, a, b, guess=res.c, precision=hq.DAVIDSON_MIXED,
+                        inner_precision=hq.PREC_FP32, tol_residual=1e-8, tol_energy=1e-11,
+                        max_iter=600)
+        assert r.status == hq.OK
+        return r.energy
+
+    worst = 0.0
+    for k in range(50):
+        if k < 25:
+            p, q = (int(x) for x in rng.integers(0, n, 2))
+            idx = {(p, q), (q, p)}
+            ana = sum(g1h[i] for i in idx)
+            dh = torch.zeros_like(h0)
+            for i in idx:
+                dh[i] = eps
+            ep, em = energy(h0 + dh, e0), energy(h0 - dh, e0)
+        else:
+            p, q, r, s = (int(x) for x in rng.integers(0, n, 4))
+            orb = _orbit(p, q, r, s)
+            ana = 0.5 * sum(g2h[i] for i in orb)
+            de = torch.zeros_like(e0)
+            for i in orb:
+                de[i] = eps
+            ep, em = energy(h0, e0 + de), energy(h0, e0 - de)
+        fd = (ep - em) / (2 * eps)
+        worst = max(worst, abs(fd - ana) / (1 + abs(ana)))
+        assert abs(fd - ana) <= 2e-6 + 2e-6 * abs(ana), (k, fd, ana)
+    assert worst < 2e-6
+
+
+def test_large_active_space_sampled_rows_and_solve():
+    """4e8 determinants: FP64 sigma on sampled rows vs the oracle; the mixed solve
+    (BF16 tensor-core inner products, FP64 refinement, subspace of 8) converges and
+    its RDMs reproduce its energy."""
+    w = synth.workload("large")
+    ham = _setup(w)
+    sub = hq.build_subspace(w["alpha"], w["beta"], w["n_orb"], w["n_alpha"], w["n_beta"])
+    assert sub.N == 400_000_000
+    la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
+    H = oracle.Ham(w["h"], w["eri"], w["e_nuc"], w["n_alpha"], w["n_beta"])
+    sa, sb = oracle.build_subspace(w["alpha"], w["beta"], w["n_alpha"], w["n_beta"])
+    c = synth.random_vector(sub.N, 22)
+    cd = torch.from_numpy(c).to("cuda")
+    got = hq.sigma(ham, sub, la, lb, cd)
+    rng = np.random.default_rng(8)
+    rows = np.sort(rng.choice(sub.N, 24, replace=False))
+    ref = oracle.sigma(H, sa, sb, c, rows=rows)
+    scale = float(got.abs().max())
+    gr = got[torch.from_numpy(rows).to("cuda")].cpu().numpy()
+    assert np.max(np.abs(gr - ref)) <= 1e-11 * scale
+    del got, cd, c
+    res = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_MIXED,
+                      inner_precision=hq.PREC_FP32_BF16AB, tol_residual=1e-5, tol_energy=1e-7,
+                      max_iter=300, max_subspace=8)
+    assert res.status == hq.OK and res.residual <= 1e-5
+    g1, g2 = hq.rdm(sub, la, lb, res.c)
+    h = torch.tensor(w["h"], device="cuda")
+    eri = torch.tensor(w["eri"], device="cuda")
+    e_id = float((h * g1).sum() + 0.5 * (eri * g2).sum()) + w["e_nuc"]
+    assert abs(e_id - res.energy) < 1e-8
+    assert abs(float(torch.trace(g1)) - 14.0) < 1e-9
