@@ -29,6 +29,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "sigma dets/s and Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B300"
+# FP64 FMA-chain rate of this B300 model (TFLOP/s), measured once with a probe kernel
+FP64_FMA_TFLOPS = 1.129
+# DRAM bytes (read + write) per launch from an ncu capture of the precision workload
+# (profiles/); None until captured for the current kernels
+PROFILED_TRAFFIC = {"same": None, "opposite": None}
 WORKLOAD = "precision"
 
 
@@ -463,38 +468,55 @@ def main():
     tt_variants = {k: best_time([r]) for k, r in runs.items() if k != "fp64"}
 
     # rooflines of the two halves of the step's product (FP32 vectors, BF16 tensor cores)
-    #   same-spin: algorithmic FMAs of the row products + diagonal + alpha-self x beta singles
+    #   same-spin: L2-resident row products; algorithmic bytes = the linked row
+    #     segments read (4 B per link and column) plus the alpha-self x beta-single
+    #     operands (8 B per single and column), against the L2 read bandwidth measured
+    #     here with a reduction over an L2-resident buffer
     #   opposite-spin: dense MMA FLOPs the tensor cores execute (and the useful share)
+    bytes_same = 4.0 * (la.n_links * sub.Nb + lb.n_links * sub.Na) + 8.0 * lb.n_singles * sub.Na
     fma_same = N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
     fma_opp_useful = la.n_singles * (lb.n_singles + sub.Nb * nb)
     K = n * (n + 1) // 2
     Kp = -(-K // 16) * 16
-    NW = 64 if la.max_row >= 0 and max_singles(la, sub.Na) <= 64 else 128
+    NW = 64 if max_singles(la, sub.Na) <= 64 else 128
     n_tiles = -(-sub.Nb // 128)
     mma_flops = 2.0 * 128 * NW * Kp * n_tiles * sub.Na * (-(-max_singles(la, sub.Na) // NW))
-    peaks = {"fp64_tflops": 1.129, "fp32_tflops": 68.82}  # measured FMA-chain peaks
-    import json as _json
+    l2buf = torch.ones(12 * 1024 * 1024, dtype=torch.float32, device=dev)  # 48 MB
+    for _ in range(3):
+        l2buf.sum()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(20):
+        l2buf.sum()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    l2_gbs = 20 * l2buf.numel() * 4 / (ev0.elapsed_time(ev1) / 1e3) / 1e9
+    del l2buf
     with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        mp = _json.load(f)
+        mp = json.load(f)
     bf16_peak = mp.get("bf16_tflops_sustained", 1371.7)
     n_inner = sum(r.n_sigma_fp32 for r in results) / len(results)
     share_same = n_inner * t_same
     share_opp = n_inner * t_opp
-    same_line = {"bound": "alu", "kernel": "hinqs_sigma_same_spin FP32 (k_spmm_rows x2, transposes)",
-                 "achieved": 2 * fma_same / t_same / 1e12, "peak": peaks["fp32_tflops"],
-                 "unit": "TFLOP/s", "frac": 2 * fma_same / t_same / 1e12 / peaks["fp32_tflops"],
-                 "traffic": None, "flops_per_launch": 2 * fma_same, "ms": 1e3 * t_same,
-                 "peak_source": "measured FP32 FMA chain on this B300 model"}
-    opp_line = {"bound": "tensor", "kernel": "hinqs_sigma_opposite_spin BF16 (k_sigma_ab_tc<64,1>)",
+    same_line = {"bound": "l2", "kernel": "hinqs_sigma_same_spin FP32 (k_spmm_rec4 x2 + transposes)",
+                 "achieved": bytes_same / t_same / 1e9, "peak": l2_gbs, "unit": "GB/s",
+                 "frac": bytes_same / t_same / 1e9 / l2_gbs,
+                 "traffic": PROFILED_TRAFFIC.get("same"), "bytes_per_launch": bytes_same,
+                 "fma_per_launch": fma_same, "ms": 1e3 * t_same,
+                 "peak_source": "L2 read bandwidth measured in this run (torch sum over a 48 MB "
+                                "L2-resident buffer)"}
+    opp_line = {"bound": "tensor", "kernel": "hinqs_sigma_opposite_spin BF16 (k_sigma_ab_tc)",
                 "achieved": mma_flops / t_opp / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": mma_flops / t_opp / 1e12 / bf16_peak, "traffic": None,
+                "frac": mma_flops / t_opp / 1e12 / bf16_peak,
+                "traffic": PROFILED_TRAFFIC.get("opposite"),
                 "flops_per_launch": mma_flops, "useful_flops_per_launch": 2 * fma_opp_useful,
                 "ms": 1e3 * t_opp, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
     roof = dict(same_line if share_same >= share_opp else opp_line)
     roof["other_half"] = opp_line if share_same >= share_opp else same_line
     roof["fp64_sigma"] = {"achieved": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12,
-                          "peak": peaks["fp64_tflops"],
-                          "frac": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12 / peaks["fp64_tflops"]}
+                          "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
+                          "frac": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12 / FP64_FMA_TFLOPS,
+                          "peak_source": "FP64 FMA-chain rate measured on this B300 model"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -69,7 +69,10 @@ extern "C" {
  * gather into D and a tcgen05 GEMM against (pq|rs) with FP32 accumulation in tensor
  * memory, operands BF16 (about 8 significant bits) ... */
 #define HINQS_PREC_FP32_BF16AB 2
-/* ... or operands split as hi + lo BF16 with hi*hi + hi*lo + lo*hi (about 16 bits) */
+/* ... or operands split as hi + lo BF16 with hi*hi + hi*lo + lo*hi (about 16 bits).
+ * In both modes, when n_orb > 32 or the operand tiles of the problem do not fit in
+ * shared memory (e.g. the split mode at n_orb = 26), the opposite-spin term is
+ * computed by the FP32 CUDA-core kernel of HINQS_PREC_FP32 instead (more accurate). */
 #define HINQS_PREC_FP32_BF16X3AB 3
 
 /* Davidson precision */

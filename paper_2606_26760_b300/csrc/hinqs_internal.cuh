@@ -75,6 +75,9 @@ struct hinqs_ham_s {
 };
 
 constexpr int kTcMaxOrb = 32;
+// sigma_ab_tc_launch: the operand tiles do not fit in shared memory (internal code;
+// the caller computes the opposite-spin term on CUDA cores instead)
+constexpr int kTcNoFit = 100;
 
 // Sorted unique alpha and beta strings of the product subspace.
 struct hinqs_subspace_s {
@@ -117,8 +120,8 @@ struct hinqs_links_s {
   int ell_width = 0;
   int2* sell = nullptr;
   int* scount = nullptr;
-  // the same slots for the tensor-core gather: {J, sign * (kpart + 1)} with kpart the
-  // byte offset of the folded pair kf = max(p,q)(max(p,q)+1)/2 + min(p,q) inside a
+  // the same slots for the tensor-core gather: {J, kpart | (sign < 0) << 31} with kpart
+  // the byte offset of the folded pair kf = max(p,q)(max(p,q)+1)/2 + min(p,q) inside a
   // K-major core-matrix row, (kf / 8) * 128 + (kf % 8) * 2
   int2* tcell = nullptr;
   // all links as packed records for the row products: element offset of the linked
@@ -158,10 +161,14 @@ int smem_optin_limit();
 // the same value: a per-launch value would race between concurrent solves.
 // The carveout preference asks for the largest shared-memory split of the unified
 // L1/shared storage, so that several large-tile CTAs can be resident on one SM.
+// The cap is the opt-in limit less the kernel's static shared memory.
 template <typename K>
 int allow_max_smem(K kern) {
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_optin_limit());
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem_optin_limit() - (int)fa.sharedSizeBytes);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              (int)cudaSharedmemCarveoutMaxShared);

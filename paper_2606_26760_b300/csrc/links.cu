@@ -173,15 +173,15 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
     for (int64_t q = srp[I]; q < srp[I + 1]; ++q, ++k) {
       const int2 l = sl[q];
       ell[(int64_t)k * N + I] = l;
-      const int kp = tc_kpart((l.y > 0 ? l.y : -l.y) - 1, n) + 1;
-      tcell[(int64_t)k * N + I] = make_int2(l.x, l.y > 0 ? kp : -kp);
+      const int kp = tc_kpart((l.y > 0 ? l.y : -l.y) - 1, n);
+      tcell[(int64_t)k * N + I] = make_int2(l.x, l.y > 0 ? kp : (int)((unsigned)kp | 0x80000000u));
     }
     uint64_t o = S[I];
     while (o) {
       int j = __ffsll((long long)o) - 1;
       o &= o - 1;
       ell[(int64_t)k * N + I] = make_int2((int)I, j * n + j + 1);
-      tcell[(int64_t)k * N + I] = make_int2((int)I, tc_kpart(j * n + j, n) + 1);
+      tcell[(int64_t)k * N + I] = make_int2((int)I, tc_kpart(j * n + j, n));
       ++k;
     }
     cnt[I] = k;

@@ -211,6 +211,95 @@ __global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, in
   }
 }
 
+// Opposite-spin 2-RDM with the rows staged in shared memory.  Block (J_a, chunk):
+// up to U alpha transitions (I_a, pq, s_a) of the ket J_a (diagonal first, then the
+// single links); the bra rows C(I_a, :) of the chunk and the ket row C(J_a, :) are
+// copied to shared memory.  The beta transitions, grouped by pair rs, are cut into
+// segments of at most kRdmSeg entries so that the lanes of a warp carry equal work;
+// a thread walks a segment once and updates U accumulators, one FP64 FMA per term:
+//   X[u][rs] += C(I_a,u, I_b) * s_b C(J_a, J_b),
+// then adds s_a X[u][rs] into gab[pq_u][rs].
+constexpr int kRdmSeg = 128;
+
+__global__ void k_seg_count(const int64_t* __restrict__ off, int n2, int64_t* __restrict__ cnt) {
+  for (int rs = blockIdx.x * blockDim.x + threadIdx.x; rs < n2; rs += gridDim.x * blockDim.x)
+    cnt[rs] = (off[rs + 1] - off[rs] + kRdmSeg - 1) / kRdmSeg;
+}
+__global__ void k_seg_fill(const int64_t* __restrict__ off, int n2,
+                           const int64_t* __restrict__ sstart, int4* __restrict__ seg) {
+  for (int rs = blockIdx.x * blockDim.x + threadIdx.x; rs < n2; rs += gridDim.x * blockDim.x) {
+    int64_t b = off[rs], q = sstart[rs];
+    for (; b < off[rs + 1]; b += kRdmSeg, ++q)
+      seg[q] = make_int4(rs, (int)(b - off[rs]), (int)min64(kRdmSeg, off[rs + 1] - b), 0);
+  }
+}
+
+template <int U>
+__global__ void __launch_bounds__(256) k_rdm_ab_staged(
+    const double* __restrict__ C, int64_t Nb, int n, const uint64_t* __restrict__ Sa,
+    const int64_t* __restrict__ a_srp, const int2* __restrict__ a_sl,
+    const int64_t* __restrict__ off, const int4* __restrict__ trans,
+    const int4* __restrict__ seg, int64_t nseg, double* __restrict__ gab) {
+  extern __shared__ __align__(16) double sm[];  // crow[Nb], rows[U][Nb]
+  __shared__ int tI[U], tpq[U], ts[U];
+  const int n2 = n * n;
+  const int64_t Ja = blockIdx.x;
+  const uint64_t x = Sa[Ja];
+  const int nd = __popcll(x);
+  const int64_t total = nd + (a_srp[Ja + 1] - a_srp[Ja]);
+  const int64_t t0 = (int64_t)blockIdx.y * U;
+  if (t0 >= total) return;
+  const int cnt = (int)min64(U, total - t0);
+  if (threadIdx.x < U) {
+    const int64_t t = t0 + threadIdx.x;
+    int I = (int)Ja, pq = 0, sg = 0;  // unused slots: zero sign, row J_a
+    if (threadIdx.x < cnt) {
+      if (t < nd) {
+        uint64_t o = x;
+        for (int k = 0; k < t; ++k) o &= o - 1;
+        const int i = __ffsll((long long)o) - 1;
+        pq = i * n + i;
+        sg = 1;
+      } else {
+        const int2 l = a_sl[a_srp[Ja] + (t - nd)];
+        I = l.x;
+        pq = (l.y > 0 ? l.y : -l.y) - 1;
+        sg = l.y > 0 ? 1 : -1;
+      }
+    }
+    tI[threadIdx.x] = I;
+    tpq[threadIdx.x] = pq;
+    ts[threadIdx.x] = sg;
+  }
+  __syncthreads();
+  double* crow = sm;
+  double* rows = sm + Nb;
+  for (int64_t j = threadIdx.x; j < Nb; j += blockDim.x) crow[j] = C[Ja * Nb + j];
+  for (int u = 0; u < U; ++u) {
+    const double* src = C + (int64_t)tI[u] * Nb;
+    for (int64_t j = threadIdx.x; j < Nb; j += blockDim.x) rows[u * Nb + j] = src[j];
+  }
+  __syncthreads();
+  for (int64_t q = threadIdx.x; q < nseg; q += blockDim.x) {
+    const int4 sgm = seg[q];
+    const int rs = sgm.x;
+    const int4* __restrict__ tr = trans + off[rs] + sgm.y;
+    double acc[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int k = 0; k < sgm.z; ++k) {
+      const int4 t = tr[k];  // {bra I_b, ket J_b, s_b}
+      const double cj = t.z > 0 ? crow[t.y] : -crow[t.y];
+      const double* rb = rows + t.x;
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc[u] = fma(rb[u * Nb], cj, acc[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (u < cnt && acc[u] != 0.0) atomicAdd(gab + (int64_t)tpq[u] * n2 + rs, ts[u] * acc[u]);
+  }
+}
+
 __global__ void k_rdm2_combine(const double* __restrict__ same, const double* __restrict__ gab,
                                int n, double* __restrict__ out) {
   const int64_t n2 = (int64_t)n * n, n4 = n2 * n2;
@@ -396,8 +485,42 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
     HQ_CUDA(cudaMemcpyAsync(cnt, off, (n2 + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, s));
     k_trans_place<<<(unsigned)std::min<int64_t>(ceil_div(Nb, 128), g), 128, 0, s>>>(
         lb->strings, Nb, n, lb->srow_ptr, lb->slink, cnt, trans);
-    k_rdm_ab<16><<<(unsigned)Na, 256, 0, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink, off,
-                                               trans, gab);
+    // staged form when at least four bra rows and the ket row fit in shared memory
+    const size_t lim = (size_t)smem_optin_limit();
+    const int max_t = B->n_alpha + la->max_srow;  // alpha transitions of one ket
+    int U = 0;
+    for (int u : {16, 8, 4})
+      if ((size_t)(u + 1) * Nb * sizeof(double) + 1024 <= lim && U == 0) U = u;
+    if (U) {
+      int64_t nseg = 0;
+      HQ_CUDA(cudaMemsetAsync(cnt, 0, (n2 + 1) * sizeof(int64_t), s));
+      k_seg_count<<<(unsigned)ceil_div(n2, 256), 256, 0, s>>>(off, (int)n2, cnt);
+      int64_t* sstart = nullptr;
+      int4* seg = nullptr;
+      auto staged = [&]() -> int {
+        HQ_TRY(dalloc(&sstart, n2 + 1, s));
+        HQ_TRY(exclusive_scan_i64(cnt, sstart, n2 + 1, &nseg, s));
+        HQ_TRY(dalloc(&seg, std::max<int64_t>(nseg, 1), s));
+        k_seg_fill<<<(unsigned)ceil_div(n2, 256), 256, 0, s>>>(off, (int)n2, sstart, seg);
+        const dim3 grid((unsigned)Na, (unsigned)ceil_div(max_t, U));
+        const size_t smem = (size_t)(U + 1) * Nb * sizeof(double);
+        auto go = [&](auto kern) -> int {
+          HQ_TRY(allow_max_smem(kern));
+          kern<<<grid, 256, smem, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink, off,
+                                       trans, seg, nseg, gab);
+          return HINQS_OK;
+        };
+        return U == 16 ? go(k_rdm_ab_staged<16>) : U == 8 ? go(k_rdm_ab_staged<8>)
+                                                          : go(k_rdm_ab_staged<4>);
+      };
+      const int r3 = staged();
+      dfree(sstart, s);
+      dfree(seg, s);
+      HQ_TRY(r3);
+    } else {
+      k_rdm_ab<16><<<(unsigned)Na, 256, 0, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink,
+                                                 off, trans, gab);
+    }
     k_rdm2_combine<<<(unsigned)std::min<int64_t>(ceil_div(n4, 256), g), 256, 0, s>>>(same, gab, n,
                                                                                    rdm2);
     HQ_LAUNCH_CHECK();

@@ -219,6 +219,102 @@ __global__ void __launch_bounds__(256) k_spmm_rec(
   }
 }
 
+// FP32 row product with four consecutive columns per lane (one 16-byte operand load
+// per link and lane) and the link records of a row read 32 at a time by the whole
+// warp (one coalesced 256-byte load) and broadcast by shuffles: per link, the L1 data
+// path moves the 512-byte operand segment and 1/32 of a record line, instead of a
+// 256-byte segment plus a warp-uniform record load.  Requires ncols % 4 == 0.
+template <int RPW>
+__global__ void __launch_bounds__(256, 4) k_spmm_rec4(
+    const float* __restrict__ X, float* __restrict__ Y, int64_t nrows, int64_t ncols,
+    const int64_t* __restrict__ rp, const int2* __restrict__ rec,
+    const int64_t* __restrict__ srp, const int2* __restrict__ sl, const float* __restrict__ VT,
+    const double* __restrict__ hd_row, const double* __restrict__ hd_col, double e_nuc,
+    const float* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * 4;
+  const bool active = c0 < ncols;
+  const int64_t cc = active ? c0 : 0;
+  const int n2 = n * n;
+  const unsigned full = 0xffffffffu;
+  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int64_t I = I0 + rr;
+    if (I >= nrows) break;  // warp-uniform
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (accumulate && active) acc = *reinterpret_cast<const float4*>(Y + I * ncols + c0);
+    if (hd_row) {
+      const float v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : 0.f;
+      const float v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : 0.f;
+      const uint64_t b0 = scol[cc], b1 = scol[cc + 1], b2 = scol[cc + 2], b3 = scol[cc + 3];
+      float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
+      for (int j = 0; j < n; ++j) {
+        const float a = __shfl_sync(full, j < 32 ? v0 : v1, j & 31);
+        if ((b0 >> j) & 1ull) x0 += a;
+        if ((b1 >> j) & 1ull) x1 += a;
+        if ((b2 >> j) & 1ull) x2 += a;
+        if ((b3 >> j) & 1ull) x3 += a;
+      }
+      if (active) {
+        const float4 x = *reinterpret_cast<const float4*>(X + I * ncols + c0);
+        const double hr = hd_row[I] + e_nuc;
+        acc.x += ((float)(hr + hd_col[c0]) + x0) * x.x;
+        acc.y += ((float)(hr + hd_col[c0 + 1]) + x1) * x.y;
+        acc.z += ((float)(hr + hd_col[c0 + 2]) + x2) * x.z;
+        acc.w += ((float)(hr + hd_col[c0 + 3]) + x3) * x.w;
+      }
+    }
+    const int2* __restrict__ r = rec + rp[I];
+    const int nk = (int)(rp[I + 1] - rp[I]);
+    const float* __restrict__ Xc = X + cc;
+    for (int k0 = 0; k0 < nk; k0 += 32) {
+      const int2 mine = (k0 + lane < nk) ? __ldg(r + k0 + lane) : make_int2(0, 0);
+      const int cnt = min(32, nk - k0);
+      int u = 0;
+      for (; u + 8 <= cnt; u += 8) {
+        float4 x[8];
+        float h[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u + v);
+          h[v] = __int_as_float(__shfl_sync(full, mine.y, u + v));
+          x[v] = __ldg(reinterpret_cast<const float4*>(Xc + off));
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          acc.x = fmaf(h[v], x[v].x, acc.x);
+          acc.y = fmaf(h[v], x[v].y, acc.y);
+          acc.z = fmaf(h[v], x[v].z, acc.z);
+          acc.w = fmaf(h[v], x[v].w, acc.w);
+        }
+      }
+      for (; u < cnt; ++u) {
+        const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u);
+        const float h = __int_as_float(__shfl_sync(full, mine.y, u));
+        const float4 x = __ldg(reinterpret_cast<const float4*>(Xc + off));
+        acc.x = fmaf(h, x.x, acc.x);
+        acc.y = fmaf(h, x.y, acc.y);
+        acc.z = fmaf(h, x.z, acc.z);
+        acc.w = fmaf(h, x.w, acc.w);
+      }
+    }
+    if (srp && active) {
+      for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
+        const int2 l = sl[q];
+        const int pair = (l.y > 0 ? l.y : -l.y) - 1;
+        const float4 vt = *reinterpret_cast<const float4*>(VT + (int64_t)pair * ncols + c0);
+        const float4 x = *reinterpret_cast<const float4*>(X + (int64_t)l.x * ncols + c0);
+        const float sg = l.y > 0 ? 1.f : -1.f;
+        acc.x += sg * vt.x * x.x;
+        acc.y += sg * vt.y * x.y;
+        acc.z += sg * vt.z * x.z;
+        acc.w += sg * vt.w * x.w;
+      }
+    }
+    if (active) *reinterpret_cast<float4*>(Y + I * ncols + c0) = acc;
+  }
+}
+
 template <typename T>
 const typename Rec<T>::type* recof(const hinqs_links_s* L);
 template <>
@@ -311,8 +407,9 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
         if (l1.y < 0) v1 = -v1;
         const T* er0 = eriT + ((l0.y > 0 ? l0.y : -l0.y) - 1) * LD;
         const T* er1 = eriT + ((l1.y > 0 ? l1.y : -l1.y) - 1) * LD;
+        // two fused multiply-adds per column (not a product, a fma and an add)
 #pragma unroll
-        for (int a = 0; a < CH; ++a) e[a] += v0 * er0[a] + v1 * er1[a];
+        for (int a = 0; a < CH; ++a) e[a] = fma(v1, er1[a], fma(v0, er0[a], e[a]));
       }
       if (k < nk) {
         const int2 l0 = ell[(int64_t)k * A.Nb];
@@ -320,7 +417,7 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
         if (l0.y < 0) v0 = -v0;
         const T* er0 = eriT + ((l0.y > 0 ? l0.y : -l0.y) - 1) * LD;
 #pragma unroll
-        for (int a = 0; a < CH; ++a) e[a] += v0 * er0[a];
+        for (int a = 0; a < CH; ++a) e[a] = fma(v0, er0[a], e[a]);
       }
       if constexpr (sizeof(T) == 4) {
         // transpose through shared memory, then float4 atomics over four
@@ -391,6 +488,23 @@ static int spmm_rows(const T* X, T* Y, int64_t nrows, int64_t ncols, const hinqs
                      const double* hd_col, double e_nuc, const T* Vrow, const uint64_t* scol,
                      int n, int accumulate, cudaStream_t s) {
   const auto* rec = recof<T>(L);
+  if constexpr (sizeof(T) == 4) {
+    if (rec && ncols % 4 == 0) {
+      const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
+      const int2* sl = Lsingles ? Lsingles->slink : nullptr;
+      const int rpw = L->tune_rows ? L->tune_rows : kRowsPerWarp;
+      auto go = [&](auto kern, int r) {
+        const dim3 g((unsigned)ceil_div(ncols, 128), (unsigned)ceil_div(nrows, kRowWarps * r));
+        kern<<<g, 32 * kRowWarps, 0, s>>>(X, Y, nrows, ncols, L->row_ptr, rec, srp, sl, VT, hd_row,
+                                          hd_col, e_nuc, Vrow, scol, n, accumulate);
+      };
+      if (rpw == 2) go(k_spmm_rec4<2>, 2);
+      else if (rpw == 8) go(k_spmm_rec4<8>, 8);
+      else go(k_spmm_rec4<4>, 4);
+      HQ_LAUNCH_CHECK();
+      return HINQS_OK;
+    }
+  }
   if (rec) {
     const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
     const int2* sl = Lsingles ? Lsingles->slink : nullptr;
@@ -449,7 +563,10 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   opposite:
     if (!(parts & kOppositeSpin) || la->nsingle == 0) return HINQS_OK;
     if constexpr (sizeof(T) == 4) {
-      if (tc_split) return sigma_ab_tc_launch(H, B, la, lb, c, sig, tc_split, s);
+      if (tc_split) {
+        const int r = sigma_ab_tc_launch(H, B, la, lb, c, sig, tc_split, s);
+        if (r != kTcNoFit) return r;
+      }
     }
     auto need = [&](int ch) { return (size_t)n2 * (ch + 16 / sizeof(T)) * sizeof(T) + 256; };
     int ch = la->tune_ch ? la->tune_ch : (sizeof(T) == 4 ? 32 : 16);

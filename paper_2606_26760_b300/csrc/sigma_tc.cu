@@ -123,7 +123,7 @@ struct Args {
   int n, KB;  // KB = padded folded K / 8 (16-byte chunks per operand row)
   const int64_t* a_srow;
   const int2* a_slink;
-  const int2* b_ell;  // slot-major {Jb, sign * (kpart + 1)} (tensor-core gather slots)
+  const int2* b_ell;  // slot-major {Jb, kpart | sign bit} (tensor-core gather slots)
   const int* b_cnt;
   const uint4* Bhi;  // [n*n][KB] BF16 rows of (pq|.) over the folded pairs
   const uint4* Blo;  // low parts (SPLIT = 3)
@@ -136,7 +136,7 @@ struct Args {
 __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int KB, int64_t Nb,
                                              bool crow) {
   const size_t np = SPLIT == 3 ? 2 : 1;
-  size_t x = STAGES * np * (size_t)kTileM * KB * 16 + np * (size_t)NW * KB * 16 + 32 + 4 * NW;
+  size_t x = STAGES * np * (size_t)kTileM * KB * 16 + np * (size_t)NW * KB * 16 + 32 + 8 * NW;
   x = (x + 15) & ~(size_t)15;
   if (crow) x += 4 * (size_t)Nb;
   return x;
@@ -161,9 +161,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   unsigned char* tail = b_buf + NP * b_bytes;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);       // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 16);
-  int* tgt = reinterpret_cast<int*>(tail + 32);             // [NW]
+  float** tgt = reinterpret_cast<float**>(tail + 32);       // [NW] target rows of sigma
   float* crow_s = reinterpret_cast<float*>(
-      smem + ((STAGES * NP * a_bytes + NP * b_bytes + 32 + 4 * NW + 15) & ~15u));
+      smem + ((STAGES * NP * a_bytes + NP * b_bytes + 32 + 8 * NW + 15) & ~15u));
 
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(1));
@@ -208,10 +208,9 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           if (k0 + 2 * u >= nk) break;
-          const int y = l[u].y;
-          float v = crow[l[u].x];
-          if (y < 0) v = -v;
-          const int off = (y > 0 ? y : -y) - 1;  // kpart of the folded pair
+          const uint32_t y = (uint32_t)l[u].y;
+          const float v = __uint_as_float(__float_as_uint(crow[l[u].x]) ^ (y & 0x80000000u));
+          const uint32_t off = y & 0x7fffffffu;  // kpart of the folded pair
           const __nv_bfloat16 hi = __float2bfloat16_rn(v);
           *reinterpret_cast<__nv_bfloat16*>(ah + off) = hi;
           if (SPLIT == 3)
@@ -267,7 +266,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
         *reinterpret_cast<uint4*>(b_buf + tile_off(a, kb * 8, KB)) = vh;
         if (SPLIT == 3) *reinterpret_cast<uint4*>(b_buf + b_bytes + tile_off(a, kb * 8, KB)) = vl;
       }
-      if (tid < NW) tgt[tid] = (tid < cnt) ? A.a_slink[a0 + tid].x : 0;
+      if (tid < NW) tgt[tid] = A.sig + (tid < cnt ? (int64_t)A.a_slink[a0 + tid].x * Nb : 0);
       for (int st = 0; st < STAGES; ++st) zero_stage(st);
       __syncthreads();
       build_d(0, 0, crow);
@@ -306,7 +305,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
             if (ib < Nb) {
 #pragma unroll
               for (int i = 0; i < 16; ++i)
-                if (c0 + i < cnt) atomicAdd(A.sig + (int64_t)tgt[c0 + i] * Nb + ib, e[i]);
+                if (c0 + i < cnt) atomicAdd(tgt[c0 + i] + ib, e[i]);
             }
           }
           zero_stage(st);  // ready for the gather of tile t + STAGES
@@ -401,7 +400,12 @@ static int launch_fit(const Args& a, cudaStream_t s) {
   if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 2>(a, false, s);
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 1>(a, true, s);
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 1>(a, false, s);
-  return fail(HINQS_ERR_ARG, "tensor-core sigma: operand tiles exceed shared memory (n_orb=%d)", a.n);
+  return kTcNoFit;
+}
+
+template <int NW, int SPLIT>
+static bool fits(const Args& a) {
+  return smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, false) <= (size_t)smem_optin_limit();
 }
 
 }  // namespace tc
@@ -424,8 +428,7 @@ int tc_tables_build(hinqs_ham_s* H, cudaStream_t s) {
 int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                        const hinqs_links_s* lb, const float* c, float* sig, int split,
                        cudaStream_t s) {
-  if (!H->tc_bhi)
-    return fail(HINQS_ERR_ARG, "tensor-core sigma: n_orb=%d above %d", H->n, kTcMaxOrb);
+  if (!H->tc_bhi) return kTcNoFit;  // n_orb above kTcMaxOrb
   tc::Args a;
   a.Na = B->Na;
   a.Nb = B->Nb;
@@ -440,9 +443,15 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   a.C = c;
   a.sig = sig;
   a.crow_smem = 0;
+  // alpha strings with more than 64 singles take 128-column chunks when the tiles fit,
+  // else 64-column chunks in several passes; kTcNoFit when neither fits
   const bool wide = la->max_srow > 64;
-  if (split == 3) return wide ? tc::launch_fit<128, 3>(a, s) : tc::launch_fit<64, 3>(a, s);
-  return wide ? tc::launch_fit<128, 1>(a, s) : tc::launch_fit<64, 1>(a, s);
+  if (split == 3) {
+    if (wide && tc::fits<128, 3>(a)) return tc::launch_fit<128, 3>(a, s);
+    return tc::fits<64, 3>(a) ? tc::launch_fit<64, 3>(a, s) : kTcNoFit;
+  }
+  if (wide && tc::fits<128, 1>(a)) return tc::launch_fit<128, 1>(a, s);
+  return tc::fits<64, 1>(a) ? tc::launch_fit<64, 1>(a, s) : kTcNoFit;
 }
 
 int tc_error_check(cudaStream_t s) {
