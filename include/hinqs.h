@@ -153,6 +153,10 @@ int hinqs_links_export(const hinqs_links* links, int64_t* row_ptr, int32_t* col,
 int hinqs_links_destroy(hinqs_links* links);
 /* largest number of single links of one string (0 for a NULL handle) */
 int hinqs_links_max_singles(const hinqs_links* links);
+/* the sigma tiles hinqs_autotune stored in these links (host outputs, each may be
+ * NULL): rows per warp of the row products, alpha-single chunk width of the CUDA-core
+ * opposite-spin kernel, tensor-core pipeline depth; 0 = built-in default */
+int hinqs_links_tuning(const hinqs_links* links, int* rows_per_warp, int* chunk, int* stages);
 
 /* ------------------------------------------------------------- diagonal --
  * hdiag[I] = <I|H|I> (FP64, [N_a*N_b]): the H_xx of Step 2 (cold-start ranking)
@@ -247,9 +251,10 @@ int hinqs_davidson(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_
  * Not in the paper (its benchmarks use one geometry each; potential-energy scans
  * are named as future work in the Conclusion, item iii).  Times the sigma product
  * of `precision` on this problem for each candidate tile configuration -- rows per
- * warp of the same-spin row products (2, 4, 8) and, for the CUDA-core
- * opposite-spin kernel (HINQS_PREC_FP64, HINQS_PREC_FP32), the alpha-single chunk
- * width (16, 32) -- and stores the fastest in la and lb; every later sigma,
+ * warp of the same-spin row products (2, 4, 8) and, for the opposite-spin term,
+ * the alpha-single chunk width (16, 32) of the CUDA-core kernel (HINQS_PREC_FP64,
+ * HINQS_PREC_FP32) or the pipeline depth (1, 2) of the tensor-core kernel (the
+ * BF16 modes) -- and stores the fastest in la and lb; every later sigma,
  * Davidson and batch call on these links uses it.  Choices are cached per
  * (n_orb, n_alpha, n_beta, precision, N_alpha and N_beta in quarter-octave
  * buckets) for the life of the process, so similar problems are timed once.

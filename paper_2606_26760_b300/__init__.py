@@ -72,7 +72,7 @@ EXPORTED = [
     "hinqs_links_destroy", "hinqs_diag", "hinqs_sigma", "hinqs_davidson_default_opts",
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
     "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
-    "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch",
+    "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch", "hinqs_links_tuning",
 ]
 
 
@@ -100,6 +100,8 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_links_export.argtypes = [P, P, P, P, P, P, P, P, P, P, P]
     lib.hinqs_links_destroy.argtypes = [P]
     lib.hinqs_links_max_singles.argtypes = [P]
+    lib.hinqs_links_tuning.argtypes = [P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]
     lib.hinqs_diag.argtypes = [P, P, P, P, P, P]
     lib.hinqs_sigma.argtypes = [P, P, P, P, P, P, I, P]
     lib.hinqs_sigma_same_spin.argtypes = [P, P, P, P, P, P, I, P]
@@ -220,6 +222,12 @@ class Links:
         _check(_lib.hinqs_links_count(handle, ctypes.byref(nl), ctypes.byref(ns), ctypes.byref(mr)))
         self.n_links, self.n_singles, self.max_row = nl.value, ns.value, mr.value
         self.max_srow = _lib.hinqs_links_max_singles(handle)
+
+    def tuning(self):
+        """(rows per warp, CUDA-core chunk, tensor-core stages) chosen by autotune (0 = default)."""
+        r, c, st = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(_lib.hinqs_links_tuning(self.handle, ctypes.byref(r), ctypes.byref(c), ctypes.byref(st)))
+        return r.value, c.value, st.value
 
     def export(self):
         dev = _dev()

@@ -2,7 +2,8 @@
 //
 // Autotuner: for one (Hamiltonian, subspace, links) it times the sigma product for
 // each candidate tile configuration -- rows per warp of the same-spin row products
-// and, for the CUDA-core opposite-spin kernel, the width of its alpha-single chunk --
+// and, for the opposite-spin term, the alpha-single chunk width of the CUDA-core
+// kernel or the pipeline depth of the tensor-core kernel --
 // and stores the fastest in the links handles.  Results are cached per problem
 // class (orbitals, electrons, precision, and the string counts in quarter-octave
 // buckets), so geometries of a scan with similar sizes are tuned once.
@@ -33,7 +34,7 @@ namespace {
 
 using TuneKey = std::tuple<int, int, int, int, int, int>;
 struct TuneVal {
-  int rows, ch;
+  int rows, ch, stages;
   double ms;
 };
 std::mutex g_tune_mutex;
@@ -61,6 +62,7 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
     if (it != g_tune_cache.end()) {
       la->tune_rows = lb->tune_rows = it->second.rows;
       la->tune_ch = it->second.ch;
+      la->tune_stages = it->second.stages;
       if (best_ms) *best_ms = it->second.ms;
       return HINQS_OK;
     }
@@ -75,20 +77,26 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
     return fail(HINQS_ERR_OOM, "hinqs_autotune: no room for two test vectors");
   }
   k_fill_pattern<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 8 * kNumSMs), 256, 0, s>>>(c, N, dbl);
+  // candidates: rows per warp x (CUDA-core chunk width | tensor-core pipeline depth)
   const bool cuda_core_ab = precision == HINQS_PREC_FP64 || precision == HINQS_PREC_FP32;
-  std::vector<std::pair<int, int>> cands;
-  for (int r : {2, 4, 8})
-    for (int ch : (cuda_core_ab ? std::vector<int>{16, 32} : std::vector<int>{0}))
-      cands.push_back({r, ch});
+  std::vector<std::tuple<int, int, int>> cands;
+  for (int r : {2, 4, 8}) {
+    if (cuda_core_ab) {
+      for (int ch : {16, 32}) cands.push_back({r, ch, 0});
+    } else {
+      for (int st : {1, 2}) cands.push_back({r, 0, st});
+    }
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   double best = 1e300;
-  TuneVal bestv{0, 0, 0.0};
+  TuneVal bestv{0, 0, 0, 0.0};
   int rc = HINQS_OK;
-  for (auto [r, ch] : cands) {
+  for (auto [r, ch, st] : cands) {
     la->tune_rows = lb->tune_rows = r;
     la->tune_ch = ch;
+    la->tune_stages = st;
     if ((rc = sigma_launch(H, B, la, lb, c, sg, precision, s)) < 0) break;  // warm-up
     cudaEventRecord(e0, s);
     const int reps = 3;
@@ -101,7 +109,7 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
     const double t = ms / reps;
     if (t < best) {
       best = t;
-      bestv = TuneVal{r, ch, t};
+      bestv = TuneVal{r, ch, st, t};
     }
   }
   cudaEventDestroy(e0);
@@ -113,6 +121,7 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
   if (e != cudaSuccess) return cuda_fail(e, "hinqs_autotune", __FILE__, __LINE__);
   la->tune_rows = lb->tune_rows = bestv.rows;
   la->tune_ch = bestv.ch;
+  la->tune_stages = bestv.stages;
   if (best_ms) *best_ms = bestv.ms;
   std::lock_guard<std::mutex> lock(g_tune_mutex);
   g_tune_cache[key] = bestv;

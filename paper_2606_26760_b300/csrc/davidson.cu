@@ -30,7 +30,8 @@ int check_triplet(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_l
 constexpr int kMaxSub = 32;
 constexpr int kRRThreads = 128;  // threads of the projected eigensolver
 constexpr int kRitzStride = kMaxSub + 2;  // (theta, y[kMaxSub], pad) per Ritz pair
-constexpr int kRedGrid = 2 * kNumSMs;
+constexpr int kRedGrid = 2 * kNumSMs;   // blocks per vector of the dot products
+constexpr int kResGrid = 8 * kNumSMs;   // blocks of the residual pass (one vector pair)
 constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------- kernels --
@@ -69,6 +70,56 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, 
   }
 }
 
+// Two products per vector in one pass over A: partial[i*gridDim.x + b] = block b's
+// share of A_i . b1 and partial[(gridDim.y + i)*gridDim.x + b] that of A_i . b2
+// (same arithmetic as k_dots).
+template <typename TA, typename TB>
+__global__ void __launch_bounds__(kRedThreads) k_dots2(const TA* __restrict__ A, int64_t lda,
+                                                       const TB* __restrict__ b1,
+                                                       const TB* __restrict__ b2, int64_t N,
+                                                       double* __restrict__ partial) {
+  const int i = blockIdx.y;
+  const TA* __restrict__ a = A + (int64_t)i * lda;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  double acc1 = 0.0, acc2 = 0.0;
+  if constexpr (std::is_same<TA, float>::value && std::is_same<TB, float>::value) {
+    for (; j + 3 * stride < N; j += 4 * stride) {
+      const float a0 = a[j], a1 = a[j + stride], a2 = a[j + 2 * stride], a3 = a[j + 3 * stride];
+      float p = a0 * b1[j], q = a0 * b2[j];
+      p = fmaf(a1, b1[j + stride], p);
+      q = fmaf(a1, b2[j + stride], q);
+      p = fmaf(a2, b1[j + 2 * stride], p);
+      q = fmaf(a2, b2[j + 2 * stride], q);
+      p = fmaf(a3, b1[j + 3 * stride], p);
+      q = fmaf(a3, b2[j + 3 * stride], q);
+      acc1 += (double)p;
+      acc2 += (double)q;
+    }
+  }
+  for (; j < N; j += stride) {
+    const double av = (double)a[j];
+    acc1 += av * (double)b1[j];
+    acc2 += av * (double)b2[j];
+  }
+  __shared__ double red[2][kRedThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc1 += __shfl_down_sync(0xffffffffu, acc1, o);
+    acc2 += __shfl_down_sync(0xffffffffu, acc2, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = acc1;
+    red[1][threadIdx.x >> 5] = acc2;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    double v = 0.0;
+    for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
+    partial[((int64_t)threadIdx.x * gridDim.y + i) * gridDim.x + blockIdx.x] = v;
+  }
+}
+
 // out[i] = sum_b partial[i*nb + b] (fixed order: deterministic); one warp per i
 __global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int m,
                                   double* __restrict__ out) {
@@ -96,7 +147,16 @@ __global__ void k_lincomb(double* __restrict__ out, const TA* __restrict__ A, in
     double v;
     if constexpr (std::is_same<TA, float>::value) {
       float f = 0.0f;
-      for (int i = 0; i < m; ++i) f = fmaf((float)c[i], A[i * lda + j], f);
+      int i = 0;
+      for (; i + 4 <= m; i += 4) {
+        const float a0 = A[i * lda + j], a1 = A[(i + 1) * lda + j];
+        const float a2 = A[(i + 2) * lda + j], a3 = A[(i + 3) * lda + j];
+        f = fmaf((float)c[i], a0, f);
+        f = fmaf((float)c[i + 1], a1, f);
+        f = fmaf((float)c[i + 2], a2, f);
+        f = fmaf((float)c[i + 3], a3, f);
+      }
+      for (; i < m; ++i) f = fmaf((float)c[i], A[i * lda + j], f);
       v = (double)f;
     } else {
       v = 0.0;
@@ -117,7 +177,16 @@ __global__ void k_lincomb_sub_f32(float* __restrict__ out, const float* __restri
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * blockDim.x) {
     float f = out[j];
-    for (int i = 0; i < m; ++i) f = fmaf(-c[i], A[i * lda + j], f);
+    int i = 0;
+    for (; i + 4 <= m; i += 4) {
+      const float a0 = A[i * lda + j], a1 = A[(i + 1) * lda + j];
+      const float a2 = A[(i + 2) * lda + j], a3 = A[(i + 3) * lda + j];
+      f = fmaf(-c[i], a0, f);
+      f = fmaf(-c[i + 1], a1, f);
+      f = fmaf(-c[i + 2], a2, f);
+      f = fmaf(-c[i + 3], a3, f);
+    }
+    for (; i < m; ++i) f = fmaf(-c[i], A[i * lda + j], f);
     out[j] = f;
   }
 }
@@ -152,8 +221,12 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     int has_x0, const double* __restrict__ D, double floor_, int64_t N, double* __restrict__ t,
     double* __restrict__ partial) {
   __shared__ double y[kMaxSub + 1];
+  __shared__ float yf[kMaxSub + 1];
   __shared__ double red[kRedThreads / 32];
-  if (threadIdx.x <= m + has_x0) y[threadIdx.x] = ritz[1 + threadIdx.x];
+  if (threadIdx.x <= m + has_x0) {
+    y[threadIdx.x] = ritz[1 + threadIdx.x];
+    yf[threadIdx.x] = (float)ritz[1 + threadIdx.x];
+  }
   __syncthreads();
   const double theta = ritz[0];
   const int o = has_x0 ? 1 : 0;
@@ -167,8 +240,23 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     }
     if constexpr (std::is_same<TV, float>::value) {
       float hf = 0.0f, xf = 0.0f;
-      for (int i = 0; i < m; ++i) {
-        const float yi = (float)y[o + i];
+      int i = 0;
+      for (; i + 4 <= m; i += 4) {  // eight loads in flight
+        float w4[4], v4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          w4[u] = W[(i + u) * ld + j];
+          v4[u] = V[(i + u) * ld + j];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float yi = yf[o + i + u];
+          hf = fmaf(yi, w4[u], hf);
+          xf = fmaf(yi, v4[u], xf);
+        }
+      }
+      for (; i < m; ++i) {
+        const float yi = yf[o + i];
         hf = fmaf(yi, W[i * ld + j], hf);
         xf = fmaf(yi, V[i * ld + j], xf);
       }
@@ -465,7 +553,7 @@ struct Ctx {
   cudaStream_t s;
   int64_t N;
   int grid;
-  double* partial = nullptr;  // [(kMaxSub+1) * kRedGrid]
+  double* partial = nullptr;  // [2 * (kMaxSub+1) * kRedGrid] >= kResGrid
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
   float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
 };
@@ -475,6 +563,18 @@ static int dots(Ctx& c, const TA* A, int64_t lda, int m, const TB* b, double* ou
   if (m <= 0) return HINQS_OK;
   k_dots<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b, c.N, c.partial);
   k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, m, out);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+// out1[i] = A_i . b1, out2[i] = A_i . b2 with one pass over A
+template <typename TA, typename TB>
+static int dots2(Ctx& c, const TA* A, int64_t lda, int m, const TB* b1, const TB* b2,
+                 double* out1, double* out2) {
+  if (m <= 0) return HINQS_OK;
+  k_dots2<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b1, b2, c.N, c.partial);
+  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, m, out1);
+  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial + (size_t)m * kRedGrid, kRedGrid, m, out2);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -631,9 +731,9 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
       k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
-      k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
+      k_residual<double><<<kResGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
                                                             D, o.denom_floor, N, t, c.partial);
-      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
       HQ_LAUNCH_CHECK();
       double hres = 0.0;
       HQ_CUDA(cudaMemcpyAsync(hr, ritz, (kMaxSub + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -703,7 +803,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
         HQ_TRY(orthonormalise(c, t, V, N, m, V + (size_t)m * N, &ratio));
         if (ratio < 1e-10) {
           // stagnated preconditioner: fall back to the plain residual direction
-          k_residual<double><<<kRedGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz,
+          k_residual<double><<<kResGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz,
                                                                 0, D, 1e300, N, t, c.partial);
           HQ_TRY(orthonormalise(c, t, V, N, m, V + (size_t)m * N, &ratio));
           if (ratio < 1e-14) {
@@ -776,10 +876,8 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
   auto add_column = [&](int j) -> int {
     const float* v = V + (size_t)(j - 1) * N;
     const float* w = W + (size_t)(j - 1) * N;
-    HQ_TRY(dots<float, double>(c, v, N, 1, sx, col));
-    HQ_TRY(dots<float, float>(c, V, N, j, w, col + 1));
-    HQ_TRY(dots<float, double>(c, v, N, 1, x, scol));
-    HQ_TRY(dots<float, float>(c, V, N, j, v, scol + 1));
+    HQ_TRY(dots2<float, double>(c, v, N, 1, sx, x, col, scol));
+    HQ_TRY(dots2<float, float>(c, V, N, j, w, v, col + 1, scol + 1));
     k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
     k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, j, scol, j + 1, 0);
     HQ_LAUNCH_CHECK();
@@ -808,9 +906,9 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         HQ_TRY(dots<double, double>(c, x, N, 1, sx, th));
         k_init_pencil<<<1, 256, 0, c.s>>>(G1, nullptr, th);
         k_rr<<<1, kRRThreads, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
-        k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
+        k_residual<float><<<kResGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
                                                              o.denom_floor, N, t, c.partial);
-        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
         HQ_LAUNCH_CHECK();
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz1, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -836,10 +934,8 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         hard = false;
       }
       // row and column 0 of the pencil for the current anchor
-      HQ_TRY(dots<double, double>(c, x, N, 1, sx, col));
-      HQ_TRY(dots<float, double>(c, V, N, m, sx, col + 1));
-      HQ_TRY(dots<double, double>(c, x, N, 1, x, scol));
-      HQ_TRY(dots<float, double>(c, V, N, m, x, scol + 1));
+      HQ_TRY(dots2<double, double>(c, x, N, 1, sx, x, col, scol));
+      HQ_TRY(dots2<float, double>(c, V, N, m, sx, x, col + 1, scol + 1));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, col, m + 1, 0);
       k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, 0, scol, m + 1, 0);
       HQ_LAUNCH_CHECK();
@@ -854,9 +950,9 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       bool restart_hard = false;
       for (;;) {
         k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
-        k_residual<float><<<kRedGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
+        k_residual<float><<<kResGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
                                                              o.denom_floor, N, t, c.partial);
-        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, 1, col + kMaxSub);
+        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
         HQ_LAUNCH_CHECK();
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -915,8 +1011,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       for (int j = 1; j <= m; ++j) {
         const float* v = V + (size_t)(j - 1) * N;
         const float* w = W + (size_t)(j - 1) * N;
-        HQ_TRY(dots<float, float>(c, V, N, j, w, col + 1));
-        HQ_TRY(dots<float, float>(c, V, N, j, v, scol + 1));
+        HQ_TRY(dots2<float, float>(c, V, N, j, w, v, col + 1, scol + 1));
         k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col + 1, j, 1);
         k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, j, scol + 1, j, 1);
       }
@@ -977,7 +1072,7 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   c.grid = (int)std::min<int64_t>(ceil_div(c.N, 256), 8 * kNumSMs);
   double* D = nullptr;
   int rc = HINQS_OK;
-  if ((rc = dalloc(&c.partial, kRedGrid * (kMaxSub + 1), c.s)) ||
+  if ((rc = dalloc(&c.partial, 2 * kRedGrid * (kMaxSub + 1), c.s)) ||
       (rc = dalloc(&c.small, 4 * (kMaxSub + 2), c.s)) || (rc = dalloc(&D, c.N, c.s))) {
   }
   if (!rc) rc = diag_launch(H, B, la, lb, D, c.s);

@@ -134,6 +134,7 @@ struct hinqs_links_s {
   // CUDA-core opposite-spin kernel (read from the alpha links)
   int tune_rows = 0;
   int tune_ch = 0;
+  int tune_stages = 0;  // tensor-core pipeline depth (1 or 2; 0 = deepest that fits)
 };
 
 namespace hinqs {

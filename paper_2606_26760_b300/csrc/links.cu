@@ -382,6 +382,15 @@ extern "C" int hinqs_links_export(const hinqs_links* L, int64_t* row_ptr, int32_
 
 extern "C" int hinqs_links_max_singles(const hinqs_links* L) { return L ? L->max_srow : 0; }
 
+extern "C" int hinqs_links_tuning(const hinqs_links* L, int* rows_per_warp, int* chunk,
+                                  int* stages) {
+  if (!L) return fail(HINQS_ERR_ARG, "hinqs_links_tuning: NULL handle");
+  if (rows_per_warp) *rows_per_warp = L->tune_rows;
+  if (chunk) *chunk = L->tune_ch;
+  if (stages) *stages = L->tune_stages;
+  return HINQS_OK;
+}
+
 extern "C" int hinqs_links_destroy(hinqs_links* L) {
   if (!L) return HINQS_OK;
   cudaDeviceSynchronize();

@@ -392,12 +392,15 @@ static int launch(const Args& a, bool crow, cudaStream_t s) {
 }
 
 // Largest configuration that fits: two stages with the C row in shared memory, then
-// without the row, then one stage.
+// without the row, then one stage (stages = 1: one stage only, which leaves room for
+// more resident CTAs per SM).
 template <int NW, int SPLIT>
-static int launch_fit(const Args& a, cudaStream_t s) {
+static int launch_fit(const Args& a, int stages, cudaStream_t s) {
   const size_t lim = (size_t)smem_optin_limit();
-  if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 2>(a, true, s);
-  if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 2>(a, false, s);
+  if (stages != 1) {
+    if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 2>(a, true, s);
+    if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 2>(a, false, s);
+  }
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 1>(a, true, s);
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 1>(a, false, s);
   return kTcNoFit;
@@ -447,11 +450,11 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   // else 64-column chunks in several passes; kTcNoFit when neither fits
   const bool wide = la->max_srow > 64;
   if (split == 3) {
-    if (wide && tc::fits<128, 3>(a)) return tc::launch_fit<128, 3>(a, s);
-    return tc::fits<64, 3>(a) ? tc::launch_fit<64, 3>(a, s) : kTcNoFit;
+    if (wide && tc::fits<128, 3>(a)) return tc::launch_fit<128, 3>(a, la->tune_stages, s);
+    return tc::fits<64, 3>(a) ? tc::launch_fit<64, 3>(a, la->tune_stages, s) : kTcNoFit;
   }
-  if (wide && tc::fits<128, 1>(a)) return tc::launch_fit<128, 1>(a, s);
-  return tc::fits<64, 1>(a) ? tc::launch_fit<64, 1>(a, s) : kTcNoFit;
+  if (wide && tc::fits<128, 1>(a)) return tc::launch_fit<128, 1>(a, la->tune_stages, s);
+  return tc::fits<64, 1>(a) ? tc::launch_fit<64, 1>(a, la->tune_stages, s) : kTcNoFit;
 }
 
 int tc_error_check(cudaStream_t s) {
