@@ -33,9 +33,10 @@ METRIC = "sigma dets/s and Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B
 FP64_FMA_TFLOPS = 1.129
 kNumSMs_B300 = 148
 SM_MAX_MHZ = 2032
-# DRAM bytes (read + write) per launch from an ncu capture of the precision workload
-# (profiles/); None until captured for the current kernels
-PROFILED_TRAFFIC = {"same": None, "opposite": None}
+# DRAM bytes (read + write) per product half from ncu captures of the precision
+# workload (profiles/): same-spin = its two row-product launches; None where the
+# kernel changed after the capture
+PROFILED_TRAFFIC = {"same": 62.77e6, "opposite": 33.36e6}
 WORKLOAD = "precision"
 
 

@@ -161,6 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   unsigned char* tail = b_buf + NP * b_bytes;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(tail);       // [2]
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tail + 16);
+  int* wait_flag = reinterpret_cast<int*>(tail + 20);
   float** tgt = reinterpret_cast<float**>(tail + 32);       // [NW] target rows of sigma
   float* crow_s = reinterpret_cast<float*>(
       smem + ((STAGES * NP * a_bytes + NP * b_bytes + 32 + 8 * NW + 15) & ~15u));
@@ -284,10 +285,12 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
           fence_after();
           if (tid == 0) issue(st ^ 1);
         }
-        // every thread waits (bounded) for tile t's MMA chain
-        // (warp-uniform, so that a warp reads tensor memory converged or not at all)
-        const bool done =
-            __all_sync(0xffffffffu, mbar_wait(smem_u32(mbar + st), st == 0 ? ph0 : ph1));
+        // one thread waits (bounded) for tile t's MMA chain and tells the block, so
+        // that the other warps sleep at the barrier instead of spinning on the
+        // mbarrier (their issue slots go to the other resident CTAs)
+        if (tid == 0) *wait_flag = mbar_wait(smem_u32(mbar + st), st == 0 ? ph0 : ph1) ? 1 : 0;
+        __syncthreads();
+        const bool done = *wait_flag != 0;
         if (st == 0) ph0 ^= 1u;
         else ph1 ^= 1u;
         if (done) {
