@@ -52,6 +52,8 @@ def _load():
         lib.oracle_links.argtypes = [i32, i32, P, P, P, i64, P, i64, P, P, P, P, P, P, P, P, P]
         lib.oracle_rdm.argtypes = [i32, P, i64, P, i64, P, P, P, i32]
         lib.oracle_marginals.argtypes = [P, i64, i64, P, P, P]
+        lib.oracle_coupling.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, P, i64,
+                                        P, P, i32]
         lib.oracle_max_threads.argtypes = []
         _lib = lib
     return _lib
@@ -115,6 +117,22 @@ def sigma(H: Ham, sa, sb, c, rows=None, n_threads: int = 0):
     if rc:
         raise ValueError(f"oracle_sigma failed ({rc})")
     return out
+
+
+def pt2_scores(H: Ham, sa, sb, c, E0: float, xa, xb, n_threads: int = 0):
+    """Step 2, Eq. pt2_score: for candidates x = (xa[k], xb[k]) return
+    (v, hxx, s) with v = <x|H|c> (sum over the subspace), hxx = <x|H|x> and
+    s = v^2 / |E0 - hxx|.  E0 and hxx both include E_nuc."""
+    lib = _load()
+    sa, sb, c = _u64(sa), _u64(sb), _f64(c)
+    xa, xb = _u64(xa), _u64(xb)
+    M = len(xa)
+    v, hxx = np.zeros(M), np.zeros(M)
+    rc = lib.oracle_coupling(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc, _p(sa), len(sa),
+                             _p(sb), len(sb), _p(c), _p(xa), _p(xb), M, _p(v), _p(hxx), n_threads)
+    if rc:
+        raise ValueError(f"oracle_coupling failed ({rc})")
+    return v, hxx, v * v / np.abs(E0 - hxx)
 
 
 def dense_h(H: Ham, sa, sb):

@@ -28,6 +28,8 @@
  *   oracle_sigma      sigma_I = sum_J H_IJ c_J       (H|I> by operator application)
  *   oracle_dense_h    the full projected matrix H_B   (Step 3)
  *   oracle_diag       H_II                            (Step 2 cold-start H_xx)
+ *   oracle_coupling   <x|H|Psi0> = sum_i c_i H_{x,x_i} and H_xx for determinants x
+ *                     inside or outside the subspace (Step 2, Eq. pt2_score)
  *   oracle_links      single/double string links, phases and same-spin elements
  *   oracle_rdm        1-RDM gamma_pq and 2-RDM Gamma_pqrs (Hellmann-Feynman
  *                     gradients; not in the paper) by operator expectation
@@ -304,6 +306,38 @@ int oracle_diag(int n, int na, int nb, const double *h, const double *eri, doubl
         diag_user du = {&D, 0.0};
         apply_h(&H, &D, diag_emit, &du);
         hd[k] = du.acc;
+    }
+    return 0;
+}
+
+/* -------------------------------------------------------- PT2 coupling --- */
+
+/* For candidate determinants x_k = (xa[k], xb[k]) (any strings with the sector's
+ * electron counts, in the subspace or not): v[k] = <x_k|H|c> = sum_J <x_k|H|J> c_J
+ * over the subspace determinants J, and hxx[k] = <x_k|H|x_k>.  H is real symmetric,
+ * so v is gathered by applying H to |x_k> and looking the results up in the subspace
+ * (the numerator of Eq. pt2_score); hxx is the diagonal of Step 2. */
+int oracle_coupling(int n, int na, int nb, const double *h, const double *eri, double enuc,
+                    const uint64_t *sa, int64_t Na, const uint64_t *sb, int64_t Nb,
+                    const double *c, const uint64_t *xa, const uint64_t *xb, int64_t M,
+                    double *v, double *hxx, int n_threads) {
+    if (check_common(n, na, nb, h, eri, sa, Na, sb, Nb) || !c || M < 0 ||
+        (M > 0 && (!xa || !xb || !v || !hxx)))
+        return -1;
+    oham H = {n, h, eri, enuc};
+    ospace B = {n, sa, sb, Na, Nb};
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < M; ++k) {
+        odet D = det_from_strings(n, xa[k], xb[k]);
+        sig_user su = {&B, c, 0.0};
+        apply_h(&H, &D, sig_emit, &su);
+        v[k] = su.acc;
+        diag_user du = {&D, 0.0};
+        apply_h(&H, &D, diag_emit, &du);
+        hxx[k] = du.acc;
     }
     return 0;
 }

@@ -357,3 +357,43 @@ def test_table1_full_space_dimensions(row):
     if comb(n, na) <= 5000:
         sa, sb = oracle.build_subspace(synth.all_strings(n, na), synth.all_strings(n, nb), na, nb)
         assert len(sa) * len(sb) == dim
+
+
+# ------------------------------------------------------ PT2 coupling pins
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(4, 2, 2, 31), (5, 2, 1, 32)])
+def test_pt2_coupling_matches_jordan_wigner(n, na, nb, seed):
+    """Eq. pt2_score numerator and H_xx for every determinant of the sector, with a
+    random c on a sampled subspace: <x|H|c> = (H_JW c_embedded)_x, H_xx = H_JW[x, x]."""
+    h, eri, _ = synth.integrals(n, seed)
+    Hjw = _jw_hamiltonian(h, eri, 0.7).toarray()
+    fa, fb = full_space(n, na, nb)
+    rng = np.random.default_rng(seed)
+    sa = np.sort(rng.choice(fa, size=max(1, len(fa) // 2), replace=False))
+    sb = np.sort(rng.choice(fb, size=max(1, (len(fb) + 1) // 2), replace=False))
+    H = oracle.Ham(h, eri, 0.7, na, nb)
+    c = synth.random_vector(len(sa) * len(sb), seed)
+    full = np.zeros(Hjw.shape[0])
+    full[_fock_index(n, sa, sb)] = c
+    xa = np.repeat(fa, len(fb))
+    xb = np.tile(fb, len(fa))
+    v, hxx, s = oracle.pt2_scores(H, sa, sb, c, -3.0, xa, xb)
+    fidx = np.array([int(a) | (int(b) << n) for a, b in zip(xa, xb)])
+    assert np.max(np.abs(v - (Hjw @ full)[fidx])) < 1e-12
+    assert np.max(np.abs(hxx - np.diag(Hjw)[fidx])) < 1e-12
+    assert np.allclose(s, v * v / np.abs(-3.0 - hxx), rtol=1e-14, atol=0)
+
+
+def test_pt2_coupling_inside_subspace_is_eigen_equation():
+    """For x in the subspace and c its ground state, <x|H|Psi0> = E0 c_x, so the
+    score of a basis member is E0^2 c_x^2 / |E0 - H_xx|."""
+    w = synth.workload("fp64_small")
+    H = oracle.Ham(w["h"], w["eri"], 0.4, 3, 3)
+    sa, sb = oracle.build_subspace(w["alpha"][:40], w["beta"][:30], 3, 3)
+    E, c = oracle.ground_state_dense(H, sa, sb)
+    xa, xb = np.repeat(sa, len(sb)), np.tile(sb, len(sa))
+    v, hxx, s = oracle.pt2_scores(H, sa, sb, c, E, xa, xb)
+    assert np.max(np.abs(v - E * c)) < 1e-11
+    hd = oracle.diag(H, sa, sb)
+    assert np.max(np.abs(hxx - hd)) < 1e-12
