@@ -292,6 +292,23 @@ int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
                          double* energies, double* const* c_outs, hinqs_davidson_info* infos,
                          void* stream);
 
+/* ---------------------------------------------------------- PT2 scores --
+ * Step 2, Eq. pt2_score: the Epstein-Nesbet importance of candidate determinants
+ * x_k = (xa[k], xb[k]) given the subspace eigenvector c (energy e0):
+ *   v[k]     = <x_k|H|Psi0> = sum_{J in subspace} <x_k|H|J> c_J
+ *   hxx[k]   = <x_k|H|x_k>            (includes E_nuc)
+ *   score[k] = v[k]^2 / |e0 - hxx[k]| (e0 includes E_nuc)
+ * Candidates may lie inside or outside the subspace (t = 1 rescoring covers both).
+ *   c      device FP64 [N]; xa, xb device uint64 [m] strings of the sector
+ *   v, hxx, score  device FP64 [m]
+ * Errors: HINQS_ERR_ARG (NULL, m < 0, handles of different problems),
+ * HINQS_ERR_PARTICLE_NUMBER (a candidate string with the wrong electron count or
+ * bits >= n_orb; its outputs are NaN, the others are valid).  Synchronises the
+ * stream (the error count is read back). */
+int hinqs_pt2_score(const hinqs_ham* ham, const hinqs_subspace* sub, const double* c, double e0,
+                    const uint64_t* xa, const uint64_t* xb, int64_t m, double* v, double* hxx,
+                    double* score, void* stream);
+
 /* ------------------------------------------------------------------ RDMs --
  * Spin-summed reduced density matrices of the state c (FP64 [N], used as given):
  *   rdm1[p*n+q]             = sum_s <c|a+_{ps} a_{qs}|c>

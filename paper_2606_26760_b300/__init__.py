@@ -73,6 +73,7 @@ EXPORTED = [
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
     "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
     "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch", "hinqs_links_tuning",
+    "hinqs_pt2_score",
 ]
 
 
@@ -114,6 +115,7 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_davidson_batch.argtypes = [I, P, P, P, P, P, ctypes.POINTER(_Opts), I, I, P, P,
                                          P, P]
     lib.hinqs_rdm.argtypes = [P, P, P, P, P, P, P]
+    lib.hinqs_pt2_score.argtypes = [P, P, P, D, P, P, I64, P, P, P, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -393,6 +395,25 @@ def davidson_batch(problems, guesses=None, precision: int = DAVIDSON_FP64, max_i
                            infos[g].n_sigma_fp64, infos[g].n_sigma_fp32, infos[g].n_restarts,
                            infos[g].n_refinements, infos[g].residual, infos[g].seconds, {})
             for g in range(G)]
+
+
+def pt2_score(ham, sub, c, e0: float, xa, xb):
+    """hinqs_pt2_score (Step 2, Eq. pt2_score): (v, hxx, score) per candidate
+    x = (xa[k], xb[k]); xa, xb int64/uint64 tensors or numpy uint64 arrays."""
+    dev = _dev()
+    xa = _u64(xa)
+    xb = _u64(xb)
+    if xa.numel() != xb.numel():
+        raise ValueError("xa and xb must have the same length")
+    if c.dtype != torch.float64 or c.numel() != sub.N:
+        raise ValueError("c must be a float64 tensor of the subspace size")
+    m = xa.numel()
+    v = torch.empty(m, dtype=torch.float64, device=dev)
+    hxx = torch.empty_like(v)
+    sc = torch.empty_like(v)
+    _check(_lib.hinqs_pt2_score(ham.handle, sub.handle, _ptr(c), float(e0), _ptr(xa), _ptr(xb), m,
+                                _ptr(v), _ptr(hxx), _ptr(sc), _stream()))
+    return v, hxx, sc
 
 
 def rdm(sub, la, lb, c, want2: bool = True):
