@@ -52,6 +52,9 @@ def _load():
         lib.oracle_links.argtypes = [i32, i32, P, P, P, i64, P, i64, P, P, P, P, P, P, P, P, P]
         lib.oracle_rdm.argtypes = [i32, P, i64, P, i64, P, P, P, i32]
         lib.oracle_marginals.argtypes = [P, i64, i64, P, P, P]
+        lib.oracle_connected.argtypes = [i32, i32, i32, P, P, ctypes.c_uint64, ctypes.c_uint64,
+                                         P, P, P, i64]
+        lib.oracle_connected.restype = i64
         lib.oracle_coupling.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, P, i64,
                                         P, P, i32]
         lib.oracle_max_threads.argtypes = []
@@ -133,6 +136,43 @@ def pt2_scores(H: Ham, sa, sb, c, E0: float, xa, xb, n_threads: int = 0):
     if rc:
         raise ValueError(f"oracle_coupling failed ({rc})")
     return v, hxx, v * v / np.abs(E0 - hxx)
+
+
+def connected(H: Ham, xa: int, xb: int, cap: int = 1 << 20):
+    """Determinants y != x with <y|H|x> != 0: (ya, yb, <y|H|x>), ascending (n <= 32)."""
+    lib = _load()
+    ya, yb, val = np.zeros(cap, np.uint64), np.zeros(cap, np.uint64), np.zeros(cap)
+    m = lib.oracle_connected(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), int(xa), int(xb),
+                             _p(ya), _p(yb), _p(val), cap)
+    if m < 0:
+        raise ValueError(f"oracle_connected failed ({m})")
+    return ya[:m], yb[:m], val[:m]
+
+
+def top_amplitudes(c, k: int):
+    """Indices of the k largest |c_i| (ties: lower index first), ascending."""
+    c = np.asarray(c)
+    order = np.lexsort((np.arange(len(c)), -np.abs(c)))
+    return np.sort(order[:k])
+
+
+def classical_expansion(H: Ham, sa, sb, c, n_top: int):
+    """Eq. classical_expansion: every y outside the product subspace S_a x S_b with
+    <y|H|x> != 0 for some x among the n_top largest |c| (Step 1'); returned as
+    (ya, yb) ascending in (alpha, beta)."""
+    sa, sb = _u64(sa), _u64(sb)
+    keys = set()
+    for I in top_amplitudes(c, n_top):
+        ya, yb, _ = connected(H, sa[I // len(sb)], sb[I % len(sb)])
+        for a, b in zip(ya.tolist(), yb.tolist()):
+            ia = np.searchsorted(sa, a)
+            ib = np.searchsorted(sb, b)
+            inside = ia < len(sa) and sa[ia] == a and ib < len(sb) and sb[ib] == b
+            if not inside:
+                keys.add((a, b))
+    out = sorted(keys)
+    return (np.array([k[0] for k in out], dtype=np.uint64),
+            np.array([k[1] for k in out], dtype=np.uint64))
 
 
 def dense_h(H: Ham, sa, sb):

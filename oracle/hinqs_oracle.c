@@ -28,6 +28,7 @@
  *   oracle_sigma      sigma_I = sum_J H_IJ c_J       (H|I> by operator application)
  *   oracle_dense_h    the full projected matrix H_B   (Step 3)
  *   oracle_diag       H_II                            (Step 2 cold-start H_xx)
+ *   oracle_connected  the determinants y != x with <y|H|x> != 0 (Eq. classical_expansion)
  *   oracle_coupling   <x|H|Psi0> = sum_i c_i H_{x,x_i} and H_xx for determinants x
  *                     inside or outside the subspace (Step 2, Eq. pt2_score)
  *   oracle_links      single/double string links, phases and same-spin elements
@@ -340,6 +341,79 @@ int oracle_coupling(int n, int na, int nb, const double *h, const double *eri, d
         hxx[k] = du.acc;
     }
     return 0;
+}
+
+/* ------------------------------------------------- connected determinants --- */
+
+typedef struct {
+    uint64_t key; /* alpha string << 32 | beta string (n <= 32) */
+    double coeff;
+} kterm;
+
+typedef struct {
+    int n;
+    kterm *buf;
+    int64_t cnt, cap;
+    int overflow;
+} conn_user;
+
+static void conn_emit(const odet *out, double coeff, void *u) {
+    conn_user *cu = (conn_user *)u;
+    if (cu->cnt >= cu->cap) {
+        cu->overflow = 1;
+        return;
+    }
+    uint64_t a, b;
+    strings_from_det(cu->n, out, &a, &b);
+    cu->buf[cu->cnt].key = (a << 32) | b;
+    cu->buf[cu->cnt].coeff = coeff;
+    cu->cnt++;
+}
+
+static int cmp_kterm(const void *x, const void *y) {
+    uint64_t a = ((const kterm *)x)->key, b = ((const kterm *)y)->key;
+    return a < b ? -1 : (a > b ? 1 : 0);
+}
+
+/* Every determinant y != x with <y|H|x> != 0 (Eq. classical_expansion's connection
+ * test), by applying H to |x> and summing the coefficients of equal results.
+ * Outputs y's strings and <y|H|x>, ascending in (alpha, beta); returns the count,
+ * or -1 (bad arguments, n > 32) / -2 (cap too small). */
+int64_t oracle_connected(int n, int na, int nb, const double *h, const double *eri,
+                         uint64_t xa, uint64_t xb, uint64_t *ya, uint64_t *yb, double *val,
+                         int64_t cap) {
+    if (n < 1 || n > 32 || na < 0 || nb < 0 || na > n || nb > n || !h || !eri) return -1;
+    oham H = {n, h, eri, 0.0};
+    odet D = det_from_strings(n, xa, xb);
+    int64_t tcap = 1 << 22;
+    conn_user cu = {n, (kterm *)malloc(sizeof(kterm) * tcap), 0, tcap, 0};
+    if (!cu.buf) return -1;
+    apply_h(&H, &D, conn_emit, &cu);
+    if (cu.overflow) {
+        free(cu.buf);
+        return -2;
+    }
+    qsort(cu.buf, cu.cnt, sizeof(kterm), cmp_kterm);
+    const uint64_t self = (xa << 32) | xb;
+    int64_t m = 0;
+    for (int64_t i = 0; i < cu.cnt;) {
+        int64_t j = i;
+        double sum = 0.0;
+        while (j < cu.cnt && cu.buf[j].key == cu.buf[i].key) sum += cu.buf[j++].coeff;
+        if (cu.buf[i].key != self && sum != 0.0) {
+            if (m >= cap) {
+                free(cu.buf);
+                return -2;
+            }
+            ya[m] = cu.buf[i].key >> 32;
+            yb[m] = cu.buf[i].key & 0xffffffffull;
+            val[m] = sum;
+            m++;
+        }
+        i = j;
+    }
+    free(cu.buf);
+    return m;
 }
 
 /* -------------------------------------------------------------- links ---- */

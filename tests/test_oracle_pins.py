@@ -397,3 +397,56 @@ def test_pt2_coupling_inside_subspace_is_eigen_equation():
     assert np.max(np.abs(v - E * c)) < 1e-11
     hd = oracle.diag(H, sa, sb)
     assert np.max(np.abs(hxx - hd)) < 1e-12
+
+
+# ------------------------------------------------- classical expansion pins
+
+
+@pytest.mark.parametrize("n,na,nb,seed", [(4, 2, 2, 51), (5, 2, 1, 52), (4, 1, 0, 53)])
+def test_connected_matches_jordan_wigner(n, na, nb, seed):
+    """Eq. classical_expansion's connection test: y != x with <y|H|x> != 0, and the
+    element, against the Fock-space matrix."""
+    h, eri, _ = synth.integrals(n, seed)
+    Hjw = _jw_hamiltonian(h, eri, 0.0).toarray()
+    H = oracle.Ham(h, eri, 0.0, na, nb)
+    fa, fb = full_space(n, na, nb)
+    for xa in fa:
+        for xb in fb:
+            x = int(xa) | (int(xb) << n)
+            ya, yb, val = oracle.connected(H, xa, xb)
+            col = Hjw[:, x].copy()
+            col[x] = 0.0
+            ref = np.nonzero(np.abs(col) > 0)[0]
+            got = np.array([int(a) | (int(b) << n) for a, b in zip(ya, yb)], dtype=np.int64)
+            assert sorted(got.tolist()) == sorted(ref.tolist())
+            assert np.max(np.abs(col[got] - val), initial=0.0) < 1e-12
+
+
+def test_connected_counts_generic_integrals():
+    """With generic integrals every single and double is connected:
+    2 x n_e(n - n_e) singles, 2 x C(n_e,2) C(n - n_e,2) doubles, (n_e(n - n_e))^2 mixed."""
+    from math import comb
+    n, ne = 8, 3
+    h, eri, _ = synth.integrals(n, 61)
+    H = oracle.Ham(h, eri, 0.0, ne, ne)
+    ya, yb, _ = oracle.connected(H, 0b10101, 0b1011)
+    s1 = ne * (n - ne)
+    assert len(ya) == 2 * s1 + 2 * comb(ne, 2) * comb(n - ne, 2) + s1 * s1
+
+
+def test_classical_expansion_excludes_subspace_and_is_union():
+    w = synth.workload("fp64_small")
+    H = oracle.Ham(w["h"], w["eri"], 0.0, 3, 3)
+    sa, sb = oracle.build_subspace(w["alpha"][:12], w["beta"][:9], 3, 3)
+    c = synth.random_vector(len(sa) * len(sb), 3)
+    top = oracle.top_amplitudes(c, 6)
+    assert len(top) == 6 and set(top) == set(np.argsort(-np.abs(c))[:6])
+    xa, xb = oracle.classical_expansion(H, sa, sb, c, 6)
+    inside = set((int(a), int(b)) for a in sa for b in sb)
+    got = set(zip(xa.tolist(), xb.tolist()))
+    assert not (got & inside)
+    union = set()
+    for I in top:
+        ya, yb, _ = oracle.connected(H, sa[I // len(sb)], sb[I % len(sb)])
+        union |= set(zip(ya.tolist(), yb.tolist()))
+    assert got == union - inside
