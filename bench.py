@@ -589,6 +589,31 @@ def main():
                           "frac": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12 / FP64_FMA_TFLOPS,
                           "peak_source": "FP64 FMA-chain rate measured on this B300 model"}
 
+    # Step 1'/Step 2 on the converged eigenvector: the 1000 largest amplitudes, their
+    # classical singles/doubles expansion (Eq. classical_expansion) and the PT2 scores
+    # of every candidate (Eq. pt2_score); public API calls, timed alone
+    c_eig = results[-1].c
+    e_eig = results[-1].energy
+
+    def timed_once(fn, reps=3):
+        fn()
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return min(ts), out
+
+    t_top, _ = timed_once(lambda: hq.top_amplitudes(sub, c_eig, 1000))
+    t_exp, (cxa, cxb) = timed_once(lambda: hq.classical_expansion(ham, sub, c_eig, 1000))
+    t_pt2, _ = timed_once(lambda: hq.pt2_score(ham, sub, c_eig, e_eig, cxa, cxb))
+    selection = {"top_1000_ms": 1e3 * t_top, "expansion_1000_ms": 1e3 * t_exp,
+                 "n_candidates": int(cxa.numel()), "pt2_ms": 1e3 * t_pt2,
+                 "pt2_candidates_per_s": cxa.numel() / t_pt2}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -641,6 +666,7 @@ def main():
         "gpu_launches_note": "library kernels of one untimed step (profiler count) x steps; "
                              "the mixed solver's iteration count varies slightly between steps",
         "roofline": roof,
+        "selection": selection,
         "cpu_baseline": cpu,
         "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
                    "mixed_sigmas_fp64_fp32": [last.n_sigma_fp64, last.n_sigma_fp32],

@@ -309,6 +309,24 @@ int hinqs_pt2_score(const hinqs_ham* ham, const hinqs_subspace* sub, const doubl
                     const uint64_t* xa, const uint64_t* xb, int64_t m, double* v, double* hxx,
                     double* score, void* stream);
 
+/* ------------------------------------------------- classical expansion --
+ * Step 1' (Eq. classical_expansion).
+ * hinqs_top_amplitudes: indices of the k largest |c_I| (ties: lower index first),
+ * written ascending to idx_out (device int64 [min(k, N)]); exact (radix selection).
+ * hinqs_classical_expansion: every determinant y outside S_alpha x S_beta with
+ * <y|H|x> != 0 for some x among the n_top largest |c_I| (the paper uses n_top = 1000):
+ * all alpha/beta singles and doubles and alpha-single x beta-single pairs of each x,
+ * kept when the Slater-Condon element is non-zero.  Output ascending in
+ * (alpha, beta), duplicates removed, into xa_out/xb_out (device uint64 [cap]);
+ * *count (host) = number of candidates.  With xa_out or xb_out NULL only *count is
+ * returned.  Requires n_orb <= 32.  Errors: HINQS_ERR_ARG (NULL, n_orb > 32,
+ * cap < *count: nothing written), HINQS_ERR_OOM.  Synchronises the stream. */
+int hinqs_top_amplitudes(const hinqs_subspace* sub, const double* c, int64_t k, int64_t* idx_out,
+                         void* stream);
+int hinqs_classical_expansion(const hinqs_ham* ham, const hinqs_subspace* sub, const double* c,
+                              int64_t n_top, uint64_t* xa_out, uint64_t* xb_out, int64_t cap,
+                              int64_t* count, void* stream);
+
 /* ------------------------------------------------------------------ RDMs --
  * Spin-summed reduced density matrices of the state c (FP64 [N], used as given):
  *   rdm1[p*n+q]             = sum_s <c|a+_{ps} a_{qs}|c>

@@ -73,7 +73,7 @@ EXPORTED = [
     "hinqs_davidson", "hinqs_rdm", "hinqs_energy_backward", "hinqs_spin_marginals",
     "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
     "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch", "hinqs_links_tuning",
-    "hinqs_pt2_score",
+    "hinqs_pt2_score", "hinqs_top_amplitudes", "hinqs_classical_expansion",
 ]
 
 
@@ -116,6 +116,8 @@ def load_library(path: str = LIB_PATH):
                                          P, P]
     lib.hinqs_rdm.argtypes = [P, P, P, P, P, P, P]
     lib.hinqs_pt2_score.argtypes = [P, P, P, D, P, P, I64, P, P, P, P]
+    lib.hinqs_top_amplitudes.argtypes = [P, P, I64, P, P]
+    lib.hinqs_classical_expansion.argtypes = [P, P, P, I64, P, P, I64, PI64, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -414,6 +416,30 @@ def pt2_score(ham, sub, c, e0: float, xa, xb):
     _check(_lib.hinqs_pt2_score(ham.handle, sub.handle, _ptr(c), float(e0), _ptr(xa), _ptr(xb), m,
                                 _ptr(v), _ptr(hxx), _ptr(sc), _stream()))
     return v, hxx, sc
+
+
+def top_amplitudes(sub, c, k: int):
+    """hinqs_top_amplitudes: indices (int64, ascending) of the k largest |c|."""
+    k = max(0, min(int(k), sub.N))
+    out = torch.empty(k, dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_top_amplitudes(sub.handle, _ptr(c), k, _ptr(out), _stream()))
+    return out
+
+
+def classical_expansion(ham, sub, c, n_top: int = 1000):
+    """hinqs_classical_expansion (Step 1', Eq. classical_expansion): (xa, xb) int64
+    tensors of the candidate strings, ascending in (alpha, beta)."""
+    if c.dtype != torch.float64 or c.numel() != sub.N:
+        raise ValueError("c must be a float64 tensor of the subspace size")
+    cnt = ctypes.c_int64()
+    _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, None, None, 0,
+                                          ctypes.byref(cnt), _stream()))
+    m = cnt.value
+    xa = torch.empty(m, dtype=torch.int64, device=_dev())
+    xb = torch.empty(m, dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, _ptr(xa),
+                                          _ptr(xb), m, ctypes.byref(cnt), _stream()))
+    return xa, xb
 
 
 def rdm(sub, la, lb, c, want2: bool = True):

@@ -193,4 +193,6 @@ __global__ void k_teacher(const double* __restrict__ pa, const double* __restric
 // stream synchronisation.
 int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* total,
                        cudaStream_t s);
+// ascending bitonic sort of a[m_pad] in place (m_pad a power of two >= 2)
+int bitonic_sort(uint64_t* a, int64_t m_pad, cudaStream_t s);
 }  // namespace hinqs
