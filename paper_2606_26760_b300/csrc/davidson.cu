@@ -36,13 +36,39 @@ constexpr int kRedThreads = 256;
 
 // ---------------------------------------------------------------- kernels --
 
+// The block that finishes last among the gridDim.x blocks of one output sums that
+// output's partials in a fixed order (lane-strided, then a shuffle tree, so the
+// result does not depend on which block came last) and re-arms the counter.
+__device__ __forceinline__ void last_block_reduce(const double* __restrict__ partial, int nb,
+                                                  unsigned int* counter, double* out) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 32) {
+    const volatile double* p = partial;
+    double v = 0.0;
+    for (int b = threadIdx.x; b < nb; b += 32) v += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0) {
+      *out = v;
+      *counter = 0u;
+    }
+  }
+}
+
 // partial[i*gridDim.x + b] = block b's share of A_i . bvec (grid.y = vector i).
 // FP32 x FP32 products are summed in FP32 over groups of four strided elements and
 // the group sums in FP64; every other combination is formed and summed in FP64.
 template <typename TA, typename TB>
 __global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, int64_t lda,
                                                       const TB* __restrict__ b, int64_t N,
-                                                      double* __restrict__ partial) {
+                                                      double* __restrict__ partial,
+                                                      unsigned int* counters, double* out) {
   const int i = blockIdx.y;
   const TA* __restrict__ a = A + (int64_t)i * lda;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -68,6 +94,8 @@ __global__ void __launch_bounds__(kRedThreads) k_dots(const TA* __restrict__ A, 
     for (int w = 0; w < kRedThreads / 32; ++w) v += red[w];
     partial[(int64_t)i * gridDim.x + blockIdx.x] = v;
   }
+  if (counters)
+    last_block_reduce(partial + (int64_t)i * gridDim.x, gridDim.x, counters + i, out + i);
 }
 
 // Two products per vector in one pass over A: partial[i*gridDim.x + b] = block b's
@@ -77,7 +105,9 @@ template <typename TA, typename TB>
 __global__ void __launch_bounds__(kRedThreads) k_dots2(const TA* __restrict__ A, int64_t lda,
                                                        const TB* __restrict__ b1,
                                                        const TB* __restrict__ b2, int64_t N,
-                                                       double* __restrict__ partial) {
+                                                       double* __restrict__ partial,
+                                                       unsigned int* counters, double* out1,
+                                                       double* out2) {
   const int i = blockIdx.y;
   const TA* __restrict__ a = A + (int64_t)i * lda;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -118,20 +148,26 @@ __global__ void __launch_bounds__(kRedThreads) k_dots2(const TA* __restrict__ A,
     for (int w = 0; w < kRedThreads / 32; ++w) v += red[threadIdx.x][w];
     partial[((int64_t)threadIdx.x * gridDim.y + i) * gridDim.x + blockIdx.x] = v;
   }
-}
-
-// out[i] = sum_b partial[i*nb + b] (fixed order: deterministic); one warp per i
-__global__ void k_reduce_partials(const double* __restrict__ partial, int nb, int m,
-                                  double* __restrict__ out) {
-  const int lane = threadIdx.x & 31;
-  for (int i = threadIdx.x >> 5; i < m; i += blockDim.x >> 5) {
+  // one counter per vector: the last block sums both outputs of vector i
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counters + i, 1u) == gridDim.x - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  if (threadIdx.x < 64) {
+    const int which = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const volatile double* p = partial + ((int64_t)which * gridDim.y + i) * gridDim.x;
     double v = 0.0;
-    for (int b = lane; b < nb; b += 32) v += partial[(int64_t)i * nb + b];
+    for (int b = lane; b < (int)gridDim.x; b += 32) v += p[b];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if (lane == 0) out[i] = v;
+    if (lane == 0) (which ? out2 : out1)[i] = v;
   }
+  if (threadIdx.x == 0) counters[i] = 0u;
 }
+
 
 // out (FP64) = (mode 0: 0, 1: out, -1: out) +/- sum_i coef[i] * A_i.  For FP32 A the
 // combination is formed in FP32 (it is a correction whose rounding is relative to
@@ -219,7 +255,7 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     const double* __restrict__ x0, const double* __restrict__ s0, const TV* __restrict__ V,
     const TV* __restrict__ W, int64_t ld, int m, const double* __restrict__ ritz, /* [0]=theta, [1..]=y */
     int has_x0, const double* __restrict__ D, double floor_, int64_t N, double* __restrict__ t,
-    double* __restrict__ partial) {
+    double* __restrict__ partial, unsigned int* counter = nullptr, double* rr_out = nullptr) {
   __shared__ double y[kMaxSub + 1];
   __shared__ float yf[kMaxSub + 1];
   __shared__ double red[kRedThreads / 32];
@@ -285,6 +321,7 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     for (int w = 0; w < kRedThreads / 32; ++w) v += red[w];
     partial[blockIdx.x] = v;
   }
+  if (counter) last_block_reduce(partial, gridDim.x, counter, rr_out);
 }
 
 // Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
@@ -556,13 +593,14 @@ struct Ctx {
   double* partial = nullptr;  // [2 * (kMaxSub+1) * kRedGrid] >= kResGrid
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
   float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
+  unsigned int* counters = nullptr;  // [kMaxSub + 1] arrival counters of the dot kernels (zero)
 };
 
 template <typename TA, typename TB>
 static int dots(Ctx& c, const TA* A, int64_t lda, int m, const TB* b, double* out) {
   if (m <= 0) return HINQS_OK;
-  k_dots<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b, c.N, c.partial);
-  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, m, out);
+  k_dots<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b, c.N, c.partial,
+                                                               c.counters, out);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -572,9 +610,8 @@ template <typename TA, typename TB>
 static int dots2(Ctx& c, const TA* A, int64_t lda, int m, const TB* b1, const TB* b2,
                  double* out1, double* out2) {
   if (m <= 0) return HINQS_OK;
-  k_dots2<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b1, b2, c.N, c.partial);
-  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kRedGrid, m, out1);
-  k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial + (size_t)m * kRedGrid, kRedGrid, m, out2);
+  k_dots2<TA, TB><<<dim3(kRedGrid, m), kRedThreads, 0, c.s>>>(A, lda, b1, b2, c.N, c.partial,
+                                                                c.counters, out1, out2);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
@@ -732,8 +769,8 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
       k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
       k_residual<double><<<kResGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
-                                                            D, o.denom_floor, N, t, c.partial);
-      k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
+                                                            D, o.denom_floor, N, t, c.partial,
+                                                            c.counters + kMaxSub, col + kMaxSub);
       HQ_LAUNCH_CHECK();
       double hres = 0.0;
       HQ_CUDA(cudaMemcpyAsync(hr, ritz, (kMaxSub + 1) * sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -907,8 +944,8 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         k_init_pencil<<<1, 256, 0, c.s>>>(G1, nullptr, th);
         k_rr<<<1, kRRThreads, 0, c.s>>>(G1, kMaxSub, 1, ritz1, nullptr);  // (theta, 1)
         k_residual<float><<<kResGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, 0, ritz1, 1, D,
-                                                             o.denom_floor, N, t, c.partial);
-        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
+                                                             o.denom_floor, N, t, c.partial,
+                                                             c.counters + kMaxSub, col + kMaxSub);
         HQ_LAUNCH_CHECK();
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz1, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -951,8 +988,8 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       for (;;) {
         k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
         k_residual<float><<<kResGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
-                                                             o.denom_floor, N, t, c.partial);
-        k_reduce_partials<<<1, 1024, 0, c.s>>>(c.partial, kResGrid, 1, col + kMaxSub);
+                                                             o.denom_floor, N, t, c.partial,
+                                                             c.counters + kMaxSub, col + kMaxSub);
         HQ_LAUNCH_CHECK();
         HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
@@ -1073,8 +1110,11 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   double* D = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&c.partial, 2 * kRedGrid * (kMaxSub + 1), c.s)) ||
-      (rc = dalloc(&c.small, 4 * (kMaxSub + 2), c.s)) || (rc = dalloc(&D, c.N, c.s))) {
+      (rc = dalloc(&c.small, 4 * (kMaxSub + 2), c.s)) ||
+      (rc = dalloc(&c.counters, kMaxSub + 1, c.s)) || (rc = dalloc(&D, c.N, c.s))) {
   }
+  if (!rc && cudaMemsetAsync(c.counters, 0, (kMaxSub + 1) * sizeof(unsigned int), c.s) != cudaSuccess)
+    rc = cuda_fail(cudaGetLastError(), "hinqs_davidson counters", __FILE__, __LINE__);
   if (!rc) rc = diag_launch(H, B, la, lb, D, c.s);
   if (!rc) {
     if (o.precision == HINQS_DAVIDSON_FP64)
@@ -1092,6 +1132,7 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   }
   dfree(c.partial, c.s);
   dfree(c.small, c.s);
+  dfree(c.counters, c.s);
   dfree(D, c.s);
   info.trace_len = tr.len;
   info.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - tr.t0).count();
