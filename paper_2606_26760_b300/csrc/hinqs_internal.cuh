@@ -122,7 +122,8 @@ struct hinqs_links_s {
   int* scount = nullptr;
   // the same slots for the tensor-core gather: {J, kpart | (sign < 0) << 31} with kpart
   // the byte offset of the folded pair kf = max(p,q)(max(p,q)+1)/2 + min(p,q) inside a
-  // K-major core-matrix row, (kf / 8) * 128 + (kf % 8) * 2
+  // K-major core-matrix row, (kf / 8) * 128 + (kf % 8) * 2; pair-major, slot k of row
+  // I at ((k / 2) * N + I) * 2 + k % 2, so one 16-byte load brings two slots
   int2* tcell = nullptr;
   // all links as packed records for the row products: element offset of the linked
   // row (J * other dimension, uint32) with the element: rec32 {off, float bits},

@@ -174,21 +174,21 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
       const int2 l = sl[q];
       ell[(int64_t)k * N + I] = l;
       const int kp = tc_kpart((l.y > 0 ? l.y : -l.y) - 1, n);
-      tcell[(int64_t)k * N + I] = make_int2(l.x, l.y > 0 ? kp : (int)((unsigned)kp | 0x80000000u));
+      tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] =
+          make_int2(l.x, l.y > 0 ? kp : (int)((unsigned)kp | 0x80000000u));
     }
     uint64_t o = S[I];
     while (o) {
       int j = __ffsll((long long)o) - 1;
       o &= o - 1;
       ell[(int64_t)k * N + I] = make_int2((int)I, j * n + j + 1);
-      tcell[(int64_t)k * N + I] = make_int2((int)I, tc_kpart(j * n + j, n));
+      tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] = make_int2((int)I, tc_kpart(j * n + j, n));
       ++k;
     }
     cnt[I] = k;
-    for (; k < width; ++k) {
-      ell[(int64_t)k * N + I] = make_int2(0, 0);
-      tcell[(int64_t)k * N + I] = make_int2(0, 0);
-    }
+    for (; k < width; ++k) ell[(int64_t)k * N + I] = make_int2(0, 0);
+    for (k = cnt[I]; k < ((width + 1) & ~1); ++k)
+      tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] = make_int2(0, 0);
   }
 }
 
@@ -322,7 +322,7 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
   if (!rc) {
     L->ell_width = L->max_srow + L->n_e;
     if (!(rc = dalloc(&L->sell, (size_t)std::max(1, L->ell_width) * N, s)) &&
-        !(rc = dalloc(&L->tcell, (size_t)std::max(1, L->ell_width) * N, s)) &&
+        !(rc = dalloc(&L->tcell, (size_t)std::max(2, (L->ell_width + 1) & ~1) * N, s)) &&
         !(rc = dalloc(&L->scount, N, s))) {
       k_build_ell<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs), 256, 0, s>>>(
           L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->tcell, L->scount);

@@ -200,17 +200,23 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
     const int64_t Ib = (int64_t)t * kTileM + m;
     if (Ib < Nb) {
       const int nk = __ldg(A.b_cnt + Ib);
-      const int2* __restrict__ ell = A.b_ell + Ib;
-      for (int k0 = hh; k0 < nk; k0 += 16) {
-        int2 l[8];  // eight link records in flight before any shared-memory store
+      // pair-major slots: thread hh takes slot pairs hh, hh + 2, ...; one 16-byte load
+      // per pair, four pairs (eight records) in flight before any shared-memory store
+      const int4* __restrict__ ell = reinterpret_cast<const int4*>(A.b_ell) + Ib;
+      const int np = (nk + 1) >> 1;
+      for (int j0 = hh; j0 < np; j0 += 8) {
+        int4 l[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          l[u] = (k0 + 2 * u < nk) ? __ldg(ell + (int64_t)(k0 + 2 * u) * Nb) : make_int2(0, 0);
+        for (int u = 0; u < 4; ++u)
+          l[u] = (j0 + 2 * u < np) ? __ldg(ell + (int64_t)(j0 + 2 * u) * Nb)
+                                   : make_int4(0, 0, 0, 0);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          if (k0 + 2 * u >= nk) break;
-          const uint32_t y = (uint32_t)l[u].y;
-          const float v = __uint_as_float(__float_as_uint(crow[l[u].x]) ^ (y & 0x80000000u));
+          const int k = 2 * (j0 + 2 * (u >> 1)) + (u & 1);
+          if (k >= nk) break;
+          const int x = (u & 1) ? l[u >> 1].z : l[u >> 1].x;
+          const uint32_t y = (uint32_t)((u & 1) ? l[u >> 1].w : l[u >> 1].y);
+          const float v = __uint_as_float(__float_as_uint(crow[x]) ^ (y & 0x80000000u));
           const uint32_t off = y & 0x7fffffffu;  // kpart of the folded pair
           const __nv_bfloat16 hi = __float2bfloat16_rn(v);
           *reinterpret_cast<__nv_bfloat16*>(ah + off) = hi;
