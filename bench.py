@@ -36,7 +36,7 @@ SM_MAX_MHZ = 2032
 # DRAM bytes (read + write) per product half from ncu captures of the precision
 # workload (profiles/): same-spin = its two row-product launches; None where the
 # kernel changed after the capture
-PROFILED_TRAFFIC = {"same": 62.77e6, "opposite": 33.36e6}
+PROFILED_TRAFFIC = {"same": 62.77e6, "opposite": 33.32e6}
 WORKLOAD = "precision"
 
 
@@ -355,6 +355,107 @@ def run_bond_scan(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------- large space --
+
+def run_large(args):
+    """n_orb = 26, (7,7), 20000 x 20000 strings (4e8 determinants): one step =
+    Hamiltonian, subspace, links, mixed Davidson (BF16 tensor-core inner sigma, FP64
+    refinement, subspace of 8) to a 1e-5 residual (energy converged far below
+    1e-6 Ha: the error is about residual^2 / gap), RDMs with the backward and the
+    marginals.  The FP64 Davidson is not run here (about 150 FP64 products of ~3 s);
+    one FP64 sigma is timed instead."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2606_26760_b300 import build as _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    import paper_2606_26760_b300 as hq
+    import synth
+
+    w = synth.workload("large")
+    n, na, nb = w["n_orb"], w["n_alpha"], w["n_beta"]
+    dev = torch.device("cuda", local)
+    h_d = torch.tensor(w["h"], device=dev)
+    eri_d = torch.tensor(w["eri"], device=dev)
+    a_d = torch.from_numpy(w["alpha"].view(np.int64)).to(dev)
+    b_d = torch.from_numpy(w["beta"].view(np.int64)).to(dev)
+    stream = torch.cuda.current_stream()
+    opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2,
+                tol_residual=1e-5, tol_energy=1e-7, max_subspace=8, max_iter=300)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    parts = {}
+
+    def step():
+        t = {}
+        ev0.record(stream)
+        ham = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
+        sub = hq.build_subspace(a_d, b_d, n, na, nb)
+        la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
+        hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16AB)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t["setup_s"] = ev0.elapsed_time(ev1) / 1e3
+        ev0.record(stream)
+        res = hq.davidson(ham, sub, la, lb, **opts)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t["solve_s"] = ev0.elapsed_time(ev1) / 1e3
+        ev0.record(stream)
+        g1, g2 = hq.rdm(sub, la, lb, res.c)
+        gh, ge = hq.energy_backward(n, 1.0, g1, g2)
+        pa, pb = hq.spin_marginals(sub, res.c)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        t["rdm_backward_marginals_s"] = ev0.elapsed_time(ev1) / 1e3
+        parts.update(t)
+        return ham, sub, la, lb, res, g1, g2
+
+    for _ in range(args.warmup):
+        step()
+    times = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ham, sub, la, lb, res, g1, g2 = step()
+        torch.cuda.synchronize()
+        times.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    e_id = float((h_d * g1).sum() + 0.5 * (eri_d * g2).sum()) + w["e_nuc"]
+    sig = {}
+    for name, p in (("fp32_bf16ab", hq.PREC_FP32_BF16AB), ("fp32", hq.PREC_FP32),
+                    ("fp64", hq.PREC_FP64)):
+        x = torch.rand(sub.N, device=dev, dtype=torch.float64 if p == hq.PREC_FP64 else torch.float32)
+        y = torch.empty_like(x)
+        hq.sigma(ham, sub, la, lb, x, out=y, precision=p)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        hq.sigma(ham, sub, la, lb, x, out=y, precision=p)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        sig[name] = ev0.elapsed_time(ev1)
+        del x, y
+    t_mean = sum(times) / len(times)
+    print(json.dumps({
+        "metric": METRIC, "value": sub.N / t_mean, "unit": "dets/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+bf16+f64", "data": "synthetic",
+        "config": {"workload": f"large: n_orb={n} n_alpha={na} n_beta={nb} {sub.Na}x{sub.Nb} "
+                               f"strings, N={sub.N} determinants",
+                   "step": "ham+subspace+links+mixed Davidson (m_max 8) to 1e-5 residual+RDM "
+                           "backward+marginals"},
+        "parts_s": parts, "sigma_ms": sig,
+        "energy": {"mixed": res.energy, "residual": res.residual, "status": int(res.status),
+                   "sigmas_fp64_fp32": [res.n_sigma_fp64, res.n_sigma_fp32],
+                   "rdm_energy_identity_Ha": e_id - res.energy},
+        "clocks": clk}), flush=True)
+
+
 # ------------------------------------------------------------------ B300 --
 
 def main():
@@ -363,6 +464,8 @@ def main():
         return run_reference(args)
     if args.workload == "bond_scan":
         return run_bond_scan(args)
+    if args.workload == "large":
+        return run_large(args)
     import numpy as np
     import torch
     import torch.distributed as dist

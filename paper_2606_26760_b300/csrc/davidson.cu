@@ -353,6 +353,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
   const int lane = threadIdx.x;  // thread index in the block
   const unsigned full = 0xffffffffu;
   __shared__ double red2[kRRThreads / 32][2];
+  __shared__ double Linv[kMaxSub];  // 1 / L[j][j]: one division per pivot, products after
   const int mm = m + (m & 1);  // even size for the tournament; the pad row/col is isolated
   bool use_s = false;
   if (S) {
@@ -366,13 +367,16 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
         use_s = false;
         break;
       }
-      const double ljj = sqrt(d);
+      const double ljj = sqrt(d), inv = 1.0 / ljj;
       for (int i = j + 1 + lane; i < m; i += kRRThreads) {
         double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
         for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-        L[i][j] = v / ljj;
+        L[i][j] = v * inv;
       }
-      if (lane == 0) L[j][j] = ljj;
+      if (lane == 0) {
+        L[j][j] = ljj;
+        Linv[j] = inv;
+      }
       __syncthreads();
     }
   }
@@ -382,7 +386,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
       for (int i = 0; i < m; ++i) {
         double v = 0.5 * (G[i * ldg + lane] + G[lane * ldg + i]);
         for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][lane];
-        X[i][lane] = v / L[i][i];
+        X[i][lane] = v * Linv[i];
       }
     }
     __syncthreads();
@@ -390,7 +394,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
       for (int i = 0; i < m; ++i) {
         double v = X[lane][i];
         for (int k = 0; k < i; ++k) v -= L[i][k] * A[k][lane];
-        A[i][lane] = v / L[i][i];
+        A[i][lane] = v * Linv[i];
       }
     }
     __syncthreads();
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
         for (int i = m - 1; i >= 0; --i) {
           double v = z[i];
           for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
-          z[i] = v / L[i][i];
+          z[i] = v * Linv[i];
         }
       }
       if (rank == 0) {
