@@ -12,6 +12,11 @@ it with ctypes and adds the numpy-level steps:
                       numpy.linalg.eigh (a library primitive) on the dense matrix.
 * lanczos          -- Step 3 for subspaces too large for a dense matrix: Lanczos
                       with full reorthogonalisation on the matrix-free sigma.
+* outer loop       -- candidate pools (Steps 1, 1'), the Step 2 basis update
+                      (select_top, basis_update), H_xx of arbitrary determinants,
+                      the Step 3 warm start (remap_vector), the Step 4 loss inputs
+                      (nqs_loss: Eqs. teacher, energy, entropy, loss) and the Step 5
+                      stopping rule, by sorts, sets and dictionaries.
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  The CUDA library never loads it.
@@ -295,3 +300,158 @@ def lanczos(H: Ham, sa, sb, tol: float = 1e-10, max_iter: int = 400, seed: int =
 def energy_from_rdm(H: Ham, g1, g2, norm2: float = 1.0):
     """<c|H|c> = sum h g1 + 1/2 sum (pq|rs) g2 + E_nuc <c|c>."""
     return float(np.sum(H.h * g1) + 0.5 * np.sum(H.eri * g2) + H.e_nuc * norm2)
+
+
+# ------------------------------------------------------------------------------------
+# Outer loop of Sec. 2.2 around the subspace solve: candidate pools (Steps 1 and 1'),
+# the basis update of Step 2, the warm start of Step 3, the inputs of the NQS losses
+# of Step 4 (Eqs. teacher, energy, entropy, loss) and the stopping rule of Step 5.
+# Plain set / sort / dictionary definitions; the matrix elements come from the C
+# oracle above.
+
+BASIS_COLD_START, BASIS_RESCORE, BASIS_APPEND = 0, 1, 2
+
+
+def select_top(values, k: int, largest: bool = True):
+    """Positions of the k largest (largest=True) or smallest values, ties to the lower
+    position, returned ascending.  Step 2 keeps the top K candidates by s(x) and the
+    cold start the K_0 lowest H_xx.  Finite values and +-inf only."""
+    v = np.asarray(values, dtype=np.float64)
+    k = max(0, min(int(k), len(v)))
+    order = np.lexsort((np.arange(len(v)), -v if largest else v))
+    return np.sort(order[:k])
+
+
+def determinant_diag(H: Ham, xa, xb):
+    """H_xx = <x|H|x> (incl. E_nuc) of arbitrary determinants x = (xa[k], xb[k]):
+    the cold-start ranking of Step 2, computed by the operator application of
+    oracle_coupling (a one-determinant subspace with a zero vector is passed, so only
+    the diagonal is used)."""
+    xa, xb = _u64(xa), _u64(xb)
+    if len(xa) == 0:
+        return np.zeros(0)
+    _, hxx, _ = pt2_scores(H, xa[:1], xb[:1], np.zeros(1), 0.0, xa, xb)
+    return hxx
+
+
+def lookup(sa, sb, xa, xb):
+    """Index I = i_a * N_b + i_b of each determinant (xa[k], xb[k]) in the product
+    subspace S_a x S_b, or -1 when it is not there."""
+    pos_a = {int(s): i for i, s in enumerate(np.asarray(sa, dtype=np.uint64).tolist())}
+    pos_b = {int(s): i for i, s in enumerate(np.asarray(sb, dtype=np.uint64).tolist())}
+    Nb = len(pos_b)
+    out = np.full(len(xa), -1, dtype=np.int64)
+    for k, (a, b) in enumerate(zip(np.asarray(xa, dtype=np.uint64).tolist(),
+                                   np.asarray(xb, dtype=np.uint64).tolist())):
+        if a in pos_a and b in pos_b:
+            out[k] = pos_a[a] * Nb + pos_b[b]
+    return out
+
+
+def candidate_pool(pools, exclude, n_alpha: int, n_beta: int):
+    """Candidate set C_t of Steps 1 and 1': the distinct determinants of the union of
+    `pools` (a list of (xa, xb) pairs of arrays: NQS samples, classical expansion)
+    that have the sector's electron counts (the particle-number safety filter of
+    Sec. 2.1) and are not in `exclude` = (ea, eb), the cumulative basis (Step 1
+    removes configurations duplicating entries of B).  Returns (ya, yb, n_dropped)
+    ascending in (alpha, beta); n_dropped counts pool entries with a wrong count."""
+    ex = set(zip(np.asarray(exclude[0], dtype=np.uint64).tolist(),
+                 np.asarray(exclude[1], dtype=np.uint64).tolist()))
+    keep, dropped = set(), 0
+    for xa, xb in pools:
+        for a, b in zip(np.asarray(xa, dtype=np.uint64).tolist(),
+                        np.asarray(xb, dtype=np.uint64).tolist()):
+            if popcount(a) != n_alpha or popcount(b) != n_beta:
+                dropped += 1
+            elif (a, b) not in ex:
+                keep.add((a, b))
+    out = sorted(keep)
+    return (np.array([t[0] for t in out], dtype=np.uint64),
+            np.array([t[1] for t in out], dtype=np.uint64), dropped)
+
+
+def basis_update(mode: int, basis, cand, k: int, b_max: int = 0):
+    """Step 2 basis update.  basis = (ba, bb, bs) and cand = (ca, cb, cs): determinants
+    with their keys (H_xx for the cold start, s(x) of Eq. pt2_score otherwise).
+      BASIS_COLD_START (t = 0): B = the k candidates with the lowest H_xx.
+      BASIS_RESCORE    (t = 1): B = the k best of B u C by s(x), no cap.
+      BASIS_APPEND     (t >= 2): the k best candidates are appended to B; while
+                       |B| > b_max (b_max > 0) the lowest-scored entries are evicted.
+    Ties go to the earlier entry of the sequence (basis first, then candidates), and
+    the kept entries stay in that order.  Returns (ba, bb, bs)."""
+    ba, bb, bs = (np.asarray(x) for x in basis)
+    ca, cb, cs = (np.asarray(x) for x in cand)
+    ba, bb, ca, cb = (x.astype(np.uint64) for x in (ba, bb, ca, cb))
+    bs, cs = bs.astype(np.float64), cs.astype(np.float64)
+    if mode == BASIS_COLD_START:
+        sel = select_top(cs, k, largest=False)
+        return ca[sel], cb[sel], cs[sel]
+    if mode == BASIS_RESCORE:
+        pa, pb, ps = (np.concatenate(x) for x in ((ba, ca), (bb, cb), (bs, cs)))
+        sel = select_top(ps, k)
+        return pa[sel], pb[sel], ps[sel]
+    if mode == BASIS_APPEND:
+        sel = select_top(cs, k)
+        pa, pb, ps = (np.concatenate(x) for x in ((ba, ca[sel]), (bb, cb[sel]), (bs, cs[sel])))
+        if b_max > 0 and len(ps) > b_max:
+            keep = select_top(ps, b_max)
+            pa, pb, ps = pa[keep], pb[keep], ps[keep]
+        return pa, pb, ps
+    raise ValueError(f"unknown basis update mode {mode}")
+
+
+def remap_vector(sa_old, sb_old, c_old, sa_new, sb_new):
+    """Warm start of Step 3 after a basis change: the previous eigenvector carried to
+    the new product subspace, c_new[I'] = c_old[I] where determinant I' of the new
+    subspace is determinant I of the old one, else 0."""
+    na_new, nb_new = len(sa_new), len(sb_new)
+    xa = np.repeat(np.asarray(sa_new, dtype=np.uint64), nb_new)
+    xb = np.tile(np.asarray(sb_new, dtype=np.uint64), na_new)
+    old = lookup(sa_old, sb_old, xa, xb)
+    c_old = np.asarray(c_old, dtype=np.float64)
+    return np.where(old >= 0, c_old[np.maximum(old, 0)], 0.0)
+
+
+def nqs_loss(H: Ham, sa, sb, c, E0: float, batch, log_pi, coef=(1.0, 1.0, 1.0), basis=None):
+    """Inputs and values of the NQS losses of Step 4 on a minibatch.
+      p_alpha, p_beta  spin marginals of |Psi0|^2 (Eqs. alpha_marginal, beta_marginal)
+      w(x)   = p_alpha(x_a) p_beta(x_b) / sum_{x' in B} p_alpha(x'_a) p_beta(x'_b)
+               (B = `basis`, product-subspace indices, or the whole product if None)
+      A(x)   = H_xx - E0                              (advantage, Eq. energy)
+      L_teacher = - sum_{x in M} w(x) log pi(x)       (Eq. teacher)
+      L_energy  =   sum_{x in M} w(x) A(x) log pi(x)  (Eq. energy)
+      L_entropy =   (1/|M|) sum_{x in M} log pi(x)    (Eq. entropy)
+      L_total   = coef . (L_teacher, L_energy, L_entropy)   (Eq. loss)
+      grad[x]   = d L_total / d log pi(x)
+    over the minibatch M = `batch` (product-subspace indices).  Returns a dict."""
+    sa, sb = _u64(sa), _u64(sb)
+    Na, Nb = len(sa), len(sb)
+    batch = np.asarray(batch, dtype=np.int64)
+    log_pi = _f64(log_pi)
+    pa, pb = marginals(c, Na, Nb)
+    members = np.arange(Na * Nb) if basis is None else np.asarray(basis, dtype=np.int64)
+    Z = 0.0
+    for I in members.tolist():
+        Z += pa[I // Nb] * pb[I % Nb]
+    w = pa[batch // Nb] * pb[batch % Nb] / Z
+    hxx = diag(H, sa, sb, rows=batch)
+    A = hxx - E0
+    M = len(batch)
+    lt = -float(np.sum(w * log_pi))
+    le = float(np.sum(w * A * log_pi))
+    ls = float(np.sum(log_pi)) / M if M else 0.0
+    ct, ce, cs = (float(x) for x in coef)
+    grad = -ct * w + ce * w * A + (cs / M if M else 0.0)
+    return dict(w=w, A=A, hxx=hxx, teacher=lt, energy=le, entropy=ls,
+                total=ct * lt + ce * le + cs * ls, grad=grad)
+
+
+def converged(energies, delta: float = 1e-9, patience: int = 5, max_iter: int = 50) -> bool:
+    """Step 5: stop when |E(t) - E(t-1)| < delta for `patience` consecutive iterations,
+    or after max_iter iterations."""
+    if len(energies) >= max_iter:
+        return True
+    if len(energies) <= patience:
+        return False
+    d = np.abs(np.diff(np.asarray(energies, dtype=np.float64)))
+    return bool(np.all(d[-patience:] < delta))
