@@ -327,6 +327,100 @@ int hinqs_classical_expansion(const hinqs_ham* ham, const hinqs_subspace* sub, c
                               int64_t n_top, uint64_t* xa_out, uint64_t* xb_out, int64_t cap,
                               int64_t* count, void* stream);
 
+/* ----------------------------------------------------------- outer loop --
+ * The steps of the HI-NQS iteration (Sec. 2.2) that surround the subspace solve.
+ * The cumulative basis B of Step 2 is a list of determinants (x_a[i], x_b[i]) with a
+ * score each; Step 3 diagonalises on the product of its distinct alpha and beta
+ * strings (hinqs_build_subspace), which contains the list.
+ *
+ * hinqs_select_top (Step 2 ranking): positions of the k largest (largest != 0) or
+ * smallest values of values[m], ties to the lower position, written ascending to
+ * idx_out (device int64 [min(k, m)]).  Exact (radix selection on order-preserving
+ * 64-bit keys; -0 equals +0; a NaN ranks below every number in both directions).
+ * Synchronises the stream. */
+int hinqs_select_top(const double* values, int64_t m, int64_t k, int largest, int64_t* idx_out,
+                     void* stream);
+
+/* hinqs_determinant_diag (Step 2 cold start ranks candidates by H_xx):
+ * hxx[k] = <x_k|H|x_k> (incl. E_nuc) for arbitrary determinants x_k = (xa[k], xb[k]),
+ * in the subspace or not.  Errors: HINQS_ERR_ARG, HINQS_ERR_PARTICLE_NUMBER (a string
+ * with the wrong electron count or bits >= n_orb: its output is NaN, the others are
+ * valid).  Synchronises the stream. */
+int hinqs_determinant_diag(const hinqs_ham* ham, const uint64_t* xa, const uint64_t* xb, int64_t m,
+                           double* hxx, void* stream);
+
+/* hinqs_lookup_determinants: idx[k] = i_a * N_b + i_b when (xa[k], xb[k]) lies in the
+ * product subspace, else -1 (device int64 [m]).  Maps basis-list entries to positions
+ * of the eigenvector (teacher weights, PT2 scores of basis entries). */
+int hinqs_lookup_determinants(const hinqs_subspace* sub, const uint64_t* xa, const uint64_t* xb,
+                              int64_t m, int64_t* idx, void* stream);
+
+/* hinqs_candidate_pool (Steps 1 and 1'): the candidate set C_t = C_NQS u C_cl.  The
+ * distinct determinants among the two proposal lists (xa1, xb1)[m1] (e.g. NQS samples)
+ * and (xa2, xb2)[m2] (e.g. the classical expansion) that pass the particle-number
+ * filter of Sec. 2.1 (n_alpha / n_beta of `ham`, no bit at or above n_orb; the
+ * rejected entries are counted in *n_dropped, host, may be NULL) and are not in the
+ * excluded list (ea, eb)[me] (the cumulative basis: Step 1 removes configurations
+ * that duplicate it).  Output ascending in (alpha, beta) into ya/yb (device uint64
+ * [cap]); *count (host) = number of candidates; with ya or yb NULL only the counts
+ * are returned.  Requires n_orb <= 32.  Errors: HINQS_ERR_ARG (NULL, n_orb > 32,
+ * cap < *count: nothing written), HINQS_ERR_OOM.  Synchronises the stream. */
+int hinqs_candidate_pool(const hinqs_ham* ham, const uint64_t* xa1, const uint64_t* xb1,
+                         int64_t m1, const uint64_t* xa2, const uint64_t* xb2, int64_t m2,
+                         const uint64_t* ea, const uint64_t* eb, int64_t me, uint64_t* ya,
+                         uint64_t* yb, int64_t cap, int64_t* count, int64_t* n_dropped,
+                         void* stream);
+
+/* hinqs_basis_update (Step 2).  Basis (ba, bb, bs)[nb] and candidates (ca, cb, cs)[nc]
+ * with their keys (H_xx for the cold start, s(x) of Eq. pt2_score otherwise); the
+ * caller keeps candidates distinct and outside the basis (hinqs_candidate_pool).
+ *   HINQS_BASIS_COLD_START (t = 0): the k candidates with the lowest key.
+ *   HINQS_BASIS_RESCORE    (t = 1): the k best of basis + candidates by score, no cap.
+ *   HINQS_BASIS_APPEND     (t >= 2): the basis plus the k best candidates; when that
+ *                          exceeds b_max > 0 entries, the lowest-scored are evicted
+ *                          down to b_max (b_max = 0: no cap).
+ * Ties go to the earlier entry of the sequence basis-then-candidates, and kept entries
+ * keep that order.  Output (oa, ob, os)[cap] (device; must not overlap the inputs),
+ * *n_out (host) entries.  Errors: HINQS_ERR_ARG (NULL, negative size, unknown mode,
+ * cap below the result), HINQS_ERR_OOM.  Synchronises the stream. */
+#define HINQS_BASIS_COLD_START 0
+#define HINQS_BASIS_RESCORE 1
+#define HINQS_BASIS_APPEND 2
+int hinqs_basis_update(int mode, const uint64_t* ba, const uint64_t* bb, const double* bs,
+                       int64_t nb, const uint64_t* ca, const uint64_t* cb, const double* cs,
+                       int64_t nc, int64_t k, int64_t b_max, uint64_t* oa, uint64_t* ob,
+                       double* os, int64_t cap, int64_t* n_out, void* stream);
+
+/* hinqs_remap_vector (Step 3 warm start across iterations): c_new[I'] = c_old[I] when
+ * determinant I' of new_sub is determinant I of old_sub, else 0 (device FP64 vectors
+ * of the two subspaces' sizes, not overlapping).  *kept_norm2 (host, may be NULL) =
+ * |c_new|^2; when it is 0 there is nothing to warm-start from.  Errors:
+ * HINQS_ERR_ARG (NULL, subspaces of different sectors), HINQS_ERR_OOM. */
+int hinqs_remap_vector(const hinqs_subspace* old_sub, const double* c_old,
+                       const hinqs_subspace* new_sub, double* c_new, double* kept_norm2,
+                       void* stream);
+
+/* hinqs_nqs_loss (Step 4, Eqs. teacher, energy, entropy and loss) on a minibatch M
+ * of basis determinants given as product-subspace positions batch[m]:
+ *   w[j]    = p_alpha(x_a) p_beta(x_b) / Z,  Z = sum over the basis of p_alpha p_beta
+ *             (basis = product positions [n_basis], or NULL for the whole product)
+ *   adv[j]  = A(x) = H_xx - e0                           (e0 includes E_nuc)
+ *   loss[1] = L_teacher = -sum_M w log pi,  loss[2] = L_energy = sum_M w A log pi,
+ *   loss[3] = L_entropy = (1/m) sum_M log pi,
+ *   loss[0] = coef[0] loss[1] + coef[1] loss[2] + coef[2] loss[3]
+ *   grad[j] = d loss[0] / d log_pi[j] = -coef[0] w + coef[1] w A + coef[2] / m
+ * p_alpha, p_beta: the spin marginals (hinqs_spin_marginals); log_pi [m]: the network's
+ * log-probabilities of the minibatch; coef: HOST double[3] (NULL = 1, 1, 1);
+ * w, adv, grad: device FP64 [m]; loss: device FP64 [4].  With M = B the sums are the
+ * paper's; on a minibatch they are the same sums restricted to it.
+ * Errors: HINQS_ERR_ARG (NULL, m = 0, handles of different problems, an index outside
+ * [0, N): its outputs are NaN), HINQS_ERR_OOM.  Synchronises the stream. */
+int hinqs_nqs_loss(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                   const hinqs_links* lb, const double* p_alpha, const double* p_beta, double e0,
+                   const int64_t* basis, int64_t n_basis, const int64_t* batch, int64_t m,
+                   const double* log_pi, const double* coef, double* w, double* adv, double* grad,
+                   double* loss, void* stream);
+
 /* ------------------------------------------------------------------ RDMs --
  * Spin-summed reduced density matrices of the state c (FP64 [N], used as given):
  *   rdm1[p*n+q]             = sum_s <c|a+_{ps} a_{qs}|c>

@@ -34,6 +34,7 @@ DROP_BAD, ERROR_BAD, FULL_SPACE = 0x0, 0x1, 0x2
 CHECK_SYMMETRY = 0x1
 PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB = 0, 1, 2, 3
 DAVIDSON_FP64, DAVIDSON_MIXED = 0, 1
+BASIS_COLD_START, BASIS_RESCORE, BASIS_APPEND = 0, 1, 2
 
 
 class HinqsError(RuntimeError):
@@ -74,6 +75,8 @@ EXPORTED = [
     "hinqs_spin_marginals_noalloc", "hinqs_sigma_same_spin", "hinqs_sigma_opposite_spin",
     "hinqs_links_max_singles", "hinqs_autotune", "hinqs_davidson_batch", "hinqs_links_tuning",
     "hinqs_pt2_score", "hinqs_top_amplitudes", "hinqs_classical_expansion",
+    "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
+    "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
 ]
 
 
@@ -118,6 +121,16 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_pt2_score.argtypes = [P, P, P, D, P, P, I64, P, P, P, P]
     lib.hinqs_top_amplitudes.argtypes = [P, P, I64, P, P]
     lib.hinqs_classical_expansion.argtypes = [P, P, P, I64, P, P, I64, PI64, P]
+    lib.hinqs_select_top.argtypes = [P, I64, I64, I, P, P]
+    lib.hinqs_determinant_diag.argtypes = [P, P, P, I64, P, P]
+    lib.hinqs_lookup_determinants.argtypes = [P, P, P, I64, P, P]
+    lib.hinqs_candidate_pool.argtypes = [P, P, P, I64, P, P, I64, P, P, I64, P, P, I64, PI64,
+                                         PI64, P]
+    lib.hinqs_basis_update.argtypes = [I, P, P, P, I64, P, P, P, I64, I64, I64, P, P, P, I64,
+                                       PI64, P]
+    lib.hinqs_remap_vector.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_double), P]
+    lib.hinqs_nqs_loss.argtypes = [P, P, P, P, P, P, D, P, I64, P, I64, P,
+                                   ctypes.POINTER(ctypes.c_double), P, P, P, P, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -440,6 +453,151 @@ def classical_expansion(ham, sub, c, n_top: int = 1000):
     _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, _ptr(xa),
                                           _ptr(xb), m, ctypes.byref(cnt), _stream()))
     return xa, xb
+
+
+def _f64_dev(x, n=None, what="values"):
+    t = _on_dev(x, torch.float64)
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{what} must have {n} elements")
+    return t
+
+
+def select_top(values, k: int, largest: bool = True):
+    """hinqs_select_top (Step 2 ranking): ascending positions (int64) of the k largest
+    (or smallest) values, ties to the lower position."""
+    v = _f64_dev(values)
+    k = max(0, min(int(k), v.numel()))
+    out = torch.empty(k, dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_select_top(_ptr(v), v.numel(), k, 1 if largest else 0, _ptr(out), _stream()))
+    return out
+
+
+def determinant_diag(ham, xa, xb):
+    """hinqs_determinant_diag: H_xx (incl. E_nuc) of arbitrary determinants."""
+    xa, xb = _u64(xa), _u64(xb)
+    if xa.numel() != xb.numel():
+        raise ValueError("xa and xb must have the same length")
+    out = torch.empty(xa.numel(), dtype=torch.float64, device=_dev())
+    _check(_lib.hinqs_determinant_diag(ham.handle, _ptr(xa), _ptr(xb), xa.numel(), _ptr(out),
+                                       _stream()))
+    return out
+
+
+def lookup_determinants(sub, xa, xb):
+    """hinqs_lookup_determinants: product-subspace position of each determinant, or -1."""
+    xa, xb = _u64(xa), _u64(xb)
+    if xa.numel() != xb.numel():
+        raise ValueError("xa and xb must have the same length")
+    out = torch.empty(xa.numel(), dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_lookup_determinants(sub.handle, _ptr(xa), _ptr(xb), xa.numel(), _ptr(out),
+                                          _stream()))
+    return out
+
+
+def candidate_pool(ham, first, second=None, exclude=None):
+    """hinqs_candidate_pool (Steps 1, 1'): distinct determinants of the proposal lists
+    `first` and `second` ((xa, xb) pairs) with the sector's electron counts, minus the
+    `exclude` list; returns (ya, yb, n_dropped), ascending in (alpha, beta)."""
+    def pair(p):
+        if p is None:
+            return None, None, 0
+        a, b = _u64(p[0]), _u64(p[1])
+        if a.numel() != b.numel():
+            raise ValueError("alpha and beta lists must have the same length")
+        return a, b, a.numel()
+    a1, b1, m1 = pair(first)
+    a2, b2, m2 = pair(second)
+    ea, eb, me = pair(exclude)
+    cnt, drop = ctypes.c_int64(), ctypes.c_int64()
+    args = (ham.handle, _ptr(a1), _ptr(b1), m1, _ptr(a2), _ptr(b2), m2, _ptr(ea), _ptr(eb), me)
+    _check(_lib.hinqs_candidate_pool(*args, None, None, 0, ctypes.byref(cnt), ctypes.byref(drop),
+                                     _stream()))
+    m = cnt.value
+    ya = torch.empty(m, dtype=torch.int64, device=_dev())
+    yb = torch.empty(m, dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_candidate_pool(*args, _ptr(ya), _ptr(yb), m, ctypes.byref(cnt),
+                                     ctypes.byref(drop), _stream()))
+    return ya, yb, drop.value
+
+
+def basis_update(mode: int, basis, cand, k: int, b_max: int = 0):
+    """hinqs_basis_update (Step 2): basis and cand are (xa, xb, key) triples (basis may
+    be None); returns the new basis (xa, xb, key)."""
+    def triple(t):
+        if t is None:
+            return None, None, None, 0
+        a, b, v = _u64(t[0]), _u64(t[1]), _f64_dev(t[2])
+        if not (a.numel() == b.numel() == v.numel()):
+            raise ValueError("determinant lists and keys must have the same length")
+        return a, b, v, a.numel()
+    ba, bb, bs, nb = triple(basis)
+    ca, cb, cs, nc = triple(cand)
+    k = max(0, int(k))
+    if mode == BASIS_COLD_START:
+        cap = min(k, nc)
+    elif mode == BASIS_RESCORE:
+        cap = min(k, nb + nc)
+    else:
+        cap = nb + min(k, nc)
+        if b_max > 0:
+            cap = min(cap, int(b_max))
+    dev = _dev()
+    oa = torch.empty(cap, dtype=torch.int64, device=dev)
+    ob = torch.empty(cap, dtype=torch.int64, device=dev)
+    os_ = torch.empty(cap, dtype=torch.float64, device=dev)
+    n_out = ctypes.c_int64()
+    _check(_lib.hinqs_basis_update(int(mode), _ptr(ba), _ptr(bb), _ptr(bs), nb, _ptr(ca), _ptr(cb),
+                                   _ptr(cs), nc, k, int(b_max), _ptr(oa), _ptr(ob), _ptr(os_), cap,
+                                   ctypes.byref(n_out), _stream()))
+    n = n_out.value
+    return oa[:n], ob[:n], os_[:n]
+
+
+def remap_vector(old_sub, c_old, new_sub):
+    """hinqs_remap_vector (Step 3 warm start): (c_new, |c_new|^2)."""
+    if c_old.dtype != torch.float64 or c_old.numel() != old_sub.N:
+        raise ValueError("c_old must be a float64 tensor of the old subspace size")
+    c_new = torch.empty(new_sub.N, dtype=torch.float64, device=_dev())
+    kept = ctypes.c_double()
+    _check(_lib.hinqs_remap_vector(old_sub.handle, _ptr(c_old), new_sub.handle, _ptr(c_new),
+                                   ctypes.byref(kept), _stream()))
+    return c_new, kept.value
+
+
+def nqs_loss(ham, sub, la, lb, p_alpha, p_beta, e0: float, batch, log_pi, coef=(1.0, 1.0, 1.0),
+             basis=None):
+    """hinqs_nqs_loss (Step 4): dict(w, adv, grad, loss) for the minibatch `batch`
+    (product-subspace positions); loss = [total, teacher, energy, entropy]."""
+    dev = _dev()
+    batch = _on_dev(batch, torch.int64)
+    lp = _f64_dev(log_pi, batch.numel(), "log_pi")
+    bas = None if basis is None else _on_dev(basis, torch.int64)
+    m = batch.numel()
+    w = torch.empty(m, dtype=torch.float64, device=dev)
+    adv, grad = torch.empty_like(w), torch.empty_like(w)
+    loss = torch.empty(4, dtype=torch.float64, device=dev)
+    cf = (ctypes.c_double * 3)(*[float(x) for x in coef])
+    _check(_lib.hinqs_nqs_loss(ham.handle, sub.handle, la.handle, lb.handle, _ptr(p_alpha),
+                               _ptr(p_beta), float(e0), _ptr(bas), 0 if bas is None else bas.numel(),
+                               _ptr(batch), m, _ptr(lp), cf, _ptr(w), _ptr(adv), _ptr(grad),
+                               _ptr(loss), _stream()))
+    return dict(w=w, adv=adv, grad=grad, loss=loss)
+
+
+class NqsLoss(torch.autograd.Function):
+    """L_total of Step 4 (Eq. loss) as a function of the network's log-probabilities
+    on a minibatch; the backward multiplies the library's d L_total / d log pi."""
+
+    @staticmethod
+    def forward(ctx, log_pi, ham, sub, la, lb, p_alpha, p_beta, e0, batch, coef, basis):
+        r = nqs_loss(ham, sub, la, lb, p_alpha, p_beta, e0, batch, log_pi.detach(), coef, basis)
+        ctx.save_for_backward(r["grad"])
+        return r["loss"][0].to(log_pi.dtype)
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return (g * grad).to(g.dtype), None, None, None, None, None, None, None, None, None, None
 
 
 def rdm(sub, la, lb, c, want2: bool = True):

@@ -28,16 +28,31 @@ __device__ __forceinline__ uint64_t abs_bits(double x) {
   return (uint64_t)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
 
+// Selection key whose unsigned order is the wanted order of the values:
+//   kSelAbs       |x| (its bit pattern is monotone for non-negative doubles);
+//   kSelLargest   x itself: positive patterns get the top bit set, negative patterns
+//                 are inverted, so the key increases with x (-0 is read as +0);
+//   kSelSmallest  the complement of that, so the smallest x has the largest key.
+// A NaN gets key 0 in the last two modes, below every number.
+__device__ __forceinline__ uint64_t sel_key(double x, int mode) {
+  if (mode == kSelAbs) return abs_bits(x);
+  if (x != x) return 0ull;
+  uint64_t u = (uint64_t)__double_as_longlong(x);
+  if ((u << 1) == 0ull) u = 0ull;  // -0 -> +0
+  const uint64_t ord = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
+  return mode == kSelLargest ? ord : ~ord;
+}
+
 // 256-bin histogram of bits [shift, shift+8) over the entries whose higher bits equal
 // `prefix` under `mask`
-__global__ void k_radix_hist(const double* __restrict__ c, int64_t N, uint64_t prefix,
+__global__ void k_radix_hist(const double* __restrict__ c, int64_t N, int mode, uint64_t prefix,
                              uint64_t mask, int shift, unsigned long long* __restrict__ hist) {
   __shared__ unsigned int h[256];
   for (int b = threadIdx.x; b < 256; b += blockDim.x) h[b] = 0;
   __syncthreads();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = abs_bits(c[i]);
+    const uint64_t u = sel_key(c[i], mode);
     if ((u & mask) == prefix) atomicAdd(&h[(u >> shift) & 255u], 1u);
   }
   __syncthreads();
@@ -45,24 +60,24 @@ __global__ void k_radix_hist(const double* __restrict__ c, int64_t N, uint64_t p
     if (h[b]) atomicAdd(hist + b, (unsigned long long)h[b]);
 }
 
-// flag[i] = |c_i| above the threshold key (mode 0) or equal to it (mode 1)
-__global__ void k_flag_key(const double* __restrict__ c, int64_t N, uint64_t key, int mode,
-                           int64_t* __restrict__ flag) {
+// flag[i] = key of c_i above the threshold key (equal = 0) or equal to it (equal = 1)
+__global__ void k_flag_key(const double* __restrict__ c, int64_t N, int mode, uint64_t key,
+                           int equal, int64_t* __restrict__ flag) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = abs_bits(c[i]);
-    flag[i] = mode == 0 ? (u > key) : (u == key);
+    const uint64_t u = sel_key(c[i], mode);
+    flag[i] = equal == 0 ? (u > key) : (u == key);
   }
 }
 
 // out[pos_gt[i] + ...]: indices above the threshold, plus the first `ties` equal ones,
 // merged in ascending index order: rank = (#greater before i) + min(#equal before i, ties)
-__global__ void k_select_scatter(const double* __restrict__ c, int64_t N, uint64_t key,
+__global__ void k_select_scatter(const double* __restrict__ c, int64_t N, int mode, uint64_t key,
                                  int64_t ties, const int64_t* __restrict__ pos_gt,
                                  const int64_t* __restrict__ pos_eq, int64_t* __restrict__ out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
        i += (int64_t)gridDim.x * blockDim.x) {
-    const uint64_t u = abs_bits(c[i]);
+    const uint64_t u = sel_key(c[i], mode);
     const bool take = u > key || (u == key && pos_eq[i] < ties);
     if (take) out[pos_gt[i] + std::min(pos_eq[i], ties)] = i;
   }
@@ -173,8 +188,10 @@ __global__ void k_split_keys(const uint64_t* __restrict__ a, int64_t m, const in
 
 }  // namespace
 
-// the k largest |c_I| (ties: lower index first), ascending indices, into out[k]
-int top_amplitudes_impl(const double* c, int64_t N, int64_t k, int64_t* out, cudaStream_t s) {
+// the k entries of c with the largest selection key (mode: kSelAbs = largest |c|,
+// kSelLargest, kSelSmallest; ties: lower index first), ascending indices, into out[k]
+int select_top_impl(const double* c, int64_t N, int64_t k, int mode, int64_t* out,
+                    cudaStream_t s) {
   k = std::min(k, N);
   if (k <= 0) return HINQS_OK;
   const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(N, 256), 8 * kNumSMs);
@@ -187,7 +204,7 @@ int top_amplitudes_impl(const double* c, int64_t N, int64_t k, int64_t* out, cud
     int64_t need = k;  // entries still to take at or below the current prefix
     for (int shift = 56; shift >= 0; shift -= 8) {
       HQ_CUDA(cudaMemsetAsync(hist, 0, 256 * sizeof(unsigned long long), s));
-      k_radix_hist<<<grid, 256, 0, s>>>(c, N, prefix, mask, shift, hist);
+      k_radix_hist<<<grid, 256, 0, s>>>(c, N, mode, prefix, mask, shift, hist);
       HQ_LAUNCH_CHECK();
       unsigned long long hh[256];
       HQ_CUDA(cudaMemcpyAsync(hh, hist, sizeof(hh), cudaMemcpyDeviceToHost, s));
@@ -203,15 +220,15 @@ int top_amplitudes_impl(const double* c, int64_t N, int64_t k, int64_t* out, cud
     // prefix is the k-th largest key; take every larger entry and `need` equal ones
     HQ_TRY(dalloc(&f_gt, N, s));
     HQ_TRY(dalloc(&f_eq, N, s));
-    k_flag_key<<<grid, 256, 0, s>>>(c, N, prefix, 0, f_gt);
-    k_flag_key<<<grid, 256, 0, s>>>(c, N, prefix, 1, f_eq);
+    k_flag_key<<<grid, 256, 0, s>>>(c, N, mode, prefix, 0, f_gt);
+    k_flag_key<<<grid, 256, 0, s>>>(c, N, mode, prefix, 1, f_eq);
     HQ_LAUNCH_CHECK();
     int64_t n_gt = 0, n_eq = 0;
     HQ_TRY(exclusive_scan_i64(f_gt, f_gt, N, &n_gt, s));
     HQ_TRY(exclusive_scan_i64(f_eq, f_eq, N, &n_eq, s));
     if (n_gt + std::min(n_eq, need) != k)
       return fail(HINQS_ERR_CUDA, "top amplitudes: selection count mismatch");
-    k_select_scatter<<<grid, 256, 0, s>>>(c, N, prefix, need, f_gt, f_eq, out);
+    k_select_scatter<<<grid, 256, 0, s>>>(c, N, mode, prefix, need, f_gt, f_eq, out);
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
   };
@@ -230,7 +247,7 @@ extern "C" int hinqs_top_amplitudes(const hinqs_subspace* B, const double* c, in
                                     int64_t* idx_out, void* stream) {
   if (!B || !c || k < 0 || (k > 0 && !idx_out))
     return fail(HINQS_ERR_ARG, "hinqs_top_amplitudes: NULL argument or negative k");
-  return top_amplitudes_impl(c, B->Na * B->Nb, k, idx_out, (cudaStream_t)stream);
+  return select_top_impl(c, B->Na * B->Nb, k, kSelAbs, idx_out, (cudaStream_t)stream);
 }
 
 extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspace* B,
@@ -274,7 +291,7 @@ extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspac
   int64_t* pos = nullptr;
   auto run = [&]() -> int {
     HQ_TRY(dalloc(&top, n_top, s));
-    HQ_TRY(top_amplitudes_impl(c, N, n_top, top, s));
+    HQ_TRY(select_top_impl(c, N, n_top, kSelAbs, top, s));
     HQ_TRY(dalloc(&keys, m_pad, s));
     A.top = top;
     A.keys = keys;

@@ -196,4 +196,11 @@ int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tota
                        cudaStream_t s);
 // ascending bitonic sort of a[m_pad] in place (m_pad a power of two >= 2)
 int bitonic_sort(uint64_t* a, int64_t m_pad, cudaStream_t s);
+// Exact top-k selection (radix selection on order-preserving 64-bit keys): positions
+// of the k entries of c[N] with the largest |c| (kSelAbs), the largest value
+// (kSelLargest) or the smallest value (kSelSmallest), ties to the lower position,
+// written ascending to out[min(k, N)].  Synchronises the stream.
+constexpr int kSelAbs = 0, kSelLargest = 1, kSelSmallest = 2;
+int select_top_impl(const double* c, int64_t N, int64_t k, int mode, int64_t* out,
+                    cudaStream_t s);
 }  // namespace hinqs

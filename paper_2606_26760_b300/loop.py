@@ -1,0 +1,151 @@
+"""The HI-NQS outer iteration (Sec. 2.2, Steps 1-5) around the subspace solve.
+
+Orchestration only: every step below is one call of the CUDA library (the binding in
+this package); this module decides which call comes next.
+
+    Step 1   the NQS samples of iteration t arrive as (x_alpha, x_beta) device arrays
+             (the Transformer sampler itself is not part of this library)
+    Step 1'  t >= 1: classical singles/doubles expansion of the n_top largest |c_i|
+             (Eq. classical_expansion)                       hinqs_classical_expansion
+             candidate set C_t: distinct, particle-number filtered, minus the basis
+                                                             hinqs_candidate_pool
+    Step 2   t = 0: the K_0 candidates with the lowest H_xx  hinqs_determinant_diag
+             t = 1: PT2 rescoring of basis and candidates, the top K, no cap
+             t >= 2: PT2 scores of the candidates, the top K appended, eviction
+             above B_max (Eq. pt2_score)                     hinqs_pt2_score,
+                                                             hinqs_basis_update
+    Step 3   Davidson on the product of the basis strings, warm-started from the
+             previous eigenvector carried over               hinqs_build_subspace,
+                                                             hinqs_remap_vector,
+                                                             hinqs_davidson
+    Step 4   teacher marginals and the loss inputs for the network
+                                                             hinqs_spin_marginals,
+                                                             hinqs_nqs_loss
+    Step 5   stop after `patience` consecutive |E(t) - E(t-1)| < delta, or max_iter
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import torch
+
+from . import (BASIS_APPEND, BASIS_COLD_START, BASIS_RESCORE, DAVIDSON_FP64, Hamiltonian,
+               basis_update, build_subspace, candidate_pool, classical_expansion, davidson,
+               determinant_diag, lookup_determinants, nqs_loss, pt2_score, remap_vector,
+               spin_marginals, string_links)
+
+
+@dataclass
+class IterationRecord:
+    t: int
+    n_candidates: int        # |C_t|
+    n_dropped: int           # proposals rejected by the particle-number filter
+    n_basis: int             # |B| after the update
+    n_alpha_strings: int
+    n_beta_strings: int
+    energy: float
+    residual: float
+    davidson_status: int
+    warm_start: bool
+
+
+@dataclass
+class HiNqsLoop:
+    """State of the outer iteration.  `ham` is a prepared Hamiltonian; k0, k and b_max
+    are the cold-start budget K_0, the per-iteration budget K and the cap B_max of
+    Step 2; n_top is N_e of Step 1' (the paper uses 1000)."""
+
+    ham: Hamiltonian
+    k0: int
+    k: int
+    b_max: int
+    n_top: int = 1000
+    delta: float = 1e-9
+    patience: int = 5
+    max_iter: int = 50
+    davidson_opts: dict = field(default_factory=lambda: dict(precision=DAVIDSON_FP64,
+                                                             tol_residual=1e-8,
+                                                             tol_energy=1e-11, max_iter=400))
+    t: int = 0
+    basis: tuple | None = None          # (x_alpha, x_beta, key) of the cumulative basis
+    sub: object = None
+    la: object = None
+    lb: object = None
+    c: torch.Tensor | None = None
+    energy: float | None = None
+    energies: list = field(default_factory=list)
+    history: list = field(default_factory=list)
+    # inputs of the last step (for inspection and checking)
+    last: dict = field(default_factory=dict)
+
+    def step(self, samples):
+        """One iteration: candidates from `samples` (and the classical expansion),
+        basis update, subspace solve.  Returns the IterationRecord."""
+        ham = self.ham
+        last = dict(t=self.t, samples=samples, basis_before=self.basis, sub_before=self.sub,
+                    c_before=self.c, energy_before=self.energy)
+        if self.t == 0:
+            ya, yb, dropped = candidate_pool(ham, samples)
+            hxx = determinant_diag(ham, ya, yb)
+            last.update(pool=(ya, yb), expansion=None, keys=hxx)
+            self.basis = basis_update(BASIS_COLD_START, None, (ya, yb, hxx), self.k0)
+        else:
+            xa_cl, xb_cl = classical_expansion(ham, self.sub, self.c, self.n_top)
+            ya, yb, dropped = candidate_pool(ham, samples, (xa_cl, xb_cl),
+                                             exclude=self.basis[:2])
+            _, _, sc = pt2_score(ham, self.sub, self.c, self.energy, ya, yb)
+            last.update(pool=(ya, yb), expansion=(xa_cl, xb_cl), keys=sc)
+            if self.t == 1:
+                # every cold-start entry gets one PT2 evaluation before any eviction
+                _, _, sb = pt2_score(ham, self.sub, self.c, self.energy, self.basis[0],
+                                     self.basis[1])
+                last.update(basis_keys=sb)
+                self.basis = basis_update(BASIS_RESCORE, (self.basis[0], self.basis[1], sb),
+                                          (ya, yb, sc), self.k)
+            else:
+                self.basis = basis_update(BASIS_APPEND, self.basis, (ya, yb, sc), self.k,
+                                          self.b_max)
+        sub = build_subspace(self.basis[0], self.basis[1], ham.n, ham.n_alpha, ham.n_beta)
+        la, lb = string_links(ham, sub, 0), string_links(ham, sub, 1)
+        guess, warm = None, False
+        if self.c is not None:
+            g, kept = remap_vector(self.sub, self.c, sub)
+            if kept > 0.0:
+                guess, warm = g, True
+        res = davidson(ham, sub, la, lb, guess=guess, **self.davidson_opts)
+        self.sub, self.la, self.lb, self.c, self.energy = sub, la, lb, res.c, res.energy
+        self.energies.append(res.energy)
+        rec = IterationRecord(self.t, int(ya.numel()), int(dropped), int(self.basis[0].numel()),
+                              sub.Na, sub.Nb, res.energy, res.residual, res.status, warm)
+        self.history.append(rec)
+        self.last = last
+        self.t += 1
+        return rec
+
+    def converged(self) -> bool:
+        """Step 5: `patience` consecutive energy changes below delta, or max_iter."""
+        e = self.energies
+        if len(e) >= self.max_iter:
+            return True
+        if len(e) <= self.patience:
+            return False
+        return all(abs(e[-i] - e[-i - 1]) < self.delta for i in range(1, self.patience + 1))
+
+    def run(self, sampler):
+        """Iterate until converged(); sampler(t) gives the Step 1 samples of iteration t."""
+        while not self.converged():
+            self.step(sampler(self.t))
+        return self.history
+
+    def basis_positions(self):
+        """Positions of the basis-list determinants in the current product subspace."""
+        return lookup_determinants(self.sub, self.basis[0], self.basis[1])
+
+    def teacher(self, batch, log_pi, coef=(1.0, 1.0, 1.0), over_list: bool = True):
+        """Step 4 on a minibatch of basis positions: dict(w, adv, grad, loss) from
+        hinqs_nqs_loss, with the teacher weights normalised over the basis list
+        (over_list) or over the whole product subspace."""
+        pa, pb = spin_marginals(self.sub, self.c)
+        basis = self.basis_positions() if over_list else None
+        return nqs_loss(self.ham, self.sub, self.la, self.lb, pa, pb, self.energy, batch, log_pi,
+                        coef, basis)
