@@ -15,6 +15,11 @@ Names follow the C ABI in include/hinqs.h:
     rdm / energy_backward  hinqs_rdm / hinqs_energy_backward (Hellmann-Feynman gradient)
     spin_marginals         hinqs_spin_marginals  (Step 4, Eqs. alpha_marginal / beta_marginal)
     HinqsEnergy            torch.autograd.Function: E(h, eri) with the RDM backward
+    pt2_score, top_amplitudes, classical_expansion   (Step 2 Eq. pt2_score, Step 1')
+    candidate_pool, determinant_diag, select_top, basis_update, lookup_determinants,
+    remap_vector           the outer loop's Steps 1, 2 and the Step 3 warm start
+    nqs_loss / NqsLoss     Step 4 loss inputs (Eqs. teacher, energy, entropy, loss)
+The outer iteration itself (Steps 1-5) is loop.HiNqsLoop.
 """
 from __future__ import annotations
 
