@@ -717,6 +717,33 @@ def main():
                  "n_candidates": int(cxa.numel()), "pt2_ms": 1e3 * t_pt2,
                  "pt2_candidates_per_s": cxa.numel() / t_pt2}
 
+    # the outer iteration around the solve (Steps 1, 1', 2, 3 warm start): four
+    # iterations of HiNqsLoop on this Hamiltonian, 200,000 seeded HF-weighted
+    # determinant samples per iteration standing in for the Transformer's draws
+    # (resident on the device before the clock starts); K_0 = 20,000, K = 10,000,
+    # B_max = 40,000, N_e = 1000, mixed Davidson as in the step
+    from paper_2606_26760_b300.loop import HiNqsLoop
+    loop_opts = {k: v for k, v in solve_opts.items() if k != "trace_cap"}
+    samples = [(torch.from_numpy(synth.hf_weighted_samples(n, na, 200_000, 900 + 2 * t).view(np.int64)).to(dev),
+                torch.from_numpy(synth.hf_weighted_samples(n, nb, 200_000, 901 + 2 * t).view(np.int64)).to(dev))
+               for t in range(4)]
+    loop = HiNqsLoop(ham, k0=20_000, k=10_000, b_max=40_000, n_top=1000, davidson_opts=loop_opts)
+    loop_iters = []
+    for t in range(4):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rec = loop.step(samples[t])
+        torch.cuda.synchronize()
+        loop_iters.append({"t": t, "ms": 1e3 * (time.perf_counter() - t0),
+                           "candidates": rec.n_candidates, "basis": rec.n_basis,
+                           "strings": [rec.n_alpha_strings, rec.n_beta_strings],
+                           "energy": rec.energy, "warm_start": rec.warm_start})
+    outer_loop = {"iterations": loop_iters,
+                  "note": "HiNqsLoop.step: candidate pool, classical expansion (t >= 1), "
+                          "H_xx or PT2 scores, basis update, product subspace, links, "
+                          "warm-started mixed Davidson"}
+    del loop, samples
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -770,6 +797,7 @@ def main():
                              "the mixed solver's iteration count varies slightly between steps",
         "roofline": roof,
         "selection": selection,
+        "outer_loop": outer_loop,
         "cpu_baseline": cpu,
         "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
                    "mixed_sigmas_fp64_fp32": [last.n_sigma_fp64, last.n_sigma_fp32],
