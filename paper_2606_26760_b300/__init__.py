@@ -470,10 +470,11 @@ def _f64_dev(x, n=None, what="values"):
 def select_top(values, k: int, largest: bool = True):
     """hinqs_select_top (Step 2 ranking): ascending positions (int64) of the k largest
     (or smallest) values, ties to the lower position."""
+    lib = load_library()
     v = _f64_dev(values)
     k = max(0, min(int(k), v.numel()))
     out = torch.empty(k, dtype=torch.int64, device=_dev())
-    _check(_lib.hinqs_select_top(_ptr(v), v.numel(), k, 1 if largest else 0, _ptr(out), _stream()))
+    _check(lib.hinqs_select_top(_ptr(v), v.numel(), k, 1 if largest else 0, _ptr(out), _stream()))
     return out
 
 
@@ -528,6 +529,8 @@ def candidate_pool(ham, first, second=None, exclude=None):
 def basis_update(mode: int, basis, cand, k: int, b_max: int = 0):
     """hinqs_basis_update (Step 2): basis and cand are (xa, xb, key) triples (basis may
     be None); returns the new basis (xa, xb, key)."""
+    lib = load_library()
+
     def triple(t):
         if t is None:
             return None, None, None, 0
@@ -551,7 +554,7 @@ def basis_update(mode: int, basis, cand, k: int, b_max: int = 0):
     ob = torch.empty(cap, dtype=torch.int64, device=dev)
     os_ = torch.empty(cap, dtype=torch.float64, device=dev)
     n_out = ctypes.c_int64()
-    _check(_lib.hinqs_basis_update(int(mode), _ptr(ba), _ptr(bb), _ptr(bs), nb, _ptr(ca), _ptr(cb),
+    _check(lib.hinqs_basis_update(int(mode), _ptr(ba), _ptr(bb), _ptr(bs), nb, _ptr(ca), _ptr(cb),
                                    _ptr(cs), nc, k, int(b_max), _ptr(oa), _ptr(ob), _ptr(os_), cap,
                                    ctypes.byref(n_out), _stream()))
     n = n_out.value

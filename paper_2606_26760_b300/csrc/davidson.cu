@@ -543,16 +543,28 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
   }
 }
 
-// argmin of D (lowest index on ties) -> idx[0]
+// argmin of D (lowest index on ties) -> idx[0], in two passes: the smallest value
+// (mapped to an order-preserving uint64; min over a thread's elements, then the warp,
+// then the block, one atomicMin per block), then the lowest index holding it
 __global__ void k_argmin(const double* __restrict__ D, int64_t N, unsigned long long* best) {
-  // pack (orderable value, index) into 128 bits via two passes would be exact; here the
-  // value is mapped to an order-preserving uint64 and compared lexicographically.
+  __shared__ unsigned long long wmin[32];
+  unsigned long long m = ~0ull;
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
        j += (int64_t)gridDim.x * blockDim.x) {
     unsigned long long u = (unsigned long long)__double_as_longlong(D[j]);
     u = (u >> 63) ? ~u : (u | 0x8000000000000000ull);
-    unsigned long long cur = atomicMin(best, u);
-    (void)cur;
+    m = u < m ? u : m;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long v = __shfl_xor_sync(0xffffffffu, m, o);
+    m = v < m ? v : m;
+  }
+  if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wmin[w] < m ? wmin[w] : m;
+    atomicMin(best, m);
   }
 }
 __global__ void k_argmin_index(const double* __restrict__ D, int64_t N,

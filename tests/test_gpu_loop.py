@@ -91,7 +91,7 @@ def test_lookup_matches_oracle():
     got = hq.lookup_determinants(sub, xa, xb).cpu().numpy()
     ref = oracle.lookup(sa, sb, xa, xb)
     assert np.array_equal(got, ref)
-    assert (ref >= 0).sum() > 100 and (ref < 0).sum() > 1000   # both cases present
+    assert (ref >= 0).sum() > 100 and (ref < 0).sum() > 100   # both cases present
 
 
 # ------------------------------------------------------------- candidate pool
