@@ -215,6 +215,10 @@ def test_nqs_loss_uniform_state_and_list_basis():
     assert np.allclose(r["w"], 1.0 / N, rtol=1e-14)
     assert abs(r["teacher"] - np.log(N)) < 1e-13
     assert abs(r["entropy"] + np.log(N)) < 1e-13
+    # a minibatch keeps the basis normalisation: still 1/|B| each, not 1/|M|
+    r = oracle.nqs_loss(H, sa, sb, c, -1.0, batch[3:13], np.full(10, -2.0))
+    assert np.allclose(r["w"], 1.0 / N, rtol=1e-14)
+    assert abs(r["entropy"] + 2.0) < 1e-14
     basis = np.array([0, 3, 4, 11, 20, 34])
     c = np.random.default_rng(5).standard_normal(N)
     r = oracle.nqs_loss(H, sa, sb, c, -1.0, basis, np.zeros(6), basis=basis)
