@@ -234,6 +234,17 @@ typedef struct hinqs_davidson_info {
   double seconds;       /* wall time of the call */
 } hinqs_davidson_info;
 
+/* Workspace queries: the device bytes that one hinqs_sigma (any of the three sigma
+ * calls) or one hinqs_davidson call with these options requests from the
+ * stream-ordered CUDA memory pool at its peak, for a subspace of N_a x N_b
+ * determinants; the caller's vectors and the handles are not included.  The pool may
+ * round each request up.  opts NULL = defaults.  Host only (no device work).
+ * Errors: HINQS_ERR_ARG (NULL bytes, negative sizes, options hinqs_davidson rejects). */
+int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings, int precision,
+                               size_t* bytes);
+int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings,
+                                  const hinqs_davidson_opts* opts, size_t* bytes);
+
 /* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace, FP32 inner). */
 void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
 

@@ -82,6 +82,7 @@ EXPORTED = [
     "hinqs_pt2_score", "hinqs_top_amplitudes", "hinqs_classical_expansion",
     "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
     "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
+    "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size",
 ]
 
 
@@ -136,6 +137,9 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_remap_vector.argtypes = [P, P, P, P, ctypes.POINTER(ctypes.c_double), P]
     lib.hinqs_nqs_loss.argtypes = [P, P, P, P, P, P, D, P, I64, P, I64, P,
                                    ctypes.POINTER(ctypes.c_double), P, P, P, P, P]
+    lib.hinqs_sigma_workspace_size.argtypes = [I64, I64, I, ctypes.POINTER(ctypes.c_size_t)]
+    lib.hinqs_davidson_workspace_size.argtypes = [I64, I64, ctypes.POINTER(_Opts),
+                                                  ctypes.POINTER(ctypes.c_size_t)]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -368,6 +372,30 @@ def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_i
                   kind=list(bufs[3][:n]))
     return DavidsonResult(e.value, c, rc, info.iterations, info.n_sigma_fp64, info.n_sigma_fp32,
                           info.n_restarts, info.n_refinements, info.residual, info.seconds, tr)
+
+
+def sigma_workspace_size(n_alpha_strings: int, n_beta_strings: int,
+                         precision: int = PREC_FP64) -> int:
+    """hinqs_sigma_workspace_size: device bytes one sigma product requests at its peak."""
+    lib = load_library()
+    b = ctypes.c_size_t()
+    _check(lib.hinqs_sigma_workspace_size(int(n_alpha_strings), int(n_beta_strings), precision,
+                                          ctypes.byref(b)))
+    return b.value
+
+
+def davidson_workspace_size(n_alpha_strings: int, n_beta_strings: int,
+                            precision: int = DAVIDSON_FP64, max_subspace: int = 16) -> int:
+    """hinqs_davidson_workspace_size: device bytes one davidson() call with these
+    options requests at its peak (besides the caller's vectors and the handles)."""
+    lib = load_library()
+    opts = _Opts()
+    lib.hinqs_davidson_default_opts(ctypes.byref(opts))
+    opts.precision, opts.max_subspace = precision, max_subspace
+    b = ctypes.c_size_t()
+    _check(lib.hinqs_davidson_workspace_size(int(n_alpha_strings), int(n_beta_strings),
+                                             ctypes.byref(opts), ctypes.byref(b)))
+    return b.value
 
 
 def autotune(ham, sub, la, lb, precision: int = PREC_FP32) -> float:

@@ -1099,6 +1099,44 @@ extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
   o->inner_precision = HINQS_PREC_FP32;
 }
 
+// Device bytes one hinqs_davidson call requests from the stream-ordered pool at its
+// peak: the context (partials, scratch, counters, the diagonal), the solver's vectors
+// and pencils (as allocated by davidson_fp64 / davidson_mixed above) and the two
+// N-element temporaries of an FP64 sigma product.  Keep in step with those allocations.
+static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) {
+  const size_t d = sizeof(double), f = sizeof(float);
+  size_t b = (2 * (size_t)kRedGrid * (kMaxSub + 1) + 4 * (kMaxSub + 2)) * d +
+             (kMaxSub + 1) * sizeof(unsigned int) + (size_t)N * d;
+  if (o.precision == HINQS_DAVIDSON_FP64) {
+    const size_t mmax = (size_t)o.max_subspace;
+    b += (2 * mmax + 5) * (size_t)N * d;                        // V, W, t, X[2], WX[2]
+    b += ((size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2)) * d;   // G, ritz, col, ycoef
+  } else {
+    const size_t mmax = (size_t)std::max(4, o.max_subspace);
+    const size_t keep = std::min<size_t>(4, mmax - 2);
+    b += 6 * (size_t)N * d;                                     // x, sx, t, xn, sxn, tmp
+    b += (2 * mmax + 2 * keep + 1) * (size_t)N * f;             // V, W, U, WU, t32
+    b += (3 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;
+  }
+  return b + 2 * (size_t)N * d;  // sigma temporaries (FP64 product)
+}
+
+extern "C" int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings,
+                                             const hinqs_davidson_opts* opts, size_t* bytes) {
+  if (!bytes || n_alpha_strings < 0 || n_beta_strings < 0)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson_workspace_size: NULL output or negative size");
+  hinqs_davidson_opts o;
+  hinqs_davidson_default_opts(&o);
+  if (opts) o = *opts;
+  if (o.max_subspace < 3 || o.max_subspace > kMaxSub)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson_workspace_size: max_subspace must be in 3..%d",
+                kMaxSub);
+  if (o.precision != HINQS_DAVIDSON_FP64 && o.precision != HINQS_DAVIDSON_MIXED)
+    return fail(HINQS_ERR_ARG, "hinqs_davidson_workspace_size: unknown precision %d", o.precision);
+  *bytes = davidson_workspace_bytes(n_alpha_strings * n_beta_strings, o);
+  return HINQS_OK;
+}
+
 extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
                               const hinqs_links* lb, const double* guess,
                               const hinqs_davidson_opts* opts, double* energy, double* c_out,

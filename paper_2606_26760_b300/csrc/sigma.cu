@@ -647,6 +647,18 @@ extern "C" int hinqs_diag(const hinqs_ham* H, const hinqs_subspace* B, const hin
   return diag_launch(H, B, la, lb, hdiag, (cudaStream_t)stream);
 }
 
+extern "C" int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings,
+                                          int precision, size_t* bytes) {
+  if (!bytes || n_alpha_strings < 0 || n_beta_strings < 0)
+    return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: NULL output or negative size");
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+    return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: unknown precision %d", precision);
+  // the transposed vector and the transposed partial result of the same-spin half
+  const size_t elem = precision == HINQS_PREC_FP64 ? sizeof(double) : sizeof(float);
+  *bytes = 2 * (size_t)(n_alpha_strings * n_beta_strings) * elem;
+  return HINQS_OK;
+}
+
 static int sigma_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
                        const hinqs_links* lb, const void* c, void* sigma, int precision,
                        void* stream, int parts, const char* who) {

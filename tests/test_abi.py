@@ -69,3 +69,25 @@ def test_product_path_has_no_cpu_fallback():
         hq.build_subspace([7, 11], [7, 11], 4, 3, 3)
     src = open(os.path.join(ROOT, "paper_2606_26760_b300", "__init__.py")).read()
     assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_workspace_queries_without_gpu(lib):
+    """Host-only size queries: linear in the number of determinants, the mixed solver
+    below the FP64 one at the same subspace size (FP32 correction basis), argument
+    errors for bad options."""
+    import paper_2606_26760_b300 as hq
+    s64 = hq.sigma_workspace_size(2000, 2000, hq.PREC_FP64)
+    assert s64 == 2 * 4_000_000 * 8
+    assert hq.sigma_workspace_size(2000, 2000, hq.PREC_FP32_BF16AB) == s64 // 2
+    small = hq.davidson_workspace_size(100, 100)
+    big = hq.davidson_workspace_size(1000, 1000)
+    const = small - (big - small) // 99           # bytes that do not grow with N
+    assert big - const == 100 * (small - const)
+    assert hq.davidson_workspace_size(2000, 2000, hq.DAVIDSON_MIXED) < \
+        hq.davidson_workspace_size(2000, 2000, hq.DAVIDSON_FP64)
+    assert hq.davidson_workspace_size(2000, 2000, max_subspace=24) > \
+        hq.davidson_workspace_size(2000, 2000, max_subspace=8)
+    with pytest.raises(hq.HinqsError):
+        hq.davidson_workspace_size(10, 10, max_subspace=2)
+    with pytest.raises(hq.HinqsError):
+        hq.sigma_workspace_size(10, 10, 7)
