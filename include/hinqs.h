@@ -303,6 +303,16 @@ int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
                          double* energies, double* const* c_outs, hinqs_davidson_info* infos,
                          void* stream);
 
+/* -------------------------------------------------------------- self-test --
+ * Not in the paper: a check of the timeout path.  Runs the bounded wait of the
+ * tensor-core sigma kernel, with `polls` polls (1..2^26; the kernel itself uses 2^26),
+ * on an mbarrier that nothing completes, in one thread of one block.  The wait gives
+ * up, the kernel raises the library's wait-timeout flag and returns; the call reads
+ * and clears the flag like hinqs_sigma does and returns HINQS_ERR_TIMEOUT, the
+ * expected result.  The device and the library stay usable.  Synchronises the
+ * stream.  Errors: HINQS_ERR_ARG (polls out of range), HINQS_ERR_CUDA. */
+int hinqs_selftest_bounded_wait(long long polls, void* stream);
+
 /* ---------------------------------------------------------- PT2 scores --
  * Step 2, Eq. pt2_score: the Epstein-Nesbet importance of candidate determinants
  * x_k = (xa[k], xb[k]) given the subspace eigenvector c (energy e0):

@@ -82,7 +82,7 @@ EXPORTED = [
     "hinqs_pt2_score", "hinqs_top_amplitudes", "hinqs_classical_expansion",
     "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
     "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
-    "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size",
+    "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size", "hinqs_selftest_bounded_wait",
 ]
 
 
@@ -140,6 +140,7 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_sigma_workspace_size.argtypes = [I64, I64, I, ctypes.POINTER(ctypes.c_size_t)]
     lib.hinqs_davidson_workspace_size.argtypes = [I64, I64, ctypes.POINTER(_Opts),
                                                   ctypes.POINTER(ctypes.c_size_t)]
+    lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -396,6 +397,14 @@ def davidson_workspace_size(n_alpha_strings: int, n_beta_strings: int,
     _check(lib.hinqs_davidson_workspace_size(int(n_alpha_strings), int(n_beta_strings),
                                              ctypes.byref(opts), ctypes.byref(b)))
     return b.value
+
+
+def selftest_bounded_wait(polls: int = 4096) -> int:
+    """hinqs_selftest_bounded_wait: run the tensor-core kernel's bounded wait on a
+    barrier nothing completes; returns the status code (ERR_TIMEOUT is expected)."""
+    lib = load_library()
+    _dev()
+    return lib.hinqs_selftest_bounded_wait(int(polls), _stream())
 
 
 def autotune(ham, sub, la, lb, precision: int = PREC_FP32) -> float:

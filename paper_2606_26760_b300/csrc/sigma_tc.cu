@@ -79,8 +79,9 @@ __device__ __forceinline__ void mma_commit(uint32_t mbar) {
       : "memory");
 }
 
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (long long it = 0; it < kWaitLimit; ++it) {
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase,
+                                          long long limit = kWaitLimit) {
+  for (long long it = 0; it < limit; ++it) {
     uint32_t done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
@@ -466,6 +467,24 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   return tc::fits<64, 1>(a) ? tc::launch_fit<64, 1>(a, la->tune_stages, s) : kTcNoFit;
 }
 
+namespace tc {
+
+// Diagnostic for the timeout path: one thread waits, with the sigma kernel's bounded
+// wait and `limit` polls, on an mbarrier whose single expected arrival never comes,
+// and raises the same error flag when the wait gives up.  Nothing else touches the
+// barrier, so the wait always ends by its limit.
+__global__ void k_wait_selftest(long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&bar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    if (!mbar_wait(smem_u32(&bar), 0u, limit)) atomicExch(&g_tc_error, 1);
+    asm volatile("mbarrier.inval.shared::cta.b64 [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  }
+}
+
+}  // namespace tc
+
 int tc_error_check(cudaStream_t s) {
   int h = 0;
   HQ_CUDA(cudaMemcpyFromSymbolAsync(&h, g_tc_error, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
@@ -479,3 +498,12 @@ int tc_error_check(cudaStream_t s) {
 }
 
 }  // namespace hinqs
+
+extern "C" int hinqs_selftest_bounded_wait(long long polls, void* stream) {
+  if (polls < 1 || polls > hinqs::tc::kWaitLimit)
+    return hinqs::fail(HINQS_ERR_ARG, "hinqs_selftest_bounded_wait: polls outside 1..2^26");
+  cudaStream_t s = (cudaStream_t)stream;
+  hinqs::tc::k_wait_selftest<<<1, 32, 0, s>>>(polls);
+  HQ_LAUNCH_CHECK();
+  return hinqs::tc_error_check(s);
+}

@@ -57,6 +57,9 @@ def test_argument_errors_without_gpu(lib):
     assert rc == -1
     rc = lib.hinqs_energy_backward(0, 1.0, None, None, None, None, None)
     assert rc == -1
+    lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, ctypes.c_void_p]
+    assert lib.hinqs_selftest_bounded_wait(0, None) == -1
+    assert lib.hinqs_selftest_bounded_wait((1 << 26) + 1, None) == -1
 
 
 def test_product_path_has_no_cpu_fallback():
