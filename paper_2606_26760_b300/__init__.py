@@ -407,6 +407,20 @@ def selftest_bounded_wait(polls: int = 4096) -> int:
     return lib.hinqs_selftest_bounded_wait(int(polls), _stream())
 
 
+def write_trace_jsonl(result: "DavidsonResult", path: str, label: str = "") -> None:
+    """Write a Davidson trace (davidson(..., trace_cap > 0)) as JSON lines: iteration,
+    theta (incl. E_nuc), residual norm estimate, seconds since the call began, and
+    whether the iterate is an FP64 one (kind 0) or an FP32 inner one (kind 1)."""
+    import json
+    tr = result.trace or {}
+    with open(path, "w") as f:
+        for i, (th, r, t, k) in enumerate(zip(tr.get("theta", []), tr.get("resid", []),
+                                              tr.get("time", []), tr.get("kind", []))):
+            f.write(json.dumps({"label": label, "iter": i, "theta": th, "residual": r,
+                                "seconds": t, "kind": "fp64" if k == 0 else "fp32_inner"})
+                    + "\n")
+
+
 def autotune(ham, sub, la, lb, precision: int = PREC_FP32) -> float:
     """hinqs_autotune: time the sigma tile candidates on this problem, keep the
     fastest in la/lb; returns the milliseconds of one sigma with the choice."""

@@ -25,8 +25,11 @@ this package); this module decides which call comes next.
 """
 from __future__ import annotations
 
+import dataclasses
+import json
 from dataclasses import dataclass, field
 
+import numpy as np
 import torch
 
 from . import (BASIS_APPEND, BASIS_COLD_START, BASIS_RESCORE, DAVIDSON_FP64, Hamiltonian,
@@ -136,6 +139,72 @@ class HiNqsLoop:
         while not self.converged():
             self.step(sampler(self.t))
         return self.history
+
+    # ------------------------------------------------------ checkpoint / resume
+    # The only state the paper carries across iterations is the basis and the
+    # eigenvector that warm-starts the next solve (Step 3); a checkpoint holds those,
+    # the energies (for the Step 5 rule) and the budgets, as host arrays in one .npz.
+
+    def save(self, path: str) -> None:
+        """Write the loop state (basis list with keys, subspace strings, eigenvector,
+        energies, iteration count, budgets) to `path` (numpy .npz)."""
+        st = dict(t=np.int64(self.t), k0=np.int64(self.k0), k=np.int64(self.k),
+                  b_max=np.int64(self.b_max), n_top=np.int64(self.n_top),
+                  delta=np.float64(self.delta), patience=np.int64(self.patience),
+                  max_iter=np.int64(self.max_iter),
+                  energies=np.asarray(self.energies, dtype=np.float64),
+                  history=np.array(json.dumps([dataclasses.asdict(r) for r in self.history])))
+        if self.basis is not None:
+            st["basis_alpha"] = self.basis[0].cpu().numpy()
+            st["basis_beta"] = self.basis[1].cpu().numpy()
+            st["basis_key"] = self.basis[2].cpu().numpy()
+        if self.sub is not None:
+            sa, sb = self.sub.strings()
+            st["sub_alpha"], st["sub_beta"] = sa.cpu().numpy(), sb.cpu().numpy()
+            st["c"] = self.c.cpu().numpy()
+            st["energy"] = np.float64(self.energy)
+        with open(path, "wb") as f:
+            np.savez(f, **st)
+
+    @classmethod
+    def load(cls, path: str, ham, davidson_opts: dict | None = None, rebuild: bool = True):
+        """Resume from a checkpoint written by save().  With rebuild the product
+        subspace and its links are built again on the device and the eigenvector is
+        put back, so the next step warm-starts from it; without rebuild only the host
+        state is restored (the basis, energies and counters, as device-free tensors)."""
+        z = np.load(path)
+        kw = dict(k0=int(z["k0"]), k=int(z["k"]), b_max=int(z["b_max"]), n_top=int(z["n_top"]),
+                  delta=float(z["delta"]), patience=int(z["patience"]),
+                  max_iter=int(z["max_iter"]))
+        if davidson_opts is not None:
+            kw["davidson_opts"] = davidson_opts
+        loop = cls(ham, **kw)
+        loop.t = int(z["t"])
+        loop.energies = [float(x) for x in z["energies"]]
+        loop.history = [IterationRecord(**r) for r in json.loads(str(z["history"]))]
+        dev = torch.device("cuda", torch.cuda.current_device()) if rebuild else torch.device("cpu")
+        if "basis_alpha" in z:
+            loop.basis = (torch.from_numpy(z["basis_alpha"]).to(dev),
+                          torch.from_numpy(z["basis_beta"]).to(dev),
+                          torch.from_numpy(z["basis_key"]).to(dev))
+        if "sub_alpha" in z:
+            loop.energy = float(z["energy"])
+            if rebuild:
+                loop.sub = build_subspace(torch.from_numpy(z["sub_alpha"]).to(dev),
+                                          torch.from_numpy(z["sub_beta"]).to(dev),
+                                          ham.n, ham.n_alpha, ham.n_beta)
+                loop.la, loop.lb = string_links(ham, loop.sub, 0), string_links(ham, loop.sub, 1)
+                loop.c = torch.from_numpy(z["c"]).to(dev)
+            else:
+                loop.c = torch.from_numpy(z["c"])
+        return loop
+
+    def write_history_jsonl(self, path: str) -> None:
+        """One JSON line per iteration (IterationRecord fields): the per-iteration
+        energy and basis size that Step 5 and the paper's convergence plots use."""
+        with open(path, "w") as f:
+            for r in self.history:
+                f.write(json.dumps(dataclasses.asdict(r)) + "\n")
 
     def basis_positions(self):
         """Positions of the basis-list determinants in the current product subspace."""
