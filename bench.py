@@ -167,9 +167,9 @@ def run_reference(args):
         times.append(time.perf_counter() - t0)
     t = sum(times) / len(times)
     dets_s = rows_per_step / t
-    # the whole path per determinant is bounded below by the sigma products of the
-    # solve; the oracle's rate is the sigma-row rate divided by the FP64 solver's
-    # sigma count on this workload (measured by the GPU arm: ~20)
+    # value = the oracle's sigma rows per second (one row = one determinant's sigma_I);
+    # the GPU arm's value counts determinants through the whole path, which costs
+    # about two hundred sigma products per determinant on this workload
     line = {
         "impl": "reference", "metric": METRIC, "value": dets_s, "unit": "dets/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -184,6 +184,63 @@ def run_reference(args):
         "e2e": {"value": dets_s, "unit": "dets/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return None
+
+
+def cpu_baseline_detail(oracle, synth, np, H_o, sa_o, sb_o, c_h):
+    """More of the CPU oracle as it stands, on bounded samples (about ten seconds):
+    one host core on the precision workload; the full 3136-determinant space (n_orb 8,
+    3/3): a whole sigma product and the oracle's Lanczos solve with its
+    time-to-1e-6 Ha against dense eigh; 500 rows of the 2.5e7-determinant
+    differentiation workload."""
+    out = {"cpu_model": cpu_model()}
+    N = len(sa_o) * len(sb_o)
+    rows = np.sort(np.random.default_rng(1).choice(N, 400, replace=False))
+    t0 = time.perf_counter()
+    oracle.sigma(H_o, sa_o, sb_o, c_h, rows=rows, n_threads=1)
+    out["single_core"] = {"value": len(rows) / (time.perf_counter() - t0), "unit": "sigma dets/s",
+                          "sample": f"{len(rows)} rows of the precision workload, 1 thread"}
+    ws = synth.workload("fp64_small")
+    Hs = oracle.Ham(ws["h"], ws["eri"], ws["e_nuc"], ws["n_alpha"], ws["n_beta"])
+    sa, sb = oracle.build_subspace(ws["alpha"], ws["beta"], ws["n_alpha"], ws["n_beta"])
+    Ns = len(sa) * len(sb)
+    E_ref, _ = oracle.ground_state_dense(Hs, sa, sb)
+    cs = synth.random_vector(Ns, 3)
+    t0 = time.perf_counter()
+    oracle.sigma(Hs, sa, sb, cs)
+    t_sig = time.perf_counter() - t0
+    trace = []
+    t0 = time.perf_counter()
+    E_l, _, res = oracle.lanczos(Hs, sa, sb, tol=1e-4, trace=trace)
+    t_solve = time.perf_counter() - t0
+    hit = next((t for th, t in trace if abs(th - E_ref) <= 1e-6), None)
+    out["small"] = {"workload": f"fp64_small: full space, N={Ns}", "sigma_dets_per_s": Ns / t_sig,
+                    "lanczos_iterations": len(trace), "solve_s": t_solve,
+                    "time_to_1e-6_Ha_s": None if hit is None else hit - t0,
+                    "energy_error_Ha": abs(E_l - E_ref), "residual": res,
+                    "solver": "oracle Lanczos (full reorthogonalisation) to a 1e-4 residual, "
+                              "E_ref from dense eigh"}
+    wd = synth.workload("differentiation")
+    Hd = oracle.Ham(wd["h"], wd["eri"], wd["e_nuc"], wd["n_alpha"], wd["n_beta"])
+    da, db = oracle.build_subspace(wd["alpha"], wd["beta"], wd["n_alpha"], wd["n_beta"])
+    Nd = len(da) * len(db)
+    cd = synth.random_vector(Nd, 4)
+    rows = np.sort(np.random.default_rng(2).choice(Nd, 500, replace=False))
+    t0 = time.perf_counter()
+    oracle.sigma(Hd, da, db, cd, rows=rows)
+    out["differentiation"] = {"sigma_dets_per_s": len(rows) / (time.perf_counter() - t0),
+                              "sample": f"500 rows of the {Nd}-determinant workload"}
+    return out
 
 
 # ------------------------------------------------------- bond scan (batch) --
@@ -757,6 +814,7 @@ def main():
         cpu = {"value": len(rows) / tcpu, "unit": "sigma dets/s", "cores": oracle.max_threads(),
                "kind": "oracle",
                "sample": f"{len(rows)} random rows of one FP64 sigma product of the {N}-determinant workload"}
+        cpu.update(cpu_baseline_detail(oracle, synth, np, H_o, sa_o, sb_o, c_h))
 
     t_step = max(times) if world == 1 else max(times)
     t_mean = sum(times) / len(times)

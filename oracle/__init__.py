@@ -26,6 +26,7 @@ from __future__ import annotations
 import ctypes
 import os
 import subprocess
+import time
 
 import numpy as np
 
@@ -264,9 +265,11 @@ def ground_state_dense(H: Ham, sa, sb):
 
 
 def lanczos(H: Ham, sa, sb, tol: float = 1e-10, max_iter: int = 400, seed: int = 7,
-            n_threads: int = 0):
+            n_threads: int = 0, trace=None):
     """Lowest eigenpair by Lanczos with full reorthogonalisation (Golub & Van Loan,
-    Sec. 10.1), on the matrix-free oracle sigma.  Returns (E0, c0, residual norm)."""
+    Sec. 10.1), on the matrix-free oracle sigma.  Returns (E0, c0, residual norm).
+    trace: optional list that receives (lowest Ritz value, time.perf_counter()) after
+    every iteration."""
     N = len(sa) * len(sb)
     rng = np.random.default_rng(seed)
     q = rng.standard_normal(N)
@@ -286,6 +289,8 @@ def lanczos(H: Ham, sa, sb, tol: float = 1e-10, max_iter: int = 400, seed: int =
         T = np.diag(alphas) + np.diag(betas, 1) + np.diag(betas, -1)
         ev, evec = np.linalg.eigh(T)
         theta, y = ev[0], evec[:, 0]
+        if trace is not None:
+            trace.append((float(theta), time.perf_counter()))
         # residual of the Ritz pair = |b * last component of y|
         if abs(b * y[-1]) < tol or b < 1e-14 or j + 1 == N:
             break
