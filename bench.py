@@ -52,7 +52,9 @@ def parse():
     ap.add_argument("--probe", default=None,
                     help="PART:PREC[:tune] -- run one sigma product (PART sigma|same|opposite, "
                          "PREC fp64|fp32|bf16ab|bf16x3ab) on the workload, untimed, and exit "
-                         "(the target of kernel-level ncu captures); ':tune' autotunes first")
+                         "(the target of kernel-level ncu captures); ':tune' autotunes first; "
+                         "'pt2' -- one classical expansion and PT2 scoring on the converged "
+                         "eigenvector")
     ap.add_argument("--profile", action="store_true",
                     help="run only the warm-up and timed steps (for a profiler's launch list)")
     return ap.parse_args()
@@ -551,6 +553,21 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
+
+    if args.probe == "pt2":
+        # Step 1'/Step 2 on a converged eigenvector: the classical expansion of the
+        # 1000 largest amplitudes and one PT2 scoring of every candidate (untimed)
+        ham_p = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
+        sub_p = hq.build_subspace(a_d, b_d, n, na, nb)
+        la_p, lb_p = hq.string_links(ham_p, sub_p, 0), hq.string_links(ham_p, sub_p, 1)
+        res = hq.davidson(ham_p, sub_p, la_p, lb_p, precision=hq.DAVIDSON_MIXED,
+                          inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2,
+                          tol_residual=1e-6, tol_energy=1e-8, max_iter=600)
+        xa, xb = hq.classical_expansion(ham_p, sub_p, res.c, 1000)
+        hq.pt2_score(ham_p, sub_p, res.c, res.energy, xa, xb)
+        torch.cuda.synchronize()
+        print(json.dumps({"probe": "pt2", "N": sub_p.N, "candidates": int(xa.numel())}))
+        return
 
     if args.probe:
         part, pname, *rest = args.probe.split(":")
