@@ -45,10 +45,24 @@ def make_case(name):
         a = synth.hf_weighted_strings(12, 4, 60, 7)
         b = synth.hf_weighted_strings(12, 4, 50, 8)
         return h, eri, -1.5, 12, 4, 4, a, b
+    if name == "wide_40_2_2":   # n_orb above 32: strings use the upper half of the word
+        h, eri, _ = synth.integrals(40, 104)
+        rng = np.random.default_rng(9)
+        A = synth.all_strings(40, 2)
+        return (h, eri, 0.2, 40, 2, 2, rng.choice(A, 30, replace=False),
+                rng.choice(A, 25, replace=False))
+    if name == "single_alpha_9_3_2":   # one alpha string: no alpha links at all
+        h, eri, _ = synth.integrals(9, 105)
+        return h, eri, 0.0, 9, 3, 2, np.array([0b111], dtype=np.uint64), synth.all_strings(9, 2)
+    if name == "filled_5_5_1":   # every alpha orbital occupied
+        h, eri, _ = synth.integrals(5, 106)
+        return (h, eri, 0.1, 5, 5, 1, np.array([0b11111], dtype=np.uint64),
+                synth.all_strings(5, 1))
     raise KeyError(name)
 
 
-SMALL = ["full_8_3_3", "ragged_10_3_4", "no_beta_6_2_0", "hf_12_4_4"]
+SMALL = ["full_8_3_3", "ragged_10_3_4", "no_beta_6_2_0", "hf_12_4_4", "wide_40_2_2",
+         "single_alpha_9_3_2", "filled_5_5_1"]
 
 
 class Built:
@@ -291,7 +305,8 @@ def test_sigma_hermitian_full_size(precision_workload):
 # ----------------------------------------------------------------- davidson --
 
 
-@pytest.mark.parametrize("name", ["full_8_3_3", "ragged_10_3_4", "hf_12_4_4"])
+@pytest.mark.parametrize("name", ["full_8_3_3", "ragged_10_3_4", "hf_12_4_4", "wide_40_2_2",
+                                  "single_alpha_9_3_2", "filled_5_5_1"])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_davidson_vs_dense(name, prec):
     B = built(name)
