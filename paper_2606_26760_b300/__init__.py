@@ -26,6 +26,7 @@ from __future__ import annotations
 import ctypes
 import os
 from dataclasses import dataclass, field
+from math import comb
 
 import torch
 
@@ -49,6 +50,9 @@ class HinqsError(RuntimeError):
 
 
 _lib = None
+# outputs up to this many entries are sized by their upper bound and filled in one
+# call; above it a counting call sizes them first (the work is then done twice)
+_ONE_PASS_CAP = 1 << 26
 
 
 class _Opts(ctypes.Structure):
@@ -501,6 +505,18 @@ def classical_expansion(ham, sub, c, n_top: int = 1000):
     if c.dtype != torch.float64 or c.numel() != sub.N:
         raise ValueError("c must be a float64 tensor of the subspace size")
     cnt = ctypes.c_int64()
+    # excitations enumerated per selected determinant: an upper bound on the output
+    n, na, nb = sub.n, sub.n_alpha, sub.n_beta
+    s1a, s1b = na * (n - na), nb * (n - nb)
+    per = (s1a + s1b + comb(na, 2) * comb(n - na, 2) + comb(nb, 2) * comb(n - nb, 2)
+           + s1a * s1b)
+    bound = min(max(0, int(n_top)), sub.N) * per
+    if bound <= _ONE_PASS_CAP:  # one call writes straight into buffers of the bound
+        xa = torch.empty(bound, dtype=torch.int64, device=_dev())
+        xb = torch.empty(bound, dtype=torch.int64, device=_dev())
+        _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, _ptr(xa),
+                                              _ptr(xb), bound, ctypes.byref(cnt), _stream()))
+        return xa[:cnt.value], xb[:cnt.value]
     _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, None, None, 0,
                                           ctypes.byref(cnt), _stream()))
     m = cnt.value
@@ -567,6 +583,12 @@ def candidate_pool(ham, first, second=None, exclude=None):
     ea, eb, me = pair(exclude)
     cnt, drop = ctypes.c_int64(), ctypes.c_int64()
     args = (ham.handle, _ptr(a1), _ptr(b1), m1, _ptr(a2), _ptr(b2), m2, _ptr(ea), _ptr(eb), me)
+    if m1 + m2 <= _ONE_PASS_CAP:  # the pool holds at most m1 + m2 candidates: one call
+        ya = torch.empty(m1 + m2, dtype=torch.int64, device=_dev())
+        yb = torch.empty(m1 + m2, dtype=torch.int64, device=_dev())
+        _check(_lib.hinqs_candidate_pool(*args, _ptr(ya), _ptr(yb), m1 + m2, ctypes.byref(cnt),
+                                         ctypes.byref(drop), _stream()))
+        return ya[:cnt.value], yb[:cnt.value], drop.value
     _check(_lib.hinqs_candidate_pool(*args, None, None, 0, ctypes.byref(cnt), ctypes.byref(drop),
                                      _stream()))
     m = cnt.value
