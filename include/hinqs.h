@@ -7,7 +7,10 @@
  * (Step 3), its Slater-Condon matrix elements, the sigma product H c inside a
  * Davidson solve for the ground state (Step 3), the 1- and 2-RDMs that give the
  * Hellmann-Feynman gradient of the energy, and the spin-marginal teacher weights
- * of Step 4 (Eqs. alpha_marginal and beta_marginal).
+ * of Step 4 (Eqs. alpha_marginal and beta_marginal); around the solve, the other
+ * classical steps of the iteration: the classical expansion (Step 1'), PT2 scores
+ * and the basis update (Step 2), the warm start (Step 3), the loss inputs of the
+ * network (Step 4, Eqs. teacher, energy, entropy and loss).
  *
  * Conventions shared by every call
  *  - Orbitals: n_orb spatial orbitals, 1 <= n_orb <= 64.  An occupation string
