@@ -14,6 +14,10 @@ on the same GPU.
 
 --impl reference runs the CPU oracle (FP64, plain C with OpenMP) on a bounded
 sample of the same workload on the host cores.
+
+nvidia-smi clock samples taken during the timed region go to
+$HINQS_CLOCK_LOG_DIR/hinqs_clocks_rank<i>.csv (default: the temp directory); their
+summary is the line's "clocks" entry.
 """
 from __future__ import annotations
 
@@ -22,6 +26,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -97,7 +102,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{gpu_index}.csv")
+        # raw nvidia-smi samples: $HINQS_CLOCK_LOG_DIR if set, else the temp directory
+        out_dir = os.environ.get("HINQS_CLOCK_LOG_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out_dir, f"hinqs_clocks_rank{gpu_index}.csv")
 
     def start(self):
         try:
