@@ -682,8 +682,8 @@ def main():
     c64 = torch.tensor(synth.random_vector(N, 3), device=dev)
     c32 = c64.float()
 
-    def timed(fn, reps=10):
-        for _ in range(3):
+    def timed(fn, reps=20):  # 5 warm-up calls, then the median of `reps` timed calls
+        for _ in range(5):
             fn()
         ts = []
         for _ in range(reps):
@@ -703,7 +703,7 @@ def main():
     for name, (p, x) in precs.items():
         out = torch.empty_like(x)
         t_sig[name] = timed(lambda: hq.sigma(ham, sub, la, lb, x, out=out, precision=p),
-                            reps=5 if name == "fp64" else 10)
+                            reps=20)
     out32 = torch.empty_like(c32)
     t_same = timed(lambda: hq.sigma_part(ham, sub, la, lb, c32, out32, "same",
                                          precision=hq.PREC_FP32_BF16AB))
