@@ -4,6 +4,7 @@ runtime, rises during one call by no more than the reported size (plus the pool'
 rounding of each request, at most 64 MiB over the call's few dozen requests) and by
 at least 90% of it."""
 import ctypes
+import gc
 
 import pytest
 import torch
@@ -27,6 +28,7 @@ def _pool():
 
 def _peak_of(fn):
     rt, pool = _pool()
+    gc.collect()   # release unreferenced handles of earlier tests before the baseline
     torch.cuda.synchronize()
     cur = ctypes.c_uint64()
     assert rt.cudaMemPoolGetAttribute(pool, USED_CURRENT, ctypes.byref(cur)) == 0
