@@ -34,15 +34,19 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "sigma dets/s and Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B300"
-# FP64 FMA-chain rate of this B300 model (TFLOP/s), measured once with a probe kernel
-FP64_FMA_TFLOPS = 1.129
 kNumSMs_B300 = 148
 SM_MAX_MHZ = 2032
-# DRAM bytes (read + write) per product half from ncu captures of the precision
-# workload (profiles/): same-spin = its two row-product launches; None where the
-# kernel changed after the capture
-PROFILED_TRAFFIC = {"same": 62.77e6, "opposite": 33.32e6}
+# DRAM bytes (read + write) per launch of a product half, from an ncu capture of the
+# precision workload (profiles/); None until the current kernel has been captured
+PROFILED_TRAFFIC = {"same": None, "opposite": None}
 WORKLOAD = "precision"
+
+
+def sig3(x):
+    """x rounded to four significant digits (None stays None), for a compact line."""
+    if x is None:
+        return None
+    return float(f"{x:.4g}")
 
 
 def parse():
@@ -63,11 +67,6 @@ def parse():
     ap.add_argument("--profile", action="store_true",
                     help="run only the warm-up and timed steps (for a profiler's launch list)")
     return ap.parse_args()
-
-
-def max_singles(links, n_rows):
-    """Largest number of single links of a string (host side, from the link counts)."""
-    return links.max_srow
 
 
 def count_launches(fn, torch):
@@ -147,6 +146,84 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- rooflines --
+
+def rooflines(hq, sub, la, lb, n, nb, t_same, t_opp, t_sig, results):
+    """Roofline of the step's dominant sigma kernel and of the other half.
+
+    Algorithmic work per launch (the scope table's per-unit figures times the units):
+      same-spin half (row products, FP32): read C + write sigma = 2 N 4 B, plus the
+        link records read once (8 B per record of both spins and per alpha-self x
+        beta-single record), the per-string tables (4 n^2 B per alpha string, 8 B of
+        diagonal per string); bound: HBM, against the measured copy bandwidth.  A
+        secondary figure gives the bytes the kernel moves between L1 and registers
+        (4 B per link and column, 8 B per alpha-self x beta-single and column) against
+        the L1 data path derived from unit counts and clocks.
+      opposite-spin half (tensor cores, BF16): the MMA FLOPs executed on 128-row tiles
+        over the padded folded K, and the useful share 2 sum (singles_a)(singles_b +
+        n_b); bound: tensor, against the measured BF16 burst rate (the kernel is timed
+        alone).
+      FP64 sigma: 2 FLOPs per FMA of the algorithmic FMA count, against the FP64 FMA
+        rate measured live by the library's probe kernel."""
+    import json as _json
+    N = sub.N
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        mp = _json.load(f)
+    hbm = mp["hbm_gbs"]
+    bf16_burst = mp["bf16_tflops"]
+    fp64_peak = hq.probe_fma_rate(hq.PREC_FP64)
+    fp32_peak = hq.probe_fma_rate(hq.PREC_FP32)
+    alg_same = (2.0 * N * 4 + 8.0 * (la.n_links + lb.n_links + lb.n_singles)
+                + 4.0 * n * n * sub.Na + 8.0 * (sub.Na + sub.Nb))
+    l1_same = 4.0 * (la.n_links * sub.Nb + lb.n_links * sub.Na) + 8.0 * lb.n_singles * sub.Na
+    fma_same = N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
+    fma_opp_useful = la.n_singles * (lb.n_singles + sub.Nb * nb)
+    mma_flops = tc_executed_flops(n, sub, la)
+    l1_peak = kNumSMs_B300 * 128 * SM_MAX_MHZ * 1e6 / 1e9
+    same_line = {
+        "bound": "hbm", "kernel": "same-spin half, FP32 row products",
+        "achieved": sig3(alg_same / t_same / 1e9), "peak": hbm, "unit": "GB/s",
+        "frac": sig3(alg_same / t_same / 1e9 / hbm), "traffic": PROFILED_TRAFFIC.get("same"),
+        "alg_bytes": alg_same, "ms": sig3(1e3 * t_same),
+        "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)",
+        "l1_secondary": {"bytes": l1_same, "achieved_gbs": sig3(l1_same / t_same / 1e9),
+                         "peak_gbs": l1_peak, "frac": sig3(l1_same / t_same / 1e9 / l1_peak),
+                         "peak_source": "derived: 148 SMs x 128 B/cycle x 2032 MHz"}}
+    opp_line = {
+        "bound": "tensor", "kernel": "opposite-spin half, BF16 tcgen05",
+        "achieved": sig3(mma_flops / t_opp / 1e12), "peak": bf16_burst, "unit": "TFLOP/s",
+        "frac": sig3(mma_flops / t_opp / 1e12 / bf16_burst),
+        "traffic": PROFILED_TRAFFIC.get("opposite"), "flops": mma_flops,
+        "useful_flops": 2.0 * fma_opp_useful,
+        "useful_frac": sig3(2.0 * fma_opp_useful / t_opp / 1e12 / bf16_burst),
+        "ms": sig3(1e3 * t_opp), "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst; "
+                                              "of measured)"}
+    n_inner = sum(r.n_sigma_fp32 for r in results) / len(results)
+    same_dominant = n_inner * t_same >= n_inner * t_opp
+    roof = dict(same_line if same_dominant else opp_line)
+    roof["other_half"] = opp_line if same_dominant else same_line
+    roof["fp64_sigma"] = {"bound": "alu", "achieved": sig3(2 * (fma_same + fma_opp_useful)
+                                                           / t_sig["fp64"] / 1e12),
+                          "peak": sig3(fp64_peak), "unit": "TFLOP/s",
+                          "frac": sig3(2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12
+                                       / fp64_peak),
+                          "peak_source": "FP64 FMA rate measured live (hinqs_probe_fma_rate)"}
+    roof["fp32_fma_peak_tflops"] = sig3(fp32_peak)
+    return roof
+
+
+def tc_executed_flops(n, sub, la):
+    """MMA FLOPs the tensor-core opposite-spin kernel executes per launch: for every
+    alpha string, its singles in chunks of 64 (128 when a string has more than 64)
+    against 128-row beta tiles over the folded K = n(n+1)/2 padded to 16."""
+    K = n * (n + 1) // 2
+    Kp = -(-K // 16) * 16
+    NW = 64 if la.max_srow <= 64 else 128
+    n_tiles = -(-sub.Nb // 128)
+    return 2.0 * 128 * NW * Kp * n_tiles * sub.Na * (-(-la.max_srow // NW))
+
+
+
 # ------------------------------------------------------------- reference --
 
 def run_reference(args):
@@ -204,8 +281,13 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{args.workload}: n_orb={n} n_alpha={na} n_beta={nb} N={N}",
-                   "sample": sample},
+        "config": {"workload": f"{args.workload} sub-problem, N={n_det} determinants (the first "
+                               f"{k} x {k} strings of the N={N} workload): n_orb={n} "
+                               f"n_alpha={na} n_beta={nb}",
+                   "sample": sample,
+                   "note": f"value is dets/s at N={n_det}, not at N={N}: per-determinant cost "
+                           "grows with N, so compare it with the GPU arm's "
+                           "same_sample_as_reference, not with its value"},
         "cpu_baseline": {"value": dets_s, "unit": "dets/s", "cores": threads, "kind": "oracle",
                          "sample": sample, "sigma_rows_per_s": sigma_rate,
                          "sigma_sample": f"4000 random rows of one sigma of the {N}-determinant workload"},
@@ -749,48 +831,7 @@ def main():
     tt_mixed = best_time(results)
     tt_variants = {k: best_time([r]) for k, r in runs.items() if k != "fp64"}
 
-    # rooflines of the two halves of the step's product (FP32 vectors, BF16 tensor cores)
-    #   same-spin: row products from L1/L2 (every operand is L2-resident); algorithmic
-    #     bytes = the linked row segments read (4 B per link and column) plus the
-    #     alpha-self x beta-single operands (8 B per single and column), against the
-    #     L1 data-path peak, the unit ncu shows busiest
-    #   opposite-spin: dense MMA FLOPs the tensor cores execute (and the useful share)
-    bytes_same = 4.0 * (la.n_links * sub.Nb + lb.n_links * sub.Na) + 8.0 * lb.n_singles * sub.Na
-    fma_same = N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
-    fma_opp_useful = la.n_singles * (lb.n_singles + sub.Nb * nb)
-    K = n * (n + 1) // 2
-    Kp = -(-K // 16) * 16
-    NW = 64 if max_singles(la, sub.Na) <= 64 else 128
-    n_tiles = -(-sub.Nb // 128)
-    mma_flops = 2.0 * 128 * NW * Kp * n_tiles * sub.Na * (-(-max_singles(la, sub.Na) // NW))
-    # L1 data-path peak from unit counts and clocks: every SM moves one 128-byte
-    # wavefront per cycle between L1/shared memory and the registers
-    l1_gbs = kNumSMs_B300 * 128 * SM_MAX_MHZ * 1e6 / 1e9
-    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-        mp = json.load(f)
-    bf16_peak = mp.get("bf16_tflops_sustained", 1371.7)
-    n_inner = sum(r.n_sigma_fp32 for r in results) / len(results)
-    share_same = n_inner * t_same
-    share_opp = n_inner * t_opp
-    same_line = {"bound": "l1", "kernel": "hinqs_sigma_same_spin FP32 (k_spmm_rec4 x2 + transposes)",
-                 "achieved": bytes_same / t_same / 1e9, "peak": l1_gbs, "unit": "GB/s",
-                 "frac": bytes_same / t_same / 1e9 / l1_gbs,
-                 "traffic": PROFILED_TRAFFIC.get("same"), "bytes_per_launch": bytes_same,
-                 "fma_per_launch": fma_same, "ms": 1e3 * t_same,
-                 "peak_source": "148 SMs x 128 B/cycle x 2032 MHz (L1/shared data path; "
-                                "derived from unit counts and the maximum SM clock)"}
-    opp_line = {"bound": "tensor", "kernel": "hinqs_sigma_opposite_spin BF16 (k_sigma_ab_tc)",
-                "achieved": mma_flops / t_opp / 1e12, "peak": bf16_peak, "unit": "TFLOP/s",
-                "frac": mma_flops / t_opp / 1e12 / bf16_peak,
-                "traffic": PROFILED_TRAFFIC.get("opposite"),
-                "flops_per_launch": mma_flops, "useful_flops_per_launch": 2 * fma_opp_useful,
-                "ms": 1e3 * t_opp, "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained"}
-    roof = dict(same_line if share_same >= share_opp else opp_line)
-    roof["other_half"] = opp_line if share_same >= share_opp else same_line
-    roof["fp64_sigma"] = {"achieved": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12,
-                          "peak": FP64_FMA_TFLOPS, "unit": "TFLOP/s",
-                          "frac": 2 * (fma_same + fma_opp_useful) / t_sig["fp64"] / 1e12 / FP64_FMA_TFLOPS,
-                          "peak_source": "FP64 FMA-chain rate measured on this B300 model"}
+    roof = rooflines(hq, sub, la, lb, n, nb, t_same, t_opp, t_sig, results)
 
     # Step 1'/Step 2 on the converged eigenvector: the 1000 largest amplitudes, their
     # classical singles/doubles expansion (Eq. classical_expansion) and the PT2 scores
@@ -844,7 +885,37 @@ def main():
                           "warm-started mixed Davidson"}
     del loop, samples
 
-    cpu = None
+    # the reference arm's sample on this GPU: the same whole path (subspace, FP64
+    # ground state to a 1e-6 residual, RDMs, marginals) on the sub-problem of the
+    # first 30 alpha and 30 beta strings, for a like-for-like ratio with that arm
+    a30, b30 = a_d[:30].contiguous(), b_d[:30].contiguous()
+
+    def small_step():
+        ham_k = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
+        sub_k = hq.build_subspace(a30, b30, n, na, nb)
+        la_k, lb_k = hq.string_links(ham_k, sub_k, 0), hq.string_links(ham_k, sub_k, 1)
+        r_k = hq.davidson(ham_k, sub_k, la_k, lb_k, precision=hq.DAVIDSON_FP64,
+                          tol_residual=1e-6, tol_energy=1e-8)
+        hq.rdm(sub_k, la_k, lb_k, r_k.c)
+        hq.spin_marginals(sub_k, r_k.c)
+        return sub_k.N
+
+    for _ in range(3):
+        N_k = small_step()
+    ts = []
+    for _ in range(10):
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        small_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(ev0.elapsed_time(ev1) / 1e3)
+    t_k = sum(ts) / len(ts)
+    same_sample = {"value": sig3(N_k / t_k), "unit": "dets/s", "N": N_k,
+                   "ms_per_step": sig3(1e3 * t_k),
+                   "sample": "whole path on the first 30 x 30 strings, as the reference arm"}
+
+    cpu, cpu_detail = None, None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         H_o = oracle.Ham(w["h"], w["eri"], w["e_nuc"], na, nb)
@@ -857,9 +928,10 @@ def main():
         cpu = {"value": len(rows) / tcpu, "unit": "sigma dets/s", "cores": oracle.max_threads(),
                "kind": "oracle",
                "sample": f"{len(rows)} random rows of one FP64 sigma product of the {N}-determinant workload"}
-        cpu.update(cpu_baseline_detail(oracle, synth, np, H_o, sa_o, sb_o, c_h))
+        cpu_detail = cpu_baseline_detail(oracle, synth, np, H_o, sa_o, sb_o, c_h)
+        cpu["single_core_dets_per_s"] = sig3(cpu_detail["single_core"]["value"])
+        cpu["small_lanczos_time_to_1e-6_Ha_s"] = sig3(cpu_detail["small"]["time_to_1e-6_Ha_s"])
 
-    t_step = max(times) if world == 1 else max(times)
     t_mean = sum(times) / len(times)
     if world > 1:
         tt = torch.tensor([t_mean], device=dev)
@@ -868,6 +940,7 @@ def main():
     value = world * N / t_mean
     e2e_mean = sum(e2e_times) / len(e2e_times)
     last = results[-1]
+    # headline figures of the metric go last on the line (the part a tail keeps)
     line = {
         "metric": METRIC,
         "value": value,
@@ -888,26 +961,28 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "e2e": {"value": world * N / e2e_mean, "unit": "dets/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
-        "sigma_dets_per_s": {k: N / v for k, v in t_sig.items()},
-        "sigma_ms": {k: 1e3 * v for k, v in t_sig.items()},
-        "time_to_1e-6_Ha_s": {"mixed_bf16": tt_mixed, "fp64": tt_fp64, **tt_variants,
-                              "speedup_mixed_vs_fp64": (tt_fp64 / tt_mixed)
-                              if (tt_fp64 and tt_mixed) else None},
         "gpu_launches": None if launches_per_step is None else launches_per_step * args.steps,
         "gpu_launches_note": "library kernels of one untimed step (profiler count) x steps; "
                              "the mixed solver's iteration count varies slightly between steps",
-        "roofline": roof,
-        "selection": selection,
-        "outer_loop": outer_loop,
+        "selection": {k: sig3(v) for k, v in selection.items()},
+        "outer_loop_ms": [sig3(it["ms"]) for it in outer_loop["iterations"]],
+        "same_sample_as_reference": same_sample,
         "cpu_baseline": cpu,
-        "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": abs(last.energy - E_ref),
+        "roofline": roof,
+        "clocks": clk,
+        "energy": {"mixed": last.energy, "fp64_ref": E_ref, "abs_err_Ha": sig3(abs(last.energy - E_ref)),
                    "mixed_sigmas_fp64_fp32": [last.n_sigma_fp64, last.n_sigma_fp32],
                    "fp64_sigmas": fp64_runs[-1].n_sigma_fp64, "mixed_status": last.status},
-        "clocks": clk,
+        "sigma_ms": {k: sig3(1e3 * v) for k, v in t_sig.items()},
+        "sigma_dets_per_s": {k: sig3(N / v) for k, v in t_sig.items()},
+        "time_to_1e-6_Ha_s": {"mixed_bf16": sig3(tt_mixed), "fp64": sig3(tt_fp64),
+                              **{k: sig3(v) for k, v in tt_variants.items()},
+                              "speedup_mixed_vs_fp64": sig3(tt_fp64 / tt_mixed)
+                              if (tt_fp64 and tt_mixed) else None},
     }
     if args.detail:
-        print(json.dumps({"trace_mixed": results[-1].trace, "trace_fp64": fp64_runs[-1].trace}),
-              file=sys.stderr)
+        print(json.dumps({"trace_mixed": results[-1].trace, "trace_fp64": fp64_runs[-1].trace,
+                          "outer_loop": outer_loop, "cpu_detail": cpu_detail}), file=sys.stderr)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

@@ -316,12 +316,24 @@ int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
  * stream.  Errors: HINQS_ERR_ARG (polls out of range), HINQS_ERR_CUDA. */
 int hinqs_selftest_bounded_wait(long long polls, void* stream);
 
+/* ------------------------------------------------------ measurement probe --
+ * Not in the paper: the rate of this GPU's fused multiply-add pipe for `precision`
+ * (HINQS_PREC_FP64 or HINQS_PREC_FP32), the roofline of the CUDA-core kernels.  Runs
+ * resident warps on every SM, each thread advancing independent FMA recurrences with
+ * no memory traffic, times five launches with CUDA events and reports the best as
+ * *tflops (host; 2 FLOPs per FMA).  Synchronises the stream; about 10 ms of GPU time.
+ * Errors: HINQS_ERR_ARG (NULL tflops, other precision), HINQS_ERR_CUDA. */
+int hinqs_probe_fma_rate(int precision, double* tflops, void* stream);
+
 /* ---------------------------------------------------------- PT2 scores --
  * Step 2, Eq. pt2_score: the Epstein-Nesbet importance of candidate determinants
  * x_k = (xa[k], xb[k]) given the subspace eigenvector c (energy e0):
  *   v[k]     = <x_k|H|Psi0> = sum_{J in subspace} <x_k|H|J> c_J
  *   hxx[k]   = <x_k|H|x_k>            (includes E_nuc)
  *   score[k] = v[k]^2 / |e0 - hxx[k]| (e0 includes E_nuc)
+ * The score is that quotient in IEEE FP64 with no regulariser, as the equation states:
+ * when e0 == hxx[k] exactly it is +inf if v[k] != 0 (ranked first by hinqs_select_top
+ * and hinqs_basis_update) and NaN if v[k] == 0 (ranked below every number there).
  * Candidates may lie inside or outside the subspace (t = 1 rescoring covers both).
  *   c      device FP64 [N]; xa, xb device uint64 [m] strings of the sector
  *   v, hxx, score  device FP64 [m]

@@ -87,6 +87,7 @@ EXPORTED = [
     "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
     "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
     "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size", "hinqs_selftest_bounded_wait",
+    "hinqs_probe_fma_rate",
 ]
 
 
@@ -145,6 +146,7 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_davidson_workspace_size.argtypes = [I64, I64, ctypes.POINTER(_Opts),
                                                   ctypes.POINTER(ctypes.c_size_t)]
     lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, P]
+    lib.hinqs_probe_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -409,6 +411,15 @@ def selftest_bounded_wait(polls: int = 4096) -> int:
     lib = load_library()
     _dev()
     return lib.hinqs_selftest_bounded_wait(int(polls), _stream())
+
+
+def probe_fma_rate(precision: int = PREC_FP64) -> float:
+    """hinqs_probe_fma_rate: measured FMA rate (TFLOP/s) of the FP64 or FP32 pipe."""
+    lib = load_library()
+    _dev()
+    r = ctypes.c_double()
+    _check(lib.hinqs_probe_fma_rate(int(precision), ctypes.byref(r), _stream()))
+    return r.value
 
 
 def write_trace_jsonl(result: "DavidsonResult", path: str, label: str = "") -> None:
@@ -697,7 +708,24 @@ def energy_backward(n_orb, grad_E, rdm1, rdm2):
     return gh, ge
 
 
+def _check_vec(t, n, what):
+    """A caller-owned FP64 buffer the kernels read or write n elements of: float64,
+    contiguous, on the current device and at least n long (a short or mistyped
+    buffer would be written past its end on the device)."""
+    if not isinstance(t, torch.Tensor):
+        raise ValueError(f"{what} must be a torch tensor")
+    if t.dtype != torch.float64:
+        raise ValueError(f"{what} must be float64, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if t.device != _dev():
+        raise ValueError(f"{what} must be on {_dev()}, got {t.device}")
+    if t.numel() < n:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs {n}")
+
+
 def spin_marginals(sub, c, want_w: bool = False):
+    _check_vec(c, sub.N, "c")
     pa = torch.empty(sub.Na, dtype=torch.float64, device=_dev())
     pb = torch.empty(sub.Nb, dtype=torch.float64, device=_dev())
     w = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if want_w else None
@@ -708,6 +736,11 @@ def spin_marginals(sub, c, want_w: bool = False):
 def spin_marginals_noalloc(sub, c, p_alpha, p_beta, w=None):
     """hinqs_spin_marginals_noalloc: the library allocates nothing (its scratch is a
     fixed 8 MiB device array); the caller provides every output buffer."""
+    _check_vec(c, sub.N, "c")
+    _check_vec(p_alpha, sub.Na, "p_alpha")
+    _check_vec(p_beta, sub.Nb, "p_beta")
+    if w is not None:
+        _check_vec(w, sub.N, "w")
     _check(_lib.hinqs_spin_marginals_noalloc(sub.handle, _ptr(c), _ptr(p_alpha), _ptr(p_beta),
                                              _ptr(w), _stream()))
     return p_alpha, p_beta, w

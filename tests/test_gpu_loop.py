@@ -263,6 +263,30 @@ def test_nqs_loss_autograd_and_bad_index():
 # ------------------------------------------------------------- the whole loop
 
 
+def _oracle_chain_step(H, chain, t, samples, na, nb, k0, k, b_max, n_top):
+    """One outer iteration done by the oracle alone (Steps 1, 1', 2 and 3 on the
+    product of the basis strings), updating `chain` in place."""
+    samples = tuple(np.asarray(x, dtype=np.uint64) for x in samples)
+    if t == 0:
+        ya, yb, _ = oracle.candidate_pool([samples], (np.zeros(0), np.zeros(0)), na, nb)
+        keys = oracle.determinant_diag(H, ya, yb)
+        basis = oracle.basis_update(oracle.BASIS_COLD_START, ([], [], []), (ya, yb, keys), k0)
+    else:
+        ea, eb = oracle.classical_expansion(H, chain["sa"], chain["sb"], chain["c"], n_top)
+        b = chain["basis"]
+        ya, yb, _ = oracle.candidate_pool([samples, (ea, eb)], (b[0], b[1]), na, nb)
+        _, _, keys = oracle.pt2_scores(H, chain["sa"], chain["sb"], chain["c"], chain["E"], ya, yb)
+        if t == 1:
+            _, _, bk = oracle.pt2_scores(H, chain["sa"], chain["sb"], chain["c"], chain["E"],
+                                         b[0], b[1])
+            basis = oracle.basis_update(oracle.BASIS_RESCORE, (b[0], b[1], bk), (ya, yb, keys), k)
+        else:
+            basis = oracle.basis_update(oracle.BASIS_APPEND, b, (ya, yb, keys), k, b_max)
+    sa, sb = oracle.build_subspace(basis[0], basis[1], na, nb)
+    E, c = oracle.ground_state_dense(H, sa, sb)
+    chain.update(basis=tuple(np.asarray(x) for x in basis), sa=sa, sb=sb, c=c, E=E)
+
+
 def test_outer_loop_stepwise_parity():
     """Five iterations of Steps 1-3 on n = 10, 2/2 (full product 45 x 45): each step
     of the library's loop is re-done by the oracle from the same inputs (the samples,
@@ -278,8 +302,16 @@ def test_outer_loop_stepwise_parity():
         return (synth.hf_weighted_samples(n, na, 150, 500 + 2 * t),
                 synth.hf_weighted_samples(n, nb, 150, 501 + 2 * t))
 
+    # an independent chain run by the oracle alone: its own keys, basis updates and
+    # dense-eigh eigenvectors carried across iterations, compared with the library's
+    chain = dict(basis=None, sa=None, sb=None, c=None, E=None)
     for t in range(5):
         rec = loop.step(sampler(t))
+        _oracle_chain_step(H, chain, t, sampler(t), na, nb, k0=30, k=25, b_max=70, n_top=20)
+        assert np.array_equal(chain["basis"][0], _np_u64(loop.basis[0]))
+        assert np.array_equal(chain["basis"][1], _np_u64(loop.basis[1]))
+        assert np.allclose(chain["basis"][2], loop.basis[2].cpu().numpy(), rtol=1e-9, atol=1e-14)
+        assert abs(chain["E"] - rec.energy) < 1e-9
         L = loop.last
         samples = tuple(np.asarray(x, dtype=np.uint64) for x in L["samples"])
         pool = tuple(_np_u64(x) for x in L["pool"])

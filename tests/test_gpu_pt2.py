@@ -107,3 +107,34 @@ def test_pt2_errors():
     assert e.value.code == hq.ERR_PARTICLE_NUMBER
     v, hxx, s = hq.pt2_score(ham, sub, c, -1.0, np.zeros(0, np.uint64), np.zeros(0, np.uint64))
     assert v.numel() == 0
+
+
+def test_pt2_score_at_a_zero_denominator():
+    """Eq. pt2_score has no regulariser: with E0 equal to a candidate's H_xx the score is
+    v^2 / 0, +inf when v != 0 and NaN when v = 0 (c = 0), on both sides, each side
+    taking E0 from its own H_xx so that the denominator is exactly zero."""
+    h, eri, e_nuc, sa, sb, fa, fb = _case(8, 3, 3, 51, 0.5, 0.5)
+    ham = hq.Hamiltonian(h, eri, 3, 3, e_nuc)
+    sub = hq.build_subspace(sa, sb, 8, 3, 3)
+    H = oracle.Ham(h, eri, e_nuc, 3, 3)
+    osa, osb = oracle.build_subspace(sa, sb, 3, 3)
+    c = synth.random_vector(len(osa) * len(osb), 51)
+    xa = np.repeat(fa[:6], 6)
+    xb = np.tile(fb[:6], 6)
+    v, hxx, _ = hq.pt2_score(ham, sub, torch.tensor(c, device="cuda"), -5.0, xa, xb)
+    rv, rh, _ = oracle.pt2_scores(H, osa, osb, c, -5.0, xa, xb)
+    k = int(np.argmax(np.abs(rv)))
+    assert abs(rv[k]) > 1e-6 and abs(v.cpu().numpy()[k]) > 1e-6
+    e0_gpu = float(hxx.cpu().numpy()[k])
+    _, _, s = hq.pt2_score(ham, sub, torch.tensor(c, device="cuda"), e0_gpu, xa, xb)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        _, _, rs = oracle.pt2_scores(H, osa, osb, c, float(rh[k]), xa, xb)
+    assert np.isposinf(s.cpu().numpy()[k]) and np.isposinf(rs[k])
+    zero = np.zeros_like(c)
+    _, _, s0 = hq.pt2_score(ham, sub, torch.tensor(zero, device="cuda"), e0_gpu, xa, xb)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        _, _, rs0 = oracle.pt2_scores(H, osa, osb, zero, float(rh[k]), xa, xb)
+    assert np.isnan(s0.cpu().numpy()[k]) and np.isnan(rs0[k])
+    # every other candidate: the finite quotient, equal on both sides
+    ok = np.abs(float(rh[k]) - rh) > 1e-3
+    assert np.all(s0.cpu().numpy()[ok] == 0.0) and np.all(rs0[ok] == 0.0)
