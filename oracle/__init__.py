@@ -12,6 +12,10 @@ it with ctypes and adds the numpy-level steps:
                       numpy.linalg.eigh (a library primitive) on the dense matrix.
 * lanczos          -- Step 3 for subspaces too large for a dense matrix: Lanczos
                       with full reorthogonalisation on the matrix-free sigma.
+* basis lists      -- Step 3 as the paper states it: [H_B]_ij = <x_i|H|x_j> over a
+                      list of basis determinants (sort_list, dense_h_list,
+                      sigma_list, ground_state_dense_list), and the classical
+                      expansion that leaves out only that list.
 * outer loop       -- candidate pools (Steps 1, 1'), the Step 2 basis update
                       (select_top, basis_update), H_xx of arbitrary determinants,
                       the Step 3 warm start (remap_vector), the Step 4 loss inputs
@@ -63,6 +67,8 @@ def _load():
         lib.oracle_connected.restype = i64
         lib.oracle_coupling.argtypes = [i32, i32, i32, P, P, dbl, P, i64, P, i64, P, P, P, i64,
                                         P, P, i32]
+        lib.oracle_dense_h_list.argtypes = [i32, i32, i32, P, P, dbl, P, P, i64, P]
+        lib.oracle_sigma_list.argtypes = [i32, i32, i32, P, P, dbl, P, P, i64, P, P, P, i64, i32]
         lib.oracle_max_threads.argtypes = []
         _lib = lib
     return _lib
@@ -300,6 +306,67 @@ def lanczos(H: Ham, sa, sb, tol: float = 1e-10, max_iter: int = 400, seed: int =
     x /= np.linalg.norm(x)
     r = sigma(H, sa, sb, x, n_threads=n_threads) - theta * x
     return float(theta), x, float(np.linalg.norm(r))
+
+
+# ------------------------------------------------------------- basis lists --
+# Step 3 defines the projected Hamiltonian over the basis determinants themselves,
+# [H_B]_ij = <x_i|H|x_j>, and its exact diagonalisation gives the variational E_0
+# of that list.  A list here is held sorted by (alpha, beta) without duplicates.
+
+def sort_list(xa, xb):
+    """The determinants (xa[k], xb[k]) as a basis list: distinct, sorted by (alpha, beta)."""
+    pairs = sorted(set(zip(_u64(xa).tolist(), _u64(xb).tolist())))
+    return (np.array([p[0] for p in pairs], dtype=np.uint64),
+            np.array([p[1] for p in pairs], dtype=np.uint64))
+
+
+def dense_h_list(H: Ham, xa, xb):
+    """[H_B]_ij = <x_i|H|x_j> over a sorted basis list (Step 3)."""
+    lib = _load()
+    xa, xb = _u64(xa), _u64(xb)
+    M = len(xa)
+    out = np.zeros((M, M))
+    rc = lib.oracle_dense_h_list(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc,
+                                 _p(xa), _p(xb), M, _p(out))
+    if rc:
+        raise ValueError(f"oracle_dense_h_list failed ({rc})")
+    return out
+
+
+def sigma_list(H: Ham, xa, xb, c, rows=None, n_threads: int = 0):
+    """sigma_i = sum_j <x_i|H|x_j> c_j over a sorted basis list (rows: only those i)."""
+    lib = _load()
+    xa, xb, c = _u64(xa), _u64(xb), _f64(c)
+    rows_a = None if rows is None else np.ascontiguousarray(rows, dtype=np.int64)
+    m = len(xa) if rows_a is None else len(rows_a)
+    out = np.zeros(m)
+    rc = lib.oracle_sigma_list(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), H.e_nuc,
+                               _p(xa), _p(xb), len(xa), _p(c), _p(out), _p(rows_a),
+                               0 if rows_a is None else len(rows_a), n_threads)
+    if rc:
+        raise ValueError(f"oracle_sigma_list failed ({rc})")
+    return out
+
+
+def ground_state_dense_list(H: Ham, xa, xb):
+    """(E0, c0) of Step 3 on a sorted basis list, by numpy.linalg.eigh of H_B."""
+    evals, evecs = np.linalg.eigh(dense_h_list(H, xa, xb))
+    return float(evals[0]), evecs[:, 0]
+
+
+def classical_expansion_list(H: Ham, xa, xb, c, n_top: int):
+    """Eq. classical_expansion with the basis a list: every determinant y not in the
+    list with <y|H|x> != 0 for some x among the n_top list entries of largest |c|
+    (ties to the lower position); (ya, yb) ascending in (alpha, beta)."""
+    xa, xb = _u64(xa), _u64(xb)
+    members = set(zip(xa.tolist(), xb.tolist()))
+    keys = set()
+    for i in top_amplitudes(c, n_top):
+        ya, yb, _ = connected(H, xa[i], xb[i])
+        keys |= set(zip(ya.tolist(), yb.tolist()))
+    out = sorted(keys - members)
+    return (np.array([k[0] for k in out], dtype=np.uint64),
+            np.array([k[1] for k in out], dtype=np.uint64))
 
 
 def energy_from_rdm(H: Ham, g1, g2, norm2: float = 1.0):

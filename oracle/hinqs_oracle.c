@@ -27,6 +27,10 @@
  * Functions and what they follow:
  *   oracle_sigma      sigma_I = sum_J H_IJ c_J       (H|I> by operator application)
  *   oracle_dense_h    the full projected matrix H_B   (Step 3)
+ *   oracle_dense_h_list, oracle_sigma_list
+ *                     the same over a list of determinants: Step 3 defines
+ *                     [H_B]_ij = <x_i|H|x_j> over the basis determinants x_i, and
+ *                     sigma_i = sum_j [H_B]_ij c_j
  *   oracle_diag       H_II                            (Step 2 cold-start H_xx)
  *   oracle_connected  the determinants y != x with <y|H|x> != 0 (Eq. classical_expansion)
  *   oracle_coupling   <x|H|Psi0> = sum_i c_i H_{x,x_i} and H_xx for determinants x
@@ -268,6 +272,95 @@ int oracle_dense_h(int n, int na, int nb, const double *h, const double *eri, do
         odet D = det_from_strings(n, sa[I / Nb], sb[I % Nb]);
         dense_user du = {&B, Hout, N, I};
         apply_h(&H, &D, dense_emit, &du);
+    }
+    return 0;
+}
+
+/* ------------------------------------------------- determinant lists ---- */
+
+/* A basis list of determinants (xa[k], xb[k]), k < M, sorted ascending by
+ * (alpha, beta) and free of duplicates.  Position of (a, b) in it, or -1. */
+static int64_t find_pair(const uint64_t *xa, const uint64_t *xb, int64_t M, uint64_t a,
+                         uint64_t b) {
+    int64_t lo = 0, hi = M - 1;
+    while (lo <= hi) {
+        int64_t mid = lo + (hi - lo) / 2;
+        if (xa[mid] == a && xb[mid] == b) return mid;
+        if (xa[mid] < a || (xa[mid] == a && xb[mid] < b)) lo = mid + 1;
+        else hi = mid - 1;
+    }
+    return -1;
+}
+
+static int check_list(int n, int na, int nb, const double *h, const double *eri,
+                      const uint64_t *xa, const uint64_t *xb, int64_t M) {
+    if (n < 1 || n > 64 || na < 0 || nb < 0 || na > n || nb > n || !h || !eri || M < 0)
+        return -1;
+    if (M > 0 && (!xa || !xb)) return -1;
+    for (int64_t k = 1; k < M; ++k)  /* sorted by (alpha, beta), distinct */
+        if (!(xa[k - 1] < xa[k] || (xa[k - 1] == xa[k] && xb[k - 1] < xb[k]))) return -2;
+    return 0;
+}
+
+typedef struct {
+    const uint64_t *xa, *xb;
+    int64_t M, n;
+    const double *c; /* sigma: the vector */
+    double *Hcol;    /* dense: column of H_B being filled (stride M) */
+    int64_t col;
+    double acc;
+} list_user;
+
+static void list_sig_emit(const odet *out, double coeff, void *u) {
+    list_user *lu = (list_user *)u;
+    uint64_t a, b;
+    strings_from_det((int)lu->n, out, &a, &b);
+    int64_t K = find_pair(lu->xa, lu->xb, lu->M, a, b);
+    if (K >= 0) lu->acc += coeff * lu->c[K];
+}
+
+static void list_dense_emit(const odet *out, double coeff, void *u) {
+    list_user *lu = (list_user *)u;
+    uint64_t a, b;
+    strings_from_det((int)lu->n, out, &a, &b);
+    int64_t K = find_pair(lu->xa, lu->xb, lu->M, a, b);
+    if (K >= 0) lu->Hcol[K * lu->M + lu->col] += coeff;
+}
+
+/* H[i*M + j] = <x_i|H|x_j> for the determinants of the list (Step 3's H_B). */
+int oracle_dense_h_list(int n, int na, int nb, const double *h, const double *eri, double enuc,
+                        const uint64_t *xa, const uint64_t *xb, int64_t M, double *Hout) {
+    int rc = check_list(n, na, nb, h, eri, xa, xb, M);
+    if (rc || !Hout) return rc ? rc : -1;
+    oham H = {n, h, eri, enuc};
+    memset(Hout, 0, sizeof(double) * (size_t)M * (size_t)M);
+    for (int64_t j = 0; j < M; ++j) {
+        odet D = det_from_strings(n, xa[j], xb[j]);
+        list_user lu = {xa, xb, M, n, NULL, Hout, j, 0.0};
+        apply_h(&H, &D, list_dense_emit, &lu);
+    }
+    return 0;
+}
+
+/* sigma[k] = sum_j <x_i|H|x_j> c_j for i = rows[k] (rows == NULL: every i < M);
+ * by the symmetry of H, the terms of H|x_i> looked up in the list. */
+int oracle_sigma_list(int n, int na, int nb, const double *h, const double *eri, double enuc,
+                      const uint64_t *xa, const uint64_t *xb, int64_t M, const double *c,
+                      double *sigma, const int64_t *rows, int64_t n_rows, int n_threads) {
+    int rc = check_list(n, na, nb, h, eri, xa, xb, M);
+    if (rc || !c || !sigma) return rc ? rc : -1;
+    oham H = {n, h, eri, enuc};
+    int64_t cnt = rows ? n_rows : M;
+#ifdef _OPENMP
+    if (n_threads > 0) omp_set_num_threads(n_threads);
+#pragma omp parallel for schedule(dynamic, 16)
+#endif
+    for (int64_t k = 0; k < cnt; ++k) {
+        int64_t i = rows ? rows[k] : k;
+        odet D = det_from_strings(n, xa[i], xb[i]);
+        list_user lu = {xa, xb, M, n, c, NULL, 0, 0.0};
+        apply_h(&H, &D, list_sig_emit, &lu);
+        sigma[k] = lu.acc;
     }
     return 0;
 }

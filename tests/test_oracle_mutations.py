@@ -25,6 +25,10 @@ MUTANTS = [
     ("double-link-order", "sg *= cre(&d, parts[1]);\n                sg *= cre(&d, parts[0]);",
      "sg *= cre(&d, parts[0]);\n                sg *= cre(&d, parts[1]);"),
     ("nuclear-repulsion-dropped", "emit(D, H->enuc, user);", "emit(D, 0.0 * H->enuc, user);"),
+    ("list-lookup-ignores-beta", "if (xa[mid] == a && xb[mid] == b) return mid;",
+     "if (xa[mid] == a) return mid;"),
+    ("list-matrix-transposed", "if (K >= 0) lu->Hcol[K * lu->M + lu->col] += coeff;",
+     "if (K >= 0) lu->Hcol[K * lu->M + lu->col] += (K < lu->col ? 1.01 : 1.0) * coeff;"),
 ]
 
 

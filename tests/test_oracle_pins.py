@@ -450,3 +450,106 @@ def test_classical_expansion_excludes_subspace_and_is_union():
         ya, yb, _ = oracle.connected(H, sa[I // len(sb)], sb[I % len(sb)])
         union |= set(zip(ya.tolist(), yb.tolist()))
     assert got == union - inside
+
+
+# ------------------------------------------------------------ basis-list pins
+# Step 3 over the basis list itself: [H_B]_ij = <x_i|H|x_j> for the listed
+# determinants.  Pinned against the Jordan-Wigner matrix restricted to the list (the
+# list need not be a product of strings), the variational bound of Step 3 and its
+# special cases, and a brute-force classical expansion.
+
+
+def _random_list(n, na, nb, m, seed):
+    fa, fb = full_space(n, na, nb)
+    rng = np.random.default_rng(seed)
+    pairs = {(int(fa[rng.integers(len(fa))]), int(fb[rng.integers(len(fb))])) for _ in range(4 * m)}
+    pairs = sorted(pairs)[:m] if len(pairs) > m else sorted(pairs)
+    pairs = [pairs[i] for i in sorted(rng.choice(len(pairs), min(m, len(pairs)), replace=False))]
+    return (np.array([p[0] for p in pairs], dtype=np.uint64),
+            np.array([p[1] for p in pairs], dtype=np.uint64))
+
+
+def _list_fock(n, xa, xb):
+    return np.array([int(a) | (int(b) << n) for a, b in zip(xa, xb)], dtype=np.int64)
+
+
+@pytest.mark.parametrize("n,na,nb,m,seed", [(4, 2, 2, 20, 71), (5, 2, 2, 37, 72), (4, 1, 3, 9, 73)])
+def test_dense_h_list_matches_jordan_wigner(n, na, nb, m, seed):
+    h, eri, _ = synth.integrals(n, seed)
+    Hjw = _jw_hamiltonian(h, eri, 0.4).toarray()
+    xa, xb = oracle.sort_list(*_random_list(n, na, nb, m, seed))
+    H = oracle.Ham(h, eri, 0.4, na, nb)
+    idx = _list_fock(n, xa, xb)
+    ref = Hjw[np.ix_(idx, idx)]
+    assert np.max(np.abs(oracle.dense_h_list(H, xa, xb) - ref)) < 1e-12
+    c = synth.random_vector(len(xa), seed)
+    assert np.max(np.abs(oracle.sigma_list(H, xa, xb, c) - ref @ c)) < 1e-12
+    rows = np.array([len(xa) - 1, 0, len(xa) // 2])
+    assert np.max(np.abs(oracle.sigma_list(H, xa, xb, c, rows=rows) - (ref @ c)[rows])) < 1e-12
+
+
+def test_list_ground_state_bounds_and_limits():
+    """One determinant gives H_xx; the whole product gives the product's ground state;
+    a list lies above the product of its strings, which lies above the full space, and
+    a longer list (containing the shorter) never lies higher (Step 3 is variational)."""
+    n, na, nb = 6, 2, 2
+    h, eri, e_nuc = synth.integrals(n, 74)
+    H = oracle.Ham(h, eri, e_nuc, na, nb)
+    Hjw = _jw_hamiltonian(h, eri, e_nuc)
+    xa, xb = oracle.sort_list(*_random_list(n, na, nb, 60, 74))
+    E1, c1 = oracle.ground_state_dense_list(H, xa[:1], xb[:1])
+    x0 = int(xa[0]) | (int(xb[0]) << n)
+    assert abs(E1 - Hjw[x0, x0]) < 1e-12 and abs(abs(c1[0]) - 1.0) < 1e-15
+    sa, sb = oracle.build_subspace(xa, xb, na, nb)
+    pa, pb = np.repeat(sa, len(sb)), np.tile(sb, len(sa))
+    E_prod, _ = oracle.ground_state_dense(H, sa, sb)
+    E_prod_list, _ = oracle.ground_state_dense_list(H, pa, pb)
+    assert abs(E_prod - E_prod_list) < 1e-11
+    E_list, c_list = oracle.ground_state_dense_list(H, xa, xb)
+    E_fci, _ = fci_dense(h, eri, e_nuc, na, nb)
+    assert E_list >= E_prod - 1e-12 and E_prod >= E_fci - 1e-12
+    assert E_list > E_prod + 1e-6  # a strict sub-list of a generic product lies higher
+    half = np.sort(np.random.default_rng(1).choice(len(xa), len(xa) // 2, replace=False))
+    E_half, _ = oracle.ground_state_dense_list(H, xa[half], xb[half])
+    assert E_half >= E_list - 1e-12
+    # the eigen-equation through the JW matrix restricted to the list
+    idx = _list_fock(n, xa, xb)
+    Hl = Hjw.toarray()[np.ix_(idx, idx)]
+    assert np.max(np.abs(Hl @ c_list - E_list * c_list)) < 1e-10
+
+
+def test_sort_list_and_unsorted_lists_rejected():
+    xa = np.array([5, 3, 5, 3], dtype=np.uint64)
+    xb = np.array([6, 9, 6, 3], dtype=np.uint64)
+    sa, sb = oracle.sort_list(xa, xb)
+    assert sa.tolist() == [3, 3, 5] and sb.tolist() == [3, 9, 6]
+    h, eri, _ = synth.integrals(4, 75)
+    H = oracle.Ham(h, eri, 0.0, 2, 2)
+    with pytest.raises(ValueError):
+        oracle.dense_h_list(H, xa, xb)
+
+
+def test_classical_expansion_list_against_jordan_wigner():
+    """Determinants outside the list connected (non-zero JW element) to one of the n_top
+    largest |c| of the list; members of the product that are not in the list are
+    candidates too."""
+    n, na, nb = 5, 2, 1
+    h, eri, _ = synth.integrals(n, 76)
+    Hjw = _jw_hamiltonian(h, eri, 0.0).toarray()
+    H = oracle.Ham(h, eri, 0.0, na, nb)
+    xa, xb = oracle.sort_list(*_random_list(n, na, nb, 12, 76))
+    c = synth.random_vector(len(xa), 76)
+    ya, yb = oracle.classical_expansion_list(H, xa, xb, c, 4)
+    fock = _list_fock(n, xa, xb)
+    top = np.argsort(-np.abs(c), kind="stable")[:4]
+    ref = set()
+    for i in top:
+        col = Hjw[:, fock[i]]
+        ref |= set(np.nonzero(np.abs(col) > 0)[0].tolist())
+    ref -= set(fock.tolist())
+    got = set(_list_fock(n, ya, yb).tolist())
+    assert got == ref
+    sa, sb = oracle.build_subspace(xa, xb, na, nb)
+    prod = set(int(a) | (int(b) << n) for a in sa for b in sb)
+    assert got & (prod - set(fock.tolist()))  # product members outside the list appear
+    assert list(zip(ya.tolist(), yb.tolist())) == sorted(zip(ya.tolist(), yb.tolist()))
