@@ -85,6 +85,7 @@ extern "C" {
 typedef struct hinqs_ham_s hinqs_ham;
 typedef struct hinqs_subspace_s hinqs_subspace;
 typedef struct hinqs_links_s hinqs_links;
+typedef struct hinqs_detlist_s hinqs_detlist;
 
 /* Thread-local description of the last error (never NULL). */
 const char* hinqs_last_error_message(void);
@@ -260,6 +261,58 @@ void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
 int hinqs_davidson(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
                    const hinqs_links* lb, const double* guess, const hinqs_davidson_opts* opts,
                    double* energy, double* c_out, hinqs_davidson_info* info, void* stream);
+/* The same solve on a basis list (Step 3 over B itself): H replaced by P H P on the
+ * list's m entries; guess and c_out are device FP64 [m] in the list's order.  In the
+ * mixed mode every inner product runs in FP32 on CUDA cores (the tensor-core inner
+ * precisions are taken as HINQS_PREC_FP32).  Errors as hinqs_davidson, plus
+ * HINQS_ERR_EMPTY for an empty list. */
+int hinqs_davidson_list(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                        const hinqs_links* lb, const hinqs_detlist* list, const double* guess,
+                        const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                        hinqs_davidson_info* info, void* stream);
+
+/* --------------------------------------------------- basis-list subspace --
+ * Step 3 as the paper states it: the projected Hamiltonian over the basis
+ * determinants themselves, [H_B]_ij = <x_i|H|x_j> for the x_i of the list B, whose
+ * exact diagonalisation gives the energy variational with respect to B.  The list
+ * lives inside the product subspace `sub` of its distinct alpha and beta strings
+ * (hinqs_build_subspace on the list's strings); the product supplies strings, links
+ * and per-string tables, and the list operator is P H P with P the projector on the
+ * list, applied to vectors of the list's length m (entry k = the k-th determinant in
+ * ascending product position, i.e. ascending (alpha, beta) string index).
+ *
+ * hinqs_detlist_create: the list of determinants (xa[k], xb[k]) (device uint64 [m],
+ * duplicates allowed, any order) as positions in `sub`, sorted and distinct.
+ * Errors: HINQS_ERR_ARG (NULL, negative m, a determinant whose strings are not in
+ * the product: nothing is created), HINQS_ERR_OOM.  Synchronises the stream.  The
+ * handle borrows the subspace's strings: destroy it before the subspace. */
+int hinqs_detlist_create(const hinqs_subspace* sub, const uint64_t* xa, const uint64_t* xb,
+                         int64_t m, hinqs_detlist** out, void* stream);
+/* host output: number of distinct list entries */
+int hinqs_detlist_size(const hinqs_detlist* list, int64_t* m);
+/* product positions I = i_a * N_b + i_b of the entries, ascending (device int64 [m]) */
+int hinqs_detlist_positions(const hinqs_detlist* list, int64_t* pos, void* stream);
+int hinqs_detlist_destroy(hinqs_detlist* list);
+/* c_product (device FP64 [N_a * N_b]) = the list vector c_list [m] placed at its
+ * positions, zero elsewhere: the same state in the product's indexing, so that
+ * hinqs_rdm, hinqs_spin_marginals, hinqs_pt2_score and hinqs_nqs_loss (with the list's
+ * positions as its basis) apply to a list eigenvector unchanged.  gather: the reverse
+ * (c_list[k] = c_product[pos[k]]).  The vectors must not overlap. */
+int hinqs_detlist_scatter(const hinqs_detlist* list, const double* c_list, double* c_product,
+                          void* stream);
+int hinqs_detlist_gather(const hinqs_detlist* list, const double* c_product, double* c_list,
+                         void* stream);
+/* hdiag[k] = <x_k|H|x_k> (incl. E_nuc), device FP64 [m] */
+int hinqs_diag_list(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                    const hinqs_links* lb, const hinqs_detlist* list, double* hdiag, void* stream);
+/* sigma[k] = sum_l <x_k|H|x_l> c[l] over the list entries; c, sigma [m] of the
+ * precision's type (double for HINQS_PREC_FP64, float for the FP32 modes, which all
+ * run on CUDA cores here); sigma is overwritten; no atomics, so the result is the same
+ * on every call.  Errors: HINQS_ERR_ARG (handles of different problems, a list of
+ * another subspace, NULL, overlapping vectors, unknown precision). */
+int hinqs_sigma_list(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_links* la,
+                     const hinqs_links* lb, const hinqs_detlist* list, const void* c, void* sigma,
+                     int precision, void* stream);
 
 /* ------------------------------------------------------------- autotune --
  * Not in the paper (its benchmarks use one geometry each; potential-energy scans
@@ -362,6 +415,13 @@ int hinqs_top_amplitudes(const hinqs_subspace* sub, const double* c, int64_t k, 
 int hinqs_classical_expansion(const hinqs_ham* ham, const hinqs_subspace* sub, const double* c,
                               int64_t n_top, uint64_t* xa_out, uint64_t* xb_out, int64_t cap,
                               int64_t* count, void* stream);
+/* The same with the basis a list: the n_top largest |c_list| among the list entries
+ * (ties: lower entry first) are expanded and only the list's own determinants are
+ * left out (determinants of the product outside the list are candidates). */
+int hinqs_classical_expansion_list(const hinqs_ham* ham, const hinqs_subspace* sub,
+                                   const hinqs_detlist* list, const double* c_list, int64_t n_top,
+                                   uint64_t* xa_out, uint64_t* xb_out, int64_t cap, int64_t* count,
+                                   void* stream);
 
 /* ----------------------------------------------------------- outer loop --
  * The steps of the HI-NQS iteration (Sec. 2.2) that surround the subspace solve.

@@ -87,7 +87,10 @@ EXPORTED = [
     "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
     "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
     "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size", "hinqs_selftest_bounded_wait",
-    "hinqs_probe_fma_rate",
+    "hinqs_probe_fma_rate", "hinqs_detlist_create", "hinqs_detlist_size",
+    "hinqs_detlist_positions", "hinqs_detlist_destroy", "hinqs_detlist_scatter",
+    "hinqs_detlist_gather", "hinqs_diag_list", "hinqs_sigma_list", "hinqs_davidson_list",
+    "hinqs_classical_expansion_list",
 ]
 
 
@@ -147,6 +150,18 @@ def load_library(path: str = LIB_PATH):
                                                   ctypes.POINTER(ctypes.c_size_t)]
     lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, P]
     lib.hinqs_probe_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
+    lib.hinqs_detlist_create.argtypes = [P, P, P, I64, PP, P]
+    lib.hinqs_detlist_size.argtypes = [P, PI64]
+    lib.hinqs_detlist_positions.argtypes = [P, P, P]
+    lib.hinqs_detlist_destroy.argtypes = [P]
+    lib.hinqs_detlist_scatter.argtypes = [P, P, P, P]
+    lib.hinqs_detlist_gather.argtypes = [P, P, P, P]
+    lib.hinqs_diag_list.argtypes = [P, P, P, P, P, P, P]
+    lib.hinqs_sigma_list.argtypes = [P, P, P, P, P, P, P, I, P]
+    lib.hinqs_davidson_list.argtypes = [P, P, P, P, P, P, ctypes.POINTER(_Opts),
+                                        ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(_Info),
+                                        P]
+    lib.hinqs_classical_expansion_list.argtypes = [P, P, P, P, I64, P, P, I64, PI64, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -348,10 +363,8 @@ def _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, deno
     return opts
 
 
-def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
-             max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
-             denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
-             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
+def _davidson_call(fn, args, n, guess, precision, max_iter, max_subspace, tol_residual,
+                   tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out):
     opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
                       inner_tol, inner_precision)
     bufs = None
@@ -363,22 +376,117 @@ def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_i
         opts.trace_resid = ctypes.cast(bufs[1], ctypes.POINTER(ctypes.c_double))
         opts.trace_time = ctypes.cast(bufs[2], ctypes.POINTER(ctypes.c_double))
         opts.trace_kind = ctypes.cast(bufs[3], ctypes.POINTER(ctypes.c_int))
-    c = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if out is None else out
-    if guess is not None and (guess.dtype != torch.float64 or guess.numel() != sub.N):
+    c = torch.empty(n, dtype=torch.float64, device=_dev()) if out is None else out
+    if out is not None:
+        _check_vec(out, n, "out")
+    if guess is not None and (guess.dtype != torch.float64 or guess.numel() != n):
         raise ValueError("guess must be a float64 tensor of the subspace size")
     e = ctypes.c_double()
     info = _Info()
-    rc = _lib.hinqs_davidson(ham.handle, sub.handle, la.handle, lb.handle, _ptr(guess),
-                             ctypes.byref(opts), ctypes.byref(e), _ptr(c), ctypes.byref(info),
-                             _stream())
+    rc = fn(*args, _ptr(guess), ctypes.byref(opts), ctypes.byref(e), _ptr(c), ctypes.byref(info),
+            _stream())
     _check(rc, allow_warning=True)
     tr = {}
     if bufs is not None:
-        n = info.trace_len
-        tr = dict(theta=list(bufs[0][:n]), resid=list(bufs[1][:n]), time=list(bufs[2][:n]),
-                  kind=list(bufs[3][:n]))
+        k = info.trace_len
+        tr = dict(theta=list(bufs[0][:k]), resid=list(bufs[1][:k]), time=list(bufs[2][:k]),
+                  kind=list(bufs[3][:k]))
     return DavidsonResult(e.value, c, rc, info.iterations, info.n_sigma_fp64, info.n_sigma_fp32,
                           info.n_restarts, info.n_refinements, info.residual, info.seconds, tr)
+
+
+def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
+             max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
+             denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
+             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
+    """hinqs_davidson: lowest eigenpair of H on the product subspace (Step 3)."""
+    return _davidson_call(_lib.hinqs_davidson, (ham.handle, sub.handle, la.handle, lb.handle),
+                          sub.N, guess, precision, max_iter, max_subspace, tol_residual,
+                          tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out)
+
+
+def davidson_list(ham, sub, la, lb, lst, guess=None, precision: int = DAVIDSON_FP64,
+                  max_iter: int = 200, max_subspace: int = 16, tol_residual: float = 1e-8,
+                  tol_energy: float = 1e-10, denom_floor: float = 1e-4, inner_tol: float = 1e-3,
+                  trace_cap: int = 0, inner_precision: int = PREC_FP32,
+                  out=None) -> DavidsonResult:
+    """hinqs_davidson_list: lowest eigenpair of H_B over the basis list `lst` (Step 3);
+    the eigenvector is indexed by the list's entries."""
+    return _davidson_call(_lib.hinqs_davidson_list,
+                          (ham.handle, sub.handle, la.handle, lb.handle, lst.handle), lst.m,
+                          guess, precision, max_iter, max_subspace, tol_residual, tol_energy,
+                          denom_floor, inner_tol, trace_cap, inner_precision, out)
+
+
+class DetList:
+    """A basis list of determinants inside a product subspace (Step 3's H_B over B)."""
+
+    def __init__(self, handle, sub):
+        self.handle, self._sub = handle, sub   # the list borrows the subspace's strings
+        m = ctypes.c_int64()
+        _check(_lib.hinqs_detlist_size(handle, ctypes.byref(m)))
+        self.m = m.value
+
+    def positions(self):
+        """Product positions (int64, ascending) of the list entries."""
+        out = torch.empty(self.m, dtype=torch.int64, device=_dev())
+        _check(_lib.hinqs_detlist_positions(self.handle, _ptr(out), _stream()))
+        return out
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.hinqs_detlist_destroy(self.handle)
+            self.handle = None
+
+
+def detlist(sub, xa, xb) -> DetList:
+    """hinqs_detlist_create: the determinants (xa[k], xb[k]) of `sub` as a basis list."""
+    xa, xb = _u64(xa), _u64(xb)
+    if xa.numel() != xb.numel():
+        raise ValueError("xa and xb must have the same length")
+    out = ctypes.c_void_p()
+    _check(_lib.hinqs_detlist_create(sub.handle, _ptr(xa), _ptr(xb), xa.numel(), ctypes.byref(out),
+                                     _stream()))
+    return DetList(out, sub)
+
+
+def detlist_scatter(lst, c_list):
+    """hinqs_detlist_scatter: the list vector placed in the product's indexing."""
+    _check_vec(c_list, lst.m, "c_list")
+    out = torch.empty(lst._sub.N, dtype=torch.float64, device=_dev())
+    _check(_lib.hinqs_detlist_scatter(lst.handle, _ptr(c_list), _ptr(out), _stream()))
+    return out
+
+
+def detlist_gather(lst, c_product):
+    """hinqs_detlist_gather: the product vector's entries at the list's positions."""
+    _check_vec(c_product, lst._sub.N, "c_product")
+    out = torch.empty(lst.m, dtype=torch.float64, device=_dev())
+    _check(_lib.hinqs_detlist_gather(lst.handle, _ptr(c_product), _ptr(out), _stream()))
+    return out
+
+
+def diag_list(ham, sub, la, lb, lst):
+    """hinqs_diag_list: <x_k|H|x_k> of the list entries."""
+    out = torch.empty(lst.m, dtype=torch.float64, device=_dev())
+    _check(_lib.hinqs_diag_list(ham.handle, sub.handle, la.handle, lb.handle, lst.handle, _ptr(out),
+                                _stream()))
+    return out
+
+
+def sigma_list(ham, sub, la, lb, lst, c, out=None, precision: int | None = None):
+    """hinqs_sigma_list: sigma = P H P c over the basis list (float64 or float32 c)."""
+    if precision is None:
+        precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
+    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    if c.dtype != dt or not c.is_cuda or not c.is_contiguous() or c.numel() != lst.m:
+        raise ValueError(f"c must be a contiguous CUDA {dt} tensor of the list's length")
+    out = torch.empty_like(c) if out is None else out
+    if out.dtype != dt or out.numel() != lst.m or not out.is_contiguous():
+        raise ValueError("out must match c")
+    _check(_lib.hinqs_sigma_list(ham.handle, sub.handle, la.handle, lb.handle, lst.handle, _ptr(c),
+                                 _ptr(out), precision, _stream()))
+    return out
 
 
 def sigma_workspace_size(n_alpha_strings: int, n_beta_strings: int,
@@ -536,6 +644,28 @@ def classical_expansion(ham, sub, c, n_top: int = 1000):
     _check(_lib.hinqs_classical_expansion(ham.handle, sub.handle, _ptr(c), n_top, _ptr(xa),
                                           _ptr(xb), m, ctypes.byref(cnt), _stream()))
     return xa, xb
+
+
+def classical_expansion_list(ham, sub, lst, c_list, n_top: int = 1000):
+    """hinqs_classical_expansion_list (Step 1' with the basis a list): (xa, xb) of the
+    determinants outside the list connected to its n_top largest |c_list| entries."""
+    _check_vec(c_list, lst.m, "c_list")
+    cnt = ctypes.c_int64()
+    n, na, nb = sub.n, sub.n_alpha, sub.n_beta
+    s1a, s1b = na * (n - na), nb * (n - nb)
+    per = (s1a + s1b + comb(na, 2) * comb(n - na, 2) + comb(nb, 2) * comb(n - nb, 2)
+           + s1a * s1b)
+    bound = min(max(0, int(n_top)), lst.m) * per
+    args = (ham.handle, sub.handle, lst.handle, _ptr(c_list), n_top)
+    if bound > _ONE_PASS_CAP:
+        _check(_lib.hinqs_classical_expansion_list(*args, None, None, 0, ctypes.byref(cnt),
+                                                   _stream()))
+        bound = cnt.value
+    xa = torch.empty(bound, dtype=torch.int64, device=_dev())
+    xb = torch.empty(bound, dtype=torch.int64, device=_dev())
+    _check(_lib.hinqs_classical_expansion_list(*args, _ptr(xa), _ptr(xb), bound, ctypes.byref(cnt),
+                                               _stream()))
+    return xa[:cnt.value], xb[:cnt.value]
 
 
 def _f64_dev(x, n=None, what="values"):

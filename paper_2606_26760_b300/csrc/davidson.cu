@@ -606,11 +606,18 @@ struct Ctx {
   cudaStream_t s;
   int64_t N;
   int grid;
+  const hinqs_detlist_s* L = nullptr;  // basis list (vectors over its entries) or NULL
   double* partial = nullptr;  // [2 * (kMaxSub+1) * kRedGrid] >= kResGrid
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
   float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
   unsigned int* counters = nullptr;  // [kMaxSub + 1] arrival counters of the dot kernels (zero)
 };
+
+// y = H x on the product subspace, or P H P x on the basis list when the context has one
+static int apply_sigma(Ctx& c, const void* x, void* y, int precision) {
+  if (c.L) return sigma_list_launch(c.H, c.B, c.la, c.lb, c.L, x, y, precision, c.s);
+  return sigma_launch(c.H, c.B, c.la, c.lb, x, y, precision, c.s);
+}
 
 template <typename TA, typename TB>
 static int dots(Ctx& c, const TA* A, int64_t lda, int m, const TB* b, double* out) {
@@ -779,7 +786,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
     for (int it = 0; it < o.max_iter; ++it) {
       double* vm = V + (size_t)(m - 1) * N;
       double* wm = W + (size_t)(m - 1) * N;
-      HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, vm, wm, HINQS_PREC_FP64, c.s));
+      HQ_TRY(apply_sigma(c, vm, wm, HINQS_PREC_FP64));
       info.n_sigma_fp64++;
       HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
@@ -952,7 +959,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     double h[2];
     for (;;) {
       if (hard) {
-        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, x, sx, HINQS_PREC_FP64, c.s));
+        HQ_TRY(apply_sigma(c, x, sx, HINQS_PREC_FP64));
         info.n_sigma_fp64++;
         total++;
         double* th = c.small + 2 * kMaxSub;
@@ -994,7 +1001,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       HQ_LAUNCH_CHECK();
       if (m == 0) {  // first direction: the preconditioned FP64 residual in t
         HQ_TRY(orthonormalise_mixed(c, t, x, V, N, 0, V, &ratio));
-        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, V, W, o.inner_precision, c.s));
+        HQ_TRY(apply_sigma(c, V, W, o.inner_precision));
         info.n_sigma_fp32++;
         total++;
         m = 1;
@@ -1026,8 +1033,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
           restart_hard = true;
           break;
         }
-        HQ_TRY(sigma_launch(c.H, c.B, c.la, c.lb, V + (size_t)m * N, W + (size_t)m * N,
-                            o.inner_precision, c.s));
+        HQ_TRY(apply_sigma(c, V + (size_t)m * N, W + (size_t)m * N, o.inner_precision));
         info.n_sigma_fp32++;
         total++;
         m++;
@@ -1137,29 +1143,36 @@ extern "C" int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_
   return HINQS_OK;
 }
 
-extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
-                              const hinqs_links* lb, const double* guess,
-                              const hinqs_davidson_opts* opts, double* energy, double* c_out,
-                              hinqs_davidson_info* info_out, void* stream) {
-  HQ_TRY(check_triplet(H, B, la, lb, "hinqs_davidson"));
-  if (!c_out) return fail(HINQS_ERR_ARG, "hinqs_davidson: c_out is NULL");
+static int davidson_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
+                          const hinqs_links* lb, const hinqs_detlist* L, const double* guess,
+                          const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                          hinqs_davidson_info* info_out, void* stream, const char* who) {
+  HQ_TRY(check_triplet(H, B, la, lb, who));
+  if (L) {
+    HQ_TRY(check_list(B, L, who));
+    if (L->m == 0) return fail(HINQS_ERR_EMPTY, "%s: empty basis list", who);
+  }
+  if (!c_out) return fail(HINQS_ERR_ARG, "%s: c_out is NULL", who);
   hinqs_davidson_opts o;
   hinqs_davidson_default_opts(&o);
   if (opts) o = *opts;
   if (o.max_subspace < 3 || o.max_subspace > kMaxSub)
-    return fail(HINQS_ERR_ARG, "hinqs_davidson: max_subspace must be in 3..%d", kMaxSub);
+    return fail(HINQS_ERR_ARG, "%s: max_subspace must be in 3..%d", who, kMaxSub);
   if (o.max_iter < 1 || !(o.tol_residual > 0.0) || !(o.denom_floor > 0.0))
-    return fail(HINQS_ERR_ARG, "hinqs_davidson: bad max_iter / tolerances");
+    return fail(HINQS_ERR_ARG, "%s: bad max_iter / tolerances", who);
   if (o.precision != HINQS_DAVIDSON_FP64 && o.precision != HINQS_DAVIDSON_MIXED)
-    return fail(HINQS_ERR_ARG, "hinqs_davidson: unknown precision %d", o.precision);
+    return fail(HINQS_ERR_ARG, "%s: unknown precision %d", who, o.precision);
   if (o.precision == HINQS_DAVIDSON_MIXED && o.inner_precision != HINQS_PREC_FP32 &&
       o.inner_precision != HINQS_PREC_FP32_BF16AB && o.inner_precision != HINQS_PREC_FP32_BF16X3AB)
-    return fail(HINQS_ERR_ARG, "hinqs_davidson: unknown inner precision %d", o.inner_precision);
+    return fail(HINQS_ERR_ARG, "%s: unknown inner precision %d", who, o.inner_precision);
+  // the list operator has no tensor-core form: its inner products run in FP32
+  if (L && o.precision == HINQS_DAVIDSON_MIXED) o.inner_precision = HINQS_PREC_FP32;
   hinqs_davidson_info info{};
   Trace tr;
   tr.o = &o;
   tr.t0 = std::chrono::steady_clock::now();
-  Ctx c{H, B, la, lb, (cudaStream_t)stream, B->Na * B->Nb, 0};
+  Ctx c{H, B, la, lb, (cudaStream_t)stream, L ? L->m : B->Na * B->Nb, 0};
+  c.L = L;
   c.grid = (int)std::min<int64_t>(ceil_div(c.N, 256), 8 * kNumSMs);
   double* D = nullptr;
   int rc = HINQS_OK;
@@ -1169,7 +1182,7 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   }
   if (!rc && cudaMemsetAsync(c.counters, 0, (kMaxSub + 1) * sizeof(unsigned int), c.s) != cudaSuccess)
     rc = cuda_fail(cudaGetLastError(), "hinqs_davidson counters", __FILE__, __LINE__);
-  if (!rc) rc = diag_launch(H, B, la, lb, D, c.s);
+  if (!rc) rc = L ? diag_list_launch(H, la, lb, L, D, c.s) : diag_launch(H, B, la, lb, D, c.s);
   if (!rc) {
     if (o.precision == HINQS_DAVIDSON_FP64)
       rc = davidson_fp64(c, guess, o, D, energy, c_out, info, tr);
@@ -1178,7 +1191,7 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   }
   if (rc >= 0) {
     cudaError_t e = cudaStreamSynchronize(c.s);
-    if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_davidson", __FILE__, __LINE__);
+    if (e != cudaSuccess) rc = cuda_fail(e, who, __FILE__, __LINE__);
   }
   if (rc >= 0 && o.precision == HINQS_DAVIDSON_MIXED && o.inner_precision != HINQS_PREC_FP32) {
     int t = tc_error_check(c.s);
@@ -1193,4 +1206,21 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
   if (rc >= 0) info.status = rc;
   if (info_out) *info_out = info;
   return rc;
+}
+
+extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
+                              const hinqs_links* lb, const double* guess,
+                              const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                              hinqs_davidson_info* info_out, void* stream) {
+  return davidson_entry(H, B, la, lb, nullptr, guess, opts, energy, c_out, info_out, stream,
+                        "hinqs_davidson");
+}
+
+extern "C" int hinqs_davidson_list(const hinqs_ham* H, const hinqs_subspace* B,
+                                   const hinqs_links* la, const hinqs_links* lb,
+                                   const hinqs_detlist* L, const double* guess,
+                                   const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                                   hinqs_davidson_info* info_out, void* stream) {
+  return davidson_entry(H, B, la, lb, L, guess, opts, energy, c_out, info_out, stream,
+                        "hinqs_davidson_list");
 }

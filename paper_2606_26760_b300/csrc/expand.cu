@@ -110,7 +110,24 @@ struct ExpArgs {
   int64_t s1a, s1b, d2a, d2b, per;  // excitation counts per determinant
   uint64_t* keys;
   int64_t total;
+  // basis list (list mode): only its determinants are left out, not the whole product
+  const int64_t* arow;
+  const int32_t* lib;
 };
+
+// is (i_a, i_b) an entry of the basis list (binary search in alpha string i_a's row)?
+__device__ __forceinline__ bool in_list(const int64_t* __restrict__ arow,
+                                        const int32_t* __restrict__ lib, int64_t a, int64_t b) {
+  int64_t lo = arow[a], hi = arow[a + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    const int64_t v = lib[mid];
+    if (v == b) return true;
+    if (v < b) lo = mid + 1;
+    else hi = mid;
+  }
+  return false;
+}
 
 __global__ void k_expand(ExpArgs A) {
   const uint64_t full = (1ull << A.n) - 1ull;
@@ -159,9 +176,18 @@ __global__ void k_expand(ExpArgs A) {
       yb = (xb & ~(1ull << qb)) | (1ull << pb);
       el = single_sign(xa, pa, qa) * single_sign(xb, pb, qb) * eri4(A.eri, A.n, pa, qa, pb, qb);
     }
-    const bool inside = find_string(A.sa, A.Na, ya) >= 0 && find_string(A.sb, A.Nb, yb) >= 0;
+    const int64_t ya_i = find_string(A.sa, A.Na, ya);
+    const int64_t yb_i = ya_i >= 0 ? find_string(A.sb, A.Nb, yb) : -1;
+    bool inside = ya_i >= 0 && yb_i >= 0;
+    if (inside && A.arow) inside = in_list(A.arow, A.lib, ya_i, yb_i);
     A.keys[g] = (el != 0.0 && !inside) ? ((ya << 32) | yb) : kNoKey;
   }
+}
+
+__global__ void k_map_positions(int64_t* idx, int64_t k, const int64_t* __restrict__ pos) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k;
+       i += (int64_t)gridDim.x * blockDim.x)
+    idx[i] = pos[idx[i]];
 }
 
 __global__ void k_fill_key(uint64_t* a, int64_t from, int64_t to) {
@@ -250,19 +276,20 @@ extern "C" int hinqs_top_amplitudes(const hinqs_subspace* B, const double* c, in
   return select_top_impl(c, B->Na * B->Nb, k, kSelAbs, idx_out, (cudaStream_t)stream);
 }
 
-extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspace* B,
-                                         const double* c, int64_t n_top, uint64_t* xa_out,
-                                         uint64_t* xb_out, int64_t cap, int64_t* count,
-                                         void* stream) {
+// Step 1' over the product (L = NULL: c over the product, the product left out) or over
+// a basis list (c over the list entries, only the list left out)
+static int expansion_impl(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_detlist* L,
+                          const double* c, int64_t n_top, uint64_t* xa_out, uint64_t* xb_out,
+                          int64_t cap, int64_t* count, void* stream, const char* who) {
   if (!H || !B || !c || !count || n_top < 0)
-    return fail(HINQS_ERR_ARG, "hinqs_classical_expansion: NULL argument or negative n_top");
+    return fail(HINQS_ERR_ARG, "%s: NULL argument or negative n_top", who);
   if (H->n != B->n || H->n_alpha != B->n_alpha || H->n_beta != B->n_beta)
-    return fail(HINQS_ERR_ARG, "hinqs_classical_expansion: Hamiltonian and subspace disagree");
-  if (H->n > 32)
-    return fail(HINQS_ERR_ARG, "hinqs_classical_expansion: n_orb=%d above 32", H->n);
+    return fail(HINQS_ERR_ARG, "%s: Hamiltonian and subspace disagree", who);
+  if (L) HQ_TRY(check_list(B, L, who));
+  if (H->n > 32) return fail(HINQS_ERR_ARG, "%s: n_orb=%d above 32", who, H->n);
   *count = 0;
   cudaStream_t s = (cudaStream_t)stream;
-  const int64_t N = B->Na * B->Nb;
+  const int64_t N = L ? L->m : B->Na * B->Nb;
   n_top = std::min(n_top, N);
   if (n_top == 0) return HINQS_OK;
   ExpArgs A;
@@ -275,6 +302,8 @@ extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspac
   A.sb = B->sb;
   A.Na = B->Na;
   A.Nb = B->Nb;
+  A.arow = L ? L->arow : nullptr;
+  A.lib = L ? L->ib : nullptr;
   const int64_t va = A.n - A.na, vb = A.n - A.nb;
   A.s1a = A.na * va;
   A.s1b = A.nb * vb;
@@ -292,6 +321,11 @@ extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspac
   auto run = [&]() -> int {
     HQ_TRY(dalloc(&top, n_top, s));
     HQ_TRY(select_top_impl(c, N, n_top, kSelAbs, top, s));
+    if (L) {  // list entries -> product positions
+      k_map_positions<<<(unsigned)std::min<int64_t>(ceil_div(n_top, 256), 1024), 256, 0, s>>>(
+          top, n_top, L->pos);
+      HQ_LAUNCH_CHECK();
+    }
     HQ_TRY(dalloc(&keys, m_pad, s));
     A.top = top;
     A.keys = keys;
@@ -308,8 +342,8 @@ extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspac
     *count = uniq;
     if (!xa_out || !xb_out) return HINQS_OK;  // count only
     if (cap < uniq)
-      return fail(HINQS_ERR_ARG, "hinqs_classical_expansion: cap %lld below the %lld candidates",
-                  (long long)cap, (long long)uniq);
+      return fail(HINQS_ERR_ARG, "%s: cap %lld below the %lld candidates", who, (long long)cap,
+                  (long long)uniq);
     k_split_keys<<<grid, 256, 0, s>>>(keys, m_pad, pos, xa_out, xb_out);
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
@@ -319,4 +353,21 @@ extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspac
   dfree(keys, s);
   dfree(pos, s);
   return rc;
+}
+
+extern "C" int hinqs_classical_expansion(const hinqs_ham* H, const hinqs_subspace* B,
+                                         const double* c, int64_t n_top, uint64_t* xa_out,
+                                         uint64_t* xb_out, int64_t cap, int64_t* count,
+                                         void* stream) {
+  return expansion_impl(H, B, nullptr, c, n_top, xa_out, xb_out, cap, count, stream,
+                        "hinqs_classical_expansion");
+}
+
+extern "C" int hinqs_classical_expansion_list(const hinqs_ham* H, const hinqs_subspace* B,
+                                              const hinqs_detlist* L, const double* c_list,
+                                              int64_t n_top, uint64_t* xa_out, uint64_t* xb_out,
+                                              int64_t cap, int64_t* count, void* stream) {
+  if (!L) return fail(HINQS_ERR_ARG, "hinqs_classical_expansion_list: NULL list");
+  return expansion_impl(H, B, L, c_list, n_top, xa_out, xb_out, cap, count, stream,
+                        "hinqs_classical_expansion_list");
 }

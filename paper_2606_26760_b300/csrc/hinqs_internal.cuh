@@ -138,6 +138,21 @@ struct hinqs_links_s {
   int tune_stages = 0;  // tensor-core pipeline depth (1 or 2; 0 = deepest that fits)
 };
 
+// A basis list of determinants inside a product subspace (Step 3's H_B over the
+// list): entries sorted by product position I = i_a * N_b + i_b, distinct.
+//   pos[m]     product positions, ascending
+//   ia[m], ib[m]  string indices of each entry
+//   arow[N_a+1]   entries of alpha string a are [arow[a], arow[a+1]), ascending in ib
+struct hinqs_detlist_s {
+  int64_t m = 0, Na = 0, Nb = 0;
+  const uint64_t* sa = nullptr;  // borrowed from the subspace
+  const uint64_t* sb = nullptr;
+  int64_t* pos = nullptr;
+  int32_t* ia = nullptr;
+  int32_t* ib = nullptr;
+  int64_t* arow = nullptr;
+};
+
 namespace hinqs {
 
 // Kernel launchers shared between translation units.
@@ -148,6 +163,14 @@ int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_li
                  cudaStream_t s, int parts = kSameSpin | kOppositeSpin);
 int diag_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                 const hinqs_links_s* lb, double* hdiag, cudaStream_t s);
+// the same two operations on the determinants of a basis list (vectors of length m);
+// list precision: HINQS_PREC_FP64, or FP32 for every FP32 mode
+int sigma_list_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                      const hinqs_links_s* lb, const hinqs_detlist_s* L, const void* c,
+                      void* sigma, int precision, cudaStream_t s);
+int diag_list_launch(const hinqs_ham_s* H, const hinqs_links_s* la, const hinqs_links_s* lb,
+                     const hinqs_detlist_s* L, double* hdiag, cudaStream_t s);
+int check_list(const hinqs_subspace_s* B, const hinqs_detlist_s* L, const char* who);
 // opposite-spin sigma term on the tensor cores (FP32 vectors; split = 1 or 3)
 int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                        const hinqs_links_s* lb, const float* c, float* sig, int split,

@@ -14,9 +14,13 @@ this package); this module decides which call comes next.
              t >= 2: PT2 scores of the candidates, the top K appended, eviction
              above B_max (Eq. pt2_score)                     hinqs_pt2_score,
                                                              hinqs_basis_update
-    Step 3   Davidson on the product of the basis strings, warm-started from the
-             previous eigenvector carried over               hinqs_build_subspace,
+    Step 3   Davidson on H_B over the basis list itself (mode "list", as Step 3
+             states: [H_B]_ij = <x_i|H|x_j>), or on the product of the basis strings
+             (mode "product", the SQD form); warm-started from the previous
+             eigenvector carried over                        hinqs_build_subspace,
+                                                             hinqs_detlist_create,
                                                              hinqs_remap_vector,
+                                                             hinqs_davidson_list /
                                                              hinqs_davidson
     Step 4   teacher marginals and the loss inputs for the network
                                                              hinqs_spin_marginals,
@@ -33,9 +37,10 @@ import numpy as np
 import torch
 
 from . import (BASIS_APPEND, BASIS_COLD_START, BASIS_RESCORE, DAVIDSON_FP64, Hamiltonian,
-               basis_update, build_subspace, candidate_pool, classical_expansion, davidson,
-               determinant_diag, lookup_determinants, nqs_loss, pt2_score, remap_vector,
-               spin_marginals, string_links)
+               basis_update, build_subspace, candidate_pool, classical_expansion,
+               classical_expansion_list, davidson, davidson_list, detlist, detlist_gather,
+               detlist_scatter, determinant_diag, lookup_determinants, nqs_loss, pt2_score,
+               remap_vector, spin_marginals, string_links)
 
 
 @dataclass
@@ -56,7 +61,11 @@ class IterationRecord:
 class HiNqsLoop:
     """State of the outer iteration.  `ham` is a prepared Hamiltonian; k0, k and b_max
     are the cold-start budget K_0, the per-iteration budget K and the cap B_max of
-    Step 2; n_top is N_e of Step 1' (the paper uses 1000)."""
+    Step 2; n_top is N_e of Step 1' (the paper uses 1000).  mode "list" diagonalises
+    H_B over the basis list (Step 3; B_max then bounds the solve), "product" over the
+    product of the list's distinct strings (which contains the list).  `c` is always
+    the eigenvector in the product's indexing (zero outside the list in list mode);
+    `c_list` is the list eigenvector in list mode."""
 
     ham: Hamiltonian
     k0: int
@@ -69,8 +78,11 @@ class HiNqsLoop:
     davidson_opts: dict = field(default_factory=lambda: dict(precision=DAVIDSON_FP64,
                                                              tol_residual=1e-8,
                                                              tol_energy=1e-11, max_iter=400))
+    mode: str = "list"
     t: int = 0
     basis: tuple | None = None          # (x_alpha, x_beta, key) of the cumulative basis
+    lst: object = None                  # the basis list inside `sub` (list mode)
+    c_list: torch.Tensor | None = None  # eigenvector over the list entries (list mode)
     sub: object = None
     la: object = None
     lb: object = None
@@ -86,14 +98,18 @@ class HiNqsLoop:
         basis update, subspace solve.  Returns the IterationRecord."""
         ham = self.ham
         last = dict(t=self.t, samples=samples, basis_before=self.basis, sub_before=self.sub,
-                    c_before=self.c, energy_before=self.energy)
+                    c_before=self.c, c_list_before=self.c_list, energy_before=self.energy)
         if self.t == 0:
             ya, yb, dropped = candidate_pool(ham, samples)
             hxx = determinant_diag(ham, ya, yb)
             last.update(pool=(ya, yb), expansion=None, keys=hxx)
             self.basis = basis_update(BASIS_COLD_START, None, (ya, yb, hxx), self.k0)
         else:
-            xa_cl, xb_cl = classical_expansion(ham, self.sub, self.c, self.n_top)
+            if self.mode == "list":
+                xa_cl, xb_cl = classical_expansion_list(ham, self.sub, self.lst, self.c_list,
+                                                        self.n_top)
+            else:
+                xa_cl, xb_cl = classical_expansion(ham, self.sub, self.c, self.n_top)
             ya, yb, dropped = candidate_pool(ham, samples, (xa_cl, xb_cl),
                                              exclude=self.basis[:2])
             _, _, sc = pt2_score(ham, self.sub, self.c, self.energy, ya, yb)
@@ -115,8 +131,19 @@ class HiNqsLoop:
             g, kept = remap_vector(self.sub, self.c, sub)
             if kept > 0.0:
                 guess, warm = g, True
-        res = davidson(ham, sub, la, lb, guess=guess, **self.davidson_opts)
-        self.sub, self.la, self.lb, self.c, self.energy = sub, la, lb, res.c, res.energy
+        if self.mode == "list":
+            lst = detlist(sub, self.basis[0], self.basis[1])
+            if guess is not None:
+                guess = detlist_gather(lst, guess)
+                if float(torch.dot(guess, guess)) == 0.0:
+                    guess, warm = None, False
+            res = davidson_list(ham, sub, la, lb, lst, guess=guess, **self.davidson_opts)
+            self.lst, self.c_list = lst, res.c
+            c_prod = detlist_scatter(lst, res.c)
+        else:
+            res = davidson(ham, sub, la, lb, guess=guess, **self.davidson_opts)
+            c_prod = res.c
+        self.sub, self.la, self.lb, self.c, self.energy = sub, la, lb, c_prod, res.energy
         self.energies.append(res.energy)
         rec = IterationRecord(self.t, int(ya.numel()), int(dropped), int(self.basis[0].numel()),
                               sub.Na, sub.Nb, res.energy, res.residual, res.status, warm)
@@ -148,7 +175,7 @@ class HiNqsLoop:
     def save(self, path: str) -> None:
         """Write the loop state (basis list with keys, subspace strings, eigenvector,
         energies, iteration count, budgets) to `path` (numpy .npz)."""
-        st = dict(t=np.int64(self.t), k0=np.int64(self.k0), k=np.int64(self.k),
+        st = dict(mode=np.array(self.mode), t=np.int64(self.t), k0=np.int64(self.k0), k=np.int64(self.k),
                   b_max=np.int64(self.b_max), n_top=np.int64(self.n_top),
                   delta=np.float64(self.delta), patience=np.int64(self.patience),
                   max_iter=np.int64(self.max_iter),
@@ -178,6 +205,8 @@ class HiNqsLoop:
                   max_iter=int(z["max_iter"]))
         if davidson_opts is not None:
             kw["davidson_opts"] = davidson_opts
+        if "mode" in z:
+            kw["mode"] = str(z["mode"])
         loop = cls(ham, **kw)
         loop.t = int(z["t"])
         loop.energies = [float(x) for x in z["energies"]]
@@ -195,6 +224,9 @@ class HiNqsLoop:
                                           ham.n, ham.n_alpha, ham.n_beta)
                 loop.la, loop.lb = string_links(ham, loop.sub, 0), string_links(ham, loop.sub, 1)
                 loop.c = torch.from_numpy(z["c"]).to(dev)
+                if loop.mode == "list":
+                    loop.lst = detlist(loop.sub, loop.basis[0], loop.basis[1])
+                    loop.c_list = detlist_gather(loop.lst, loop.c)
             else:
                 loop.c = torch.from_numpy(z["c"])
         return loop

@@ -263,16 +263,27 @@ def test_nqs_loss_autograd_and_bad_index():
 # ------------------------------------------------------------- the whole loop
 
 
-def _oracle_chain_step(H, chain, t, samples, na, nb, k0, k, b_max, n_top):
-    """One outer iteration done by the oracle alone (Steps 1, 1', 2 and 3 on the
-    product of the basis strings), updating `chain` in place."""
+def _embed(sa, sb, xa, xb, c_list):
+    """A vector over the sorted list (xa, xb) placed in the product's indexing."""
+    c = np.zeros(len(sa) * len(sb))
+    c[oracle.lookup(sa, sb, xa, xb)] = c_list
+    return c
+
+
+def _oracle_chain_step(H, chain, t, samples, na, nb, k0, k, b_max, n_top, mode):
+    """One outer iteration done by the oracle alone (Steps 1, 1', 2 and 3 on the basis
+    list or on the product of its strings), updating `chain` in place."""
     samples = tuple(np.asarray(x, dtype=np.uint64) for x in samples)
     if t == 0:
         ya, yb, _ = oracle.candidate_pool([samples], (np.zeros(0), np.zeros(0)), na, nb)
         keys = oracle.determinant_diag(H, ya, yb)
         basis = oracle.basis_update(oracle.BASIS_COLD_START, ([], [], []), (ya, yb, keys), k0)
     else:
-        ea, eb = oracle.classical_expansion(H, chain["sa"], chain["sb"], chain["c"], n_top)
+        if mode == "list":
+            ea, eb = oracle.classical_expansion_list(H, chain["la"], chain["lb"], chain["c_list"],
+                                                     n_top)
+        else:
+            ea, eb = oracle.classical_expansion(H, chain["sa"], chain["sb"], chain["c"], n_top)
         b = chain["basis"]
         ya, yb, _ = oracle.candidate_pool([samples, (ea, eb)], (b[0], b[1]), na, nb)
         _, _, keys = oracle.pt2_scores(H, chain["sa"], chain["sb"], chain["c"], chain["E"], ya, yb)
@@ -283,11 +294,18 @@ def _oracle_chain_step(H, chain, t, samples, na, nb, k0, k, b_max, n_top):
         else:
             basis = oracle.basis_update(oracle.BASIS_APPEND, b, (ya, yb, keys), k, b_max)
     sa, sb = oracle.build_subspace(basis[0], basis[1], na, nb)
-    E, c = oracle.ground_state_dense(H, sa, sb)
+    if mode == "list":
+        la_, lb_ = oracle.sort_list(basis[0], basis[1])
+        E, c_list = oracle.ground_state_dense_list(H, la_, lb_)
+        c = _embed(sa, sb, la_, lb_, c_list)
+        chain.update(la=la_, lb=lb_, c_list=c_list)
+    else:
+        E, c = oracle.ground_state_dense(H, sa, sb)
     chain.update(basis=tuple(np.asarray(x) for x in basis), sa=sa, sb=sb, c=c, E=E)
 
 
-def test_outer_loop_stepwise_parity():
+@pytest.mark.parametrize("mode", ["list", "product"])
+def test_outer_loop_stepwise_parity(mode):
     """Five iterations of Steps 1-3 on n = 10, 2/2 (full product 45 x 45): each step
     of the library's loop is re-done by the oracle from the same inputs (the samples,
     the previous basis, eigenvector and energy) and must give the same candidate set,
@@ -296,7 +314,7 @@ def test_outer_loop_stepwise_parity():
     h, eri, e_nuc = synth.integrals(n, 6)
     ham = hq.Hamiltonian(h, eri, na, nb, e_nuc)
     H = oracle.Ham(h, eri, e_nuc, na, nb)
-    loop = HiNqsLoop(ham, k0=30, k=25, b_max=70, n_top=20)
+    loop = HiNqsLoop(ham, k0=30, k=25, b_max=70, n_top=20, mode=mode)
 
     def sampler(t):
         return (synth.hf_weighted_samples(n, na, 150, 500 + 2 * t),
@@ -307,10 +325,13 @@ def test_outer_loop_stepwise_parity():
     chain = dict(basis=None, sa=None, sb=None, c=None, E=None)
     for t in range(5):
         rec = loop.step(sampler(t))
-        _oracle_chain_step(H, chain, t, sampler(t), na, nb, k0=30, k=25, b_max=70, n_top=20)
+        _oracle_chain_step(H, chain, t, sampler(t), na, nb, k0=30, k=25, b_max=70, n_top=20,
+                           mode=mode)
         assert np.array_equal(chain["basis"][0], _np_u64(loop.basis[0]))
         assert np.array_equal(chain["basis"][1], _np_u64(loop.basis[1]))
-        assert np.allclose(chain["basis"][2], loop.basis[2].cpu().numpy(), rtol=1e-9, atol=1e-14)
+        # the chain's PT2 keys come from its own dense-eigh eigenvector, the library's from
+        # a Davidson eigenvector at a 1e-8 residual: they differ by about residual / gap
+        assert np.allclose(chain["basis"][2], loop.basis[2].cpu().numpy(), rtol=1e-6, atol=1e-14)
         assert abs(chain["E"] - rec.energy) < 1e-9
         L = loop.last
         samples = tuple(np.asarray(x, dtype=np.uint64) for x in L["samples"])
@@ -330,7 +351,12 @@ def test_outer_loop_stepwise_parity():
             c_p = L["c_before"].cpu().numpy()
             E_p = L["energy_before"]
             xa_cl, xb_cl = (_np_u64(x) for x in L["expansion"])
-            ea, eb = oracle.classical_expansion(H, sa_p, sb_p, c_p, 20)
+            if mode == "list":
+                lxa, lxb = oracle.sort_list(*(_np_u64(x) for x in L["basis_before"][:2]))
+                ea, eb = oracle.classical_expansion_list(H, lxa, lxb,
+                                                         L["c_list_before"].cpu().numpy(), 20)
+            else:
+                ea, eb = oracle.classical_expansion(H, sa_p, sb_p, c_p, 20)
             assert np.array_equal(xa_cl, ea) and np.array_equal(xb_cl, eb)
             bb = tuple(_np_u64(x) for x in L["basis_before"][:2])
             ra, rb, _ = oracle.candidate_pool([samples, (ea, eb)], bb, na, nb)
@@ -350,7 +376,12 @@ def test_outer_loop_stepwise_parity():
         assert np.array_equal(basis[0], ref_basis[0]) and np.array_equal(basis[1], ref_basis[1])
         assert np.array_equal(loop.basis[2].cpu().numpy(), ref_basis[2])
         sa, sb = oracle.build_subspace(basis[0], basis[1], na, nb)
-        E_ref, _ = oracle.ground_state_dense(H, sa, sb)
+        if mode == "list":
+            E_ref, _ = oracle.ground_state_dense_list(H, *oracle.sort_list(basis[0], basis[1]))
+            E_prod, _ = oracle.ground_state_dense(H, sa, sb)
+            assert rec.energy >= E_prod - 1e-9  # the list is a subset of the product
+        else:
+            E_ref, _ = oracle.ground_state_dense(H, sa, sb)
         assert abs(rec.energy - E_ref) < 1e-9, (t, rec.energy, E_ref)
         assert rec.n_basis <= (30 if t == 0 else 70 if t >= 2 else 25)
     # Step 4 on the final basis list, one minibatch of its positions
