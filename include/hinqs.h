@@ -159,8 +159,17 @@ int hinqs_links_destroy(hinqs_links* links);
 int hinqs_links_max_singles(const hinqs_links* links);
 /* the sigma tiles hinqs_autotune stored in these links (host outputs, each may be
  * NULL): rows per warp of the row products, alpha-single chunk width of the CUDA-core
- * opposite-spin kernel, tensor-core pipeline depth; 0 = built-in default */
+ * opposite-spin kernel, form of the tensor-core kernel (1, 2: pipeline depth of the
+ * persistent kernel; 3: the tile-stationary warp-specialised kernel of the BF16 mode,
+ * for n_orb <= 22, at most 64 singles and 64 gather slots per string; the persistent
+ * kernel otherwise); 0 = built-in default */
 int hinqs_links_tuning(const hinqs_links* links, int* rows_per_warp, int* chunk, int* stages);
+/* Not in the paper: store sigma tiles in the alpha links la and beta links lb without
+ * timing them (what hinqs_autotune stores after timing): rows_per_warp in {0, 2, 4, 8},
+ * chunk in {0, 8, 16, 32}, stages in 0..3 as above (0 = default).  Results do not depend
+ * on the choice beyond summation order.  Errors: HINQS_ERR_ARG. */
+int hinqs_links_set_tuning(hinqs_links* la, hinqs_links* lb, int rows_per_warp, int chunk,
+                           int stages);
 
 /* ------------------------------------------------------------- diagonal --
  * hdiag[I] = <I|H|I> (FP64, [N_a*N_b]): the H_xx of Step 2 (cold-start ranking)
@@ -201,8 +210,9 @@ int hinqs_sigma_opposite_spin(const hinqs_ham* ham, const hinqs_subspace* sub,
  * optional warm start from a previous eigenvector (Step 3 warm-starts from the
  * previous iteration).  Preconditioner t = r / (H_diag - theta) with
  * |H_diag - theta| floored at denom_floor (sign kept); classical Gram-Schmidt
- * applied twice; restart at max_subspace keeping the current and previous Ritz
- * vectors; projected eigenproblem, orthogonalisation, residual norms and the final
+ * applied twice; restart at max_subspace keeping restart_keep vectors (the current
+ * and previous Ritz vectors, then the next-lowest ones); projected eigenproblem,
+ * orthogonalisation, residual norms and the final
  * energy in FP64 on the device.  Converged when ||H x - theta x||_2 <= tol_residual
  * (x of unit norm) and |theta - theta_prev| <= tol_energy.
  * HINQS_DAVIDSON_MIXED runs the bulk of the sigma products in FP32 and refines
@@ -223,6 +233,10 @@ typedef struct hinqs_davidson_opts {
   int* trace_kind;      /* host [trace_cap] or NULL: 0 = FP64 iterate, 1 = FP32 inner iterate */
   int inner_precision;  /* mixed: sigma precision of the inner products: HINQS_PREC_FP32,
                            HINQS_PREC_FP32_BF16AB or HINQS_PREC_FP32_BF16X3AB */
+  int restart_keep;     /* vectors kept at a restart (0 = default).  FP64: the current
+                           Ritz vector, the previous one and the next-lowest Ritz vectors,
+                           this many in all (1 .. max_subspace - 1); mixed: the FP64 anchor
+                           and the next-lowest FP32 Ritz vectors (1 .. max_subspace - 2) */
 } hinqs_davidson_opts;
 
 typedef struct hinqs_davidson_info {
@@ -249,7 +263,8 @@ int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings, 
 int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings,
                                   const hinqs_davidson_opts* opts, size_t* bytes);
 
-/* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace, FP32 inner). */
+/* Fill opts with defaults (FP64, 200, 16, 1e-8, 1e-10, 1e-4, 1e-3, no trace, FP32 inner,
+ * restart_keep 0). */
 void hinqs_davidson_default_opts(hinqs_davidson_opts* opts);
 
 /*   guess   device FP64 [N] or NULL (then e_k at argmin H_diag, lowest index on ties)

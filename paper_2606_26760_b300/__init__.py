@@ -64,7 +64,7 @@ class _Opts(ctypes.Structure):
                 ("trace_resid", ctypes.POINTER(ctypes.c_double)),
                 ("trace_time", ctypes.POINTER(ctypes.c_double)),
                 ("trace_kind", ctypes.POINTER(ctypes.c_int)),
-                ("inner_precision", ctypes.c_int)]
+                ("inner_precision", ctypes.c_int), ("restart_keep", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -90,7 +90,7 @@ EXPORTED = [
     "hinqs_probe_fma_rate", "hinqs_detlist_create", "hinqs_detlist_size",
     "hinqs_detlist_positions", "hinqs_detlist_destroy", "hinqs_detlist_scatter",
     "hinqs_detlist_gather", "hinqs_diag_list", "hinqs_sigma_list", "hinqs_davidson_list",
-    "hinqs_classical_expansion_list",
+    "hinqs_classical_expansion_list", "hinqs_links_set_tuning",
 ]
 
 
@@ -162,6 +162,7 @@ def load_library(path: str = LIB_PATH):
                                         ctypes.POINTER(ctypes.c_double), P, ctypes.POINTER(_Info),
                                         P]
     lib.hinqs_classical_expansion_list.argtypes = [P, P, P, P, I64, P, P, I64, PI64, P]
+    lib.hinqs_links_set_tuning.argtypes = [P, P, I, I, I]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -306,6 +307,12 @@ def string_links(ham: Hamiltonian, sub: Subspace, spin: int) -> Links:
     return Links(out, spin, sub)
 
 
+def set_tuning(la, lb, rows_per_warp: int = 0, chunk: int = 0, stages: int = 0):
+    """hinqs_links_set_tuning: pin the sigma tiles of (la, lb) without timing them."""
+    _check(_lib.hinqs_links_set_tuning(la.handle, lb.handle, int(rows_per_warp), int(chunk),
+                                       int(stages)))
+
+
 def diag(ham, sub, la, lb, out=None):
     out = torch.empty(sub.N, dtype=torch.float64, device=_dev()) if out is None else out
     _check(_lib.hinqs_diag(ham.handle, sub.handle, la.handle, lb.handle, _ptr(out), _stream()))
@@ -353,20 +360,22 @@ class DavidsonResult:
 
 
 def _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor, inner_tol,
-               inner_precision):
+               inner_precision, restart_keep=0):
     opts = _Opts()
     _lib.hinqs_davidson_default_opts(ctypes.byref(opts))
     opts.precision, opts.max_iter, opts.max_subspace = precision, max_iter, max_subspace
     opts.tol_residual, opts.tol_energy, opts.denom_floor = tol_residual, tol_energy, denom_floor
     opts.inner_tol = inner_tol
     opts.inner_precision = inner_precision
+    opts.restart_keep = restart_keep
     return opts
 
 
 def _davidson_call(fn, args, n, guess, precision, max_iter, max_subspace, tol_residual,
-                   tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out):
+                   tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out,
+                   restart_keep=0):
     opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
-                      inner_tol, inner_precision)
+                      inner_tol, inner_precision, restart_keep)
     bufs = None
     if trace_cap > 0:
         bufs = ((ctypes.c_double * trace_cap)(), (ctypes.c_double * trace_cap)(),
@@ -398,24 +407,25 @@ def _davidson_call(fn, args, n, guess, precision, max_iter, max_subspace, tol_re
 def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
              max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
              denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
-             inner_precision: int = PREC_FP32, out=None) -> DavidsonResult:
+             inner_precision: int = PREC_FP32, out=None, restart_keep: int = 0) -> DavidsonResult:
     """hinqs_davidson: lowest eigenpair of H on the product subspace (Step 3)."""
     return _davidson_call(_lib.hinqs_davidson, (ham.handle, sub.handle, la.handle, lb.handle),
                           sub.N, guess, precision, max_iter, max_subspace, tol_residual,
-                          tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out)
+                          tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out,
+                          restart_keep)
 
 
 def davidson_list(ham, sub, la, lb, lst, guess=None, precision: int = DAVIDSON_FP64,
                   max_iter: int = 200, max_subspace: int = 16, tol_residual: float = 1e-8,
                   tol_energy: float = 1e-10, denom_floor: float = 1e-4, inner_tol: float = 1e-3,
                   trace_cap: int = 0, inner_precision: int = PREC_FP32,
-                  out=None) -> DavidsonResult:
+                  out=None, restart_keep: int = 0) -> DavidsonResult:
     """hinqs_davidson_list: lowest eigenpair of H_B over the basis list `lst` (Step 3);
     the eigenvector is indexed by the list's entries."""
     return _davidson_call(_lib.hinqs_davidson_list,
                           (ham.handle, sub.handle, la.handle, lb.handle, lst.handle), lst.m,
                           guess, precision, max_iter, max_subspace, tol_residual, tol_energy,
-                          denom_floor, inner_tol, trace_cap, inner_precision, out)
+                          denom_floor, inner_tol, trace_cap, inner_precision, out, restart_keep)
 
 
 class DetList:
@@ -500,13 +510,14 @@ def sigma_workspace_size(n_alpha_strings: int, n_beta_strings: int,
 
 
 def davidson_workspace_size(n_alpha_strings: int, n_beta_strings: int,
-                            precision: int = DAVIDSON_FP64, max_subspace: int = 16) -> int:
+                            precision: int = DAVIDSON_FP64, max_subspace: int = 16,
+                            restart_keep: int = 0) -> int:
     """hinqs_davidson_workspace_size: device bytes one davidson() call with these
     options requests at its peak (besides the caller's vectors and the handles)."""
     lib = load_library()
     opts = _Opts()
     lib.hinqs_davidson_default_opts(ctypes.byref(opts))
-    opts.precision, opts.max_subspace = precision, max_subspace
+    opts.precision, opts.max_subspace, opts.restart_keep = precision, max_subspace, restart_keep
     b = ctypes.c_size_t()
     _check(lib.hinqs_davidson_workspace_size(int(n_alpha_strings), int(n_beta_strings),
                                              ctypes.byref(opts), ctypes.byref(b)))

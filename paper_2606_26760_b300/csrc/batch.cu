@@ -3,7 +3,8 @@
 // Autotuner: for one (Hamiltonian, subspace, links) it times the sigma product for
 // each candidate tile configuration -- rows per warp of the same-spin row products
 // and, for the opposite-spin term, the alpha-single chunk width of the CUDA-core
-// kernel or the pipeline depth of the tensor-core kernel --
+// kernel or the form of the tensor-core kernel (pipeline depth 1 or 2, or the
+// tile-stationary warp-specialised kernel) --
 // and stores the fastest in the links handles.  Results are cached per problem
 // class (orbitals, electrons, precision, and the string counts in quarter-octave
 // buckets), so geometries of a scan with similar sizes are tuned once.
@@ -84,7 +85,10 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
     if (cuda_core_ab) {
       for (int ch : {16, 32}) cands.push_back({r, ch, 0});
     } else {
-      for (int st : {1, 2}) cands.push_back({r, 0, st});
+      // tensor-core pipeline depth 1 or 2 of the persistent kernel, or 3: the
+      // tile-stationary warp-specialised kernel (BF16 operands only)
+      for (int st : {1, 2, 3})
+        if (st != 3 || precision == HINQS_PREC_FP32_BF16AB) cands.push_back({r, 0, st});
     }
   }
   cudaEvent_t e0, e1;

@@ -140,6 +140,7 @@ extern "C" int hinqs_ham_destroy(hinqs_ham* H) {
   dfree(H->eri32, s);
   dfree(H->tc_bhi, s);
   dfree(H->tc_blo, s);
+  dfree(H->tc_bfold, s);
   delete H;
   return HINQS_OK;
 }

@@ -33,6 +33,8 @@ constexpr int kRitzStride = kMaxSub + 2;  // (theta, y[kMaxSub], pad) per Ritz p
 constexpr int kRedGrid = 2 * kNumSMs;   // blocks per vector of the dot products
 constexpr int kResGrid = 8 * kNumSMs;   // blocks of the residual pass (one vector pair)
 constexpr int kRedThreads = 256;
+constexpr int kDefaultKeepFp64 = 4;   // vectors kept at a restart (restart_keep = 0)
+constexpr int kDefaultKeepMixed = 4;
 
 // ---------------------------------------------------------------- kernels --
 
@@ -742,17 +744,32 @@ __global__ void k_init_pencil(double* G, double* S, const double* theta) {
   }
 }
 
+// vectors kept at a restart: FP64 solver (current + previous + next Ritz vectors) and
+// mixed solver (anchor + FP32 Ritz vectors); restart_keep = 0 takes the defaults
+static int restart_keep_fp64(const hinqs_davidson_opts& o) {
+  const int k = o.restart_keep > 0 ? o.restart_keep : kDefaultKeepFp64;
+  return std::max(1, std::min(k, o.max_subspace - 1));
+}
+static int restart_keep_mixed(const hinqs_davidson_opts& o) {
+  const int mmax = std::max(4, o.max_subspace);
+  const int k = o.restart_keep > 0 ? o.restart_keep : kDefaultKeepMixed;
+  return std::max(1, std::min(k, mmax - 2));
+}
+
 static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
                          double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
   const int mmax = o.max_subspace;
+  const int kr = restart_keep_fp64(o);  // vectors kept at a restart
   const int64_t N = c.N;
   double *V = nullptr, *W = nullptr, *t = nullptr, *X = nullptr, *WX = nullptr, *G = nullptr,
-         *ritz = nullptr, *col = nullptr, *ycoef = nullptr;
+         *ritz = nullptr, *col = nullptr, *ycoef = nullptr, *all = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
-      (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, 2 * N, c.s)) || (rc = dalloc(&WX, 2 * N, c.s)) ||
-      (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&col, kMaxSub + 2, c.s)) || (rc = dalloc(&ycoef, 2 * (kMaxSub + 2), c.s))) {
+      (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, (size_t)kr * N, c.s)) ||
+      (rc = dalloc(&WX, (size_t)kr * N, c.s)) || (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) ||
+      (rc = dalloc(&ritz, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s)) ||
+      (rc = dalloc(&ycoef, (size_t)kr * (kMaxSub + 2), c.s)) ||
+      (rc = dalloc(&all, kMaxSub * kRitzStride, c.s))) {
   }
   auto cleanup = [&]() {
     dfree(V, c.s);
@@ -764,6 +781,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
     dfree(ritz, c.s);
     dfree(col, c.s);
     dfree(ycoef, c.s);
+    dfree(all, c.s);
   };
   if (rc) {
     cleanup();
@@ -815,46 +833,77 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       theta_prev = theta;
       have_prev = true;
       if (m == mmax) {
-        // Thick restart with the current Ritz vector x = V y and the previous one,
-        // orthonormalised against y in the m-dimensional coefficient space (the
-        // two are nearly parallel near convergence; doing it on the N-vectors
-        // would lose orthogonality).
-        double y[kMaxSub], yp[kMaxSub];
-        for (int i = 0; i < m; ++i) {
-          y[i] = hr[1 + i];
-          yp[i] = (i < m - 1) ? hr_prev[1 + i] : 0.0;
+        // Thick restart: keep the current Ritz vector, the previous one (the search
+        // direction of the last step) and the next-lowest Ritz vectors, kr in all,
+        // orthonormalised in the m-dimensional coefficient space (near convergence the
+        // current and previous vectors are nearly parallel; doing this on the N-vectors
+        // would lose orthogonality).  The kept pencil is Y G Y^T, formed on the host.
+        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr, all);
+        HQ_LAUNCH_CHECK();
+        std::vector<double> hall((size_t)kMaxSub * kRitzStride), hG((size_t)kMaxSub * kMaxSub);
+        HQ_CUDA(cudaMemcpyAsync(hall.data(), all, hall.size() * sizeof(double),
+                                cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaMemcpyAsync(hG.data(), G, hG.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                                c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));
+        std::vector<std::vector<double>> Y;
+        auto add = [&](std::vector<double> v) {
+          for (int pass = 0; pass < 2; ++pass)
+            for (const auto& u : Y) {
+              double d = 0.0;
+              for (int i = 0; i < m; ++i) d += u[i] * v[i];
+              for (int i = 0; i < m; ++i) v[i] -= d * u[i];
+            }
+          double nn = 0.0;
+          for (int i = 0; i < m; ++i) nn += v[i] * v[i];
+          if (nn > 1e-24) {
+            for (int i = 0; i < m; ++i) v[i] /= std::sqrt(nn);
+            Y.push_back(v);
+          }
+        };
+        std::vector<double> v(m);
+        for (int i = 0; i < m; ++i) v[i] = hr[1 + i];
+        add(v);
+        if (kr >= 2) {
+          for (int i = 0; i < m; ++i) v[i] = (i < m - 1) ? hr_prev[1 + i] : 0.0;
+          add(v);
         }
-        for (int pass = 0; pass < 2; ++pass) {
-          double d = 0.0;
-          for (int i = 0; i < m; ++i) d += y[i] * yp[i];
-          for (int i = 0; i < m; ++i) yp[i] -= d * y[i];
+        for (int j = 1; j < m && (int)Y.size() < kr; ++j) {
+          for (int i = 0; i < m; ++i) v[i] = hall[(size_t)j * kRitzStride + 1 + i];
+          add(v);
         }
-        double nn = 0.0;
-        for (int i = 0; i < m; ++i) nn += yp[i] * yp[i];
-        const bool two = nn > 1e-24;
-        double hc[2 * (kMaxSub + 2)] = {0};
-        for (int i = 0; i < m; ++i) {
-          hc[i] = y[i];
-          hc[kMaxSub + 2 + i] = two ? yp[i] / std::sqrt(nn) : 0.0;
+        const int mnew = (int)Y.size();
+        std::vector<double> hc((size_t)mnew * (kMaxSub + 2), 0.0);
+        for (int j = 0; j < mnew; ++j)
+          for (int i = 0; i < m; ++i) hc[(size_t)j * (kMaxSub + 2) + i] = Y[j][i];
+        std::vector<double> hGn((size_t)kMaxSub * kMaxSub, 0.0);  // Y G Y^T
+        for (int a2 = 0; a2 < mnew; ++a2)
+          for (int b2 = 0; b2 < mnew; ++b2) {
+            double acc = 0.0;
+            for (int i = 0; i < m; ++i) {
+              double gi = 0.0;
+              for (int j = 0; j < m; ++j)
+                gi += 0.5 * (hG[(size_t)i * kMaxSub + j] + hG[(size_t)j * kMaxSub + i]) * Y[b2][j];
+              acc += Y[a2][i] * gi;
+            }
+            hGn[(size_t)a2 * kMaxSub + b2] = acc;
+          }
+        HQ_CUDA(cudaMemcpyAsync(ycoef, hc.data(), hc.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, c.s));
+        for (int j = 0; j < mnew; ++j) {
+          HQ_TRY(lincomb<double>(c, X + (size_t)j * N, V, N, m, ycoef + (size_t)j * (kMaxSub + 2), 0));
+          HQ_TRY(lincomb<double>(c, WX + (size_t)j * N, W, N, m, ycoef + (size_t)j * (kMaxSub + 2), 0));
         }
-        HQ_CUDA(cudaMemcpyAsync(ycoef, hc, sizeof(hc), cudaMemcpyHostToDevice, c.s));
-        double* yc1 = ycoef + kMaxSub + 2;
-        HQ_TRY(lincomb<double>(c, X, V, N, m, ycoef, 0));
-        HQ_TRY(lincomb<double>(c, WX, W, N, m, ycoef, 0));
-        if (two) {
-          HQ_TRY(lincomb<double>(c, X + N, V, N, m, yc1, 0));
-          HQ_TRY(lincomb<double>(c, WX + N, W, N, m, yc1, 0));
-        }
-        const int mnew = two ? 2 : 1;
-        HQ_CUDA(cudaMemcpyAsync(V, X, mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-        HQ_CUDA(cudaMemcpyAsync(W, WX, mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
-        HQ_CUDA(cudaStreamSynchronize(c.s));  // hc lives on the host stack
+        HQ_CUDA(cudaMemcpyAsync(V, X, (size_t)mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaMemcpyAsync(W, WX, (size_t)mnew * N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
+        HQ_CUDA(cudaMemcpyAsync(G, hGn.data(), hGn.size() * sizeof(double), cudaMemcpyHostToDevice,
+                                c.s));
+        // the current Ritz vector is now V[0]: its coefficients in the new basis
+        for (int i = 1; i <= kMaxSub; ++i) hr[i] = (i == 1) ? 1.0 : 0.0;
+        HQ_CUDA(cudaMemcpyAsync(ritz, hr, (kMaxSub + 1) * sizeof(double), cudaMemcpyHostToDevice,
+                                c.s));
+        HQ_CUDA(cudaStreamSynchronize(c.s));  // the host arrays above go out of scope
         m = mnew;
-        k_init_pencil<<<1, 256, 0, c.s>>>(G, nullptr, nullptr);
-        for (int j = 0; j < m; ++j) {
-          HQ_TRY(dots<double, double>(c, V, N, j + 1, W + (size_t)j * N, col));
-          k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
-        }
         // the residual t of the current Ritz vector (now V[0]) is still valid
         info.n_restarts++;
       }
@@ -900,7 +949,7 @@ constexpr int kSoftRestarts = 3;
 static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
                           double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
   const int mmax = std::max(4, o.max_subspace);  // pencil order 1 + m <= mmax
-  const int keep = std::min(4, mmax - 2);         // Ritz vectors kept at a restart (with x)
+  const int keep = restart_keep_mixed(o);         // Ritz vectors kept at a restart (with x)
   const int64_t N = c.N;
   double *x = nullptr, *sx = nullptr, *t = nullptr, *xn = nullptr, *sxn = nullptr, *G = nullptr,
          *S = nullptr, *G1 = nullptr, *ritz = nullptr, *ritz1 = nullptr, *all = nullptr,
@@ -1103,6 +1152,7 @@ extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
   o->trace_time = nullptr;
   o->trace_kind = nullptr;
   o->inner_precision = HINQS_PREC_FP32;
+  o->restart_keep = 0;
 }
 
 // Device bytes one hinqs_davidson call requests from the stream-ordered pool at its
@@ -1114,12 +1164,12 @@ static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) 
   size_t b = (2 * (size_t)kRedGrid * (kMaxSub + 1) + 4 * (kMaxSub + 2)) * d +
              (kMaxSub + 1) * sizeof(unsigned int) + (size_t)N * d;
   if (o.precision == HINQS_DAVIDSON_FP64) {
-    const size_t mmax = (size_t)o.max_subspace;
-    b += (2 * mmax + 5) * (size_t)N * d;                        // V, W, t, X[2], WX[2]
-    b += ((size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2)) * d;   // G, ritz, col, ycoef
+    const size_t mmax = (size_t)o.max_subspace, kr = (size_t)restart_keep_fp64(o);
+    b += (2 * mmax + 1 + 2 * kr) * (size_t)N * d;               // V, W, t, X[kr], WX[kr]
+    b += ((size_t)kMaxSub * kMaxSub + (2 + kr) * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;
   } else {
     const size_t mmax = (size_t)std::max(4, o.max_subspace);
-    const size_t keep = std::min<size_t>(4, mmax - 2);
+    const size_t keep = (size_t)restart_keep_mixed(o);
     b += 6 * (size_t)N * d;                                     // x, sx, t, xn, sxn, tmp
     b += (2 * mmax + 2 * keep + 1) * (size_t)N * f;             // V, W, U, WU, t32
     b += (3 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;

@@ -72,6 +72,10 @@ struct hinqs_ham_s {
   uint16_t* tc_bhi = nullptr;
   uint16_t* tc_blo = nullptr;
   int tc_KB = 0;
+  // the whole folded table as the stationary B operand of the tile-stationary kernel
+  // (n <= 22): rows = folded pairs pq, columns = folded pairs rs, Kp = tc_KB * 8 of
+  // each, stored as the shared-memory image of a K-major core-matrix tile
+  uint16_t* tc_bfold = nullptr;
 };
 
 constexpr int kTcMaxOrb = 32;

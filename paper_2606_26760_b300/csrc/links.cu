@@ -391,6 +391,20 @@ extern "C" int hinqs_links_tuning(const hinqs_links* L, int* rows_per_warp, int*
   return HINQS_OK;
 }
 
+extern "C" int hinqs_links_set_tuning(hinqs_links* la, hinqs_links* lb, int rows_per_warp, int chunk,
+                                      int stages) {
+  if (!la || !lb || la->spin != 0 || lb->spin != 1)
+    return fail(HINQS_ERR_ARG, "hinqs_links_set_tuning: la must be alpha links and lb beta links");
+  if ((rows_per_warp != 0 && rows_per_warp != 2 && rows_per_warp != 4 && rows_per_warp != 8) ||
+      (chunk != 0 && chunk != 8 && chunk != 16 && chunk != 32) || stages < 0 || stages > 3)
+    return fail(HINQS_ERR_ARG, "hinqs_links_set_tuning: rows_per_warp in {0,2,4,8}, chunk in "
+                               "{0,8,16,32}, stages in 0..3");
+  la->tune_rows = lb->tune_rows = rows_per_warp;
+  la->tune_ch = chunk;
+  la->tune_stages = stages;
+  return HINQS_OK;
+}
+
 extern "C" int hinqs_links_destroy(hinqs_links* L) {
   if (!L) return HINQS_OK;
   cudaDeviceSynchronize();

@@ -423,6 +423,535 @@ static bool fits(const Args& a) {
 
 }  // namespace tc
 
+// ---------------------------------------------------------------------------
+// Tile-stationary, warp-specialised form of the same term (BF16 operands, n <= 22,
+// at most 64 alpha singles per string, at most 64 gather slots per beta string).
+//
+// A CTA works through items (beta tile t, alpha string Ja), tile by tile, so that a
+// beta tile's gather slots and the non-zero pattern of D stay fixed while the alpha
+// strings change: each gather thread keeps its slots in registers for the whole tile,
+// and a D stage is cleared only when it meets a new tile (every item of a tile writes
+// the same positions).  The whole folded table (pq|rs) stays in shared memory for the
+// CTA's life; per item, the rows of Ja's singles (signs folded into the BF16 sign
+// bits) are copied from it into a B stage of N = 16..64 rows, so that the accumulator
+// holds exactly the singles' columns and the epilogue reads them 16 columns at a time.
+// Warp roles, with mbarrier handoffs and no block-wide barrier inside the loop:
+//   warp 0      copies the row C(Ja, :) into a shared stage (one cp.async.bulk when
+//               the rows are 16-byte aligned, else plain loads)
+//   warp 1      one thread issues the tcgen05.mma chain of each item (K = Kp in
+//               steps of 16) into one of two tensor-memory accumulators
+//   warps 2-9   gather: two threads per beta string (its even and odd slots) write D
+//               into one of two shared stages; the warps also copy the item's B rows
+//   warps 10-13 epilogue: tcgen05.ld of the accumulator (lane = beta string) and
+//               reductions into sigma (a warp covers 32 consecutive beta strings of one
+//               target row)
+// Items of CTA b: the alpha strings Ja = b, b + G, b + 2G, ... (G CTAs) for every
+// beta tile, tiles visited from tile b mod T on; each role walks them with counters
+// (no integer division in the loop).  Every wait is bounded and suspends the waiting
+// thread; when one gives up the CTA raises the error flag, the other roles stop at
+// their next wait or item, and the copies and MMAs in flight are waited for (bounded)
+// before tensor memory is freed.
+namespace tc2 {
+
+using tc::fence_after;
+using tc::fence_before;
+using tc::fence_proxy_async;
+using tc::make_desc;
+using tc::make_idesc;
+using tc::mma_bf16;
+using tc::mma_commit;
+using tc::smem_u32;
+
+constexpr int kWarps = 14;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kTileM = 128;
+constexpr int kMaxKp = 256;        // folded K of the stationary table (n <= 22)
+constexpr int kMaxSingles = 64;    // N of one item's MMA (alpha singles of one string)
+constexpr int kMaxSlots = 64;      // gather slots (beta singles + occupied) per beta string
+constexpr int kThreadsPerRow = 2;  // gather threads of one beta string
+constexpr int kMySlots = kMaxSlots / kThreadsPerRow;
+constexpr int kTmemCols = 128;     // two accumulators of kMaxSingles columns
+constexpr int kGatherWarps = 8;
+constexpr int kGather = 32 * kGatherWarps;
+constexpr int kEpiWarps = 4;
+constexpr int kSlotJbBits = 19;    // packed slot: Jb | kpart << 19 | sign << 31
+// A waiting thread polls with a growing sleep between polls (16 to 256 ns) and gives
+// up after kWaitNs of wall time (the global timer): a legitimate wait here lasts
+// microseconds, also on a GPU shared with other work.
+constexpr uint32_t kSuspendNs = 20000;
+constexpr uint64_t kWaitNs = 2000000000ull;
+
+struct Args {
+  int64_t Na, Nb, T;
+  int n, KB, Kp;
+  const int64_t* a_srow;
+  const int2* a_slink;
+  const int2* b_tcell;  // pair-major {Jb, kpart | sign << 31}
+  const int* b_cnt;
+  const uint4* Bimg;    // shared-memory image of the folded table, Kp * KB chunks
+  const float* C;
+  float* sig;
+  int bulk_row;         // rows of C may be fetched with one cp.async.bulk
+  uint32_t off_Bs, off_D, off_C, off_F, off_bar, crow_stride;
+};
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(b)), "r"(count));
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(b))
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(
+                   smem_u32(b)),
+               "r"(bytes)
+               : "memory");
+}
+// bulk copy of `bytes` (multiple of 16, both addresses 16-byte aligned) from global
+// memory into shared memory, completing on the mbarrier's transaction count
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* b) {
+  asm volatile(
+      "cp.async.bulk.shared::cta.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(b))
+      : "memory");
+}
+__device__ __forceinline__ void tmem_ld16_nowait(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_wait_ld() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool wait_phase(uint64_t* b, uint32_t parity) {
+  const uint32_t a = smem_u32(b);
+  const uint64_t t0 = global_ns();
+  uint32_t sleep_ns = 16;
+  for (uint32_t i = 1;; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity), "r"(kSuspendNs)
+        : "memory");
+    if (done) return true;
+    // back off: a spinning warp would take issue slots from the working warps of its
+    // sub-partition (the copy and MMA warps wait most of the time)
+    __nanosleep(sleep_ns);
+    if (sleep_ns < 256u) sleep_ns <<= 1;
+    if ((i & 15u) == 0 && global_ns() - t0 > kWaitNs) return false;
+  }
+}
+// every lane waits (each wait is bounded, so every lane gets here) and the warp agrees
+// on the outcome, so that the warp-collective instructions after it stay uniform
+__device__ __forceinline__ bool warp_wait(uint64_t* b, uint32_t parity) {
+  return __all_sync(0xffffffffu, wait_phase(b, parity) ? 1 : 0) != 0;
+}
+__device__ __forceinline__ bool warp_aborted(volatile int* f, int lane) {
+  const int v = lane == 0 ? *f : 0;
+  return __shfl_sync(0xffffffffu, v, 0) != 0;
+}
+
+// The item sequence of one CTA, walked with counters: item k is (tile, Ja) with
+// Ja = b + (k mod nJ) G and tile = (b mod T + k div nJ) mod T.
+struct Cursor {
+  int64_t k = 0, end = 0, j = 0, nJ = 0, b = 0, G = 1, T = 1;
+  int64_t tile = 0, Ja = 0;
+  int64_t e0 = 0;  // first single of Ja
+  int ns = 0;      // singles of Ja
+  __device__ void init(int64_t b_, int64_t G_, int64_t Na, int64_t T_) {
+    b = b_;
+    G = G_;
+    T = T_;
+    nJ = b < Na ? (Na - b + G - 1) / G : 0;
+    end = T * nJ;
+    k = 0;
+    j = 0;
+    tile = b % T;
+    Ja = b;
+  }
+  __device__ void advance() {
+    ++k;
+    Ja += G;
+    if (++j == nJ) {
+      j = 0;
+      Ja = b;
+      if (++tile == T) tile = 0;
+    }
+  }
+  // move to the next item (this one included) whose alpha string has singles
+  __device__ bool next(const Args& A) {
+    while (k < end) {
+      e0 = __ldg(A.a_srow + Ja);
+      ns = (int)(__ldg(A.a_srow + Ja + 1) - e0);
+      if (ns > 0) return true;
+      advance();
+    }
+    return false;
+  }
+};
+
+__device__ __forceinline__ int mma_n(int ns) { return ns <= 16 ? 16 : (ns + 15) & ~15; }
+
+__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc2(Args A) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int KB = A.KB, Kp = A.Kp, n = A.n;
+  const uint32_t d_bytes = (uint32_t)kTileM * KB * 16;
+  const uint32_t bs_bytes = (uint32_t)kMaxSingles * KB * 16;
+  unsigned char* sB = smem;                // the folded table
+  unsigned char* sBs = smem + A.off_Bs;    // [2] the item's B operand
+  unsigned char* sD = smem + A.off_D;      // [2] D
+  unsigned char* sC = smem + A.off_C;      // [2] C(Ja, :)
+  uint16_t* sF = reinterpret_cast<uint16_t*>(smem + A.off_F);  // [n*n] folded pair
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + A.off_bar);
+  uint64_t* crow_full = bar;       // [2] copy of C(Ja, :) landed
+  uint64_t* crow_empty = bar + 2;  // [2] gather done reading it (one arrival per warp)
+  uint64_t* d_full = bar + 4;      // [2] D and B stages written (one arrival per warp)
+  uint64_t* mma_done = bar + 6;    // [2] MMA chain of the stage finished (commit)
+  uint64_t* acc_empty = bar + 8;   // [2] epilogue done with the accumulator (per warp)
+  uint64_t* cleared = bar + 10;    // [2] D stage cleared for a new tile (per gather warp)
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 12);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(bar + 12) + 1;
+
+  if (tid == 0) {
+    for (int s = 0; s < 2; ++s) {
+      mbar_init(crow_full + s, 1);
+      mbar_init(crow_empty + s, kGatherWarps);
+      mbar_init(d_full + s, kGatherWarps);
+      mbar_init(mma_done + s, 1);
+      mbar_init(acc_empty + s, kEpiWarps);
+      mbar_init(cleared + s, kGatherWarps);
+    }
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  for (int i = tid; i < Kp * KB; i += kThreads)  // the stationary table
+    reinterpret_cast<uint4*>(sB)[i] = __ldg(A.Bimg + i);
+  for (int i = tid; i < (int)(2 * d_bytes / 16); i += kThreads)  // D stages start at zero
+    reinterpret_cast<uint4*>(sD)[i] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < n * n; i += kThreads) {
+    const int p = i / n, q = i - p * n;
+    sF[i] = (uint16_t)(p >= q ? p * (p + 1) / 2 + q : q * (q + 1) / 2 + p);
+  }
+  fence_proxy_async();
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  auto give_up = [&]() {
+    ok = false;
+    *abort_flag = 1;
+    atomicExch(&g_tc_error, 1);
+  };
+  Cursor cur;
+  cur.init(blockIdx.x, gridDim.x, A.Na, A.T);
+
+  if (warp == 0) {
+    // --------------------------------------------- C rows into shared stages
+    int q = 0;
+    for (; ok && !warp_aborted(abort_flag, lane) && cur.next(A); cur.advance(), ++q) {
+      const int s = q & 1;
+      float* dst = reinterpret_cast<float*>(sC + (size_t)s * A.crow_stride);
+      if (q >= 2 && !warp_wait(crow_empty + s, ((q - 2) >> 1) & 1)) {
+        if (lane == 0) give_up();
+        break;
+      }
+      const float* src = A.C + cur.Ja * A.Nb;
+      if (A.bulk_row) {
+        if (lane == 0) {
+          mbar_expect_tx(crow_full + s, (uint32_t)(A.Nb * 4));
+          bulk_g2s(dst, src, (uint32_t)(A.Nb * 4), crow_full + s);
+        }
+      } else {
+        for (int64_t j = lane; j < A.Nb; j += 32) dst[j] = __ldg(src + j);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(crow_full + s);
+      }
+      __syncwarp();
+    }
+    // copies still in flight land before the CTA can exit
+    if (A.bulk_row && lane == 0) {
+      for (int k = (q >= 2 ? q - 2 : 0); k < q; ++k) wait_phase(crow_full + (k & 1), (k >> 1) & 1);
+    }
+  } else if (warp == 1) {
+    // --------------------------------------------------------------- MMA issue
+    if (lane == 0) {
+      const uint32_t sbo = (uint32_t)KB * 128;
+      int q = 0;
+      for (; ok && !*abort_flag && cur.next(A); cur.advance(), ++q) {
+        const int s = q & 1;
+        if (!wait_phase(d_full + s, (q >> 1) & 1) ||
+            (q >= 2 && !wait_phase(acc_empty + s, ((q - 2) >> 1) & 1))) {
+          give_up();
+          break;
+        }
+        fence_after();
+        const uint32_t idesc = make_idesc(kTileM, mma_n(cur.ns));
+        const uint32_t a0 = smem_u32(sD + (size_t)s * d_bytes);
+        const uint32_t b0 = smem_u32(sBs + (size_t)s * bs_bytes);
+        const uint32_t d = tmem + (uint32_t)(s * kMaxSingles);
+        for (int kk = 0; kk < KB / 2; ++kk) {
+          const uint32_t off = (uint32_t)kk * 256;  // 16 K elements = two core matrices
+          mma_bf16(d, make_desc(a0 + off, 128, sbo), make_desc(b0 + off, 128, sbo), idesc,
+                   kk > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_u32(mma_done + s));
+      }
+      // MMAs in flight finish before tensor memory is freed
+      for (int k = (q >= 2 ? q - 2 : 0); k < q; ++k) wait_phase(mma_done + (k & 1), (k >> 1) & 1);
+    }
+  } else if (warp < 2 + kGatherWarps) {
+    // ------------------------------------------------------------------ gather
+    const int g = tid - 64, gw = g >> 5, m = g & (kTileM - 1), h = g >> 7;  // row m, slots h, h+2..
+    unsigned char* rowD = sD + (m >> 3) * (KB * 128) + (m & 7) * 16;
+    int64_t tile = -1, stage_tile[2] = {-1, -1};
+    int clears[2] = {0, 0};
+    uint32_t slot[kMySlots];
+    int mine = 0;  // this thread's slots of the row (slots h, h + 2, ...)
+    int q = 0;
+    for (; ok && !warp_aborted(abort_flag, lane) && cur.next(A); cur.advance(), ++q) {
+      const int s = q & 1;
+      const int64_t t = cur.tile;
+      const int ns = cur.ns;
+      // the item's singles (lane u holds singles u and u + 32), read early
+      const int sp0 = lane < ns ? __ldg(&A.a_slink[cur.e0 + lane].y) : 1;
+      const int sp1 = lane + 32 < ns ? __ldg(&A.a_slink[cur.e0 + lane + 32].y) : 1;
+      if (t != tile) {  // this beta string's slots of the new tile
+        tile = t;
+        const int64_t Ib = t * kTileM + m;
+        const int all = Ib < A.Nb ? __ldg(A.b_cnt + Ib) : 0;
+        mine = all > h ? (all - h + kThreadsPerRow - 1) / kThreadsPerRow : 0;
+#pragma unroll
+        for (int i = 0; i < kMySlots; ++i) {
+          if (i >= mine) break;
+          const int j = kThreadsPerRow * i + h;
+          const int2 r = __ldg(A.b_tcell + ((((int64_t)(j >> 1) * A.Nb + Ib) << 1) + (j & 1)));
+          slot[i] = (uint32_t)r.x | (((uint32_t)r.y & 0xFFFu) << kSlotJbBits) |
+                    ((uint32_t)r.y & 0x80000000u);
+        }
+      }
+      if (q >= 2 && !warp_wait(mma_done + s, ((q - 2) >> 1) & 1)) {
+        if (lane == 0) give_up();
+        break;
+      }
+      if (stage_tile[s] != t) {
+        // a new tile in this stage: the gather warps clear the stage together (the two
+        // threads of a row write the same 16-byte chunks, so every clear must land
+        // before any write)
+        for (int i = g; i < (int)(d_bytes / 16); i += kGather)
+          reinterpret_cast<uint4*>(sD + (size_t)s * d_bytes)[i] = make_uint4(0, 0, 0, 0);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(cleared + s);
+        if (!warp_wait(cleared + s, clears[s] & 1)) {
+          if (lane == 0) give_up();
+          break;
+        }
+        ++clears[s];
+        stage_tile[s] = t;
+      }
+      // B stage s: the (pq|.) rows of Ja's singles with the sign folded in, copied from
+      // the stationary table; warp gw takes singles gw, gw + 8, ..., lane = 16-byte chunk
+      // (rows ns .. N-1 of the MMA are left as they are: the epilogue never reads them)
+      unsigned char* bst = sBs + (size_t)s * bs_bytes;
+      for (int a0 = gw; a0 < ns; a0 += 4 * kGatherWarps) {  // four singles' loads in flight
+        uint4 v[4];
+        int sp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = a0 + u * kGatherWarps;
+          sp[u] = __shfl_sync(0xffffffffu, a < 32 ? sp0 : sp1, a & 31);
+          v[u] = make_uint4(0, 0, 0, 0);
+          if (a < ns && lane < KB) {
+            const int r = sF[(sp[u] > 0 ? sp[u] : -sp[u]) - 1];
+            v[u] = *reinterpret_cast<const uint4*>(sB + (r >> 3) * (KB * 128) + lane * 128 + (r & 7) * 16);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int a = a0 + u * kGatherWarps;
+          if (a < ns && lane < KB) {
+            uint4 w = v[u];
+            if (sp[u] < 0) w.x ^= 0x80008000u, w.y ^= 0x80008000u, w.z ^= 0x80008000u, w.w ^= 0x80008000u;
+            *reinterpret_cast<uint4*>(bst + (a >> 3) * (KB * 128) + lane * 128 + (a & 7) * 16) = w;
+          }
+        }
+      }
+      if (!warp_wait(crow_full + s, (q >> 1) & 1)) {
+        if (lane == 0) give_up();
+        break;
+      }
+      const float* row = reinterpret_cast<const float*>(sC + (size_t)s * A.crow_stride);
+      unsigned char* dst = rowD + (size_t)s * d_bytes;
+      constexpr uint32_t kJb = (1u << kSlotJbBits) - 1u;
+      {  // every load of the item in flight before the stores: one shared-memory latency
+        float v[kMySlots];
+#pragma unroll
+        for (int i = 0; i < kMySlots; ++i) v[i] = i < mine ? row[slot[i] & kJb] : 0.0f;
+#pragma unroll
+        for (int i = 0; i < kMySlots; ++i)
+          if (i < mine)
+            *reinterpret_cast<__nv_bfloat16*>(dst + ((slot[i] >> kSlotJbBits) & 0xFFFu)) =
+                __float2bfloat16_rn(__uint_as_float(__float_as_uint(v[i]) ^ (slot[i] & 0x80000000u)));
+      }
+      // each thread's shared-memory writes are made visible to the tensor cores, the
+      // warp synchronises, and one lane arrives for the warp
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(crow_empty + s);
+        mbar_arrive(d_full + s);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue
+    const int quarter = warp & 3;  // the 32 tensor-memory lanes this warp may read
+    const uint32_t lane_base = (uint32_t)(32 * quarter) << 16;
+    const unsigned full = 0xffffffffu;
+    int q = 0;
+    for (; ok && !warp_aborted(abort_flag, lane) && cur.next(A); cur.advance(), ++q) {
+      const int s = q & 1;
+      const int ns = cur.ns;
+      // target rows of the item's singles (lane u holds singles u and u + 32), read
+      // before the wait so that their latency overlaps the MMA
+      const int tgt0 = lane < ns ? __ldg(&A.a_slink[cur.e0 + lane].x) : 0;
+      const int tgt1 = lane + 32 < ns ? __ldg(&A.a_slink[cur.e0 + lane + 32].x) : 0;
+      if (!warp_wait(mma_done + s, (q >> 1) & 1)) {
+        if (lane == 0) give_up();
+        break;
+      }
+      fence_after();
+      const int64_t ib = cur.tile * kTileM + 32 * quarter + lane;
+      const uint32_t acc = tmem + lane_base + (uint32_t)(s * kMaxSingles);
+      float* srow = A.sig + ib;
+      const bool live = ib < A.Nb;
+      // 32 accumulator columns at a time; the accumulator is released after the last read
+#pragma unroll
+      for (int h0 = 0; h0 < kMaxSingles; h0 += 32) {
+        if (h0 >= ns) break;
+        float v[32];
+        tmem_ld16_nowait(acc + (uint32_t)h0, v);
+        if (h0 + 16 < ns) tmem_ld16_nowait(acc + (uint32_t)(h0 + 16), v + 16);
+        tmem_wait_ld();
+        if (h0 + 32 >= ns) {
+          fence_before();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(acc_empty + s);  // the next MMA may start
+        }
+        const int tg = h0 < 32 ? tgt0 : tgt1;
+#pragma unroll
+        for (int u = 0; u < 32; ++u) {
+          const int J = __shfl_sync(full, tg, u);
+          if (h0 + u < ns && live) atomicAdd(srow + (int64_t)J * A.Nb, v[u]);
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
+  }
+}
+
+// Shared-memory image of the folded table: element (row kf_pq, column kf_rs) at the
+// K-major core-matrix offset (row / 8) * KB * 128 + (col / 8) * 128 + (row % 8) * 16
+// + (col % 8) * 2; rows and columns at or above K are zero.
+__global__ void k_bfold(const float* __restrict__ eri32, int n, int K, int KB,
+                        __nv_bfloat16* __restrict__ img) {
+  const int Kp = KB * 8, n2 = n * n;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)Kp * Kp;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(i / Kp), k = (int)(i % Kp);
+    float v = 0.0f;
+    if (r < K && k < K) {
+      int p = 0, x = 0;
+      while ((p + 1) * (p + 2) / 2 <= r) ++p;
+      while ((x + 1) * (x + 2) / 2 <= k) ++x;
+      const int q = r - p * (p + 1) / 2, y = k - x * (x + 1) / 2;
+      v = eri32[(int64_t)(p * n + q) * n2 + x * n + y];
+    }
+    const int64_t off = ((int64_t)(r >> 3) * (KB * 128) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2) / 2;
+    img[off] = __float2bfloat16_rn(v);
+  }
+}
+
+static size_t align128(size_t x) { return (x + 127) & ~(size_t)127; }
+
+// kTcNoFit when the problem is outside this kernel's range (the caller falls back)
+static int launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                  const hinqs_links_s* lb, const float* c, float* sig, cudaStream_t s) {
+  if (!H->tc_bfold || B->Nb >= (int64_t(1) << kSlotJbBits) || B->Na == 0 || B->Nb == 0 ||
+      la->max_srow > kMaxSingles || lb->ell_width > kMaxSlots)
+    return kTcNoFit;
+  Args a;
+  a.Na = B->Na;
+  a.Nb = B->Nb;
+  a.T = ceil_div(B->Nb, kTileM);
+  a.n = H->n;
+  a.KB = H->tc_KB;
+  a.Kp = H->tc_KB * 8;
+  a.a_srow = la->srow_ptr;
+  a.a_slink = la->slink;
+  a.b_tcell = lb->tcell;
+  a.b_cnt = lb->scount;
+  a.Bimg = reinterpret_cast<const uint4*>(H->tc_bfold);
+  a.C = c;
+  a.sig = sig;
+  a.bulk_row = (B->Nb % 4 == 0) && ((reinterpret_cast<uintptr_t>(c) & 15u) == 0);
+  const size_t b_bytes = (size_t)a.Kp * a.KB * 16;
+  const size_t bs_bytes = (size_t)kMaxSingles * a.KB * 16;
+  const size_t d_bytes = (size_t)kTileM * a.KB * 16;
+  a.crow_stride = (uint32_t)align128((size_t)B->Nb * 4);
+  a.off_Bs = (uint32_t)align128(b_bytes);
+  a.off_D = a.off_Bs + (uint32_t)(2 * bs_bytes);
+  a.off_C = a.off_D + (uint32_t)(2 * d_bytes);
+  a.off_F = a.off_C + 2 * a.crow_stride;
+  a.off_bar = (uint32_t)align128(a.off_F + (size_t)H->n * H->n * 2);
+  const size_t bytes = a.off_bar + 12 * 8 + 8;
+  if (bytes > (size_t)smem_optin_limit()) return kTcNoFit;
+  auto kern = k_sigma_ab_tc2;
+  HQ_TRY(allow_max_smem(kern));
+  // one CTA per SM (the persistent grid covers the SMs once): the request is padded
+  // above half of an SM's shared memory
+  const size_t req = std::max(bytes, (size_t)120 * 1024);
+  int dev = 0, sms = kNumSMs;
+  HQ_CUDA(cudaGetDevice(&dev));
+  HQ_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int grid = (int)std::min<int64_t>(B->Na, sms);
+  kern<<<grid, kThreads, req, s>>>(a);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+}  // namespace tc2
+
 int tc_tables_build(hinqs_ham_s* H, cudaStream_t s) {
   const int n = H->n;
   if (n > kTcMaxOrb) return HINQS_OK;  // the tensor-core path is not offered
@@ -435,6 +964,13 @@ int tc_tables_build(hinqs_ham_s* H, cudaStream_t s) {
       H->eri32, n, K, H->tc_KB, reinterpret_cast<__nv_bfloat16*>(H->tc_bhi),
       reinterpret_cast<__nv_bfloat16*>(H->tc_blo));
   HQ_LAUNCH_CHECK();
+  const int Kp = H->tc_KB * 8;
+  if (Kp <= tc2::kMaxKp) {
+    HQ_TRY(dalloc(&H->tc_bfold, (int64_t)Kp * Kp, s));
+    tc2::k_bfold<<<(unsigned)std::min<int64_t>(ceil_div((int64_t)Kp * Kp, 256), 1024), 256, 0, s>>>(
+        H->eri32, n, K, H->tc_KB, reinterpret_cast<__nv_bfloat16*>(H->tc_bfold));
+    HQ_LAUNCH_CHECK();
+  }
   return HINQS_OK;
 }
 
@@ -442,6 +978,10 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
                        const hinqs_links_s* lb, const float* c, float* sig, int split,
                        cudaStream_t s) {
   if (!H->tc_bhi) return kTcNoFit;  // n_orb above kTcMaxOrb
+  if (split == 1 && la->tune_stages == 3) {  // the tile-stationary form, when chosen
+    const int r2 = tc2::launch(H, B, la, lb, c, sig, s);
+    if (r2 != kTcNoFit) return r2;
+  }
   tc::Args a;
   a.Na = B->Na;
   a.Nb = B->Nb;
