@@ -358,10 +358,11 @@ def cpu_baseline_detail(oracle, synth, np, H_o, sa_o, sb_o, c_h):
 def run_bond_scan(args):
     """24 geometries of the synthetic 16-orbital (5,5) bond scan with 500..4000
     strings per spin: one step = Hamiltonians, subspaces and links of every
-    geometry + the batched mixed solve (autotuned tiles, BF16 tensor-core inner
-    sigma, FP64 refinement) to a 1e-6 residual.  Compared, untimed by the step
-    loop but on the same GPU: the same solves one after another on one stream,
-    and the plain FP64 Davidson one after another."""
+    geometry + the batched mixed solve in lockstep (one batched launch per sigma
+    stage per round, BF16 tensor-core inner sigma, FP64 refinement) to a 1e-6
+    residual.  Compared, untimed by the step loop but on the same GPU: the worker-
+    stream batch, the same solves one after another on one stream, and the plain
+    FP64 Davidson one after another."""
     import numpy as np
     import torch
 
@@ -417,7 +418,7 @@ def run_bond_scan(args):
 
     def step(inputs):
         probs = prepare(inputs)
-        return probs, hq.davidson_batch(probs, autotune=True, n_streams=4, **mixed)
+        return probs, hq.davidson_batch(probs, autotune=True, n_streams=0, **mixed)
 
     for _ in range(args.warmup):
         step(resident)
@@ -482,7 +483,8 @@ def run_bond_scan(args):
         torch.cuda.synchronize()
         return ev0.elapsed_time(ev1) / 1e3, out
 
-    t_batch, rb = solve_time(lambda: hq.davidson_batch(probs, n_streams=4, **mixed))
+    t_batch, rb = solve_time(lambda: hq.davidson_batch(probs, n_streams=0, **mixed))
+    t_workers, _ = solve_time(lambda: hq.davidson_batch(probs, n_streams=4, **mixed))
     t_seq_mixed, rs = solve_time(lambda: [hq.davidson(*p, **mixed) for p in probs])
     t_seq_fp64, rf = solve_time(lambda: [hq.davidson(*p, precision=hq.DAVIDSON_FP64,
                                                      tol_residual=1e-6, tol_energy=1e-8,
@@ -507,12 +509,12 @@ def run_bond_scan(args):
                                f"500..4000 strings per spin, {Ntot} determinants in all",
                    "step": "24 x (ham+subspace+links) + batched mixed Davidson to 1e-6 residual",
                    "l2": "256 MB buffer written between timed steps",
-                   "parallelism": "4 worker streams, longest geometry first"},
+                   "parallelism": "lockstep: one batched launch per sigma stage per round"},
         "e2e": {"value": Ntot / (sum(e2e) / len(e2e)), "unit": "dets/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": None if launches is None else launches * args.steps,
-        "solve_s": {"batch_mixed_bf16": t_batch, "sequential_mixed_bf16": t_seq_mixed,
-                    "sequential_fp64": t_seq_fp64,
+        "solve_s": {"batch_mixed_bf16": t_batch, "worker_streams_mixed_bf16": t_workers,
+                    "sequential_mixed_bf16": t_seq_mixed, "sequential_fp64": t_seq_fp64,
                     "speedup_batch_vs_fp64": t_seq_fp64 / t_batch,
                     "speedup_batch_vs_sequential_mixed": t_seq_mixed / t_batch},
         "energy": {"max_abs_diff_batch_mixed_vs_fp64_Ha": err,

@@ -205,6 +205,19 @@ int hinqs_sigma_opposite_spin(const hinqs_ham* ham, const hinqs_subspace* sub,
                               const hinqs_links* la, const hinqs_links* lb, const void* c,
                               void* sigma, int precision, void* stream);
 
+/* The sigma products of n independent problems in one call (not in the paper: the
+ * products of a batched solve, hinqs_davidson_batch): sigmas[g] = H_g cs[g] for
+ * problem g = (hams[g], subs[g], las[g], lbs[g]), all in `precision`.  The FP32 modes
+ * run each same-spin stage as one launch over every problem's rows and the BF16
+ * tensor-core term as one persistent kernel over a device work queue of (problem,
+ * alpha string) items (problems of different n_orb, or whose tensor-core tiles do not
+ * fit, run one by one); FP64 products and the FP32 CUDA-core opposite-spin term run
+ * problem by problem.  Same results as n hinqs_sigma calls up to summation order.
+ * Errors as hinqs_sigma, with the problem's index in the message. */
+int hinqs_sigma_batch(int n, const hinqs_ham* const* hams, const hinqs_subspace* const* subs,
+                      const hinqs_links* const* las, const hinqs_links* const* lbs,
+                      const void* const* cs, void* const* sigmas, int precision, void* stream);
+
 /* ------------------------------------------------------------- Davidson --
  * Lowest eigenpair of H_B by Davidson's method (Step 3, Davidson 1975), with an
  * optional warm start from a previous eigenvector (Step 3 warm-starts from the
@@ -350,12 +363,21 @@ int hinqs_autotune(const hinqs_ham* ham, const hinqs_subspace* sub, hinqs_links*
 /* ------------------------------------------------------- batched solve --
  * Not in the paper (see hinqs_autotune): lowest eigenpairs of n_geom independent
  * problems, e.g. the geometries of a bond scan, each exactly as hinqs_davidson
- * would solve it with `opts` (NULL = defaults).  The problems are ordered by an
- * estimate of their sigma cost, longest first, and taken from a shared queue by
- * n_streams host workers (<= 0: 4), each running its solves on a CUDA stream of
- * its own, so solves of different geometries overlap on the GPU.  The worker
- * streams start after the work already queued on `stream`, and `stream` waits for
- * all of them before later work; the call itself returns when every solve is done.
+ * would solve it with `opts` (NULL = defaults).
+ *   n_streams <= 0 (lockstep): every geometry's solve runs on a host thread and a CUDA
+ *             stream of its own and hands its sigma products to a shared batch: when
+ *             every unconverged solve has handed in one, the round runs as one launch
+ *             per sigma stage for all of them -- the same-spin row products and
+ *             transposes over a flattened grid of every geometry's rows, the BF16
+ *             tensor-core opposite-spin term as one persistent kernel taking
+ *             (geometry, alpha string) items from a device work queue (FP64 products
+ *             and the FP32 CUDA-core opposite-spin term run geometry by geometry) --
+ *             and a converged solve leaves the rounds;
+ *   n_streams > 0: that many host workers take the problems, longest first by an
+ *             estimate of their sigma cost, each running its solves one after another
+ *             on a stream of its own.
+ * The streams start after the work already queued on `stream`, and `stream` waits
+ * for all of them before later work; the call itself returns when every solve is done.
  *   hams, subs, las, lbs  arrays of n_geom handles (la/lb: alpha/beta links of subs[g])
  *   guesses   NULL or array of n_geom device FP64 pointers (each may be NULL)
  *   autotune  nonzero: run hinqs_autotune on each problem first, for the sigma

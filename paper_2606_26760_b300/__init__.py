@@ -90,7 +90,7 @@ EXPORTED = [
     "hinqs_probe_fma_rate", "hinqs_detlist_create", "hinqs_detlist_size",
     "hinqs_detlist_positions", "hinqs_detlist_destroy", "hinqs_detlist_scatter",
     "hinqs_detlist_gather", "hinqs_diag_list", "hinqs_sigma_list", "hinqs_davidson_list",
-    "hinqs_classical_expansion_list", "hinqs_links_set_tuning",
+    "hinqs_classical_expansion_list", "hinqs_links_set_tuning", "hinqs_sigma_batch",
 ]
 
 
@@ -163,6 +163,7 @@ def load_library(path: str = LIB_PATH):
                                         P]
     lib.hinqs_classical_expansion_list.argtypes = [P, P, P, P, I64, P, P, I64, PI64, P]
     lib.hinqs_links_set_tuning.argtypes = [P, P, I, I, I]
+    lib.hinqs_sigma_batch.argtypes = [I, P, P, P, P, P, P, I, P]
     lib.hinqs_energy_backward.argtypes = [I, D, P, P, P, P, P]
     lib.hinqs_spin_marginals.argtypes = [P, P, P, P, P, P]
     lib.hinqs_spin_marginals_noalloc.argtypes = [P, P, P, P, P, P]
@@ -333,6 +334,28 @@ def sigma(ham, sub, la, lb, c, out=None, precision: int | None = None):
     _check(_lib.hinqs_sigma(ham.handle, sub.handle, la.handle, lb.handle, _ptr(c), _ptr(out),
                             precision, _stream()))
     return out
+
+
+def sigma_batch(problems, cs, precision: int | None = None, outs=None):
+    """hinqs_sigma_batch: [H_g c_g] for problems [(ham, sub, la, lb), ...] in one call."""
+    G = len(problems)
+    if G == 0:
+        return []
+    if precision is None:
+        precision = PREC_FP64 if cs[0].dtype == torch.float64 else PREC_FP32
+    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    for c, p in zip(cs, problems):
+        if c.dtype != dt or not c.is_cuda or not c.is_contiguous() or c.numel() != p[1].N:
+            raise ValueError(f"each c must be a contiguous CUDA {dt} tensor of its subspace size")
+    outs = [torch.empty_like(c) for c in cs] if outs is None else outs
+    VP = ctypes.c_void_p * G
+    _check(_lib.hinqs_sigma_batch(G, VP(*[p[0].handle for p in problems]),
+                                  VP(*[p[1].handle for p in problems]),
+                                  VP(*[p[2].handle for p in problems]),
+                                  VP(*[p[3].handle for p in problems]),
+                                  VP(*[c.data_ptr() for c in cs]), VP(*[o.data_ptr() for o in outs]),
+                                  precision, _stream()))
+    return outs
 
 
 def sigma_part(ham, sub, la, lb, c, out, part: str, precision: int | None = None):
@@ -567,10 +590,11 @@ def autotune(ham, sub, la, lb, precision: int = PREC_FP32) -> float:
 def davidson_batch(problems, guesses=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
                    max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
                    denom_floor: float = 1e-4, inner_tol: float = 1e-3,
-                   inner_precision: int = PREC_FP32, n_streams: int = 4, autotune: bool = False,
+                   inner_precision: int = PREC_FP32, n_streams: int = 0, autotune: bool = False,
                    outs=None):
     """hinqs_davidson_batch over `problems` = [(ham, sub, la, lb), ...]: every
-    geometry solved as davidson() would, several at a time on their own streams.
+    geometry solved as davidson() would; n_streams <= 0 runs them in lockstep with one
+    batched launch per sigma stage per round, n_streams > 0 on that many worker streams.
     Returns a list of DavidsonResult (no trace), in the order of `problems`."""
     G = len(problems)
     if G == 0:

@@ -10,12 +10,19 @@
 // buckets), so geometries of a scan with similar sizes are tuned once.
 //
 // Batched solve: the geometries of a scan are independent eigenproblems of uneven
-// size.  They are ordered by estimated cost (longest first) and handed out from a
-// shared counter to worker threads, each driving the single-geometry Davidson on a
-// stream of its own, so several solves -- each a chain of dependent launches with a
-// host decision per iteration -- run on the GPU at the same time.
+// size.  In the lockstep form (the default) every geometry's Davidson runs on a host
+// thread and a stream of its own, and hands each sigma product to a shared batcher:
+// when every solve still running has handed in its product, the round runs as one
+// batched launch per sigma stage over all of them -- for the tensor-core term a
+// persistent kernel taking (geometry, alpha string) items from a device work queue --
+// and each solve continues when its product is done.  A solve that has converged
+// leaves the rounds.  The vector operations of the solves stay on their own streams
+// and overlap.  In the worker form, the geometries are ordered by estimated cost
+// (longest first) and handed out to n_streams worker threads, each driving the
+// single-geometry Davidson on a stream of its own.
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
 #include <cmath>
 #include <map>
 #include <mutex>
@@ -132,6 +139,57 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
   return HINQS_OK;
 }
 
+// Rounds of sigma products.  Each running solve hands in one product per round
+// (sigma) or leaves (leave); the thread whose hand-in completes a round launches it on
+// the batch stream, after the ready events of every product's stream, and every
+// product's stream then waits for the round's done event.
+struct SigmaBatcher {
+  std::mutex mu;
+  std::condition_variable cv;
+  int active = 0;
+  uint64_t round = 0;
+  int round_rc = HINQS_OK;
+  std::vector<SigmaReq> reqs;
+  std::vector<cudaStream_t> streams;
+  cudaStream_t bs = nullptr;
+  cudaEvent_t done = nullptr;
+
+  // with mu held
+  void flush() {
+    int rc = HINQS_OK;
+    const int n = (int)reqs.size();
+    if (n > 0) {
+      rc = sigma_batch_launch(reqs.data(), n, bs);
+      cudaError_t e = cudaEventRecord(done, bs);
+      for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(streams[i], done, 0);
+      if (rc >= 0 && e != cudaSuccess) rc = cuda_fail(e, "sigma batch round", __FILE__, __LINE__);
+    }
+    reqs.clear();
+    streams.clear();
+    round_rc = rc;
+    ++round;
+    cv.notify_all();
+  }
+};
+
+int batcher_sigma(SigmaBatcher* b, const SigmaReq& r, cudaStream_t s, cudaEvent_t ready) {
+  HQ_CUDA(cudaEventRecord(ready, s));
+  std::unique_lock<std::mutex> lk(b->mu);
+  HQ_CUDA(cudaStreamWaitEvent(b->bs, ready, 0));  // the round starts after this x is ready
+  b->reqs.push_back(r);
+  b->streams.push_back(s);
+  const uint64_t my = b->round;
+  if ((int)b->reqs.size() >= b->active) b->flush();
+  else b->cv.wait(lk, [&] { return b->round != my; });
+  return b->round_rc;
+}
+
+static void batcher_leave(SigmaBatcher* b) {
+  std::lock_guard<std::mutex> lk(b->mu);
+  --b->active;
+  if (b->active > 0 && (int)b->reqs.size() >= b->active) b->flush();
+}
+
 }  // namespace hinqs
 
 using namespace hinqs;
@@ -169,6 +227,67 @@ extern "C" int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
   if (autotune) {
     const int p = o.precision == HINQS_DAVIDSON_MIXED ? o.inner_precision : HINQS_PREC_FP64;
     for (int g = 0; g < n_geom; ++g) HQ_TRY(autotune_impl(hams[g], subs[g], las[g], lbs[g], p, nullptr, s));
+  }
+  if (n_streams <= 0) {
+    // lockstep: one thread and stream per geometry, sigma products batched per round
+    cudaEvent_t start;
+    HQ_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
+    HQ_CUDA(cudaEventRecord(start, s));
+    SigmaBatcher bat;
+    bat.active = n_geom;
+    HQ_CUDA(cudaStreamCreateWithFlags(&bat.bs, cudaStreamNonBlocking));
+    HQ_CUDA(cudaEventCreateWithFlags(&bat.done, cudaEventDisableTiming));
+    HQ_CUDA(cudaStreamWaitEvent(bat.bs, start, 0));
+    std::vector<cudaStream_t> gs(n_geom);
+    std::vector<cudaEvent_t> ready(n_geom);
+    for (int g = 0; g < n_geom; ++g) {
+      HQ_CUDA(cudaStreamCreateWithFlags(&gs[g], cudaStreamNonBlocking));
+      HQ_CUDA(cudaEventCreateWithFlags(&ready[g], cudaEventDisableTiming));
+      HQ_CUDA(cudaStreamWaitEvent(gs[g], start, 0));
+    }
+    std::vector<int> status(n_geom, HINQS_OK);
+    std::vector<std::string> msg(n_geom);
+    std::vector<hinqs_davidson_info> inf(n_geom);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::vector<std::thread> threads;
+    for (int g = 0; g < n_geom; ++g)
+      threads.emplace_back([&, g]() {
+        cudaSetDevice(dev);
+        double e = 0.0;
+        status[g] = davidson_run(hams[g], subs[g], las[g], lbs[g], nullptr,
+                                 guesses ? guesses[g] : nullptr, &o,
+                                 &e, c_outs[g], &inf[g], (void*)gs[g], "hinqs_davidson_batch", &bat,
+                                 ready[g]);
+        energies[g] = e;
+        if (status[g] < 0) msg[g] = hinqs_last_error_message();
+        batcher_leave(&bat);
+      });
+    for (auto& t : threads) t.join();
+    for (int g = 0; g < n_geom; ++g) {
+      cudaEvent_t done;
+      cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+      cudaEventRecord(done, gs[g]);
+      cudaStreamWaitEvent(s, done, 0);
+      cudaEventDestroy(done);
+      cudaStreamDestroy(gs[g]);
+      cudaEventDestroy(ready[g]);
+    }
+    cudaStreamSynchronize(bat.bs);
+    cudaStreamDestroy(bat.bs);
+    cudaEventDestroy(bat.done);
+    cudaEventDestroy(start);
+    int rc = HINQS_OK;
+    for (int g = 0; g < n_geom; ++g) {
+      if (infos) infos[g] = inf[g];
+      if (status[g] < 0 && rc >= 0) {
+        rc = status[g];
+        set_error("hinqs_davidson_batch: geometry %d: %s", g, msg[g].c_str());
+      } else if (status[g] > 0 && rc == HINQS_OK) {
+        rc = status[g];
+      }
+    }
+    return rc;
   }
   // longest first: cost ~ N * (links per alpha string + links per beta string + singles product)
   std::vector<std::pair<double, int>> order;

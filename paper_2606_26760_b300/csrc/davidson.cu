@@ -609,6 +609,8 @@ struct Ctx {
   int64_t N;
   int grid;
   const hinqs_detlist_s* L = nullptr;  // basis list (vectors over its entries) or NULL
+  SigmaBatcher* batcher = nullptr;     // lockstep batch this solve belongs to, or NULL
+  cudaEvent_t ready = nullptr;         // this solve's event for the batcher
   double* partial = nullptr;  // [2 * (kMaxSub+1) * kRedGrid] >= kResGrid
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
   float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
@@ -618,6 +620,8 @@ struct Ctx {
 // y = H x on the product subspace, or P H P x on the basis list when the context has one
 static int apply_sigma(Ctx& c, const void* x, void* y, int precision) {
   if (c.L) return sigma_list_launch(c.H, c.B, c.la, c.lb, c.L, x, y, precision, c.s);
+  if (c.batcher)
+    return batcher_sigma(c.batcher, SigmaReq{c.H, c.B, c.la, c.lb, x, y, precision}, c.s, c.ready);
   return sigma_launch(c.H, c.B, c.la, c.lb, x, y, precision, c.s);
 }
 
@@ -1193,10 +1197,11 @@ extern "C" int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_
   return HINQS_OK;
 }
 
-static int davidson_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
-                          const hinqs_links* lb, const hinqs_detlist* L, const double* guess,
-                          const hinqs_davidson_opts* opts, double* energy, double* c_out,
-                          hinqs_davidson_info* info_out, void* stream, const char* who) {
+int hinqs::davidson_run(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_links* la,
+                        const hinqs_links* lb, const hinqs_detlist* L, const double* guess,
+                        const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                        hinqs_davidson_info* info_out, void* stream, const char* who,
+                        SigmaBatcher* batcher, cudaEvent_t ready) {
   HQ_TRY(check_triplet(H, B, la, lb, who));
   if (L) {
     HQ_TRY(check_list(B, L, who));
@@ -1223,6 +1228,10 @@ static int davidson_entry(const hinqs_ham* H, const hinqs_subspace* B, const hin
   tr.t0 = std::chrono::steady_clock::now();
   Ctx c{H, B, la, lb, (cudaStream_t)stream, L ? L->m : B->Na * B->Nb, 0};
   c.L = L;
+  if (!L) {
+    c.batcher = batcher;
+    c.ready = ready;
+  }
   c.grid = (int)std::min<int64_t>(ceil_div(c.N, 256), 8 * kNumSMs);
   double* D = nullptr;
   int rc = HINQS_OK;
@@ -1262,8 +1271,8 @@ extern "C" int hinqs_davidson(const hinqs_ham* H, const hinqs_subspace* B, const
                               const hinqs_links* lb, const double* guess,
                               const hinqs_davidson_opts* opts, double* energy, double* c_out,
                               hinqs_davidson_info* info_out, void* stream) {
-  return davidson_entry(H, B, la, lb, nullptr, guess, opts, energy, c_out, info_out, stream,
-                        "hinqs_davidson");
+  return davidson_run(H, B, la, lb, nullptr, guess, opts, energy, c_out, info_out, stream,
+                      "hinqs_davidson", nullptr, nullptr);
 }
 
 extern "C" int hinqs_davidson_list(const hinqs_ham* H, const hinqs_subspace* B,
@@ -1271,6 +1280,6 @@ extern "C" int hinqs_davidson_list(const hinqs_ham* H, const hinqs_subspace* B,
                                    const hinqs_detlist* L, const double* guess,
                                    const hinqs_davidson_opts* opts, double* energy, double* c_out,
                                    hinqs_davidson_info* info_out, void* stream) {
-  return davidson_entry(H, B, la, lb, L, guess, opts, energy, c_out, info_out, stream,
-                        "hinqs_davidson_list");
+  return davidson_run(H, B, la, lb, L, guess, opts, energy, c_out, info_out, stream,
+                      "hinqs_davidson_list", nullptr, nullptr);
 }

@@ -175,6 +175,34 @@ int sigma_list_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
 int diag_list_launch(const hinqs_ham_s* H, const hinqs_links_s* la, const hinqs_links_s* lb,
                      const hinqs_detlist_s* L, double* hdiag, cudaStream_t s);
 int check_list(const hinqs_subspace_s* B, const hinqs_detlist_s* L, const char* who);
+// One sigma product of a batch: y = H x for problem (H, B, la, lb) in `precision`.
+struct SigmaReq {
+  const hinqs_ham_s* H;
+  const hinqs_subspace_s* B;
+  const hinqs_links_s* la;
+  const hinqs_links_s* lb;
+  const void* x;
+  void* y;
+  int precision;
+};
+// The sigma products of several problems at once: FP32-family products run their
+// same-spin stages and their tensor-core opposite-spin term as one launch per stage over
+// all of them (a device work queue of (problem, alpha string) items for the tensor-core
+// term); FP64 products, and those outside the batched kernels' range, run one by one.
+int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s);
+// tensor-core opposite-spin term of the requests reqs[idx[0..n)] (split 1 or 3) in one
+// launch; kTcNoFit when the batch cannot run as one launch (the caller runs them singly)
+int sigma_ab_tc_batch(const SigmaReq* reqs, const int* idx, int n, int split, cudaStream_t s);
+// Lockstep batching of Davidson solves (batch.cu): a solver with a batcher hands its
+// sigma products to it, and each round's products run as one batched launch.
+struct SigmaBatcher;
+int batcher_sigma(SigmaBatcher* b, const SigmaReq& r, cudaStream_t s, cudaEvent_t ready);
+// hinqs_davidson / hinqs_davidson_list with an optional batcher (davidson.cu)
+int davidson_run(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                 const hinqs_links_s* lb, const hinqs_detlist_s* L, const double* guess,
+                 const hinqs_davidson_opts* opts, double* energy, double* c_out,
+                 hinqs_davidson_info* info_out, void* stream, const char* who,
+                 SigmaBatcher* batcher, cudaEvent_t ready);
 // opposite-spin sigma term on the tensor cores (FP32 vectors; split = 1 or 3)
 int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                        const hinqs_links_s* lb, const float* c, float* sig, int split,

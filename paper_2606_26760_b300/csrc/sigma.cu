@@ -13,6 +13,7 @@
 // every operand load is a coalesced 128/256-byte row segment; 32 consecutive rows
 // per block share most of their linked rows, which stay in L1.
 #include <algorithm>
+#include <vector>
 
 #include "hinqs_internal.cuh"
 
@@ -224,29 +225,45 @@ __global__ void __launch_bounds__(256) k_spmm_rec(
 // warp (one coalesced 256-byte load) and broadcast by shuffles: per link, the L1 data
 // path moves the 512-byte operand segment and 1/32 of a record line, instead of a
 // 256-byte segment plus a warp-uniform record load.  Requires ncols % 4 == 0.
-template <int RPW>
-__global__ void __launch_bounds__(256, 4) k_spmm_rec4(
+// four consecutive columns from p: one 16-byte load when the rows are 16-byte aligned
+// (the column count a multiple of 4), else up to `nv` guarded scalar loads
+template <bool ALIGNED>
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p, int nv) {
+  if (ALIGNED) return __ldg(reinterpret_cast<const float4*>(p));
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (nv > 0) v.x = __ldg(p);
+  if (nv > 1) v.y = __ldg(p + 1);
+  if (nv > 2) v.z = __ldg(p + 2);
+  if (nv > 3) v.w = __ldg(p + 3);
+  return v;
+}
+
+template <int RPW, bool ALIGNED>
+__device__ __forceinline__ void spmm_rec4_block(
     const float* __restrict__ X, float* __restrict__ Y, int64_t nrows, int64_t ncols,
     const int64_t* __restrict__ rp, const int2* __restrict__ rec,
     const int64_t* __restrict__ srp, const int2* __restrict__ sl, const float* __restrict__ VT,
     const double* __restrict__ hd_row, const double* __restrict__ hd_col, double e_nuc,
-    const float* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
+    const float* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate,
+    int64_t bx, int64_t by) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * 4;
+  const int64_t c0 = (bx * 32 + lane) * 4;
   const bool active = c0 < ncols;
   const int64_t cc = active ? c0 : 0;
+  const int nv = active ? (int)min64(4, ncols - c0) : 0;  // columns of this lane
   const int n2 = n * n;
   const unsigned full = 0xffffffffu;
-  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  const int64_t I0 = (by * kRowWarps + warp) * RPW;
   for (int rr = 0; rr < RPW; ++rr) {
     const int64_t I = I0 + rr;
     if (I >= nrows) break;  // warp-uniform
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (accumulate && active) acc = *reinterpret_cast<const float4*>(Y + I * ncols + c0);
+    if (accumulate && active) acc = ld4<ALIGNED>(Y + I * ncols + c0, nv);
     if (hd_row) {
       const float v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : 0.f;
       const float v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : 0.f;
-      const uint64_t b0 = scol[cc], b1 = scol[cc + 1], b2 = scol[cc + 2], b3 = scol[cc + 3];
+      const uint64_t b0 = nv > 0 ? scol[cc] : 0, b1 = nv > 1 ? scol[cc + 1] : 0;
+      const uint64_t b2 = nv > 2 ? scol[cc + 2] : 0, b3 = nv > 3 ? scol[cc + 3] : 0;
       float x0 = 0.f, x1 = 0.f, x2 = 0.f, x3 = 0.f;
       for (int j = 0; j < n; ++j) {
         const float a = __shfl_sync(full, j < 32 ? v0 : v1, j & 31);
@@ -256,12 +273,12 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
         if ((b3 >> j) & 1ull) x3 += a;
       }
       if (active) {
-        const float4 x = *reinterpret_cast<const float4*>(X + I * ncols + c0);
+        const float4 x = ld4<ALIGNED>(X + I * ncols + c0, nv);
         const double hr = hd_row[I] + e_nuc;
         acc.x += ((float)(hr + hd_col[c0]) + x0) * x.x;
-        acc.y += ((float)(hr + hd_col[c0 + 1]) + x1) * x.y;
-        acc.z += ((float)(hr + hd_col[c0 + 2]) + x2) * x.z;
-        acc.w += ((float)(hr + hd_col[c0 + 3]) + x3) * x.w;
+        if (nv > 1) acc.y += ((float)(hr + hd_col[c0 + 1]) + x1) * x.y;
+        if (nv > 2) acc.z += ((float)(hr + hd_col[c0 + 2]) + x2) * x.z;
+        if (nv > 3) acc.w += ((float)(hr + hd_col[c0 + 3]) + x3) * x.w;
       }
     }
     const int2* __restrict__ r = rec + rp[I];
@@ -278,7 +295,7 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
         for (int v = 0; v < 8; ++v) {
           const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u + v);
           h[v] = __int_as_float(__shfl_sync(full, mine.y, u + v));
-          x[v] = __ldg(reinterpret_cast<const float4*>(Xc + off));
+          x[v] = ld4<ALIGNED>(Xc + off, nv);
         }
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
@@ -291,7 +308,7 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
       for (; u < cnt; ++u) {
         const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u);
         const float h = __int_as_float(__shfl_sync(full, mine.y, u));
-        const float4 x = __ldg(reinterpret_cast<const float4*>(Xc + off));
+        const float4 x = ld4<ALIGNED>(Xc + off, nv);
         acc.x = fmaf(h, x.x, acc.x);
         acc.y = fmaf(h, x.y, acc.y);
         acc.z = fmaf(h, x.z, acc.z);
@@ -302,8 +319,8 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
       for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
         const int2 l = sl[q];
         const int pair = (l.y > 0 ? l.y : -l.y) - 1;
-        const float4 vt = *reinterpret_cast<const float4*>(VT + (int64_t)pair * ncols + c0);
-        const float4 x = *reinterpret_cast<const float4*>(X + (int64_t)l.x * ncols + c0);
+        const float4 vt = ld4<ALIGNED>(VT + (int64_t)pair * ncols + c0, nv);
+        const float4 x = ld4<ALIGNED>(X + (int64_t)l.x * ncols + c0, nv);
         const float sg = l.y > 0 ? 1.f : -1.f;
         acc.x += sg * vt.x * x.x;
         acc.y += sg * vt.y * x.y;
@@ -311,8 +328,78 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
         acc.w += sg * vt.w * x.w;
       }
     }
-    if (active) *reinterpret_cast<float4*>(Y + I * ncols + c0) = acc;
+    if (active) {
+      float* y = Y + I * ncols + c0;
+      if (ALIGNED) {
+        *reinterpret_cast<float4*>(y) = acc;
+      } else {
+        y[0] = acc.x;
+        if (nv > 1) y[1] = acc.y;
+        if (nv > 2) y[2] = acc.z;
+        if (nv > 3) y[3] = acc.w;
+      }
+    }
   }
+}
+
+template <int RPW>
+__global__ void __launch_bounds__(256, 4) k_spmm_rec4(
+    const float* __restrict__ X, float* __restrict__ Y, int64_t nrows, int64_t ncols,
+    const int64_t* __restrict__ rp, const int2* __restrict__ rec,
+    const int64_t* __restrict__ srp, const int2* __restrict__ sl, const float* __restrict__ VT,
+    const double* __restrict__ hd_row, const double* __restrict__ hd_col, double e_nuc,
+    const float* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
+  spmm_rec4_block<RPW, true>(X, Y, nrows, ncols, rp, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow,
+                             scol, n, accumulate, blockIdx.x, blockIdx.y);
+}
+
+// The same row product for several problems in one launch: problem r's blocks are
+// [first[r], first[r+1]) of the flattened grid, cols_blocks[r] column tiles per row block.
+struct SpmmJob {
+  const float* X;
+  float* Y;
+  int64_t nrows, ncols;
+  const int64_t* rp;
+  const int2* rec;
+  const int64_t* srp;
+  const int2* sl;
+  const float* VT;
+  const double* hd_row;
+  const double* hd_col;
+  double e_nuc;
+  const float* Vrow;
+  const uint64_t* scol;
+  int n, accumulate;
+  int64_t col_blocks;
+};
+
+__device__ __forceinline__ int find_job(const int64_t* __restrict__ first, int R, int64_t b) {
+  int lo = 0, hi = R;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (first[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+constexpr int kBatchRpw = 4;
+
+__global__ void __launch_bounds__(256, 4) k_spmm_rec4_batch(const SpmmJob* __restrict__ jobs,
+                                                           const int64_t* __restrict__ first,
+                                                           int R) {
+  const int64_t b = blockIdx.x;
+  const int r = find_job(first, R, b);
+  const SpmmJob J = jobs[r];
+  const int64_t local = b - first[r];
+  if (J.ncols % 4 == 0)
+    spmm_rec4_block<kBatchRpw, true>(J.X, J.Y, J.nrows, J.ncols, J.rp, J.rec, J.srp, J.sl, J.VT,
+                                     J.hd_row, J.hd_col, J.e_nuc, J.Vrow, J.scol, J.n, J.accumulate,
+                                     local % J.col_blocks, local / J.col_blocks);
+  else
+    spmm_rec4_block<kBatchRpw, false>(J.X, J.Y, J.nrows, J.ncols, J.rp, J.rec, J.srp, J.sl, J.VT,
+                                      J.hd_row, J.hd_col, J.e_nuc, J.Vrow, J.scol, J.n, J.accumulate,
+                                      local % J.col_blocks, local / J.col_blocks);
 }
 
 template <typename T>
@@ -324,10 +411,11 @@ const int4* recof<double>(const hinqs_links_s* L) { return L->rec64; }
 
 // out[j][i] = in[i][j] (+ out[j][i] if accumulate) for in of rows x cols; 32x32 tiles.
 template <typename T>
-__global__ void k_transpose_t(const T* __restrict__ in, T* __restrict__ out, int64_t rows,
-                              int64_t cols, int accumulate) {
+__device__ __forceinline__ void transpose_tile(const T* __restrict__ in, T* __restrict__ out,
+                                               int64_t rows, int64_t cols, int accumulate,
+                                               int64_t tx, int64_t ty) {
   __shared__ T tile[32][33];
-  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  const int64_t bx = tx * 32, by = ty * 32;
   for (int k = threadIdx.y; k < 32; k += blockDim.y) {
     const int64_t i = by + k, j = bx + threadIdx.x;
     if (i < rows && j < cols) tile[k][threadIdx.x] = in[i * cols + j];
@@ -341,6 +429,28 @@ __global__ void k_transpose_t(const T* __restrict__ in, T* __restrict__ out, int
       out[j * rows + i] = v;
     }
   }
+}
+
+template <typename T>
+__global__ void k_transpose_t(const T* __restrict__ in, T* __restrict__ out, int64_t rows,
+                              int64_t cols, int accumulate) {
+  transpose_tile<T>(in, out, rows, cols, accumulate, blockIdx.x, blockIdx.y);
+}
+
+struct TransJob {
+  const float* in;
+  float* out;
+  int64_t rows, cols, col_tiles;
+};
+
+// transposes of several problems in one launch (problem r's tiles [first[r], first[r+1]))
+__global__ void k_transpose_batch(const TransJob* __restrict__ jobs,
+                                  const int64_t* __restrict__ first, int R) {
+  const int64_t b = blockIdx.x;
+  const int r = find_job(first, R, b);
+  const TransJob J = jobs[r];
+  const int64_t local = b - first[r];
+  transpose_tile<float>(J.in, J.out, J.rows, J.cols, 0, local % J.col_tiles, local / J.col_tiles);
 }
 
 struct AbArgs {
@@ -582,6 +692,118 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   return rc;
 }
 
+int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
+  std::vector<int> f32;
+  for (int i = 0; i < n; ++i) {
+    const SigmaReq& r = reqs[i];
+    if (r.precision == HINQS_PREC_FP64 || !r.la->rec32 || !r.lb->rec32) {
+      HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
+    } else {
+      f32.push_back(i);
+    }
+  }
+  if (f32.empty()) return HINQS_OK;
+  const int R = (int)f32.size();
+  std::vector<float*> CT(R, nullptr), ST(R, nullptr);
+  SpmmJob* d_spmm = nullptr;
+  TransJob* d_tr = nullptr;
+  int64_t* d_first = nullptr;
+  auto run = [&]() -> int {
+    for (int i = 0; i < R; ++i) {
+      const int64_t N = reqs[f32[i]].B->Na * reqs[f32[i]].B->Nb;
+      HQ_TRY(dalloc(&CT[i], N, s));
+      HQ_TRY(dalloc(&ST[i], N, s));
+    }
+    HQ_TRY(dalloc(&d_spmm, R, s));
+    HQ_TRY(dalloc(&d_tr, R, s));
+    HQ_TRY(dalloc(&d_first, R + 1, s));
+    std::vector<int64_t> first(R + 1, 0);
+    // a transpose stage over every request: in (rows x cols) -> out
+    auto transpose_all = [&](bool forward) -> int {
+      std::vector<TransJob> jobs(R);
+      for (int i = 0; i < R; ++i) {
+        const SigmaReq& r = reqs[f32[i]];
+        const int64_t rows = forward ? r.B->Na : r.B->Nb, cols = forward ? r.B->Nb : r.B->Na;
+        jobs[i] = TransJob{forward ? static_cast<const float*>(r.x) : ST[i],
+                           forward ? CT[i] : static_cast<float*>(r.y), rows, cols, ceil_div(cols, 32)};
+        first[i + 1] = first[i] + jobs[i].col_tiles * ceil_div(rows, 32);
+      }
+      HQ_CUDA(cudaMemcpyAsync(d_tr, jobs.data(), R * sizeof(TransJob), cudaMemcpyHostToDevice, s));
+      HQ_CUDA(cudaMemcpyAsync(d_first, first.data(), (R + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+      k_transpose_batch<<<(unsigned)first[R], dim3(32, 8), 0, s>>>(d_tr, d_first, R);
+      HQ_LAUNCH_CHECK();
+      return HINQS_OK;
+    };
+    // a row-product stage over every request: beta rows on C^T, or alpha rows on C
+    auto rows_all = [&](bool beta) -> int {
+      std::vector<SpmmJob> jobs(R);
+      for (int i = 0; i < R; ++i) {
+        const SigmaReq& r = reqs[f32[i]];
+        const hinqs_links_s* L = beta ? r.lb : r.la;
+        SpmmJob j{};
+        j.X = beta ? CT[i] : static_cast<const float*>(r.x);
+        j.Y = beta ? ST[i] : static_cast<float*>(r.y);
+        j.nrows = beta ? r.B->Nb : r.B->Na;
+        j.ncols = beta ? r.B->Na : r.B->Nb;
+        j.rp = L->row_ptr;
+        j.rec = L->rec32;
+        j.srp = beta ? r.lb->srow_ptr : nullptr;
+        j.sl = beta ? r.lb->slink : nullptr;
+        j.VT = beta ? r.la->VT32 : nullptr;
+        j.hd_row = beta ? nullptr : r.la->hdiag;
+        j.hd_col = beta ? nullptr : r.lb->hdiag;
+        j.e_nuc = beta ? 0.0 : r.H->e_nuc;
+        j.Vrow = beta ? nullptr : r.la->V32;
+        j.scol = beta ? nullptr : r.B->sb;
+        j.n = r.H->n;
+        j.accumulate = beta ? 0 : 1;
+        j.col_blocks = ceil_div(j.ncols, 128);
+        jobs[i] = j;
+        first[i + 1] = first[i] + j.col_blocks * ceil_div(j.nrows, kRowWarps * kBatchRpw);
+      }
+      HQ_CUDA(cudaMemcpyAsync(d_spmm, jobs.data(), R * sizeof(SpmmJob), cudaMemcpyHostToDevice, s));
+      HQ_CUDA(cudaMemcpyAsync(d_first, first.data(), (R + 1) * sizeof(int64_t),
+                              cudaMemcpyHostToDevice, s));
+      k_spmm_rec4_batch<<<(unsigned)first[R], 32 * kRowWarps, 0, s>>>(d_spmm, d_first, R);
+      HQ_LAUNCH_CHECK();
+      return HINQS_OK;
+    };
+    HQ_TRY(transpose_all(true));   // C^T
+    HQ_TRY(rows_all(true));        // beta same-spin + alpha self x beta singles, on C^T
+    HQ_TRY(transpose_all(false));  // sigma = (...)^T
+    HQ_TRY(rows_all(false));       // += alpha same-spin + diagonal
+    // the opposite-spin term: one tensor-core launch per split mode, the rest singly
+    for (int split : {1, 3}) {
+      std::vector<int> ids;
+      const int prec = split == 1 ? HINQS_PREC_FP32_BF16AB : HINQS_PREC_FP32_BF16X3AB;
+      for (int i : f32)
+        if (reqs[i].precision == prec && reqs[i].la->nsingle > 0) ids.push_back(i);
+      if (ids.empty()) continue;
+      const int rc = sigma_ab_tc_batch(reqs, ids.data(), (int)ids.size(), split, s);
+      if (rc < 0) return rc;
+      if (rc == kTcNoFit)
+        for (int i : ids)
+          HQ_TRY(sigma_launch(reqs[i].H, reqs[i].B, reqs[i].la, reqs[i].lb, reqs[i].x, reqs[i].y,
+                              reqs[i].precision, s, kOppositeSpin));
+    }
+    for (int i : f32)
+      if (reqs[i].precision == HINQS_PREC_FP32 && reqs[i].la->nsingle > 0)
+        HQ_TRY(sigma_launch(reqs[i].H, reqs[i].B, reqs[i].la, reqs[i].lb, reqs[i].x, reqs[i].y,
+                            reqs[i].precision, s, kOppositeSpin));
+    return HINQS_OK;
+  };
+  const int rc = run();
+  for (int i = 0; i < R; ++i) {
+    dfree(CT[i], s);
+    dfree(ST[i], s);
+  }
+  dfree(d_spmm, s);
+  dfree(d_tr, s);
+  dfree(d_first, s);
+  return rc;
+}
+
 int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                  const hinqs_links_s* lb, const void* c, void* sigma, int precision,
                  cudaStream_t s, int parts) {
@@ -668,6 +890,28 @@ static int sigma_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_
   HQ_TRY(sigma_launch(H, B, la, lb, c, sigma, precision, (cudaStream_t)stream, parts));
   if ((parts & kOppositeSpin) &&
       (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB))
+    return tc_error_check((cudaStream_t)stream);
+  return HINQS_OK;
+}
+
+extern "C" int hinqs_sigma_batch(int n, const hinqs_ham* const* hams,
+                                 const hinqs_subspace* const* subs, const hinqs_links* const* las,
+                                 const hinqs_links* const* lbs, const void* const* cs,
+                                 void* const* sigmas, int precision, void* stream) {
+  if (n < 0 || (n > 0 && (!hams || !subs || !las || !lbs || !cs || !sigmas)))
+    return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: NULL arrays");
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+    return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: unknown precision %d", precision);
+  std::vector<SigmaReq> reqs;
+  for (int g = 0; g < n; ++g) {
+    HQ_TRY(check_triplet(hams[g], subs[g], las[g], lbs[g], "hinqs_sigma_batch"));
+    if (!cs[g] || !sigmas[g] || cs[g] == sigmas[g])
+      return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: problem %d: NULL or overlapping vectors", g);
+    reqs.push_back(SigmaReq{hams[g], subs[g], las[g], lbs[g], cs[g], sigmas[g], precision});
+  }
+  if (n == 0) return HINQS_OK;
+  HQ_TRY(sigma_batch_launch(reqs.data(), n, (cudaStream_t)stream));
+  if (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB)
     return tc_error_check((cudaStream_t)stream);
   return HINQS_OK;
 }

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cstdint>
+#include <vector>
 
 #include "hinqs_internal.cuh"
 
@@ -133,6 +134,17 @@ struct Args {
   int crow_smem;  // stage the row C(Ja, :) in shared memory
 };
 
+// A device work queue of (problem, alpha string) items for the batched launch: problem
+// r has starts[r+1] - starts[r] alpha strings (starts[0] = 0, starts[R] = total), and
+// CTAs take items in turn from *counter.  reqs == NULL: one problem, the kernel's Args.
+struct Queue {
+  const Args* reqs = nullptr;
+  const int64_t* starts = nullptr;
+  int R = 0;
+  unsigned long long* counter = nullptr;
+  int64_t total = 0;
+};
+
 // Shared-memory bytes of one CTA (the layout of the kernel below).
 __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int KB, int64_t Nb,
                                              bool crow) {
@@ -144,17 +156,21 @@ __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int 
 }
 
 // Persistent CTAs of 8 warps; each takes alpha strings Ja = blockIdx.x, +gridDim.x, ...
-// and, per chunk of at most NW alpha singles of Ja, runs the beta tiles through a
+// (or, in the batched launch, (problem, alpha string) items from the work queue) and,
+// per chunk of at most NW alpha singles of Ja, runs the beta tiles through a
 // STAGES-deep pipeline: while the MMA of tile t runs, the warps gather D for tile
 // t+1 into the other A buffer; then they read tile t's accumulator (its own TMEM
 // columns) and add it into sigma with coalesced reductions (lane = beta string).
 template <int NW, int SPLIT, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
+__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A0, Queue Q) {
   extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ int64_t s_item;
+  __shared__ int s_req;
   constexpr int NP = SPLIT == 3 ? 2 : 1;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int KB = A.KB;
-  const int64_t Nb = A.Nb;
+  Args A = A0;
+  const int KB = A.KB;  // the same for every problem of a batch
+  int64_t Nb = A.Nb;
   const uint32_t a_bytes = (uint32_t)kTileM * KB * 16;
   const uint32_t b_bytes = (uint32_t)NW * KB * 16;
   unsigned char* a_buf = smem;                              // [STAGES][NP][a_bytes]
@@ -186,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
   const uint32_t sbo = (uint32_t)KB * 128;
   uint32_t ph0 = 0, ph1 = 0;
   bool ok = true;
-  const int T = (int)((Nb + kTileM - 1) / kTileM);
+  int T = (int)((Nb + kTileM - 1) / kTileM);
 
   // zero one A stage (both planes)
   auto zero_stage = [&](int st) {
@@ -246,7 +262,37 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
     mma_commit(smem_u32(mbar + st));
   };
 
-  for (int64_t Ja = blockIdx.x; Ja < A.Na && ok; Ja += gridDim.x) {
+  int64_t next_ja = blockIdx.x;
+  for (;;) {
+    int64_t Ja;
+    if (Q.reqs) {
+      __syncthreads();  // the previous item's readers of A, crow_s, b_buf and tgt are done
+      if (tid == 0) {
+        const int64_t item = (int64_t)atomicAdd(Q.counter, 1ull);
+        int r = 0;
+        if (item < Q.total) {  // the problem whose range holds the item
+          int lo = 0, hi = Q.R;
+          while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (Q.starts[mid] <= item) lo = mid;
+            else hi = mid;
+          }
+          r = lo;
+        }
+        s_item = item;
+        s_req = r;
+      }
+      __syncthreads();
+      if (s_item >= Q.total || !ok) break;
+      A = Q.reqs[s_req];
+      Ja = s_item - Q.starts[s_req];
+      Nb = A.Nb;
+      T = (int)((Nb + kTileM - 1) / kTileM);
+    } else {
+      if (next_ja >= A.Na || !ok) break;
+      Ja = next_ja;
+      next_ja += gridDim.x;
+    }
     const int64_t a_beg = A.a_srow[Ja], a_end = A.a_srow[Ja + 1];
     if (a_beg == a_end) continue;
     const float* crow = A.C + Ja * Nb;
@@ -396,9 +442,70 @@ static int launch(const Args& a, bool crow, cudaStream_t s) {
   if (per_sm < 1)
     return fail(HINQS_ERR_ARG, "tensor-core sigma: a CTA of %zu bytes does not fit an SM", bytes);
   const int grid = (int)std::min<int64_t>(a.Na, (int64_t)per_sm * kNumSMs);
-  kern<<<grid, kThreads, req, s>>>(b);
+  kern<<<grid, kThreads, req, s>>>(b, Queue{});
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
+}
+
+// The batched launch: one persistent grid over the (problem, alpha string) items of
+// every problem in reqs (same n_orb; the C row staged when the largest fits), one
+// stage.  kTcNoFit when the operand tiles do not fit.
+template <int NW, int SPLIT>
+static int launch_batch(std::vector<Args>& reqs, cudaStream_t s) {
+  int64_t nb_max = 0, total = 0;
+  for (const Args& a : reqs) nb_max = std::max(nb_max, a.Nb);
+  const size_t lim = (size_t)smem_optin_limit();
+  const int KB = reqs[0].KB;
+  bool crow = smem_bytes(NW, SPLIT, 1, KB, nb_max, true) <= lim;
+  if (!crow && smem_bytes(NW, SPLIT, 1, KB, nb_max, false) > lim) return kTcNoFit;
+  std::vector<int64_t> starts(reqs.size() + 1, 0);
+  for (size_t r = 0; r < reqs.size(); ++r) {
+    reqs[r].crow_smem = crow ? 1 : 0;
+    starts[r + 1] = starts[r] + reqs[r].Na;
+  }
+  total = starts.back();
+  const size_t bytes = smem_bytes(NW, SPLIT, 1, KB, nb_max, crow);
+  auto kern = k_sigma_ab_tc<NW, SPLIT, 1>;
+  HQ_TRY(allow_max_smem(kern));
+  const int cap = 512 / NW;
+  cudaFuncAttributes fa;
+  HQ_CUDA(cudaFuncGetAttributes(&fa, kern));
+  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = 65536 / (warp_regs * (kThreads / 32));
+  size_t req = bytes;
+  if ((int)(233472 / (req + 1024)) > cap) req = 233472 / (cap + 1);
+  const int per_sm = std::min(std::min(cap, (int)(233472 / (req + 1024))),
+                              std::min(by_regs, 2048 / kThreads));
+  if (per_sm < 1) return kTcNoFit;
+  Args* d_reqs = nullptr;
+  int64_t* d_starts = nullptr;
+  unsigned long long* d_counter = nullptr;
+  auto run = [&]() -> int {
+    HQ_TRY(dalloc(&d_reqs, reqs.size(), s));
+    HQ_TRY(dalloc(&d_starts, starts.size(), s));
+    HQ_TRY(dalloc(&d_counter, 1, s));
+    HQ_CUDA(cudaMemcpyAsync(d_reqs, reqs.data(), reqs.size() * sizeof(Args), cudaMemcpyHostToDevice, s));
+    HQ_CUDA(cudaMemcpyAsync(d_starts, starts.data(), starts.size() * sizeof(int64_t),
+                            cudaMemcpyHostToDevice, s));
+    HQ_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
+    Queue q;
+    q.reqs = d_reqs;
+    q.starts = d_starts;
+    q.R = (int)reqs.size();
+    q.counter = d_counter;
+    q.total = total;
+    const int grid = (int)std::min<int64_t>(total, (int64_t)per_sm * kNumSMs);
+    kern<<<grid, kThreads, req, s>>>(reqs[0], q);
+    HQ_LAUNCH_CHECK();
+    // the host arrays are copied before the call returns
+    HQ_CUDA(cudaStreamSynchronize(s));
+    return HINQS_OK;
+  };
+  const int rc = run();
+  dfree(d_reqs, s);
+  dfree(d_starts, s);
+  dfree(d_counter, s);
+  return rc;
 }
 
 // Largest configuration that fits: two stages with the C row in shared memory, then
@@ -972,6 +1079,35 @@ int tc_tables_build(hinqs_ham_s* H, cudaStream_t s) {
     HQ_LAUNCH_CHECK();
   }
   return HINQS_OK;
+}
+
+int sigma_ab_tc_batch(const SigmaReq* reqs, const int* idx, int n, int split, cudaStream_t s) {
+  if (n <= 0) return HINQS_OK;
+  std::vector<tc::Args> args;
+  bool wide = false;
+  for (int i = 0; i < n; ++i) {
+    const SigmaReq& r = reqs[idx[i]];
+    if (!r.H->tc_bhi || r.H->tc_KB != reqs[idx[0]].H->tc_KB) return kTcNoFit;
+    tc::Args a;
+    a.Na = r.B->Na;
+    a.Nb = r.B->Nb;
+    a.n = r.H->n;
+    a.KB = r.H->tc_KB;
+    a.a_srow = r.la->srow_ptr;
+    a.a_slink = r.la->slink;
+    a.b_ell = r.lb->tcell;
+    a.b_cnt = r.lb->scount;
+    a.Bhi = reinterpret_cast<const uint4*>(r.H->tc_bhi);
+    a.Blo = reinterpret_cast<const uint4*>(r.H->tc_blo);
+    a.C = static_cast<const float*>(r.x);
+    a.sig = static_cast<float*>(r.y);
+    a.crow_smem = 0;
+    wide = wide || r.la->max_srow > 64;
+    args.push_back(a);
+  }
+  if (split == 3)
+    return wide ? tc::launch_batch<128, 3>(args, s) : tc::launch_batch<64, 3>(args, s);
+  return wide ? tc::launch_batch<128, 1>(args, s) : tc::launch_batch<64, 1>(args, s);
 }
 
 int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,

@@ -156,3 +156,52 @@ def test_bond_scan_mixed_batch_vs_fp64_batch():
         assert r.status == hq.OK and m.status == hq.OK
         assert abs(r.energy - m.energy) < 1e-6
         assert abs(abs(torch.dot(r.c, m.c).item()) - 1.0) < 1e-5
+
+
+# ------------------------------------------------ lockstep batch (one launch per stage)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6), (2, 1e-5), (3, 1e-6)])
+def test_sigma_batch_equals_single_products(small_scan, prec, tol):
+    """The batched kernels (flattened row products and transposes over every geometry,
+    the tensor-core term over a device work queue) against one product per geometry:
+    the same arithmetic up to the order of the reductions; the scan's string counts
+    are mostly not multiples of 4 (the unaligned row-product path)."""
+    ws, gs, probs = small_scan
+    dt = torch.float64 if prec == 0 else torch.float32
+    cs = [torch.tensor(synth.random_vector(p[1].N, 30 + i), dtype=dt, device="cuda")
+          for i, p in enumerate(probs)]
+    assert any(p[1].Nb % 4 for p in probs) and any(p[1].Na % 4 for p in probs)
+    got = hq.sigma_batch(probs, cs, precision=prec)
+    for p, c, g in zip(probs, cs, got):
+        ref = hq.sigma(*p, c, precision=prec)
+        assert float(torch.max(torch.abs(g - ref))) <= tol * float(torch.max(torch.abs(ref)))
+
+
+def test_batch_lockstep_matches_oracle(small_scan):
+    ws, gs, probs = small_scan
+    res = hq.davidson_batch(probs, n_streams=0, tol_residual=1e-9)
+    for r, (_, _, _, E, c) in zip(res, gs):
+        assert r.status == hq.OK and abs(r.energy - E) < 1e-9
+        assert abs(abs(np.dot(r.c.cpu().numpy(), c)) - 1.0) < 1e-8
+    for inner in (hq.PREC_FP32, hq.PREC_FP32_BF16AB, hq.PREC_FP32_BF16X3AB):
+        res = hq.davidson_batch(probs, precision=hq.DAVIDSON_MIXED, inner_precision=inner,
+                                tol_residual=1e-7, tol_energy=1e-9, max_iter=600, n_streams=0)
+        for r, (_, _, _, E, _) in zip(res, gs):
+            assert r.status == hq.OK and abs(r.energy - E) < 1e-6
+
+
+def test_batch_lockstep_equals_worker_form(small_scan):
+    """Lockstep rounds change the launches, not the solves: the same FP64 answers as the
+    worker form, including a warm-started geometry that leaves the rounds at once and a
+    geometry that hits max_iter."""
+    ws, gs, probs = small_scan
+    guesses = [None] * len(probs)
+    guesses[1] = torch.tensor(gs[1][4], dtype=torch.float64, device="cuda")
+    a = hq.davidson_batch(probs, guesses=guesses, n_streams=0)
+    b = hq.davidson_batch(probs, guesses=guesses, n_streams=3)
+    for x, y in zip(a, b):
+        assert abs(x.energy - y.energy) < 1e-10 and x.status == y.status
+    assert a[1].iterations <= 2
+    short = hq.davidson_batch(probs, max_iter=3, n_streams=0)
+    assert any(r.status == hq.NOT_CONVERGED for r in short)
