@@ -491,6 +491,19 @@ def run_bond_scan(args):
                                                      max_subspace=16, max_iter=600)
                                          for p in probs])
     err = max(abs(a.energy - b.energy) for a, b in zip(rb, rf))
+    # the same scan with small subspaces (60..400 strings per spin), where every sigma
+    # is launch-bound and the lockstep rounds batch all 24 geometries
+    small = []
+    for w in synth.bond_scan_workload(lo=60, hi=400):
+        ham = hq.Hamiltonian(torch.tensor(w["h"], device=dev), torch.tensor(w["eri"], device=dev),
+                             ne, ne, w["e_nuc"])
+        sub = hq.build_subspace(torch.from_numpy(w["alpha"].view(np.int64).copy()).to(dev),
+                                torch.from_numpy(w["beta"].view(np.int64).copy()).to(dev), n, ne, ne)
+        small.append((ham, sub, hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)))
+    hq.davidson_batch(small, autotune=True, n_streams=0, **mixed)
+    ts_batch, rsb = solve_time(lambda: hq.davidson_batch(small, n_streams=0, **mixed))
+    ts_workers, _ = solve_time(lambda: hq.davidson_batch(small, n_streams=4, **mixed))
+    ts_seq, rss = solve_time(lambda: [hq.davidson(*p, **mixed) for p in small])
     t_mean = sum(times) / len(times)
     line = {
         "metric": METRIC,
@@ -517,6 +530,12 @@ def run_bond_scan(args):
                     "sequential_mixed_bf16": t_seq_mixed, "sequential_fp64": t_seq_fp64,
                     "speedup_batch_vs_fp64": t_seq_fp64 / t_batch,
                     "speedup_batch_vs_sequential_mixed": t_seq_mixed / t_batch},
+        "solve_s_small_scan": {"subspaces": "60..400 strings per spin, "
+                                            f"{sum(p[1].N for p in small)} determinants in all",
+                               "batch_mixed_bf16": ts_batch, "worker_streams_mixed_bf16": ts_workers,
+                               "sequential_mixed_bf16": ts_seq,
+                               "max_abs_diff_batch_vs_sequential_Ha":
+                                   max(abs(a.energy - b.energy) for a, b in zip(rsb, rss))},
         "energy": {"max_abs_diff_batch_mixed_vs_fp64_Ha": err,
                    "statuses": sorted(set(int(x.status) for x in rb + rf))},
         "clocks": clk,

@@ -211,7 +211,8 @@ int hinqs_sigma_opposite_spin(const hinqs_ham* ham, const hinqs_subspace* sub,
  * run each same-spin stage as one launch over every problem's rows and the BF16
  * tensor-core term as one persistent kernel over a device work queue of (problem,
  * alpha string) items (problems of different n_orb, or whose tensor-core tiles do not
- * fit, run one by one); FP64 products and the FP32 CUDA-core opposite-spin term run
+ * fit, run one by one); FP64 products, the FP32 CUDA-core opposite-spin term and
+ * problems of 2^20 determinants or more (whose own tuned launches fill the GPU) run
  * problem by problem.  Same results as n hinqs_sigma calls up to summation order.
  * Errors as hinqs_sigma, with the problem's index in the message. */
 int hinqs_sigma_batch(int n, const hinqs_ham* const* hams, const hinqs_subspace* const* subs,
@@ -364,15 +365,17 @@ int hinqs_autotune(const hinqs_ham* ham, const hinqs_subspace* sub, hinqs_links*
  * Not in the paper (see hinqs_autotune): lowest eigenpairs of n_geom independent
  * problems, e.g. the geometries of a bond scan, each exactly as hinqs_davidson
  * would solve it with `opts` (NULL = defaults).
- *   n_streams <= 0 (lockstep): every geometry's solve runs on a host thread and a CUDA
- *             stream of its own and hands its sigma products to a shared batch: when
- *             every unconverged solve has handed in one, the round runs as one launch
- *             per sigma stage for all of them -- the same-spin row products and
- *             transposes over a flattened grid of every geometry's rows, the BF16
- *             tensor-core opposite-spin term as one persistent kernel taking
- *             (geometry, alpha string) items from a device work queue (FP64 products
- *             and the FP32 CUDA-core opposite-spin term run geometry by geometry) --
- *             and a converged solve leaves the rounds;
+ *   n_streams <= 0 (lockstep): the solve of every geometry below 2^20
+ *             determinants runs on a host thread and a CUDA stream of its own and
+ *             hands its sigma products to a shared batch: when every unconverged such
+ *             solve has handed in one, the round runs as one launch per sigma stage for
+ *             all of them -- the same-spin row products and transposes over a flattened
+ *             grid of every geometry's rows, the BF16 tensor-core opposite-spin term as
+ *             one persistent kernel taking (geometry, alpha string) items from a device
+ *             work queue (FP64 products and the FP32 CUDA-core opposite-spin term run
+ *             geometry by geometry) -- and a converged solve leaves the rounds.  The
+ *             larger geometries, whose own launches fill the GPU, are solved at the
+ *             same time by 4 workers as below;
  *   n_streams > 0: that many host workers take the problems, longest first by an
  *             estimate of their sigma cost, each running its solves one after another
  *             on a stream of its own.

@@ -228,87 +228,49 @@ extern "C" int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
     const int p = o.precision == HINQS_DAVIDSON_MIXED ? o.inner_precision : HINQS_PREC_FP64;
     for (int g = 0; g < n_geom; ++g) HQ_TRY(autotune_impl(hams[g], subs[g], las[g], lbs[g], p, nullptr, s));
   }
-  if (n_streams <= 0) {
-    // lockstep: one thread and stream per geometry, sigma products batched per round
-    cudaEvent_t start;
-    HQ_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
-    HQ_CUDA(cudaEventRecord(start, s));
-    SigmaBatcher bat;
-    bat.active = n_geom;
-    HQ_CUDA(cudaStreamCreateWithFlags(&bat.bs, cudaStreamNonBlocking));
-    HQ_CUDA(cudaEventCreateWithFlags(&bat.done, cudaEventDisableTiming));
-    HQ_CUDA(cudaStreamWaitEvent(bat.bs, start, 0));
-    std::vector<cudaStream_t> gs(n_geom);
-    std::vector<cudaEvent_t> ready(n_geom);
-    for (int g = 0; g < n_geom; ++g) {
-      HQ_CUDA(cudaStreamCreateWithFlags(&gs[g], cudaStreamNonBlocking));
-      HQ_CUDA(cudaEventCreateWithFlags(&ready[g], cudaEventDisableTiming));
-      HQ_CUDA(cudaStreamWaitEvent(gs[g], start, 0));
-    }
-    std::vector<int> status(n_geom, HINQS_OK);
-    std::vector<std::string> msg(n_geom);
-    std::vector<hinqs_davidson_info> inf(n_geom);
-    int dev = 0;
-    cudaGetDevice(&dev);
-    std::vector<std::thread> threads;
-    for (int g = 0; g < n_geom; ++g)
-      threads.emplace_back([&, g]() {
-        cudaSetDevice(dev);
-        double e = 0.0;
-        status[g] = davidson_run(hams[g], subs[g], las[g], lbs[g], nullptr,
-                                 guesses ? guesses[g] : nullptr, &o,
-                                 &e, c_outs[g], &inf[g], (void*)gs[g], "hinqs_davidson_batch", &bat,
-                                 ready[g]);
-        energies[g] = e;
-        if (status[g] < 0) msg[g] = hinqs_last_error_message();
-        batcher_leave(&bat);
-      });
-    for (auto& t : threads) t.join();
-    for (int g = 0; g < n_geom; ++g) {
-      cudaEvent_t done;
-      cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
-      cudaEventRecord(done, gs[g]);
-      cudaStreamWaitEvent(s, done, 0);
-      cudaEventDestroy(done);
-      cudaStreamDestroy(gs[g]);
-      cudaEventDestroy(ready[g]);
-    }
-    cudaStreamSynchronize(bat.bs);
-    cudaStreamDestroy(bat.bs);
-    cudaEventDestroy(bat.done);
-    cudaEventDestroy(start);
-    int rc = HINQS_OK;
-    for (int g = 0; g < n_geom; ++g) {
-      if (infos) infos[g] = inf[g];
-      if (status[g] < 0 && rc >= 0) {
-        rc = status[g];
-        set_error("hinqs_davidson_batch: geometry %d: %s", g, msg[g].c_str());
-      } else if (status[g] > 0 && rc == HINQS_OK) {
-        rc = status[g];
-      }
-    }
-    return rc;
-  }
-  // longest first: cost ~ N * (links per alpha string + links per beta string + singles product)
-  std::vector<std::pair<double, int>> order;
+  // Lockstep (n_streams <= 0): the geometries below kBatchSoloN determinants hand their
+  // sigma products to shared rounds (one thread and stream each); the larger ones, and
+  // every geometry when n_streams > 0, go to worker streams, longest first.  Both sets
+  // run at the same time.
+  std::vector<int> small;
+  std::vector<std::pair<double, int>> order;  // (cost, geometry) of the worker set
   for (int g = 0; g < n_geom; ++g) {
     const double Na = (double)subs[g]->Na, Nb = (double)subs[g]->Nb;
+    if (n_streams <= 0 && subs[g]->Na * subs[g]->Nb < kBatchSoloN) {
+      small.push_back(g);
+      continue;
+    }
+    // cost ~ N * (links per alpha string + links per beta string + singles product)
     const double cost = Na * Nb *
                         ((double)las[g]->nnz / Na + (double)lbs[g]->nnz / Nb +
                          ((double)las[g]->nsingle / Na) * ((double)lbs[g]->nsingle / Nb + 1.0));
     order.push_back({cost, g});
   }
   std::sort(order.begin(), order.end(), [](auto& a, auto& b) { return a.first > b.first; });
-  int nw = n_streams > 0 ? n_streams : 4;
-  nw = std::max(1, std::min(nw, n_geom));
-  // worker streams start after the caller's stream reaches this point
+  const int nw = order.empty() ? 0 : std::max(1, std::min(n_streams > 0 ? n_streams : 4,
+                                                          (int)order.size()));
+  const int ns = (int)small.size();
+  // every stream starts after the caller's stream reaches this point
   cudaEvent_t start;
   HQ_CUDA(cudaEventCreateWithFlags(&start, cudaEventDisableTiming));
   HQ_CUDA(cudaEventRecord(start, s));
-  std::vector<cudaStream_t> ws(nw);
-  for (int w = 0; w < nw; ++w) {
-    HQ_CUDA(cudaStreamCreateWithFlags(&ws[w], cudaStreamNonBlocking));
-    HQ_CUDA(cudaStreamWaitEvent(ws[w], start, 0));
+  std::vector<cudaStream_t> ws(nw), gs(ns);
+  std::vector<cudaEvent_t> ready(ns);
+  SigmaBatcher bat;
+  bat.active = ns;
+  auto make_stream = [&](cudaStream_t* st) -> int {
+    HQ_CUDA(cudaStreamCreateWithFlags(st, cudaStreamNonBlocking));
+    HQ_CUDA(cudaStreamWaitEvent(*st, start, 0));
+    return HINQS_OK;
+  };
+  if (ns > 0) {
+    HQ_TRY(make_stream(&bat.bs));
+    HQ_CUDA(cudaEventCreateWithFlags(&bat.done, cudaEventDisableTiming));
+  }
+  for (int w = 0; w < nw; ++w) HQ_TRY(make_stream(&ws[w]));
+  for (int k = 0; k < ns; ++k) {
+    HQ_TRY(make_stream(&gs[k]));
+    HQ_CUDA(cudaEventCreateWithFlags(&ready[k], cudaEventDisableTiming));
   }
   std::atomic<int> next{0};
   std::vector<int> status(n_geom, HINQS_OK);
@@ -316,30 +278,45 @@ extern "C" int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
   std::vector<hinqs_davidson_info> inf(n_geom);
   int dev = 0;
   cudaGetDevice(&dev);
-  auto worker = [&](int w) {
-    cudaSetDevice(dev);
-    for (;;) {
-      const int k = next.fetch_add(1);
-      if (k >= n_geom) break;
-      const int g = order[k].second;
-      double e = 0.0;
-      status[g] = hinqs_davidson(hams[g], subs[g], las[g], lbs[g], guesses ? guesses[g] : nullptr,
-                                 &o, &e, c_outs[g], &inf[g], (void*)ws[w]);
-      energies[g] = e;
-      if (status[g] < 0) msg[g] = hinqs_last_error_message();
-    }
+  auto solve = [&](int g, cudaStream_t st, SigmaBatcher* b, cudaEvent_t rdy) {
+    double e = 0.0;
+    status[g] = davidson_run(hams[g], subs[g], las[g], lbs[g], nullptr,
+                             guesses ? guesses[g] : nullptr, &o, &e, c_outs[g], &inf[g],
+                             (void*)st, "hinqs_davidson_batch", b, rdy);
+    energies[g] = e;
+    if (status[g] < 0) msg[g] = hinqs_last_error_message();
   };
   std::vector<std::thread> threads;
-  for (int w = 0; w < nw; ++w) threads.emplace_back(worker, w);
+  for (int w = 0; w < nw; ++w)
+    threads.emplace_back([&, w]() {
+      cudaSetDevice(dev);
+      for (int k; (k = next.fetch_add(1)) < (int)order.size();)
+        solve(order[k].second, ws[w], nullptr, nullptr);
+    });
+  for (int k = 0; k < ns; ++k)
+    threads.emplace_back([&, k]() {
+      cudaSetDevice(dev);
+      solve(small[k], gs[k], &bat, ready[k]);
+      batcher_leave(&bat);
+    });
   for (auto& t : threads) t.join();
-  // the caller's stream continues after every worker stream
-  for (int w = 0; w < nw; ++w) {
+  // the caller's stream continues after every stream
+  auto join_stream = [&](cudaStream_t st) {
     cudaEvent_t done;
     cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
-    cudaEventRecord(done, ws[w]);
+    cudaEventRecord(done, st);
     cudaStreamWaitEvent(s, done, 0);
     cudaEventDestroy(done);
-    cudaStreamDestroy(ws[w]);
+    cudaStreamDestroy(st);
+  };
+  for (int w = 0; w < nw; ++w) join_stream(ws[w]);
+  for (int k = 0; k < ns; ++k) {
+    join_stream(gs[k]);
+    cudaEventDestroy(ready[k]);
+  }
+  if (ns > 0) {
+    join_stream(bat.bs);
+    cudaEventDestroy(bat.done);
   }
   cudaEventDestroy(start);
   int rc = HINQS_OK;

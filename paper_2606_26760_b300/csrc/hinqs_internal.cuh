@@ -159,6 +159,13 @@ struct hinqs_detlist_s {
 
 namespace hinqs {
 
+// From this many determinants on, a problem's own (tuned) launches fill the GPU and
+// it leaves the batched launches (measured on B300 with the 16-orbital (5,5) bond scan,
+// sigma alone: batched 4.4x faster at 1e4 determinants per problem, 1.7x at 1.6e5,
+// 1.2x at 6.4e5, 1.1x at 2.3e6, 0.94x at 6.3e6; within a solve the rendezvous of the
+// rounds costs more than 1.1x gains).
+constexpr int64_t kBatchSoloN = 1 << 20;
+
 // Kernel launchers shared between translation units.
 constexpr int kSameSpin = 1;      // H_a C + C H_b^T + diagonal + alpha-self x beta singles
 constexpr int kOppositeSpin = 2;  // += alpha singles x (beta singles + beta self)

@@ -385,13 +385,21 @@ __device__ __forceinline__ int find_job(const int64_t* __restrict__ first, int R
 
 constexpr int kBatchRpw = 4;
 
-__global__ void __launch_bounds__(256, 4) k_spmm_rec4_batch(const SpmmJob* __restrict__ jobs,
-                                                           const int64_t* __restrict__ first,
-                                                           int R) {
+// The jobs of one batched launch, passed by value as a kernel parameter (no host to
+// device copy): kMaxJobs per launch, a longer batch is split.
+constexpr int kMaxJobs = 48;
+template <typename J>
+struct JobTab {
+  J job[kMaxJobs];
+  int64_t first[kMaxJobs + 1];
+  int R;
+};
+
+__global__ void __launch_bounds__(256, 4) k_spmm_rec4_batch(const __grid_constant__ JobTab<SpmmJob> tab) {
   const int64_t b = blockIdx.x;
-  const int r = find_job(first, R, b);
-  const SpmmJob J = jobs[r];
-  const int64_t local = b - first[r];
+  const int r = find_job(tab.first, tab.R, b);
+  const SpmmJob& J = tab.job[r];
+  const int64_t local = b - tab.first[r];
   if (J.ncols % 4 == 0)
     spmm_rec4_block<kBatchRpw, true>(J.X, J.Y, J.nrows, J.ncols, J.rp, J.rec, J.srp, J.sl, J.VT,
                                      J.hd_row, J.hd_col, J.e_nuc, J.Vrow, J.scol, J.n, J.accumulate,
@@ -444,12 +452,11 @@ struct TransJob {
 };
 
 // transposes of several problems in one launch (problem r's tiles [first[r], first[r+1]))
-__global__ void k_transpose_batch(const TransJob* __restrict__ jobs,
-                                  const int64_t* __restrict__ first, int R) {
+__global__ void k_transpose_batch(const __grid_constant__ JobTab<TransJob> tab) {
   const int64_t b = blockIdx.x;
-  const int r = find_job(first, R, b);
-  const TransJob J = jobs[r];
-  const int64_t local = b - first[r];
+  const int r = find_job(tab.first, tab.R, b);
+  const TransJob& J = tab.job[r];
+  const int64_t local = b - tab.first[r];
   transpose_tile<float>(J.in, J.out, J.rows, J.cols, 0, local % J.col_tiles, local / J.col_tiles);
 }
 
@@ -692,11 +699,28 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   return rc;
 }
 
+// Launch the jobs in tables of kMaxJobs; per_job(i, job) fills job i and returns its
+// block count.
+template <typename J, typename Fill, typename Kern>
+static int launch_jobs(int R, Fill per_job, Kern kern, dim3 block, cudaStream_t s) {
+  for (int r0 = 0; r0 < R; r0 += kMaxJobs) {
+    JobTab<J> tab;
+    tab.R = std::min(kMaxJobs, R - r0);
+    tab.first[0] = 0;
+    for (int i = 0; i < tab.R; ++i) tab.first[i + 1] = tab.first[i] + per_job(r0 + i, tab.job[i]);
+    if (tab.first[tab.R] == 0) continue;
+    kern<<<(unsigned)tab.first[tab.R], block, 0, s>>>(tab);
+    HQ_LAUNCH_CHECK();
+  }
+  return HINQS_OK;
+}
+
 int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
   std::vector<int> f32;
   for (int i = 0; i < n; ++i) {
     const SigmaReq& r = reqs[i];
-    if (r.precision == HINQS_PREC_FP64 || !r.la->rec32 || !r.lb->rec32) {
+    if (r.precision == HINQS_PREC_FP64 || !r.la->rec32 || !r.lb->rec32 ||
+        r.B->Na * r.B->Nb >= kBatchSoloN) {
       HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
     } else {
       f32.push_back(i);
@@ -705,43 +729,29 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
   if (f32.empty()) return HINQS_OK;
   const int R = (int)f32.size();
   std::vector<float*> CT(R, nullptr), ST(R, nullptr);
-  SpmmJob* d_spmm = nullptr;
-  TransJob* d_tr = nullptr;
-  int64_t* d_first = nullptr;
   auto run = [&]() -> int {
     for (int i = 0; i < R; ++i) {
       const int64_t N = reqs[f32[i]].B->Na * reqs[f32[i]].B->Nb;
       HQ_TRY(dalloc(&CT[i], N, s));
       HQ_TRY(dalloc(&ST[i], N, s));
     }
-    HQ_TRY(dalloc(&d_spmm, R, s));
-    HQ_TRY(dalloc(&d_tr, R, s));
-    HQ_TRY(dalloc(&d_first, R + 1, s));
-    std::vector<int64_t> first(R + 1, 0);
     // a transpose stage over every request: in (rows x cols) -> out
     auto transpose_all = [&](bool forward) -> int {
-      std::vector<TransJob> jobs(R);
-      for (int i = 0; i < R; ++i) {
+      auto fill = [&](int i, TransJob& j) -> int64_t {
         const SigmaReq& r = reqs[f32[i]];
         const int64_t rows = forward ? r.B->Na : r.B->Nb, cols = forward ? r.B->Nb : r.B->Na;
-        jobs[i] = TransJob{forward ? static_cast<const float*>(r.x) : ST[i],
-                           forward ? CT[i] : static_cast<float*>(r.y), rows, cols, ceil_div(cols, 32)};
-        first[i + 1] = first[i] + jobs[i].col_tiles * ceil_div(rows, 32);
-      }
-      HQ_CUDA(cudaMemcpyAsync(d_tr, jobs.data(), R * sizeof(TransJob), cudaMemcpyHostToDevice, s));
-      HQ_CUDA(cudaMemcpyAsync(d_first, first.data(), (R + 1) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, s));
-      k_transpose_batch<<<(unsigned)first[R], dim3(32, 8), 0, s>>>(d_tr, d_first, R);
-      HQ_LAUNCH_CHECK();
-      return HINQS_OK;
+        j = TransJob{forward ? static_cast<const float*>(r.x) : ST[i],
+                     forward ? CT[i] : static_cast<float*>(r.y), rows, cols, ceil_div(cols, 32)};
+        return j.col_tiles * ceil_div(rows, 32);
+      };
+      return launch_jobs<TransJob>(R, fill, k_transpose_batch, dim3(32, 8), s);
     };
     // a row-product stage over every request: beta rows on C^T, or alpha rows on C
     auto rows_all = [&](bool beta) -> int {
-      std::vector<SpmmJob> jobs(R);
-      for (int i = 0; i < R; ++i) {
+      auto fill = [&](int i, SpmmJob& j) -> int64_t {
         const SigmaReq& r = reqs[f32[i]];
         const hinqs_links_s* L = beta ? r.lb : r.la;
-        SpmmJob j{};
+        j = SpmmJob{};
         j.X = beta ? CT[i] : static_cast<const float*>(r.x);
         j.Y = beta ? ST[i] : static_cast<float*>(r.y);
         j.nrows = beta ? r.B->Nb : r.B->Na;
@@ -759,15 +769,9 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
         j.n = r.H->n;
         j.accumulate = beta ? 0 : 1;
         j.col_blocks = ceil_div(j.ncols, 128);
-        jobs[i] = j;
-        first[i + 1] = first[i] + j.col_blocks * ceil_div(j.nrows, kRowWarps * kBatchRpw);
-      }
-      HQ_CUDA(cudaMemcpyAsync(d_spmm, jobs.data(), R * sizeof(SpmmJob), cudaMemcpyHostToDevice, s));
-      HQ_CUDA(cudaMemcpyAsync(d_first, first.data(), (R + 1) * sizeof(int64_t),
-                              cudaMemcpyHostToDevice, s));
-      k_spmm_rec4_batch<<<(unsigned)first[R], 32 * kRowWarps, 0, s>>>(d_spmm, d_first, R);
-      HQ_LAUNCH_CHECK();
-      return HINQS_OK;
+        return j.col_blocks * ceil_div(j.nrows, kRowWarps * kBatchRpw);
+      };
+      return launch_jobs<SpmmJob>(R, fill, k_spmm_rec4_batch, dim3(32 * kRowWarps), s);
     };
     HQ_TRY(transpose_all(true));   // C^T
     HQ_TRY(rows_all(true));        // beta same-spin + alpha self x beta singles, on C^T
@@ -798,9 +802,6 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
     dfree(CT[i], s);
     dfree(ST[i], s);
   }
-  dfree(d_spmm, s);
-  dfree(d_tr, s);
-  dfree(d_first, s);
   return rc;
 }
 

@@ -145,6 +145,17 @@ struct Queue {
   int64_t total = 0;
 };
 
+// The problems of one batched launch, passed by value as a kernel parameter (no host to
+// device copy, so that a launch never waits for the host): kMaxBatch problems at most
+// per launch, a longer batch is split.
+constexpr int kMaxBatch = 48;
+struct BatchTab {
+  Args reqs[kMaxBatch];
+  int64_t starts[kMaxBatch + 1];
+  int R;
+  int64_t total;
+};
+
 // Shared-memory bytes of one CTA (the layout of the kernel below).
 __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int KB, int64_t Nb,
                                              bool crow) {
@@ -162,7 +173,7 @@ __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int 
 // t+1 into the other A buffer; then they read tile t's accumulator (its own TMEM
 // columns) and add it into sigma with coalesced reductions (lane = beta string).
 template <int NW, int SPLIT, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A0, Queue Q) {
+__device__ __forceinline__ void sigma_ab_tc_body(const Args& A0, const Queue& Q) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ int64_t s_item;
   __shared__ int s_req;
@@ -399,6 +410,24 @@ __global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A0, Queue Q) {
   }
 }
 
+template <int NW, int SPLIT, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
+  sigma_ab_tc_body<NW, SPLIT, STAGES>(A, Queue{});
+}
+
+// The batched form: the table lives in the parameter space for the whole launch.
+template <int NW, int SPLIT, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc_batch(
+    const __grid_constant__ BatchTab tab, unsigned long long* counter) {
+  Queue q;
+  q.reqs = tab.reqs;
+  q.starts = tab.starts;
+  q.R = tab.R;
+  q.counter = counter;
+  q.total = tab.total;
+  sigma_ab_tc_body<NW, SPLIT, STAGES>(tab.reqs[0], q);
+}
+
 // BF16 (hi, lo) rows of the folded integral matrix: row pq, column k < K holds
 // (pq|rs) for the k-th folded pair (r >= s), columns K..8KB-1 are zero.
 __global__ void k_btable(const float* __restrict__ eri32, int n, int K, int KB,
@@ -442,30 +471,26 @@ static int launch(const Args& a, bool crow, cudaStream_t s) {
   if (per_sm < 1)
     return fail(HINQS_ERR_ARG, "tensor-core sigma: a CTA of %zu bytes does not fit an SM", bytes);
   const int grid = (int)std::min<int64_t>(a.Na, (int64_t)per_sm * kNumSMs);
-  kern<<<grid, kThreads, req, s>>>(b, Queue{});
+  kern<<<grid, kThreads, req, s>>>(b);
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
 }
 
 // The batched launch: one persistent grid over the (problem, alpha string) items of
 // every problem in reqs (same n_orb; the C row staged when the largest fits), one
-// stage.  kTcNoFit when the operand tiles do not fit.
+// stage, kMaxBatch problems per launch.  kTcNoFit when the operand tiles do not fit.
+// Nothing waits for the device: the table is a kernel parameter and the item counter
+// a stream-ordered allocation.
 template <int NW, int SPLIT>
 static int launch_batch(std::vector<Args>& reqs, cudaStream_t s) {
-  int64_t nb_max = 0, total = 0;
+  int64_t nb_max = 0;
   for (const Args& a : reqs) nb_max = std::max(nb_max, a.Nb);
   const size_t lim = (size_t)smem_optin_limit();
   const int KB = reqs[0].KB;
-  bool crow = smem_bytes(NW, SPLIT, 1, KB, nb_max, true) <= lim;
+  const bool crow = smem_bytes(NW, SPLIT, 1, KB, nb_max, true) <= lim;
   if (!crow && smem_bytes(NW, SPLIT, 1, KB, nb_max, false) > lim) return kTcNoFit;
-  std::vector<int64_t> starts(reqs.size() + 1, 0);
-  for (size_t r = 0; r < reqs.size(); ++r) {
-    reqs[r].crow_smem = crow ? 1 : 0;
-    starts[r + 1] = starts[r] + reqs[r].Na;
-  }
-  total = starts.back();
   const size_t bytes = smem_bytes(NW, SPLIT, 1, KB, nb_max, crow);
-  auto kern = k_sigma_ab_tc<NW, SPLIT, 1>;
+  auto kern = k_sigma_ab_tc_batch<NW, SPLIT, 1>;
   HQ_TRY(allow_max_smem(kern));
   const int cap = 512 / NW;
   cudaFuncAttributes fa;
@@ -477,33 +502,30 @@ static int launch_batch(std::vector<Args>& reqs, cudaStream_t s) {
   const int per_sm = std::min(std::min(cap, (int)(233472 / (req + 1024))),
                               std::min(by_regs, 2048 / kThreads));
   if (per_sm < 1) return kTcNoFit;
-  Args* d_reqs = nullptr;
-  int64_t* d_starts = nullptr;
+  const int chunks = (int)((reqs.size() + kMaxBatch - 1) / kMaxBatch);
   unsigned long long* d_counter = nullptr;
+  HQ_TRY(dalloc(&d_counter, (size_t)chunks, s));
   auto run = [&]() -> int {
-    HQ_TRY(dalloc(&d_reqs, reqs.size(), s));
-    HQ_TRY(dalloc(&d_starts, starts.size(), s));
-    HQ_TRY(dalloc(&d_counter, 1, s));
-    HQ_CUDA(cudaMemcpyAsync(d_reqs, reqs.data(), reqs.size() * sizeof(Args), cudaMemcpyHostToDevice, s));
-    HQ_CUDA(cudaMemcpyAsync(d_starts, starts.data(), starts.size() * sizeof(int64_t),
-                            cudaMemcpyHostToDevice, s));
-    HQ_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), s));
-    Queue q;
-    q.reqs = d_reqs;
-    q.starts = d_starts;
-    q.R = (int)reqs.size();
-    q.counter = d_counter;
-    q.total = total;
-    const int grid = (int)std::min<int64_t>(total, (int64_t)per_sm * kNumSMs);
-    kern<<<grid, kThreads, req, s>>>(reqs[0], q);
-    HQ_LAUNCH_CHECK();
-    // the host arrays are copied before the call returns
-    HQ_CUDA(cudaStreamSynchronize(s));
+    HQ_CUDA(cudaMemsetAsync(d_counter, 0, chunks * sizeof(unsigned long long), s));
+    for (int c = 0; c < chunks; ++c) {
+      BatchTab tab;
+      const size_t r0 = (size_t)c * kMaxBatch;
+      tab.R = (int)std::min<size_t>(kMaxBatch, reqs.size() - r0);
+      tab.starts[0] = 0;
+      for (int r = 0; r < tab.R; ++r) {
+        tab.reqs[r] = reqs[r0 + r];
+        tab.reqs[r].crow_smem = crow ? 1 : 0;
+        tab.starts[r + 1] = tab.starts[r] + tab.reqs[r].Na;
+      }
+      tab.total = tab.starts[tab.R];
+      if (tab.total == 0) continue;
+      const int grid = (int)std::min<int64_t>(tab.total, (int64_t)per_sm * kNumSMs);
+      kern<<<grid, kThreads, req, s>>>(tab, d_counter + c);
+      HQ_LAUNCH_CHECK();
+    }
     return HINQS_OK;
   };
   const int rc = run();
-  dfree(d_reqs, s);
-  dfree(d_starts, s);
   dfree(d_counter, s);
   return rc;
 }

@@ -205,3 +205,21 @@ def test_batch_lockstep_equals_worker_form(small_scan):
     assert a[1].iterations <= 2
     short = hq.davidson_batch(probs, max_iter=3, n_streams=0)
     assert any(r.status == hq.NOT_CONVERGED for r in short)
+
+
+def test_batch_lockstep_with_large_geometry(small_scan):
+    """A geometry of 2^20 determinants or more runs on a worker stream beside the
+    lockstep rounds of the small ones: the energies equal those of single solves."""
+    ws, gs, probs = small_scan
+    big = synth.bond_scan_workload(n_geom=1)[0]
+    pb = _problem(big)
+    assert pb[1].N >= 1 << 20
+    opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB,
+                tol_residual=1e-6, tol_energy=1e-9, max_iter=600)
+    res = hq.davidson_batch(probs[:3] + [pb], n_streams=0, **opts)
+    single = [hq.davidson(*p, **opts) for p in probs[:3] + [pb]]
+    for r, s1 in zip(res, single):
+        assert r.status == hq.OK and s1.status == hq.OK
+        assert abs(r.energy - s1.energy) < 1e-8
+    for r, (_, _, _, E, _) in zip(res[:3], gs[:3]):
+        assert abs(r.energy - E) < 1e-6
