@@ -701,7 +701,7 @@ def main():
     if args.probe:
         part, pname, *rest = args.probe.split(":")
         prec = {"fp64": hq.PREC_FP64, "fp32": hq.PREC_FP32, "bf16ab": hq.PREC_FP32_BF16AB,
-                "bf16x3ab": hq.PREC_FP32_BF16X3AB}[pname]
+                "bf16x3ab": hq.PREC_FP32_BF16X3AB, "bf16c": hq.PREC_FP32_BF16C}[pname]
         ham_p = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
         sub_p = hq.build_subspace(a_d, b_d, n, na, nb)
         la_p, lb_p = hq.string_links(ham_p, sub_p, 0), hq.string_links(ham_p, sub_p, 1)
@@ -820,7 +820,8 @@ def main():
         return ts[len(ts) // 2]
 
     precs = {"fp64": (hq.PREC_FP64, c64), "fp32": (hq.PREC_FP32, c32),
-             "fp32_bf16ab": (hq.PREC_FP32_BF16AB, c32), "fp32_bf16x3ab": (hq.PREC_FP32_BF16X3AB, c32)}
+             "fp32_bf16ab": (hq.PREC_FP32_BF16AB, c32), "fp32_bf16x3ab": (hq.PREC_FP32_BF16X3AB, c32),
+             "fp32_bf16c": (hq.PREC_FP32_BF16C, c32)}
     t_sig = {}
     for name, (p, x) in precs.items():
         out = torch.empty_like(x)
@@ -837,7 +838,9 @@ def main():
                 "mixed_fp32": dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32,
                                    inner_tol=3e-2),
                 "mixed_bf16x3": dict(precision=hq.DAVIDSON_MIXED,
-                                     inner_precision=hq.PREC_FP32_BF16X3AB, inner_tol=3e-2)}
+                                     inner_precision=hq.PREC_FP32_BF16X3AB, inner_tol=3e-2),
+                "mixed_bf16c": dict(precision=hq.DAVIDSON_MIXED,
+                                    inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2)}
     runs = {}
     for name, kw in variants.items():
         runs[name] = hq.davidson(ham, sub, la, lb, tol_residual=1e-6, tol_energy=1e-8,

@@ -77,6 +77,14 @@ extern "C" {
  * shared memory (e.g. the split mode at n_orb = 26), the opposite-spin term is
  * computed by the FP32 CUDA-core kernel of HINQS_PREC_FP32 instead (more accurate). */
 #define HINQS_PREC_FP32_BF16X3AB 3
+/* c, sigma: float; the opposite-spin term as HINQS_PREC_FP32_BF16AB, and the
+ * same-spin row products (H_a C, C H_b^T and the alpha-diagonal x beta-singles term)
+ * on C rounded to BF16 (round to nearest even, once per product; products and sums
+ * in FP32), so that a link reads half the bytes; the diagonal term on the FP32 C.
+ * Not in the paper: an inner-product precision for the mixed Davidson, whose FP64
+ * refinement removes the rounding.  Links of more than 2^32 padded elements take the
+ * FP32 same-spin half. */
+#define HINQS_PREC_FP32_BF16C 4
 
 /* Davidson precision */
 #define HINQS_DAVIDSON_FP64 0   /* every sigma in FP64 */
@@ -246,7 +254,8 @@ typedef struct hinqs_davidson_opts {
   double* trace_time;   /* host [trace_cap] or NULL: seconds since the call began */
   int* trace_kind;      /* host [trace_cap] or NULL: 0 = FP64 iterate, 1 = FP32 inner iterate */
   int inner_precision;  /* mixed: sigma precision of the inner products: HINQS_PREC_FP32,
-                           HINQS_PREC_FP32_BF16AB or HINQS_PREC_FP32_BF16X3AB */
+                           HINQS_PREC_FP32_BF16AB, HINQS_PREC_FP32_BF16X3AB or
+                           HINQS_PREC_FP32_BF16C */
   int restart_keep;     /* vectors kept at a restart (0 = default).  FP64: the current
                            Ritz vector, the previous one and the next-lowest Ritz vectors,
                            this many in all (1 .. max_subspace - 1); mixed: the FP64 anchor

@@ -38,7 +38,7 @@ ERR_ARG, ERR_PARTICLE_NUMBER, ERR_ASYMMETRIC, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ER
     -1, -2, -3, -4, -5, -6, -7)
 DROP_BAD, ERROR_BAD, FULL_SPACE = 0x0, 0x1, 0x2
 CHECK_SYMMETRY = 0x1
-PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB = 0, 1, 2, 3
+PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB, PREC_FP32_BF16C = 0, 1, 2, 3, 4
 DAVIDSON_FP64, DAVIDSON_MIXED = 0, 1
 BASIS_COLD_START, BASIS_RESCORE, BASIS_APPEND = 0, 1, 2
 

@@ -95,7 +95,7 @@ int autotune_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, hinqs_links_s
       // tensor-core pipeline depth 1 or 2 of the persistent kernel, or 3: the
       // tile-stationary warp-specialised kernel (BF16 operands only)
       for (int st : {1, 2, 3})
-        if (st != 3 || precision == HINQS_PREC_FP32_BF16AB) cands.push_back({r, 0, st});
+        if (st != 3 || precision != HINQS_PREC_FP32_BF16X3AB) cands.push_back({r, 0, st});
     }
   }
   cudaEvent_t e0, e1;
@@ -197,7 +197,7 @@ using namespace hinqs;
 extern "C" int hinqs_autotune(const hinqs_ham* H, const hinqs_subspace* B, hinqs_links* la,
                               hinqs_links* lb, int precision, double* best_ms, void* stream) {
   HQ_TRY(check_triplet(H, B, la, lb, "hinqs_autotune"));
-  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16C)
     return fail(HINQS_ERR_ARG, "hinqs_autotune: unknown precision %d", precision);
   return autotune_impl(H, B, la, lb, precision, best_ms, (cudaStream_t)stream);
 }

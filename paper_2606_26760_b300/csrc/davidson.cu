@@ -1218,7 +1218,8 @@ int hinqs::davidson_run(const hinqs_ham* H, const hinqs_subspace* B, const hinqs
   if (o.precision != HINQS_DAVIDSON_FP64 && o.precision != HINQS_DAVIDSON_MIXED)
     return fail(HINQS_ERR_ARG, "%s: unknown precision %d", who, o.precision);
   if (o.precision == HINQS_DAVIDSON_MIXED && o.inner_precision != HINQS_PREC_FP32 &&
-      o.inner_precision != HINQS_PREC_FP32_BF16AB && o.inner_precision != HINQS_PREC_FP32_BF16X3AB)
+      o.inner_precision != HINQS_PREC_FP32_BF16AB && o.inner_precision != HINQS_PREC_FP32_BF16X3AB &&
+      o.inner_precision != HINQS_PREC_FP32_BF16C)
     return fail(HINQS_ERR_ARG, "%s: unknown inner precision %d", who, o.inner_precision);
   // the list operator has no tensor-core form: its inner products run in FP32
   if (L && o.precision == HINQS_DAVIDSON_MIXED) o.inner_precision = HINQS_PREC_FP32;

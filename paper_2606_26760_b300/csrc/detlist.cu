@@ -300,7 +300,7 @@ int sigma_list_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   if (precision == HINQS_PREC_FP64) {
     k_sigma_list<double><<<grid, 32 * kListWarps, 0, s>>>(list_args<double>(H, la, lb, L),
                                                            (const double*)c, (double*)sigma);
-  } else if (precision >= HINQS_PREC_FP32 && precision <= HINQS_PREC_FP32_BF16X3AB) {
+  } else if (precision >= HINQS_PREC_FP32 && precision <= HINQS_PREC_FP32_BF16C) {
     k_sigma_list<float><<<grid, 32 * kListWarps, 0, s>>>(list_args<float>(H, la, lb, L),
                                                           (const float*)c, (float*)sigma);
   } else {

@@ -134,6 +134,11 @@ struct hinqs_links_s {
   // rec64 {off, 0, double bits}; null when N_a * N_b >= 2^32
   int2* rec32 = nullptr;
   int4* rec64 = nullptr;
+  // the same records for the BF16 copy of the operand (HINQS_PREC_FP32_BF16C), whose
+  // rows are padded to ld16 = the other dimension rounded up to 64 elements (128-byte
+  // rows): {J * ld16, float bits}; null when N * ld16 >= 2^32
+  int2* rec16 = nullptr;
+  int64_t ld16 = 0;
   // sigma tiles chosen by hinqs_autotune (0 = built-in default): rows per warp of
   // the row products that use these links, and the alpha-single chunk width of the
   // CUDA-core opposite-spin kernel (read from the alpha links)

@@ -195,7 +195,7 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
 // Packed link records for the row products (see hinqs_links_s).
 __global__ void k_pack_records(const int32_t* __restrict__ col, const double* __restrict__ h64,
                                int64_t nnz, int64_t other, int2* __restrict__ r32,
-                               int4* __restrict__ r64) {
+                               int4* __restrict__ r64, int64_t ld16, int2* __restrict__ r16) {
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < nnz;
        k += (int64_t)gridDim.x * blockDim.x) {
     const uint32_t off = (uint32_t)((int64_t)col[k] * other);
@@ -203,6 +203,7 @@ __global__ void k_pack_records(const int32_t* __restrict__ col, const double* __
     r32[k] = make_int2((int)off, __float_as_int((float)h));
     const long long b = __double_as_longlong(h);
     r64[k] = make_int4((int)off, 0, (int)(b & 0xffffffffll), (int)(b >> 32));
+    if (r16) r16[k] = make_int2((int)(uint32_t)((int64_t)col[k] * ld16), __float_as_int((float)h));
   }
 }
 
@@ -247,6 +248,7 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->scount, s);
   dfree(L->rec32, s);
   dfree(L->rec64, s);
+  dfree(L->rec16, s);
 }
 
 }  // namespace hinqs
@@ -332,9 +334,13 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
   }
   if (!rc && (uint64_t)B->Na * (uint64_t)B->Nb < (1ull << 32)) {
     const int64_t other = spin ? B->Na : B->Nb;
-    if (!(rc = dalloc(&L->rec32, L->nnz, s)) && !(rc = dalloc(&L->rec64, L->nnz, s))) {
+    const int64_t ld16 = (other + 63) / 64 * 64;
+    const bool want16 = (uint64_t)N * (uint64_t)ld16 < (1ull << 32);
+    if (!(rc = dalloc(&L->rec32, L->nnz, s)) && !(rc = dalloc(&L->rec64, L->nnz, s)) &&
+        !(want16 && (rc = dalloc(&L->rec16, L->nnz, s)))) {
+      L->ld16 = want16 ? ld16 : 0;
       k_pack_records<<<(unsigned)std::min<int64_t>(ceil_div(L->nnz, 256) + 1, 16 * kNumSMs), 256, 0,
-                       s>>>(L->col, L->hval64, L->nnz, other, L->rec32, L->rec64);
+                       s>>>(L->col, L->hval64, L->nnz, other, L->rec32, L->rec64, ld16, L->rec16);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "k_pack_records", __FILE__, __LINE__);
     }

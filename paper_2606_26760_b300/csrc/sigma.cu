@@ -12,6 +12,8 @@
 // lanes 32 consecutive columns, so every link record is a warp-uniform load and
 // every operand load is a coalesced 128/256-byte row segment; 32 consecutive rows
 // per block share most of their linked rows, which stay in L1.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <vector>
 
@@ -351,6 +353,162 @@ __global__ void __launch_bounds__(256, 4) k_spmm_rec4(
     const float* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
   spmm_rec4_block<RPW, true>(X, Y, nrows, ncols, rp, rec, srp, sl, VT, hd_row, hd_col, e_nuc, Vrow,
                              scol, n, accumulate, blockIdx.x, blockIdx.y);
+}
+
+// ---------------------------------------------------------------------------
+// HINQS_PREC_FP32_BF16C: the same-spin row products read a BF16 copy of C (rounded
+// once per product) with rows padded to 128 bytes, so a link moves half the bytes of
+// the FP32 form and no operand segment straddles an extra line; products and sums in
+// FP32, the diagonal term on the FP32 C.
+
+// C (rows x cols, FP32) -> Cb (rows x ldc, BF16, round to nearest even) and its
+// transpose CTb (cols x ldr, BF16); the padding columns of both are zero.  The grid
+// covers ldc columns and ldr rows in 32 x 32 tiles.
+__global__ void k_bf16_pack(const float* __restrict__ C, int64_t rows, int64_t cols,
+                            __nv_bfloat16* __restrict__ Cb, int64_t ldc,
+                            __nv_bfloat16* __restrict__ CTb, int64_t ldr) {
+  __shared__ float tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = by + k, j = bx + threadIdx.x;
+    const float v = (i < rows && j < cols) ? C[i * cols + j] : 0.f;
+    tile[k][threadIdx.x] = v;
+    if (i < rows && j < ldc) Cb[i * ldc + j] = __float2bfloat16_rn(v);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t j = bx + k, i = by + threadIdx.x;
+    if (j < cols && i < ldr) CTb[j * ldr + i] = __float2bfloat16_rn(tile[threadIdx.x][k]);
+  }
+}
+
+// eight consecutive FP32 values from p (nv of them valid): two 16-byte loads when the
+// rows are 16-byte aligned (then nv is 4 or 8), else guarded scalar loads
+template <bool ALIGNED>
+__device__ __forceinline__ void ld8(const float* __restrict__ p, int nv, float* v) {
+  if (ALIGNED) {
+    const float4 a = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 b = nv > 4 ? __ldg(reinterpret_cast<const float4*>(p + 4))
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+    v[0] = a.x, v[1] = a.y, v[2] = a.z, v[3] = a.w, v[4] = b.x, v[5] = b.y, v[6] = b.z, v[7] = b.w;
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = i < nv ? __ldg(p + i) : 0.f;
+  }
+}
+
+template <bool ALIGNED>
+__device__ __forceinline__ void st8(float* __restrict__ p, int nv, const float* v) {
+  if (ALIGNED) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    if (nv > 4) *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (i < nv) p[i] = v[i];
+  }
+}
+
+// acc[0..7] += h * (eight BF16 values packed in x); BF16 -> FP32 is a 16-bit shift
+__device__ __forceinline__ void fma_bf16x8(float h, const uint4& x, float* acc) {
+  const uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    acc[2 * i] = fmaf(h, __uint_as_float(w[i] << 16), acc[2 * i]);
+    acc[2 * i + 1] = fmaf(h, __uint_as_float(w[i] & 0xffff0000u), acc[2 * i + 1]);
+  }
+}
+
+// The row product of k_spmm_rec4 on the BF16 operand: eight columns per lane (one
+// 16-byte load per link and lane, a 512-byte segment of a 128-byte aligned row per
+// warp), records {J * ldx, h} read 32 at a time and broadcast by shuffles.  X32 is
+// the FP32 C for the diagonal term (alpha rows only); VT rows are FP32.
+template <int RPW, bool ALIGNED>
+__global__ void __launch_bounds__(256, 3) k_spmm_bf16(
+    const __nv_bfloat16* __restrict__ Xb, int64_t ldx, const float* __restrict__ X32,
+    float* __restrict__ Y, int64_t nrows, int64_t ncols, const int64_t* __restrict__ rp,
+    const int2* __restrict__ rec, const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+    const float* __restrict__ VT, const double* __restrict__ hd_row,
+    const double* __restrict__ hd_col, double e_nuc, const float* __restrict__ Vrow,
+    const uint64_t* __restrict__ scol, int n, int accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * 8;
+  const bool active = c0 < ncols;
+  const int64_t cc = active ? c0 : 0;
+  const int nv = active ? (int)min64(8, ncols - c0) : 0;  // columns of this lane
+  const int n2 = n * n;
+  const unsigned full = 0xffffffffu;
+  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int64_t I = I0 + rr;
+    if (I >= nrows) break;  // warp-uniform
+    float acc[8];
+#pragma unroll
+    for (int v = 0; v < 8; ++v) acc[v] = 0.f;
+    if (accumulate && active) ld8<ALIGNED>(Y + I * ncols + c0, nv, acc);
+    if (hd_row) {
+      const float v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : 0.f;
+      const float v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : 0.f;
+      uint64_t b[8];
+      float xs[8];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) b[v] = v < nv ? scol[cc + v] : 0, xs[v] = 0.f;
+      for (int j = 0; j < n; ++j) {
+        const float a = __shfl_sync(full, j < 32 ? v0 : v1, j & 31);
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+          if ((b[v] >> j) & 1ull) xs[v] += a;
+      }
+      if (active) {
+        float x[8];
+        ld8<ALIGNED>(X32 + I * ncols + c0, nv, x);
+        const double hr = hd_row[I] + e_nuc;
+#pragma unroll
+        for (int v = 0; v < 8; ++v)
+          if (v < nv) acc[v] += ((float)(hr + hd_col[c0 + v]) + xs[v]) * x[v];
+      }
+    }
+    const int2* __restrict__ r = rec + rp[I];
+    const int nk = (int)(rp[I + 1] - rp[I]);
+    const __nv_bfloat16* __restrict__ Xc = Xb + cc;
+    for (int k0 = 0; k0 < nk; k0 += 32) {
+      const int2 mine = (k0 + lane < nk) ? __ldg(r + k0 + lane) : make_int2(0, 0);
+      const int cnt = min(32, nk - k0);
+      int u = 0;
+      for (; u + 8 <= cnt; u += 8) {
+        uint4 x[8];
+        float h[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+          const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u + v);
+          h[v] = __int_as_float(__shfl_sync(full, mine.y, u + v));
+          x[v] = __ldg(reinterpret_cast<const uint4*>(Xc + off));
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) fma_bf16x8(h[v], x[v], acc);
+      }
+      for (; u < cnt; ++u) {
+        const uint32_t off = (uint32_t)__shfl_sync(full, mine.x, u);
+        const float h = __int_as_float(__shfl_sync(full, mine.y, u));
+        fma_bf16x8(h, __ldg(reinterpret_cast<const uint4*>(Xc + off)), acc);
+      }
+    }
+    if (srp && active) {
+      for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
+        const int2 l = sl[q];
+        const int pair = (l.y > 0 ? l.y : -l.y) - 1;
+        float vt[8], t[8];
+        ld8<ALIGNED>(VT + (int64_t)pair * ncols + c0, nv, vt);
+#pragma unroll
+        for (int v = 0; v < 8; ++v) t[v] = 0.f;
+        fma_bf16x8(1.f, __ldg(reinterpret_cast<const uint4*>(Xb + (int64_t)l.x * ldx + c0)), t);
+        const float sg = l.y > 0 ? 1.f : -1.f;
+#pragma unroll
+        for (int v = 0; v < 8; ++v) acc[v] += sg * vt[v] * t[v];
+      }
+    }
+    if (active) st8<ALIGNED>(Y + I * ncols + c0, nv, acc);
+  }
 }
 
 // The same row product for several problems in one launch: problem r's blocks are
@@ -699,6 +857,74 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   return rc;
 }
 
+// One row product on the BF16 operand (rows per warp from the links' tuning).
+static int spmm_bf16(const __nv_bfloat16* Xb, int64_t ldx, const float* X32, float* Y,
+                     int64_t nrows, int64_t ncols, const hinqs_links_s* L,
+                     const hinqs_links_s* Lsingles, const float* VT, const double* hd_row,
+                     const double* hd_col, double e_nuc, const float* Vrow, const uint64_t* scol,
+                     int n, int accumulate, cudaStream_t s) {
+  const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
+  const int2* sl = Lsingles ? Lsingles->slink : nullptr;
+  const int rpw = L->tune_rows ? L->tune_rows : kRowsPerWarp;
+  auto go = [&](auto kern, int r) {
+    const dim3 g((unsigned)ceil_div(ncols, 256), (unsigned)ceil_div(nrows, kRowWarps * r));
+    kern<<<g, 32 * kRowWarps, 0, s>>>(Xb, ldx, X32, Y, nrows, ncols, L->row_ptr, L->rec16, srp,
+                                      sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n, accumulate);
+  };
+  if (ncols % 4 == 0) {
+    if (rpw == 2) go(k_spmm_bf16<2, true>, 2);
+    else if (rpw == 8) go(k_spmm_bf16<8, true>, 8);
+    else go(k_spmm_bf16<4, true>, 4);
+  } else {
+    if (rpw == 2) go(k_spmm_bf16<2, false>, 2);
+    else if (rpw == 8) go(k_spmm_bf16<8, false>, 8);
+    else go(k_spmm_bf16<4, false>, 4);
+  }
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
+// HINQS_PREC_FP32_BF16C: the same-spin half on BF16 copies of C and C^T (rows padded
+// to 64 elements), the opposite-spin half as HINQS_PREC_FP32_BF16AB.  Links without
+// BF16 records (N * padded row >= 2^32) take the FP32 same-spin half instead.
+static int sigma_bf16c(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                       const hinqs_links_s* lb, const float* c, float* sig, cudaStream_t s,
+                       int parts) {
+  if (!la->rec16 || !lb->rec16 || !la->rec32 || !lb->rec32) {
+    HQ_TRY(sigma_impl<float>(H, B, la, lb, c, sig, s, 1, parts & kSameSpin));
+    return (parts & kOppositeSpin) ? sigma_impl<float>(H, B, la, lb, c, sig, s, 1, kOppositeSpin)
+                                   : HINQS_OK;
+  }
+  if (parts & kSameSpin) {
+    const int64_t Na = B->Na, Nb = B->Nb, ldc = la->ld16, ldr = lb->ld16;
+    __nv_bfloat16 *Cb = nullptr, *CTb = nullptr;
+    float* ST = nullptr;
+    int rc = HINQS_OK;
+    if (!(rc = dalloc(&Cb, (size_t)(Na * ldc), s)) && !(rc = dalloc(&CTb, (size_t)(Nb * ldr), s)) &&
+        !(rc = dalloc(&ST, (size_t)(Na * Nb), s))) {
+      auto run = [&]() -> int {
+        const dim3 tg((unsigned)ceil_div(ldc, 32), (unsigned)ceil_div(ldr, 32));
+        k_bf16_pack<<<tg, dim3(32, 8), 0, s>>>(c, Na, Nb, Cb, ldc, CTb, ldr);
+        HQ_LAUNCH_CHECK();
+        // beta same-spin links and alpha-self x beta singles, rows = beta strings
+        HQ_TRY(spmm_bf16(CTb, ldr, nullptr, ST, Nb, Na, lb, lb, la->VT32, nullptr, nullptr, 0.0,
+                         nullptr, nullptr, H->n, 0, s));
+        HQ_TRY(transpose<float>(ST, sig, Nb, Na, 0, s));
+        // alpha same-spin links and the diagonal, rows = alpha strings
+        return spmm_bf16(Cb, ldc, c, sig, Na, Nb, la, nullptr, nullptr, la->hdiag, lb->hdiag,
+                         H->e_nuc, la->V32, B->sb, H->n, 1, s);
+      };
+      rc = run();
+    }
+    dfree(Cb, s);
+    dfree(CTb, s);
+    dfree(ST, s);
+    HQ_TRY(rc);
+  }
+  return (parts & kOppositeSpin) ? sigma_impl<float>(H, B, la, lb, c, sig, s, 1, kOppositeSpin)
+                                 : HINQS_OK;
+}
+
 // Launch the jobs in tables of kMaxJobs; per_job(i, job) fills job i and returns its
 // block count.
 template <typename J, typename Fill, typename Kern>
@@ -719,7 +945,8 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
   std::vector<int> f32;
   for (int i = 0; i < n; ++i) {
     const SigmaReq& r = reqs[i];
-    if (r.precision == HINQS_PREC_FP64 || !r.la->rec32 || !r.lb->rec32 ||
+    if (r.precision == HINQS_PREC_FP64 || r.precision == HINQS_PREC_FP32_BF16C ||
+        !r.la->rec32 || !r.lb->rec32 ||
         r.B->Na * r.B->Nb >= kBatchSoloN) {
       HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
     } else {
@@ -816,6 +1043,8 @@ int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_li
     return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 1, parts);
   if (precision == HINQS_PREC_FP32_BF16X3AB)
     return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 3, parts);
+  if (precision == HINQS_PREC_FP32_BF16C)
+    return sigma_bf16c(H, B, la, lb, (const float*)c, (float*)sigma, s, parts);
   return fail(HINQS_ERR_ARG, "hinqs_sigma: unknown precision %d", precision);
 }
 
@@ -874,11 +1103,18 @@ extern "C" int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_bet
                                           int precision, size_t* bytes) {
   if (!bytes || n_alpha_strings < 0 || n_beta_strings < 0)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: NULL output or negative size");
-  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16C)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: unknown precision %d", precision);
   // the transposed vector and the transposed partial result of the same-spin half
+  // (BF16C: the two padded BF16 copies and the transposed FP32 partial result)
   const size_t elem = precision == HINQS_PREC_FP64 ? sizeof(double) : sizeof(float);
   *bytes = 2 * (size_t)(n_alpha_strings * n_beta_strings) * elem;
+  if (precision == HINQS_PREC_FP32_BF16C) {
+    const size_t pa = (size_t)(n_alpha_strings + 63) / 64 * 64;
+    const size_t pb = (size_t)(n_beta_strings + 63) / 64 * 64;
+    *bytes = 2 * ((size_t)n_alpha_strings * pb + (size_t)n_beta_strings * pa) +
+             4 * (size_t)(n_alpha_strings * n_beta_strings);
+  }
   return HINQS_OK;
 }
 
@@ -890,7 +1126,8 @@ static int sigma_entry(const hinqs_ham* H, const hinqs_subspace* B, const hinqs_
   if (c == sigma) return fail(HINQS_ERR_ARG, "%s: c and sigma must not overlap", who);
   HQ_TRY(sigma_launch(H, B, la, lb, c, sigma, precision, (cudaStream_t)stream, parts));
   if ((parts & kOppositeSpin) &&
-      (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB))
+      (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB ||
+       precision == HINQS_PREC_FP32_BF16C))
     return tc_error_check((cudaStream_t)stream);
   return HINQS_OK;
 }
@@ -901,7 +1138,7 @@ extern "C" int hinqs_sigma_batch(int n, const hinqs_ham* const* hams,
                                  void* const* sigmas, int precision, void* stream) {
   if (n < 0 || (n > 0 && (!hams || !subs || !las || !lbs || !cs || !sigmas)))
     return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: NULL arrays");
-  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16X3AB)
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16C)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: unknown precision %d", precision);
   std::vector<SigmaReq> reqs;
   for (int g = 0; g < n; ++g) {
@@ -912,7 +1149,8 @@ extern "C" int hinqs_sigma_batch(int n, const hinqs_ham* const* hams,
   }
   if (n == 0) return HINQS_OK;
   HQ_TRY(sigma_batch_launch(reqs.data(), n, (cudaStream_t)stream));
-  if (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB)
+  if (precision == HINQS_PREC_FP32_BF16AB || precision == HINQS_PREC_FP32_BF16X3AB ||
+      precision == HINQS_PREC_FP32_BF16C)
     return tc_error_check((cudaStream_t)stream);
   return HINQS_OK;
 }

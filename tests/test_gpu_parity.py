@@ -259,12 +259,83 @@ def test_sigma_tensor_core_full_size(precision_workload):
         assert float(torch.max(torch.abs(s - s32))) <= rel * float(torch.max(torch.abs(s32)))
 
 
+def _bf16(x):
+    """Round to BF16 (round to nearest, ties to even), returned as float64."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_sigma_bf16c_mode(name):
+    """HINQS_PREC_FP32_BF16C against the oracle: C rounded to BF16 (u = 2^-9) in every
+    off-diagonal product bounds the error by ~1e-2 of the sigma scale; the diagonal
+    term stays on the FP32 C, so the error of hdiag * c is FP32-sized.  The small
+    cases have row lengths that are not multiples of 4 or of the 64-element padding
+    of the BF16 copies (the guarded loads and the padded tails)."""
+    B = built(name)
+    N = len(B.sa) * len(B.sb)
+    c = synth.random_vector(N, 1)
+    ref = oracle.sigma(B.H, B.sa, B.sb, c)
+    hd = oracle.diag(B.H, B.sa, B.sb)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=hq.PREC_FP32_BF16C).double().cpu().numpy()
+    assert np.all(np.abs(s - ref) <= 2e-2 * np.max(np.abs(ref - hd * c)) + 2e-5 * np.abs(ref) +
+                  1e-5 * np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("name", SMALL)
+def test_sigma_bf16c_exact_parts(name):
+    """What the BF16 operand changes and nothing else.  (1) For a vector whose entries
+    are BF16 numbers the rounding is the identity, so the mode equals the FP32
+    same-spin half plus the BF16 tensor-core term (HINQS_PREC_FP32_BF16AB) up to FP32
+    summation order.  (2) The same-spin half is linear and rounds only the operand of
+    the off-diagonal products: same(c) - same(bf16(c)) = hdiag * (c - bf16(c)), with
+    hdiag from the oracle."""
+    B = built(name)
+    N = len(B.sa) * len(B.sb)
+    c = synth.random_vector(N, 2)
+    cb = _bf16(c)
+    cbt = torch.tensor(cb, dtype=torch.float32, device="cuda")
+    a = hq.sigma(B.ham, B.sub, B.la, B.lb, cbt, precision=hq.PREC_FP32_BF16C)
+    b = hq.sigma(B.ham, B.sub, B.la, B.lb, cbt, precision=hq.PREC_FP32_BF16AB)
+    assert float(torch.max(torch.abs(a - b))) <= 2e-6 * float(torch.max(torch.abs(b)))
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.empty_like(ct), torch.empty_like(ct)
+    hq.sigma_part(B.ham, B.sub, B.la, B.lb, ct, s1, "same", precision=hq.PREC_FP32_BF16C)
+    hq.sigma_part(B.ham, B.sub, B.la, B.lb, cbt, s2, "same", precision=hq.PREC_FP32_BF16C)
+    hd = oracle.diag(B.H, B.sa, B.sb)
+    d = (s1 - s2).double().cpu().numpy()
+    want = hd * (ct.double().cpu().numpy() - cb)
+    scale = float(torch.max(torch.abs(s1)))
+    assert np.all(np.abs(d - want) <= 1e-6 * scale + 1e-5 * np.abs(want))
+
+
+def test_sigma_bf16c_full_size(precision_workload):
+    """The bench configuration: 256 sampled rows against the oracle, and the whole
+    vector against the FP32 CUDA-core product (the rows are 2000 floats: 16-byte
+    aligned, BF16 copies padded from 2000 to 2048)."""
+    B = precision_workload
+    c = synth.random_vector(B.sub.N, 3)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(4).choice(B.sub.N, size=256, replace=False))
+    ref = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
+    hd = oracle.diag(B.H, B.sa, B.sb, rows=rows)
+    s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=hq.PREC_FP32_BF16C).double()
+    sr = s.cpu().numpy()[rows]
+    off = ref - hd * c[rows]
+    assert np.all(np.abs(sr - ref) <= 2e-2 * np.max(np.abs(off)) + 2e-5 * np.abs(ref))
+    s32 = hq.sigma(B.ham, B.sub, B.la, B.lb, ct).double()
+    assert float(torch.max(torch.abs(s - s32))) <= 2e-2 * float(torch.max(torch.abs(s32)))
+
+
 def test_sigma_halves_sum_to_sigma(precision_workload):
     """hinqs_sigma_same_spin + hinqs_sigma_opposite_spin == hinqs_sigma in every mode."""
     B = precision_workload
     c = torch.tensor(synth.random_vector(B.sub.N, 7), device="cuda")
     for prec, x in ((hq.PREC_FP64, c), (hq.PREC_FP32, c.float()),
-                    (hq.PREC_FP32_BF16AB, c.float()), (hq.PREC_FP32_BF16X3AB, c.float())):
+                    (hq.PREC_FP32_BF16AB, c.float()), (hq.PREC_FP32_BF16X3AB, c.float()),
+                    (hq.PREC_FP32_BF16C, c.float())):
         full = hq.sigma(B.ham, B.sub, B.la, B.lb, x, precision=prec)
         part = torch.empty_like(x)
         hq.sigma_part(B.ham, B.sub, B.la, B.lb, x, part, "same", precision=prec)
@@ -344,13 +415,15 @@ def test_davidson_full_size_properties(precision_workload):
         assert np.max(np.abs(Hc - res.energy * c[rows])) <= 1e-8
 
 
-@pytest.mark.parametrize("inner", ["bf16", "bf16x3"])
+@pytest.mark.parametrize("inner", ["bf16", "bf16x3", "bf16c"])
 def test_davidson_mixed_tensor_core_inner(inner):
-    """Mixed Davidson whose inner products use the tensor-core term: the FP64
-    refinement still reaches the FP64 energy."""
+    """Mixed Davidson whose inner products use the tensor-core term (and, bf16c, BF16
+    operands in the same-spin products too): the FP64 refinement still reaches the
+    FP64 energy."""
     B = built("hf_12_4_4")
     E, c0 = ground_state(B)
-    p = hq.PREC_FP32_BF16AB if inner == "bf16" else hq.PREC_FP32_BF16X3AB
+    p = {"bf16": hq.PREC_FP32_BF16AB, "bf16x3": hq.PREC_FP32_BF16X3AB,
+         "bf16c": hq.PREC_FP32_BF16C}[inner]
     res = hq.davidson(B.ham, B.sub, B.la, B.lb, precision=hq.DAVIDSON_MIXED, inner_precision=p,
                       tol_residual=1e-8, max_subspace=12, max_iter=400)
     assert res.status == hq.OK
