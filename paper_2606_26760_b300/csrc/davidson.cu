@@ -63,6 +63,29 @@ __device__ __forceinline__ void last_block_reduce(const double* __restrict__ par
   }
 }
 
+// The same for K outputs at once: out[k] = sum of partial[k * nb .. k * nb + nb).
+__device__ __forceinline__ void last_block_reduce_k(const double* __restrict__ partial, int nb,
+                                                    int K, unsigned int* counter, double* out) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = atomicAdd(counter, 1u) == (unsigned)nb - 1u;
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k = w; k < K; k += blockDim.x >> 5) {
+    const volatile double* p = partial + (int64_t)k * nb;
+    double v = 0.0;
+    for (int b = lane; b < nb; b += 32) v += p[b];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) out[k] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) *counter = 0u;
+}
+
 // partial[i*gridDim.x + b] = block b's share of A_i . bvec (grid.y = vector i).
 // FP32 x FP32 products are summed in FP32 over groups of four strided elements and
 // the group sums in FP64; every other combination is formed and summed in FP64.
@@ -324,6 +347,234 @@ __global__ void __launch_bounds__(kRedThreads) k_residual(
     partial[blockIdx.x] = v;
   }
   if (counter) last_block_reduce(partial, gridDim.x, counter, rr_out);
+}
+
+// ------------------------------------------- mixed inner iteration, FP32 --
+//
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this part, so the
+// passes of the mixed inner iteration do no FP64 arithmetic per element: the anchor
+// enters through x32 = fp32(x) and the FP32 anchor residual ra = fp32(s - theta_a x)
+// (theta_a = x.s), whose rounding is relative to the residual itself, and the
+// coupling to the anchor is G_0i = theta_a S_0i + ra.v_i with the same S_0i = x32.v_i
+// that goes into S, so the pencil stays consistent.  MB bounds the number of basis
+// vectors a pass reads (a register array).
+
+constexpr int kVecGrid = 4 * kNumSMs;  // blocks of the fused vector passes
+constexpr int kVecOut = 2 * kMaxSub + 4;  // dot products one fused pass can return
+// per-block partial sums: the dot kernels and the fused passes
+constexpr int kPartial = std::max(2 * kRedGrid * (kMaxSub + 1), kVecOut * kVecGrid);
+
+// K running sums of one thread (FP32: a thread sums N / (kVecGrid * 256) products, a
+// relative error far below what the inner iteration needs, whose pencil and
+// directions already carry the FP32 / BF16 rounding of the products), combined in
+// FP64 across threads and blocks.
+template <int K>
+struct Sums {
+  float f[K];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int k = 0; k < K; ++k) f[k] = 0.f;
+  }
+  // Block sums into partial[slot * gridDim.x + blockIdx.x], then the last block writes
+  // out[slot]: sums 0 .. nA-1 go to slots 0 .. nA-1, sums offB .. offB+nB-1 to slots
+  // nA .. nA+nB-1 (the sums stay in registers: every index into f is a constant).
+  __device__ __forceinline__ void finish(int nA, int offB, int nB, double* __restrict__ partial,
+                                         unsigned int* counter, double* out) {
+    __shared__ double red[kVecOut][kRedThreads / 32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      const int slot = k < nA ? k : (k >= offB && k < offB + nB) ? nA + k - offB : -1;
+      if (slot < 0) continue;  // uniform over the block
+      double v = (double)f[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) red[slot][w] = v;
+    }
+    __syncthreads();
+    const int n = nA + nB;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) {
+      double v = 0.0;
+      for (int q = 0; q < kRedThreads / 32; ++q) v += red[k][q];
+      partial[(int64_t)k * gridDim.x + blockIdx.x] = v;
+    }
+    last_block_reduce_k(partial, gridDim.x, n, counter, out);
+  }
+};
+
+// The inner residual and its correction, with the dot products the orthogonalisation
+// needs:  u = y0 x + V y,  r = y0 ra + y0 (theta_a - theta) x32 + W y - theta V y,
+// t = r / floor(D32 - theta);  out = {r.r, t.t, x32.t, V_i.t (i < m)}.
+template <int MB>
+__global__ void __launch_bounds__(kRedThreads) k_res32(
+    const float* __restrict__ ra, const float* __restrict__ x32, const float* __restrict__ V,
+    const float* __restrict__ W, int64_t ld, int m, const double* __restrict__ ritz,
+    const double* __restrict__ theta_a, const float* __restrict__ D32, float floor_, int64_t N,
+    float* __restrict__ t, double* __restrict__ partial, unsigned int* counter,
+    double* __restrict__ out) {
+  __shared__ float y[kMaxSub + 1];
+  if (threadIdx.x <= m) y[threadIdx.x] = (float)ritz[1 + threadIdx.x];
+  __syncthreads();
+  const float theta = (float)ritz[0];
+  const float y0 = y[0], a0 = (float)((*theta_a - ritz[0]) * ritz[1]);
+  Sums<MB + 3> acc;
+  acc.zero();
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float v[MB];
+    float hv = 0.f, xv = 0.f;
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      v[i] = 0.f;
+      if (i < m) {
+        v[i] = V[i * ld + j];
+        hv = fmaf(y[1 + i], W[i * ld + j], hv);
+        xv = fmaf(y[1 + i], v[i], xv);
+      }
+    }
+    const float xj = x32[j];
+    const float r = fmaf(y0, ra[j], fmaf(a0, xj, fmaf(-theta, xv, hv)));
+    float den = D32[j] - theta;
+    if (fabsf(den) < floor_) den = (den < 0.0f) ? -floor_ : floor_;
+    const float tj = __fdividef(r, den);
+    t[j] = tj;
+    acc.f[0] = fmaf(r, r, acc.f[0]);
+    acc.f[1] = fmaf(tj, tj, acc.f[1]);
+    acc.f[2] = fmaf(xj, tj, acc.f[2]);
+#pragma unroll
+    for (int i = 0; i < MB; ++i) acc.f[3 + i] = fmaf(v[i], tj, acc.f[3 + i]);
+  }
+  acc.finish(m + 3, 0, 0, partial, counter, out);
+}
+
+// Coefficients of one Gram-Schmidt pass, passed by value (no host-to-device copy).
+struct OrthoCoef {
+  float c[kMaxSub + 1];  // c[0] for x32, c[1 + i] for V_i
+  float scale;
+};
+
+// o = (t - c0 x32 - sum_i c_i V_i) * scale (o may be t); out = {x32.o, V_i.o (i < m), o.o}.
+template <int MB>
+__global__ void __launch_bounds__(kRedThreads) k_ortho32(
+    const float* t, const float* __restrict__ x32, const float* __restrict__ V,
+    int64_t ld, int m, const OrthoCoef cf, float* o, int64_t N,
+    double* __restrict__ partial, unsigned int* counter, double* __restrict__ out) {
+  Sums<MB + 2> acc;
+  acc.zero();
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float v[MB];
+    const float xj = x32[j];
+    float p = fmaf(-cf.c[0], xj, t[j]);
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      v[i] = 0.f;
+      if (i < m) {
+        v[i] = V[i * ld + j];
+        p = fmaf(-cf.c[1 + i], v[i], p);
+      }
+    }
+    p *= cf.scale;
+    o[j] = p;
+    acc.f[0] = fmaf(xj, p, acc.f[0]);
+#pragma unroll
+    for (int i = 0; i < MB; ++i) acc.f[1 + i] = fmaf(v[i], p, acc.f[1 + i]);
+    acc.f[MB + 1] = fmaf(p, p, acc.f[MB + 1]);
+  }
+  acc.finish(m + 1, MB + 1, 1, partial, counter, out);  // the norm lands in out[m + 1]
+}
+
+// The pencil column of a new vector v = V_j with product w = W_j:
+// out = {x32.v, ra.v, V_i.w (i <= j), V_i.v (i <= j)}.
+template <int MB>
+__global__ void __launch_bounds__(kRedThreads) k_col32(
+    const float* __restrict__ x32, const float* __restrict__ ra, const float* __restrict__ V,
+    const float* __restrict__ W, int64_t ld, int j, int64_t N, double* __restrict__ partial,
+    unsigned int* counter, double* __restrict__ out) {
+  Sums<2 * MB + 2> acc;
+  acc.zero();
+  const int n = j + 1;  // vectors V_0 .. V_j
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float vj = V[j * ld + e], wj = W[j * ld + e];
+    acc.f[0] = fmaf(x32[e], vj, acc.f[0]);
+    acc.f[1] = fmaf(ra[e], vj, acc.f[1]);
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      if (i < n) {
+        const float vi = V[i * ld + e];
+        acc.f[2 + i] = fmaf(vi, wj, acc.f[2 + i]);
+        acc.f[2 + MB + i] = fmaf(vi, vj, acc.f[2 + MB + i]);
+      }
+    }
+  }
+  acc.finish(2 + n, 2 + MB, n, partial, counter, out);  // {x.v, ra.v, V.w[0..n), V.v[0..n)}
+}
+
+// The anchor row of the pencil for the kept vectors V_0 .. V_{m-1}:
+// out = {x32.V_i (i < m), ra.V_i (i < m)}.
+template <int MB>
+__global__ void __launch_bounds__(kRedThreads) k_anchor_row32(
+    const float* __restrict__ x32, const float* __restrict__ ra, const float* __restrict__ V,
+    int64_t ld, int m, int64_t N, double* __restrict__ partial, unsigned int* counter,
+    double* __restrict__ out) {
+  Sums<2 * MB> acc;
+  acc.zero();
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const float xe = x32[e], re = ra[e];
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      if (i < m) {
+        const float vi = V[i * ld + e];
+        acc.f[i] = fmaf(xe, vi, acc.f[i]);
+        acc.f[MB + i] = fmaf(re, vi, acc.f[MB + i]);
+      }
+    }
+  }
+  acc.finish(m, MB, m, partial, counter, out);  // {x32.V_i, ra.V_i}
+}
+
+// x32 = fp32(x), ra = fp32(s - theta_a x) with theta_a = G00 / S00 (written to *theta_a)
+__global__ void k_anchor32(const double* __restrict__ x, const double* __restrict__ s,
+                           const double* __restrict__ gs, double* __restrict__ theta_a,
+                           float* __restrict__ x32, float* __restrict__ ra, int64_t N) {
+  const double th = gs[0] / gs[1];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *theta_a = th;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double xj = x[j];
+    x32[j] = (float)xj;
+    ra[j] = (float)fma(-th, xj, s[j]);
+  }
+}
+
+// G, S entries of column col from a k_col32 result (n = col vectors before the anchor
+// offset): G[0][col] = theta_a x.v + ra.v, S[0][col] = x.v, G[i+1][col] = V_i.w,
+// S[i+1][col] = V_i.v (symmetric)
+__global__ void k_set_col32(double* G, double* S, int ldg, int col, const double* sums, int n,
+                            const double* theta_a) {
+  const int i = threadIdx.x;
+  if (i == 0) {
+    const double g = *theta_a * sums[0] + sums[1];
+    G[col] = g, G[col * ldg] = g;
+    S[col] = sums[0], S[col * ldg] = sums[0];
+  } else if (i <= n) {
+    const double g = sums[1 + i], sv = sums[1 + n + i];
+    G[i * ldg + col] = g, G[col * ldg + i] = g;
+    S[i * ldg + col] = sv, S[col * ldg + i] = sv;
+  }
+}
+
+// Row 0 of (G, S) for the kept vectors from a k_anchor_row32 result
+__global__ void k_set_row32(double* G, double* S, int ldg, const double* sums, int m,
+                            const double* theta_a) {
+  const int i = threadIdx.x;
+  if (i < m) {
+    const double sv = sums[i], g = *theta_a * sv + sums[m + i];
+    G[1 + i] = g, G[(1 + i) * ldg] = g;
+    S[1 + i] = sv, S[(1 + i) * ldg] = sv;
+  }
 }
 
 // Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
@@ -611,7 +862,7 @@ struct Ctx {
   const hinqs_detlist_s* L = nullptr;  // basis list (vectors over its entries) or NULL
   SigmaBatcher* batcher = nullptr;     // lockstep batch this solve belongs to, or NULL
   cudaEvent_t ready = nullptr;         // this solve's event for the batcher
-  double* partial = nullptr;  // [2 * (kMaxSub+1) * kRedGrid] >= kResGrid
+  double* partial = nullptr;  // [kPartial] >= kResGrid
   double* small = nullptr;    // scratch [4 * (kMaxSub+2)]
   float* t32 = nullptr;       // FP32 work vector [N] (mixed mode)
   unsigned int* counters = nullptr;  // [kMaxSub + 1] arrival counters of the dot kernels (zero)
@@ -950,6 +1201,41 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
 
 constexpr int kSoftRestarts = 3;
 
+// basis-vector bound of the fused passes for m vectors
+static int vec_bound(int m) { return m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32; }
+
+template <template <int> class F, typename... A>
+static void launch_mb(int m, cudaStream_t s, A... a) {
+  switch (vec_bound(m)) {
+    case 4: F<4>::go(s, a...); break;
+    case 8: F<8>::go(s, a...); break;
+    case 16: F<16>::go(s, a...); break;
+    default: F<32>::go(s, a...); break;
+  }
+}
+template <int MB>
+struct Res32 {
+  template <typename... A>
+  static void go(cudaStream_t s, A... a) { k_res32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+};
+template <int MB>
+struct Ortho32 {
+  template <typename... A>
+  static void go(cudaStream_t s, A... a) { k_ortho32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+};
+template <int MB>
+struct Col32 {
+  template <typename... A>
+  static void go(cudaStream_t s, A... a) { k_col32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+};
+template <int MB>
+struct Row32 {
+  template <typename... A>
+  static void go(cudaStream_t s, A... a) {
+    k_anchor_row32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...);
+  }
+};
+
 static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts& o, double* D,
                           double* energy, double* c_out, hinqs_davidson_info& info, Trace& tr) {
   const int mmax = std::max(4, o.max_subspace);  // pencil order 1 + m <= mmax
@@ -957,8 +1243,9 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
   const int64_t N = c.N;
   double *x = nullptr, *sx = nullptr, *t = nullptr, *xn = nullptr, *sxn = nullptr, *G = nullptr,
          *S = nullptr, *G1 = nullptr, *ritz = nullptr, *ritz1 = nullptr, *all = nullptr,
-         *col = nullptr, *scol = nullptr, *tmp = nullptr;
-  float *V = nullptr, *W = nullptr, *U = nullptr, *WU = nullptr;
+         *col = nullptr, *scol = nullptr, *tmp = nullptr, *vsum = nullptr;
+  float *V = nullptr, *W = nullptr, *U = nullptr, *WU = nullptr, *x32 = nullptr, *ra = nullptr,
+        *D32 = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&x, N, c.s)) || (rc = dalloc(&sx, N, c.s)) || (rc = dalloc(&t, N, c.s)) ||
       (rc = dalloc(&xn, N, c.s)) || (rc = dalloc(&sxn, N, c.s)) || (rc = dalloc(&tmp, N, c.s)) ||
@@ -968,35 +1255,37 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       (rc = dalloc(&G1, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
       (rc = dalloc(&ritz1, kMaxSub + 2, c.s)) || (rc = dalloc(&all, kMaxSub * kRitzStride, c.s)) ||
       (rc = dalloc(&col, kMaxSub + 2, c.s)) || (rc = dalloc(&scol, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&c.t32, N, c.s))) {
+      (rc = dalloc(&vsum, kVecOut, c.s)) || (rc = dalloc(&c.t32, N, c.s)) ||
+      (rc = dalloc(&x32, N, c.s)) || (rc = dalloc(&ra, N, c.s)) || (rc = dalloc(&D32, N, c.s))) {
   }
   auto cleanup = [&]() {
-    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol}) {
+    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol, vsum}) {
       double* q = p;
       dfree(q, c.s);
     }
-    dfree(V, c.s);
-    dfree(W, c.s);
-    dfree(U, c.s);
-    dfree(WU, c.s);
-    dfree(c.t32, c.s);
+    for (float* p : {V, W, U, WU, c.t32, x32, ra, D32}) {
+      float* q = p;
+      dfree(q, c.s);
+    }
   };
   if (rc) {
     cleanup();
     return rc;
   }
-  // G, S column for basis vector index j (j >= 1, FP32 vector V[j-1] with product W[j-1])
+  double* theta_a = c.small + 2 * kMaxSub + 2;  // x.s / x.x of the current anchor
+  double* gs = c.small + 2 * kMaxSub + 6;       // {x.s, x.x}
+  unsigned int* ctr = c.counters + kMaxSub;
+  const float floor32 = (float)o.denom_floor;
+  // the pencil column of V_j (pencil index j + 1) and its product W_j
   auto add_column = [&](int j) -> int {
-    const float* v = V + (size_t)(j - 1) * N;
-    const float* w = W + (size_t)(j - 1) * N;
-    HQ_TRY(dots2<float, double>(c, v, N, 1, sx, x, col, scol));
-    HQ_TRY(dots2<float, float>(c, V, N, j, w, v, col + 1, scol + 1));
-    k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, j, col, j + 1, 0);
-    k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, j, scol, j + 1, 0);
+    launch_mb<Col32>(j + 1, c.s, (const float*)x32, (const float*)ra, (const float*)V,
+                     (const float*)W, (int64_t)N, j, N, c.partial, ctr, vsum);
+    k_set_col32<<<1, kMaxSub + 1, 0, c.s>>>(G, S, kMaxSub, j + 1, vsum, j + 1, theta_a);
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
   };
   auto run = [&]() -> int {
+    k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(D, D32, N);
     if (guess) {
       HQ_CUDA(cudaMemcpyAsync(t, guess, N * sizeof(double), cudaMemcpyDeviceToDevice, c.s));
     } else {
@@ -1010,6 +1299,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     bool hard = true, have_prev = false;
     double theta_prev = 0.0, target = 0.0;
     double h[2];
+    std::vector<double> hs(kVecOut + 1);
     for (;;) {
       if (hard) {
         HQ_TRY(apply_sigma(c, x, sx, HINQS_PREC_FP64));
@@ -1046,11 +1336,16 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         soft = 0;
         hard = false;
       }
-      // row and column 0 of the pencil for the current anchor
-      HQ_TRY(dots2<double, double>(c, x, N, 1, sx, x, col, scol));
-      HQ_TRY(dots2<float, double>(c, V, N, m, sx, x, col + 1, scol + 1));
-      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, col, m + 1, 0);
-      k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, 0, scol, m + 1, 0);
+      // the anchor in FP32 form and row / column 0 of the pencil
+      HQ_TRY(dots2<double, double>(c, x, N, 1, sx, x, gs, gs + 1));
+      k_anchor32<<<c.grid, 256, 0, c.s>>>(x, sx, gs, theta_a, x32, ra, N);
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, gs, 1, 0);
+      k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, 0, gs + 1, 1, 0);
+      if (m > 0) {
+        launch_mb<Row32>(m, c.s, (const float*)x32, (const float*)ra, (const float*)V, (int64_t)N,
+                         m, N, c.partial, ctr, vsum);
+        k_set_row32<<<1, kMaxSub, 0, c.s>>>(G, S, kMaxSub, vsum, m, theta_a);
+      }
       HQ_LAUNCH_CHECK();
       if (m == 0) {  // first direction: the preconditioned FP64 residual in t
         HQ_TRY(orthonormalise_mixed(c, t, x, V, N, 0, V, &ratio));
@@ -1058,21 +1353,24 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         info.n_sigma_fp32++;
         total++;
         m = 1;
-        HQ_TRY(add_column(1));
+        HQ_TRY(add_column(0));
       }
       bool restart_hard = false;
       for (;;) {
+        // residual and correction of the pencil's lowest Ritz pair, with the dot products
+        // of its Gram-Schmidt pass against {x, V}
         k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
-        k_residual<float><<<kResGrid, kRedThreads, 0, c.s>>>(x, sx, V, W, N, m, ritz, 1, D,
-                                                             o.denom_floor, N, t, c.partial,
-                                                             c.counters + kMaxSub, col + kMaxSub);
+        launch_mb<Res32>(m, c.s, (const float*)ra, (const float*)x32, (const float*)V,
+                         (const float*)W, (int64_t)N, m, (const double*)ritz, (const double*)theta_a,
+                         (const float*)D32, floor32, N, c.t32, c.partial, ctr, vsum);
         HQ_LAUNCH_CHECK();
-        HQ_CUDA(cudaMemcpyAsync(&h[0], ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
-        HQ_CUDA(cudaMemcpyAsync(&h[1], col + kMaxSub, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaMemcpyAsync(hs.data(), ritz, sizeof(double), cudaMemcpyDeviceToHost, c.s));
+        HQ_CUDA(cudaMemcpyAsync(hs.data() + 1, vsum, (m + 3) * sizeof(double),
+                                cudaMemcpyDeviceToHost, c.s));
         HQ_CUDA(cudaStreamSynchronize(c.s));
-        const double rin = std::sqrt(std::max(h[1], 0.0));
+        const double rin = std::sqrt(std::max(hs[1], 0.0));
         info.iterations++;
-        tr.add(h[0], rin, 1);
+        tr.add(hs[0], rin, 1);
         if (rin <= target || total >= o.max_iter) {
           restart_hard = true;
           break;
@@ -1081,16 +1379,55 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
           restart_hard = (++soft > kSoftRestarts);
           break;
         }
-        HQ_TRY(orthonormalise_mixed(c, t, x, V, N, m, V + (size_t)m * N, &ratio));
-        if (ratio < 1e-12) {
+        // classical Gram-Schmidt against {x, V} (unit vectors up to FP32 rounding; the
+        // pencil carries their exact overlaps): one pass when it keeps more than half
+        // of |t|^2 (then a second pass would change nothing that matters), else a
+        // second pass from the dot products of the first
+        const double tt = hs[2];
+        OrthoCoef cf;
+        double p2 = tt;
+        cf.c[0] = (float)hs[3];
+        p2 -= hs[3] * hs[3];
+        for (int i = 0; i < m; ++i) {
+          cf.c[1 + i] = (float)hs[4 + i];
+          p2 -= hs[4 + i] * hs[4 + i];
+        }
+        float* vm = V + (size_t)m * N;
+        if (!(tt > 0.0)) {
           restart_hard = true;
           break;
         }
-        HQ_TRY(apply_sigma(c, V + (size_t)m * N, W + (size_t)m * N, o.inner_precision));
+        if (p2 > 0.5 * tt) {
+          cf.scale = (float)(1.0 / std::sqrt(p2));
+          launch_mb<Ortho32>(m, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
+                             (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
+        } else {
+          cf.scale = 1.0f;
+          launch_mb<Ortho32>(m, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
+                             (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
+          HQ_CUDA(cudaMemcpyAsync(hs.data(), vsum, (m + 2) * sizeof(double), cudaMemcpyDeviceToHost,
+                                  c.s));
+          HQ_CUDA(cudaStreamSynchronize(c.s));
+          const double oo = hs[m + 1];
+          if (!(oo > 1e-24 * tt)) {  // t lies in span{x, V}: no new direction
+            restart_hard = true;
+            break;
+          }
+          double q2 = oo;
+          for (int i = 0; i <= m; ++i) {
+            cf.c[i] = (float)hs[i];
+            q2 -= hs[i] * hs[i];
+          }
+          cf.scale = (float)(1.0 / std::sqrt(q2 > 0.5 * oo ? q2 : oo));
+          launch_mb<Ortho32>(m, c.s, (const float*)vm, (const float*)x32, (const float*)V,
+                             (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
+        }
+        HQ_LAUNCH_CHECK();
+        HQ_TRY(apply_sigma(c, vm, W + (size_t)m * N, o.inner_precision));
         info.n_sigma_fp32++;
         total++;
-        m++;
         HQ_TRY(add_column(m));
+        m++;
       }
       // restart: anchor = lowest Ritz vector, plus keep-1 FP32 Ritz vectors
       const int kk = std::min(keep, m + 1);
@@ -1165,7 +1502,7 @@ extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
 // N-element temporaries of an FP64 sigma product.  Keep in step with those allocations.
 static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) {
   const size_t d = sizeof(double), f = sizeof(float);
-  size_t b = (2 * (size_t)kRedGrid * (kMaxSub + 1) + 4 * (kMaxSub + 2)) * d +
+  size_t b = ((size_t)kPartial + 4 * (kMaxSub + 2)) * d +
              (kMaxSub + 1) * sizeof(unsigned int) + (size_t)N * d;
   if (o.precision == HINQS_DAVIDSON_FP64) {
     const size_t mmax = (size_t)o.max_subspace, kr = (size_t)restart_keep_fp64(o);
@@ -1175,8 +1512,9 @@ static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) 
     const size_t mmax = (size_t)std::max(4, o.max_subspace);
     const size_t keep = (size_t)restart_keep_mixed(o);
     b += 6 * (size_t)N * d;                                     // x, sx, t, xn, sxn, tmp
-    b += (2 * mmax + 2 * keep + 1) * (size_t)N * f;             // V, W, U, WU, t32
-    b += (3 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;
+    b += (2 * mmax + 2 * keep + 4) * (size_t)N * f;             // V, W, U, WU, t32, x32, ra, D32
+    b += (3 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride +
+          kVecOut) * d;
   }
   return b + 2 * (size_t)N * d;  // sigma temporaries (FP64 product)
 }
@@ -1236,7 +1574,7 @@ int hinqs::davidson_run(const hinqs_ham* H, const hinqs_subspace* B, const hinqs
   c.grid = (int)std::min<int64_t>(ceil_div(c.N, 256), 8 * kNumSMs);
   double* D = nullptr;
   int rc = HINQS_OK;
-  if ((rc = dalloc(&c.partial, 2 * kRedGrid * (kMaxSub + 1), c.s)) ||
+  if ((rc = dalloc(&c.partial, kPartial, c.s)) ||
       (rc = dalloc(&c.small, 4 * (kMaxSub + 2), c.s)) ||
       (rc = dalloc(&c.counters, kMaxSub + 1, c.s)) || (rc = dalloc(&D, c.N, c.s))) {
   }
