@@ -594,7 +594,8 @@ __global__ void k_set_row32(double* G, double* S, int ldg, const double* sums, i
 __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G, int ldg, int m,
                                            double* __restrict__ out,
                                            const double* __restrict__ S,
-                                           double* __restrict__ all = nullptr) {
+                                           double* __restrict__ all = nullptr,
+                                           double* __restrict__ qkeep = nullptr, int warm = 0) {
   __shared__ double A[kMaxSub][kMaxSub + 1];
   __shared__ double Q[kMaxSub][kMaxSub + 1];
   __shared__ double L[kMaxSub][kMaxSub + 1];
@@ -664,6 +665,39 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
   }
   if (lane < mm) order[lane] = lane;
   __syncthreads();
+  if (qkeep && warm && m >= 2) {
+    // The pencil grew by one row and column since the last call, whose eigenvectors
+    // (of the same leading block, the Cholesky factor's leading block being the same)
+    // are in qkeep: start from Q0 = diag(Q_old, 1), so that A = Q0^T C Q0 is diagonal
+    // but for its last row and column and the sweeps converge in a few passes.
+    const int mo = m - 1;
+    for (int i = lane; i < mm * mm; i += kRRThreads) {
+      const int r = i / mm, c = i % mm;
+      Q[r][c] = (r < mo && c < mo) ? qkeep[r * kMaxSub + c] : (r == c ? 1.0 : 0.0);
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // X = A Q0
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v += A[r][k] * Q[k][c];
+      X[r][c] = v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // A = Q0^T X
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v += Q[k][r] * X[k][c];
+      A[r][c] = v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // symmetric part
+      const int r = i / m, c = i % m;
+      X[r][c] = 0.5 * (A[r][c] + A[c][r]);
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) A[i / m][i % m] = X[i / m][i % m];
+    __syncthreads();
+  }
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int i = lane; i < m * m; i += kRRThreads) {
@@ -746,6 +780,8 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
       __syncthreads();
     }
   }
+  if (qkeep)
+    for (int i = lane; i < m * m; i += kRRThreads) qkeep[(i / m) * kMaxSub + i % m] = Q[i / m][i % m];
   // rank of each eigenvalue (ascending, ties by index)
   if (lane < m) {
     const double lj = A[lane][lane];
@@ -1017,16 +1053,18 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
   const int kr = restart_keep_fp64(o);  // vectors kept at a restart
   const int64_t N = c.N;
   double *V = nullptr, *W = nullptr, *t = nullptr, *X = nullptr, *WX = nullptr, *G = nullptr,
-         *ritz = nullptr, *col = nullptr, *ycoef = nullptr, *all = nullptr;
+         *ritz = nullptr, *col = nullptr, *ycoef = nullptr, *all = nullptr, *qk = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
       (rc = dalloc(&t, N, c.s)) || (rc = dalloc(&X, (size_t)kr * N, c.s)) ||
       (rc = dalloc(&WX, (size_t)kr * N, c.s)) || (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) ||
       (rc = dalloc(&ritz, kMaxSub + 2, c.s)) || (rc = dalloc(&col, kMaxSub + 2, c.s)) ||
       (rc = dalloc(&ycoef, (size_t)kr * (kMaxSub + 2), c.s)) ||
-      (rc = dalloc(&all, kMaxSub * kRitzStride, c.s))) {
+      (rc = dalloc(&all, kMaxSub * kRitzStride, c.s)) ||
+      (rc = dalloc(&qk, kMaxSub * kMaxSub, c.s))) {
   }
   auto cleanup = [&]() {
+    dfree(qk, c.s);
     dfree(V, c.s);
     dfree(W, c.s);
     dfree(t, c.s);
@@ -1056,6 +1094,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
     double theta_prev = 0.0;
     bool have_prev = false;
     double hr[kMaxSub + 2] = {0}, hr_prev[kMaxSub + 2] = {0};
+    int rr_warm = 0;  // the pencil grew by one column since the last k_rr
     for (int it = 0; it < o.max_iter; ++it) {
       double* vm = V + (size_t)(m - 1) * N;
       double* wm = W + (size_t)(m - 1) * N;
@@ -1063,7 +1102,8 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
       info.n_sigma_fp64++;
       HQ_TRY(dots<double, double>(c, V, N, m, wm, col));
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, m - 1, col, m, 0);
-      k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr);
+      k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m, ritz, nullptr, nullptr, qk, rr_warm);
+      rr_warm = 1;
       k_residual<double><<<kResGrid, kRedThreads, 0, c.s>>>(nullptr, nullptr, V, W, N, m, ritz, 0,
                                                             D, o.denom_floor, N, t, c.partial,
                                                             c.counters + kMaxSub, col + kMaxSub);
@@ -1159,6 +1199,7 @@ static int davidson_fp64(Ctx& c, const double* guess, const hinqs_davidson_opts&
                                 c.s));
         HQ_CUDA(cudaStreamSynchronize(c.s));  // the host arrays above go out of scope
         m = mnew;
+        rr_warm = 0;
         // the residual t of the current Ritz vector (now V[0]) is still valid
         info.n_restarts++;
       }
@@ -1213,26 +1254,48 @@ static void launch_mb(int m, cudaStream_t s, A... a) {
     default: F<32>::go(s, a...); break;
   }
 }
+// One full wave of a fused pass: the SMs times the blocks of the kernel that fit on
+// one (its registers decide), at most kVecGrid (the partial-sum buffer).
+template <typename K>
+static int vec_grid(K kern) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRedThreads, 0) != cudaSuccess ||
+      per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  return std::min(kVecGrid, per_sm * kNumSMs);
+}
 template <int MB>
 struct Res32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) { k_res32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+  static void go(cudaStream_t s, A... a) {
+    static const int g = vec_grid(k_res32<MB>);
+    k_res32<MB><<<g, kRedThreads, 0, s>>>(a...);
+  }
 };
 template <int MB>
 struct Ortho32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) { k_ortho32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+  static void go(cudaStream_t s, A... a) {
+    static const int g = vec_grid(k_ortho32<MB>);
+    k_ortho32<MB><<<g, kRedThreads, 0, s>>>(a...);
+  }
 };
 template <int MB>
 struct Col32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) { k_col32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...); }
+  static void go(cudaStream_t s, A... a) {
+    static const int g = vec_grid(k_col32<MB>);
+    k_col32<MB><<<g, kRedThreads, 0, s>>>(a...);
+  }
 };
 template <int MB>
 struct Row32 {
   template <typename... A>
   static void go(cudaStream_t s, A... a) {
-    k_anchor_row32<MB><<<kVecGrid, kRedThreads, 0, s>>>(a...);
+    static const int g = vec_grid(k_anchor_row32<MB>);
+    k_anchor_row32<MB><<<g, kRedThreads, 0, s>>>(a...);
   }
 };
 
@@ -1243,7 +1306,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
   const int64_t N = c.N;
   double *x = nullptr, *sx = nullptr, *t = nullptr, *xn = nullptr, *sxn = nullptr, *G = nullptr,
          *S = nullptr, *G1 = nullptr, *ritz = nullptr, *ritz1 = nullptr, *all = nullptr,
-         *col = nullptr, *scol = nullptr, *tmp = nullptr, *vsum = nullptr;
+         *col = nullptr, *scol = nullptr, *tmp = nullptr, *vsum = nullptr, *qk = nullptr;
   float *V = nullptr, *W = nullptr, *U = nullptr, *WU = nullptr, *x32 = nullptr, *ra = nullptr,
         *D32 = nullptr;
   int rc = HINQS_OK;
@@ -1255,11 +1318,12 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       (rc = dalloc(&G1, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&ritz, kMaxSub + 2, c.s)) ||
       (rc = dalloc(&ritz1, kMaxSub + 2, c.s)) || (rc = dalloc(&all, kMaxSub * kRitzStride, c.s)) ||
       (rc = dalloc(&col, kMaxSub + 2, c.s)) || (rc = dalloc(&scol, kMaxSub + 2, c.s)) ||
-      (rc = dalloc(&vsum, kVecOut, c.s)) || (rc = dalloc(&c.t32, N, c.s)) ||
+      (rc = dalloc(&vsum, kVecOut, c.s)) || (rc = dalloc(&qk, kMaxSub * kMaxSub, c.s)) ||
+      (rc = dalloc(&c.t32, N, c.s)) ||
       (rc = dalloc(&x32, N, c.s)) || (rc = dalloc(&ra, N, c.s)) || (rc = dalloc(&D32, N, c.s))) {
   }
   auto cleanup = [&]() {
-    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol, vsum}) {
+    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol, vsum, qk}) {
       double* q = p;
       dfree(q, c.s);
     }
@@ -1356,10 +1420,12 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         HQ_TRY(add_column(0));
       }
       bool restart_hard = false;
+      int rr_warm = 0;  // the pencil grew by one column since the last k_rr
       for (;;) {
         // residual and correction of the pencil's lowest Ritz pair, with the dot products
         // of its Gram-Schmidt pass against {x, V}
-        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
+        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all, qk, rr_warm);
+        rr_warm = 1;
         launch_mb<Res32>(m, c.s, (const float*)ra, (const float*)x32, (const float*)V,
                          (const float*)W, (int64_t)N, m, (const double*)ritz, (const double*)theta_a,
                          (const float*)D32, floor32, N, c.t32, c.partial, ctr, vsum);
@@ -1507,13 +1573,13 @@ static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) 
   if (o.precision == HINQS_DAVIDSON_FP64) {
     const size_t mmax = (size_t)o.max_subspace, kr = (size_t)restart_keep_fp64(o);
     b += (2 * mmax + 1 + 2 * kr) * (size_t)N * d;               // V, W, t, X[kr], WX[kr]
-    b += ((size_t)kMaxSub * kMaxSub + (2 + kr) * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;
+    b += (2 * (size_t)kMaxSub * kMaxSub + (2 + kr) * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride) * d;
   } else {
     const size_t mmax = (size_t)std::max(4, o.max_subspace);
     const size_t keep = (size_t)restart_keep_mixed(o);
     b += 6 * (size_t)N * d;                                     // x, sx, t, xn, sxn, tmp
     b += (2 * mmax + 2 * keep + 4) * (size_t)N * f;             // V, W, U, WU, t32, x32, ra, D32
-    b += (3 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride +
+    b += (4 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride +
           kVecOut) * d;
   }
   return b + 2 * (size_t)N * d;  // sigma temporaries (FP64 product)

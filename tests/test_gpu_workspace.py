@@ -62,7 +62,7 @@ def test_davidson_workspace_matches_pool_usage(problem, prec):
     assert 0.9 * bound <= peak <= bound + SLACK, (peak, bound)
 
 
-@pytest.mark.parametrize("prec", [hq.PREC_FP64, hq.PREC_FP32])
+@pytest.mark.parametrize("prec", [hq.PREC_FP64, hq.PREC_FP32, hq.PREC_FP32_BF16C])
 def test_sigma_workspace_matches_pool_usage(problem, prec):
     ham, sub, la, lb = problem
     dt = torch.float64 if prec == hq.PREC_FP64 else torch.float32
