@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-ref", action="store_true",
+                    help="large workload: also the FP64 Davidson to a 1e-8 residual as E_ref")
     ap.add_argument("--detail", action="store_true", help="per-component timings to stderr")
     ap.add_argument("--probe", default=None,
                     help="PART:PREC[:tune] -- run one sigma product (PART sigma|same|opposite, "
@@ -152,12 +154,12 @@ def rooflines(hq, sub, la, lb, n, nb, t_same, t_opp, t_sig, results):
     """Roofline of the step's dominant sigma kernel and of the other half.
 
     Algorithmic work per launch (the scope table's per-unit figures times the units):
-      same-spin half (row products, FP32): read C + write sigma = 2 N 4 B, plus the
+      same-spin half (row products, BF16 operand, FP32 sums): read C + write sigma = 2 N 4 B, plus the
         link records read once (8 B per record of both spins and per alpha-self x
         beta-single record), the per-string tables (4 n^2 B per alpha string, 8 B of
         diagonal per string); bound: HBM, against the measured copy bandwidth.  A
         secondary figure gives the bytes the kernel moves between L1 and registers
-        (4 B per link and column, 8 B per alpha-self x beta-single and column) against
+        (2 B per link and column, 6 B per alpha-self x beta-single and column) against
         the L1 data path derived from unit counts and clocks.
       opposite-spin half (tensor cores, BF16): the MMA FLOPs executed on 128-row tiles
         over the padded folded K, and the useful share 2 sum (singles_a)(singles_b +
@@ -175,13 +177,15 @@ def rooflines(hq, sub, la, lb, n, nb, t_same, t_opp, t_sig, results):
     fp32_peak = hq.probe_fma_rate(hq.PREC_FP32)
     alg_same = (2.0 * N * 4 + 8.0 * (la.n_links + lb.n_links + lb.n_singles)
                 + 4.0 * n * n * sub.Na + 8.0 * (sub.Na + sub.Nb))
-    l1_same = 4.0 * (la.n_links * sub.Nb + lb.n_links * sub.Na) + 8.0 * lb.n_singles * sub.Na
+    # operand bytes per link and column: 2 (the BF16 copy of C); the alpha-self x
+    # beta-single term also reads its FP32 table entry
+    l1_same = 2.0 * (la.n_links * sub.Nb + lb.n_links * sub.Na) + 6.0 * lb.n_singles * sub.Na
     fma_same = N + sub.Na * (lb.n_links + lb.n_singles) + sub.Nb * la.n_links
     fma_opp_useful = la.n_singles * (lb.n_singles + sub.Nb * nb)
     mma_flops = tc_executed_flops(n, sub, la)
     l1_peak = kNumSMs_B300 * 128 * SM_MAX_MHZ * 1e6 / 1e9
     same_line = {
-        "bound": "hbm", "kernel": "same-spin half, FP32 row products",
+        "bound": "hbm", "kernel": "same-spin half, row products on the BF16 copy of C (FP32 sums)",
         "achieved": sig3(alg_same / t_same / 1e9), "peak": hbm, "unit": "GB/s",
         "frac": sig3(alg_same / t_same / 1e9 / hbm), "traffic": PROFILED_TRAFFIC.get("same"),
         "alg_bytes": alg_same, "ms": sig3(1e3 * t_same),
@@ -405,7 +409,7 @@ def run_bond_scan(args):
     resident = [tuple(x.to(dev) for x in hw) for hw in host]
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    mixed = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2,
+    mixed = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2,
                  tol_residual=1e-6, tol_energy=1e-8, max_subspace=16, max_iter=600)
 
     def prepare(inputs):
@@ -571,7 +575,7 @@ def run_large(args):
     a_d = torch.from_numpy(w["alpha"].view(np.int64)).to(dev)
     b_d = torch.from_numpy(w["beta"].view(np.int64)).to(dev)
     stream = torch.cuda.current_stream()
-    opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2,
+    opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2,
                 tol_residual=1e-5, tol_energy=1e-7, max_subspace=8, max_iter=300)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     parts = {}
@@ -582,7 +586,7 @@ def run_large(args):
         ham = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
         sub = hq.build_subspace(a_d, b_d, n, na, nb)
         la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
-        hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16AB)
+        hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16C)
         ev1.record(stream)
         torch.cuda.synchronize()
         t["setup_s"] = ev0.elapsed_time(ev1) / 1e3
@@ -615,7 +619,8 @@ def run_large(args):
     clk = clocks.stop()
     e_id = float((h_d * g1).sum() + 0.5 * (eri_d * g2).sum()) + w["e_nuc"]
     sig = {}
-    for name, p in (("fp32_bf16ab", hq.PREC_FP32_BF16AB), ("fp32", hq.PREC_FP32),
+    for name, p in (("fp32_bf16c", hq.PREC_FP32_BF16C), ("fp32_bf16ab", hq.PREC_FP32_BF16AB),
+                    ("fp32", hq.PREC_FP32),
                     ("fp64", hq.PREC_FP64)):
         x = torch.rand(sub.N, device=dev, dtype=torch.float64 if p == hq.PREC_FP64 else torch.float32)
         y = torch.empty_like(x)
@@ -627,8 +632,26 @@ def run_large(args):
         torch.cuda.synchronize()
         sig[name] = ev0.elapsed_time(ev1)
         del x, y
+    ref = None
+    if args.fp64_ref:
+        # E_ref: the FP64 Davidson at a 1e-8 residual, and the time-to-1e-6 Ha of both
+        # solvers against it (trace clocks)
+        del g1, g2
+        torch.cuda.empty_cache()
+        rf = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-8,
+                         tol_energy=1e-11, max_subspace=8, max_iter=600, trace_cap=1024)
+        rm = hq.davidson(ham, sub, la, lb, trace_cap=1024, **opts)
+
+        def tt(r):
+            return next((t for th, t, k in zip(r.trace["theta"], r.trace["time"], r.trace["kind"])
+                         if k == 0 and abs(th - rf.energy) <= 1e-6), None)
+        ref = {"E_ref_fp64": rf.energy, "E_ref_residual": rf.residual, "E_ref_status": int(rf.status),
+               "fp64_solve_s": sig3(rf.seconds), "fp64_sigmas": rf.n_sigma_fp64,
+               "fp64_time_to_1e-6_Ha_s": sig3(tt(rf)), "mixed_time_to_1e-6_Ha_s": sig3(tt(rm)),
+               "mixed_abs_err_Ha": abs(rm.energy - rf.energy), "mixed_residual": rm.residual}
     t_mean = sum(times) / len(times)
     print(json.dumps({
+        "fp64_reference": ref,
         "metric": METRIC, "value": sub.N / t_mean, "unit": "dets/s", "n_gpus": 1,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_mean,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -644,6 +667,64 @@ def run_large(args):
         "clocks": clk}), flush=True)
 
 
+# ------------------------------------------------------------- time to 1e-6 --
+
+def run_time_to(args):
+    """Time-to-1e-6 Ha of the FP64 and mixed Davidson on the same B300 for the
+    plain-FP64 (n=8, 3/3, full 56 x 56), precision (n=16, 5/5, 2000 x 2000) and
+    differentiation (n=20, 7/7, 5000 x 5000) configurations: E_ref is the FP64 GPU
+    solve at a 1e-9 residual; each solver's time is the first FP64-evaluated Ritz
+    value within 1e-6 Ha of E_ref (trace clock), after one untimed solve."""
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    from paper_2606_26760_b300 import build as _build
+    if not os.path.exists(_build.LIB):
+        _build.build()
+    import paper_2606_26760_b300 as hq
+    import synth
+
+    dev = torch.device("cuda", local)
+    out = {}
+    for wl in ("fp64_small", "precision", "differentiation"):
+        w = synth.workload(wl)
+        n, na, nb = w["n_orb"], w["n_alpha"], w["n_beta"]
+        ham = hq.Hamiltonian(torch.tensor(w["h"], device=dev), torch.tensor(w["eri"], device=dev),
+                             na, nb, w["e_nuc"])
+        sub = hq.build_subspace(torch.from_numpy(w["alpha"].view(np.int64).copy()).to(dev),
+                                torch.from_numpy(w["beta"].view(np.int64).copy()).to(dev), n, na, nb)
+        la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
+        hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16C)
+        ref = hq.davidson(ham, sub, la, lb, tol_residual=1e-9, tol_energy=1e-12, max_iter=2000)
+        e_ref = ref.energy
+        row = {"N": sub.N, "E_ref": e_ref, "E_ref_residual": ref.residual}
+        for name, kw in (("fp64", dict(precision=hq.DAVIDSON_FP64)),
+                         ("mixed_bf16c", dict(precision=hq.DAVIDSON_MIXED,
+                                              inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2)),
+                         ("mixed_bf16ab", dict(precision=hq.DAVIDSON_MIXED,
+                                               inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2)),
+                         ("mixed_fp32", dict(precision=hq.DAVIDSON_MIXED,
+                                             inner_precision=hq.PREC_FP32, inner_tol=3e-2))):
+            for rep in range(2):
+                r = hq.davidson(ham, sub, la, lb, tol_residual=1e-6, tol_energy=1e-8,
+                                max_subspace=16, max_iter=2000, trace_cap=4096, **kw)
+            tt = next((t for th, t, k in zip(r.trace["theta"], r.trace["time"], r.trace["kind"])
+                       if k == 0 and abs(th - e_ref) <= 1e-6), None)
+            row[name] = {"time_to_1e-6_Ha_s": sig3(tt), "solve_s": sig3(r.seconds),
+                         "abs_err_Ha": abs(r.energy - e_ref),
+                         "sigmas_fp64_fp32": [r.n_sigma_fp64, r.n_sigma_fp32]}
+        a, b = row["fp64"]["time_to_1e-6_Ha_s"], row["mixed_bf16c"]["time_to_1e-6_Ha_s"]
+        row["speedup_mixed_bf16c_vs_fp64"] = sig3(a / b) if a and b else None
+        out[wl] = row
+        del ham, sub, la, lb
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B300",
+                      "unit": "s", "higher_is_better": False, "data": "synthetic",
+                      "configs": out}), flush=True)
+
+
 # ------------------------------------------------------------------ B300 --
 
 def main():
@@ -654,6 +735,8 @@ def main():
         return run_bond_scan(args)
     if args.workload == "large":
         return run_large(args)
+    if args.workload == "time_to":
+        return run_time_to(args)
     import numpy as np
     import torch
     import torch.distributed as dist
@@ -722,7 +805,7 @@ def main():
 
     # inner_tol 3e-2: the BF16 inner operator is accurate to ~1e-2, so asking the
     # inner solve for more only adds FP32 iterations before the next FP64 refinement
-    solve_opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16AB,
+    solve_opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16C,
                       inner_tol=3e-2,
                       tol_residual=1e-6, tol_energy=1e-8, max_subspace=16, max_iter=600,
                       trace_cap=1024)
@@ -731,7 +814,7 @@ def main():
         ham_s = hq.Hamiltonian(h_in, eri_in, na, nb, w["e_nuc"])
         sub_s = hq.build_subspace(a_in, b_in, n, na, nb)
         la_s, lb_s = hq.string_links(ham_s, sub_s, 0), hq.string_links(ham_s, sub_s, 1)
-        hq.autotune(ham_s, sub_s, la_s, lb_s, hq.PREC_FP32_BF16AB)  # cached after the first step
+        hq.autotune(ham_s, sub_s, la_s, lb_s, hq.PREC_FP32_BF16C)  # cached after the first step
         res = hq.davidson(ham_s, sub_s, la_s, lb_s, **solve_opts)
         g1, g2 = hq.rdm(sub_s, la_s, lb_s, res.c)
         gh, ge = hq.energy_backward(n, 1.0, g1, g2)
@@ -749,7 +832,7 @@ def main():
     ham = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
     sub = hq.build_subspace(a_d, b_d, n, na, nb)
     la, lb = hq.string_links(ham, sub, 0), hq.string_links(ham, sub, 1)
-    hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16AB)
+    hq.autotune(ham, sub, la, lb, hq.PREC_FP32_BF16C)
     N = sub.N
     ref = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-9,
                       max_iter=400, max_subspace=24)
@@ -829,9 +912,9 @@ def main():
                             reps=20)
     out32 = torch.empty_like(c32)
     t_same = timed(lambda: hq.sigma_part(ham, sub, la, lb, c32, out32, "same",
-                                         precision=hq.PREC_FP32_BF16AB))
+                                         precision=hq.PREC_FP32_BF16C))
     t_opp = timed(lambda: hq.sigma_part(ham, sub, la, lb, c32, out32, "opposite",
-                                        precision=hq.PREC_FP32_BF16AB))
+                                        precision=hq.PREC_FP32_BF16C))
 
     # FP64 and the mixed variants: time-to-1e-6 Ha on the same GPU
     variants = {"fp64": dict(precision=hq.DAVIDSON_FP64),
@@ -839,8 +922,8 @@ def main():
                                    inner_tol=3e-2),
                 "mixed_bf16x3": dict(precision=hq.DAVIDSON_MIXED,
                                      inner_precision=hq.PREC_FP32_BF16X3AB, inner_tol=3e-2),
-                "mixed_bf16c": dict(precision=hq.DAVIDSON_MIXED,
-                                    inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2)}
+                "mixed_bf16ab": dict(precision=hq.DAVIDSON_MIXED,
+                                     inner_precision=hq.PREC_FP32_BF16AB, inner_tol=3e-2)}
     runs = {}
     for name, kw in variants.items():
         runs[name] = hq.davidson(ham, sub, la, lb, tol_residual=1e-6, tol_energy=1e-8,
@@ -976,7 +1059,7 @@ def main():
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32+f64",
+        "dtype": "f32+bf16+f64",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: n_orb={n} n_alpha={na} n_beta={nb} "
                                f"{sub.Na}x{sub.Nb} strings, N={N} determinants",
@@ -999,7 +1082,7 @@ def main():
                    "fp64_sigmas": fp64_runs[-1].n_sigma_fp64, "mixed_status": last.status},
         "sigma_ms": {k: sig3(1e3 * v) for k, v in t_sig.items()},
         "sigma_dets_per_s": {k: sig3(N / v) for k, v in t_sig.items()},
-        "time_to_1e-6_Ha_s": {"mixed_bf16": sig3(tt_mixed), "fp64": sig3(tt_fp64),
+        "time_to_1e-6_Ha_s": {"mixed_bf16c": sig3(tt_mixed), "fp64": sig3(tt_fp64),
                               **{k: sig3(v) for k, v in tt_variants.items()},
                               "speedup_mixed_vs_fp64": sig3(tt_fp64 / tt_mixed)
                               if (tt_fp64 and tt_mixed) else None},
