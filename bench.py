@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--detail", action="store_true", help="per-component timings to stderr")
     ap.add_argument("--probe", default=None,
                     help="PART:PREC[:tune] -- run one sigma product (PART sigma|same|opposite, "
-                         "PREC fp64|fp32|bf16ab|bf16x3ab) on the workload, untimed, and exit "
+                         "PREC fp64|fp32|bf16ab|bf16x3ab|bf16c|fp64dfab) on the workload, untimed, and exit "
                          "(the target of kernel-level ncu captures); ':tune' autotunes first; "
                          "'pt2' -- one classical expansion and PT2 scoring on the converged "
                          "eigenvector")
@@ -784,7 +784,8 @@ def main():
     if args.probe:
         part, pname, *rest = args.probe.split(":")
         prec = {"fp64": hq.PREC_FP64, "fp32": hq.PREC_FP32, "bf16ab": hq.PREC_FP32_BF16AB,
-                "bf16x3ab": hq.PREC_FP32_BF16X3AB, "bf16c": hq.PREC_FP32_BF16C}[pname]
+                "bf16x3ab": hq.PREC_FP32_BF16X3AB, "bf16c": hq.PREC_FP32_BF16C,
+                "fp64dfab": hq.PREC_FP64_DFAB}[pname]
         ham_p = hq.Hamiltonian(h_d, eri_d, na, nb, w["e_nuc"])
         sub_p = hq.build_subspace(a_d, b_d, n, na, nb)
         la_p, lb_p = hq.string_links(ham_p, sub_p, 0), hq.string_links(ham_p, sub_p, 1)
@@ -793,7 +794,7 @@ def main():
             hq.autotune(ham_p, sub_p, la_p, lb_p, prec)
             tuning = la_p.tuning()
         x = torch.tensor(synth.random_vector(sub_p.N, 3), device=dev)
-        x = x if prec == hq.PREC_FP64 else x.float()
+        x = x if prec in (hq.PREC_FP64, hq.PREC_FP64_DFAB) else x.float()
         y = torch.zeros_like(x)
         if part == "sigma":
             hq.sigma(ham_p, sub_p, la_p, lb_p, x, out=y, precision=prec)
@@ -904,7 +905,7 @@ def main():
 
     precs = {"fp64": (hq.PREC_FP64, c64), "fp32": (hq.PREC_FP32, c32),
              "fp32_bf16ab": (hq.PREC_FP32_BF16AB, c32), "fp32_bf16x3ab": (hq.PREC_FP32_BF16X3AB, c32),
-             "fp32_bf16c": (hq.PREC_FP32_BF16C, c32)}
+             "fp32_bf16c": (hq.PREC_FP32_BF16C, c32), "fp64_dfab": (hq.PREC_FP64_DFAB, c64)}
     t_sig = {}
     for name, (p, x) in precs.items():
         out = torch.empty_like(x)

@@ -85,6 +85,12 @@ extern "C" {
  * refinement removes the rounding.  Links of more than 2^32 padded elements take the
  * FP32 same-spin half. */
 #define HINQS_PREC_FP32_BF16C 4
+/* c, sigma: double; as HINQS_PREC_FP64 but the opposite-spin term in double-float
+ * arithmetic (each value an unevaluated sum of two FP32 numbers; error-free products by
+ * fused multiply-add, two-sum accumulation; about 1e-13 relative), which runs several
+ * times faster than FP64 on this part.  Not in the paper: the refinement product of
+ * the mixed Davidson (hinqs_davidson_opts.refine_precision). */
+#define HINQS_PREC_FP64_DFAB 5
 
 /* Davidson precision */
 #define HINQS_DAVIDSON_FP64 0   /* every sigma in FP64 */
@@ -260,12 +266,14 @@ typedef struct hinqs_davidson_opts {
                            Ritz vector, the previous one and the next-lowest Ritz vectors,
                            this many in all (1 .. max_subspace - 1); mixed: the FP64 anchor
                            and the next-lowest FP32 Ritz vectors (1 .. max_subspace - 2) */
+  int refine_precision; /* mixed: precision of the refinement products H x of the FP64
+                           vector: HINQS_PREC_FP64_DFAB (default) or HINQS_PREC_FP64 */
 } hinqs_davidson_opts;
 
 typedef struct hinqs_davidson_info {
   int status;           /* HINQS_OK or HINQS_NOT_CONVERGED */
   int iterations;       /* Davidson iterations */
-  int n_sigma_fp64;     /* FP64 sigma products */
+  int n_sigma_fp64;     /* FP64 sigma products (refinement products included) */
   int n_sigma_fp32;     /* FP32 sigma products */
   int n_restarts;
   int n_refinements;    /* mixed: outer FP64 refinement cycles */

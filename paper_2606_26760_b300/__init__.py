@@ -38,7 +38,8 @@ ERR_ARG, ERR_PARTICLE_NUMBER, ERR_ASYMMETRIC, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ER
     -1, -2, -3, -4, -5, -6, -7)
 DROP_BAD, ERROR_BAD, FULL_SPACE = 0x0, 0x1, 0x2
 CHECK_SYMMETRY = 0x1
-PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB, PREC_FP32_BF16C = 0, 1, 2, 3, 4
+PREC_FP64, PREC_FP32, PREC_FP32_BF16AB, PREC_FP32_BF16X3AB, PREC_FP32_BF16C, PREC_FP64_DFAB = (
+    0, 1, 2, 3, 4, 5)
 DAVIDSON_FP64, DAVIDSON_MIXED = 0, 1
 BASIS_COLD_START, BASIS_RESCORE, BASIS_APPEND = 0, 1, 2
 
@@ -64,7 +65,8 @@ class _Opts(ctypes.Structure):
                 ("trace_resid", ctypes.POINTER(ctypes.c_double)),
                 ("trace_time", ctypes.POINTER(ctypes.c_double)),
                 ("trace_kind", ctypes.POINTER(ctypes.c_int)),
-                ("inner_precision", ctypes.c_int), ("restart_keep", ctypes.c_int)]
+                ("inner_precision", ctypes.c_int), ("restart_keep", ctypes.c_int),
+                ("refine_precision", ctypes.c_int)]
 
 
 class _Info(ctypes.Structure):
@@ -325,7 +327,7 @@ def sigma(ham, sub, la, lb, c, out=None, precision: int | None = None):
     given (the tensor-core modes take float32 vectors)."""
     if precision is None:
         precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
-    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    dt = _vec_dtype(precision)
     if c.dtype != dt or not c.is_cuda or not c.is_contiguous():
         raise ValueError(f"c must be a contiguous CUDA {dt} tensor")
     if c.numel() != sub.N:
@@ -343,7 +345,7 @@ def sigma_batch(problems, cs, precision: int | None = None, outs=None):
         return []
     if precision is None:
         precision = PREC_FP64 if cs[0].dtype == torch.float64 else PREC_FP32
-    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    dt = _vec_dtype(precision)
     for c, p in zip(cs, problems):
         if c.dtype != dt or not c.is_cuda or not c.is_contiguous() or c.numel() != p[1].N:
             raise ValueError(f"each c must be a contiguous CUDA {dt} tensor of its subspace size")
@@ -382,8 +384,13 @@ class DavidsonResult:
     trace: dict = field(default_factory=dict)
 
 
+def _vec_dtype(precision):
+    """Vector dtype of a sigma precision: float64 for the FP64 modes, else float32."""
+    return torch.float64 if precision in (PREC_FP64, PREC_FP64_DFAB) else torch.float32
+
+
 def _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor, inner_tol,
-               inner_precision, restart_keep=0):
+               inner_precision, restart_keep=0, refine_precision=None):
     opts = _Opts()
     _lib.hinqs_davidson_default_opts(ctypes.byref(opts))
     opts.precision, opts.max_iter, opts.max_subspace = precision, max_iter, max_subspace
@@ -391,14 +398,16 @@ def _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, deno
     opts.inner_tol = inner_tol
     opts.inner_precision = inner_precision
     opts.restart_keep = restart_keep
+    if refine_precision is not None:
+        opts.refine_precision = refine_precision
     return opts
 
 
 def _davidson_call(fn, args, n, guess, precision, max_iter, max_subspace, tol_residual,
                    tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out,
-                   restart_keep=0):
+                   restart_keep=0, refine_precision=None):
     opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
-                      inner_tol, inner_precision, restart_keep)
+                      inner_tol, inner_precision, restart_keep, refine_precision)
     bufs = None
     if trace_cap > 0:
         bufs = ((ctypes.c_double * trace_cap)(), (ctypes.c_double * trace_cap)(),
@@ -430,25 +439,28 @@ def _davidson_call(fn, args, n, guess, precision, max_iter, max_subspace, tol_re
 def davidson(ham, sub, la, lb, guess=None, precision: int = DAVIDSON_FP64, max_iter: int = 200,
              max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
              denom_floor: float = 1e-4, inner_tol: float = 1e-3, trace_cap: int = 0,
-             inner_precision: int = PREC_FP32, out=None, restart_keep: int = 0) -> DavidsonResult:
+             inner_precision: int = PREC_FP32, out=None, restart_keep: int = 0,
+             refine_precision: int | None = None) -> DavidsonResult:
     """hinqs_davidson: lowest eigenpair of H on the product subspace (Step 3)."""
     return _davidson_call(_lib.hinqs_davidson, (ham.handle, sub.handle, la.handle, lb.handle),
                           sub.N, guess, precision, max_iter, max_subspace, tol_residual,
                           tol_energy, denom_floor, inner_tol, trace_cap, inner_precision, out,
-                          restart_keep)
+                          restart_keep, refine_precision)
 
 
 def davidson_list(ham, sub, la, lb, lst, guess=None, precision: int = DAVIDSON_FP64,
                   max_iter: int = 200, max_subspace: int = 16, tol_residual: float = 1e-8,
                   tol_energy: float = 1e-10, denom_floor: float = 1e-4, inner_tol: float = 1e-3,
                   trace_cap: int = 0, inner_precision: int = PREC_FP32,
-                  out=None, restart_keep: int = 0) -> DavidsonResult:
+                  out=None, restart_keep: int = 0,
+                  refine_precision: int | None = None) -> DavidsonResult:
     """hinqs_davidson_list: lowest eigenpair of H_B over the basis list `lst` (Step 3);
     the eigenvector is indexed by the list's entries."""
     return _davidson_call(_lib.hinqs_davidson_list,
                           (ham.handle, sub.handle, la.handle, lb.handle, lst.handle), lst.m,
                           guess, precision, max_iter, max_subspace, tol_residual, tol_energy,
-                          denom_floor, inner_tol, trace_cap, inner_precision, out, restart_keep)
+                          denom_floor, inner_tol, trace_cap, inner_precision, out, restart_keep,
+                          refine_precision)
 
 
 class DetList:
@@ -511,7 +523,7 @@ def sigma_list(ham, sub, la, lb, lst, c, out=None, precision: int | None = None)
     """hinqs_sigma_list: sigma = P H P c over the basis list (float64 or float32 c)."""
     if precision is None:
         precision = PREC_FP64 if c.dtype == torch.float64 else PREC_FP32
-    dt = torch.float64 if precision == PREC_FP64 else torch.float32
+    dt = _vec_dtype(precision)
     if c.dtype != dt or not c.is_cuda or not c.is_contiguous() or c.numel() != lst.m:
         raise ValueError(f"c must be a contiguous CUDA {dt} tensor of the list's length")
     out = torch.empty_like(c) if out is None else out
@@ -591,7 +603,7 @@ def davidson_batch(problems, guesses=None, precision: int = DAVIDSON_FP64, max_i
                    max_subspace: int = 16, tol_residual: float = 1e-8, tol_energy: float = 1e-10,
                    denom_floor: float = 1e-4, inner_tol: float = 1e-3,
                    inner_precision: int = PREC_FP32, n_streams: int = 0, autotune: bool = False,
-                   outs=None):
+                   outs=None, refine_precision: int | None = None):
     """hinqs_davidson_batch over `problems` = [(ham, sub, la, lb), ...]: every
     geometry solved as davidson() would; n_streams <= 0 runs them in lockstep with one
     batched launch per sigma stage per round, n_streams > 0 on that many worker streams.
@@ -600,7 +612,7 @@ def davidson_batch(problems, guesses=None, precision: int = DAVIDSON_FP64, max_i
     if G == 0:
         return []
     opts = _make_opts(precision, max_iter, max_subspace, tol_residual, tol_energy, denom_floor,
-                      inner_tol, inner_precision)
+                      inner_tol, inner_precision, refine_precision=refine_precision)
     dev = _dev()
     cs = outs if outs is not None else [torch.empty(p[1].N, dtype=torch.float64, device=dev)
                                         for p in problems]

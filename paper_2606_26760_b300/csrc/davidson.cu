@@ -865,10 +865,25 @@ __global__ void k_argmin_index(const double* __restrict__ D, int64_t N,
     if (u == *best) atomicMin(idx, (unsigned long long)j);
   }
 }
+// The cold guess: the unit vector at the lowest diagonal entry plus a seeded
+// perturbation of norm ~1e-3 (components eps * u_j, u_j uniform in [-1, 1) from
+// SplitMix64 (Steele, Lea and Flood 2014) of the index j).  A unit vector alone has no
+// component along eigenvectors that H never couples to it (the Krylov space of e_k
+// misses them, e.g. a ground state of another spin than the lowest determinant), and
+// Davidson would then converge to the lowest state it can reach instead of the lowest.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
 __global__ void k_unit(double* x, int64_t N, const unsigned long long* idx) {
+  const double eps = 1e-3 * sqrt(3.0 / (double)N);
   for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
-       j += (int64_t)gridDim.x * blockDim.x)
-    x[j] = (j == (int64_t)*idx) ? 1.0 : 0.0;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    const double u = (double)(splitmix64((uint64_t)j) >> 11) * 0x1.0p-52 - 1.0;
+    x[j] = ((j == (int64_t)*idx) ? 1.0 : 0.0) + eps * u;
+  }
 }
 
 __global__ void k_set_G(double* G, int ldg, int col, const double* vals, int m, int row_off) {
@@ -1366,7 +1381,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
     std::vector<double> hs(kVecOut + 1);
     for (;;) {
       if (hard) {
-        HQ_TRY(apply_sigma(c, x, sx, HINQS_PREC_FP64));
+        HQ_TRY(apply_sigma(c, x, sx, o.refine_precision));
         info.n_sigma_fp64++;
         total++;
         double* th = c.small + 2 * kMaxSub;
@@ -1560,6 +1575,7 @@ extern "C" void hinqs_davidson_default_opts(hinqs_davidson_opts* o) {
   o->trace_kind = nullptr;
   o->inner_precision = HINQS_PREC_FP32;
   o->restart_keep = 0;
+  o->refine_precision = HINQS_PREC_FP64_DFAB;
 }
 
 // Device bytes one hinqs_davidson call requests from the stream-ordered pool at its
@@ -1625,6 +1641,9 @@ int hinqs::davidson_run(const hinqs_ham* H, const hinqs_subspace* B, const hinqs
       o.inner_precision != HINQS_PREC_FP32_BF16AB && o.inner_precision != HINQS_PREC_FP32_BF16X3AB &&
       o.inner_precision != HINQS_PREC_FP32_BF16C)
     return fail(HINQS_ERR_ARG, "%s: unknown inner precision %d", who, o.inner_precision);
+  if (o.precision == HINQS_DAVIDSON_MIXED && o.refine_precision != HINQS_PREC_FP64 &&
+      o.refine_precision != HINQS_PREC_FP64_DFAB)
+    return fail(HINQS_ERR_ARG, "%s: unknown refinement precision %d", who, o.refine_precision);
   // the list operator has no tensor-core form: its inner products run in FP32
   if (L && o.precision == HINQS_DAVIDSON_MIXED) o.inner_precision = HINQS_PREC_FP32;
   hinqs_davidson_info info{};

@@ -297,7 +297,7 @@ int sigma_list_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   (void)B;
   if (L->m == 0) return HINQS_OK;
   const unsigned grid = list_grid(L->m, kListWarps);
-  if (precision == HINQS_PREC_FP64) {
+  if (precision == HINQS_PREC_FP64 || precision == HINQS_PREC_FP64_DFAB) {
     k_sigma_list<double><<<grid, 32 * kListWarps, 0, s>>>(list_args<double>(H, la, lb, L),
                                                            (const double*)c, (double*)sigma);
   } else if (precision >= HINQS_PREC_FP32 && precision <= HINQS_PREC_FP32_BF16C) {

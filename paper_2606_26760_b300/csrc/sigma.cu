@@ -724,6 +724,120 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
   }
 }
 
+// ---------------------------------------------------------------------------
+// HINQS_PREC_FP64_DFAB: the opposite-spin term of an FP64 product in double-float
+// arithmetic (a value is an unevaluated sum hi + lo of two FP32 numbers): FP64 runs at
+// 1/64 of the FP32 rate on this part, and a double-float multiply-add is about twelve
+// FP32 operations.  Products are exact up to the dropped lo*lo term (the error-free
+// product by fused multiply-add), sums use the two-sum of Knuth, so each term carries
+// about 2^-44 relative error and the result about 1e-13 relative: far below what the
+// refinement residual of the mixed solver needs.
+
+// (sh, sl) += (ah + al) * (bh + bl)
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh,
+                                       float& sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl += err + e;
+}
+
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
+// The structure of k_sigma_ab (one block per alpha string Ja, CH alpha singles per
+// pass, (pq|.) rows transposed in shared memory), with the rows and C split into
+// double-float pairs once when they are staged and the sums kept as pairs.
+template <int CH, bool ROW_SMEM>
+__global__ void __launch_bounds__(256) k_sigma_ab_df(const double* __restrict__ C,
+                                                     double* __restrict__ sig, AbArgs A,
+                                                     const double* __restrict__ eri) {
+  constexpr int LD = CH + 2;  // padded row of eriT (float2 entries)
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int n2 = A.n * A.n;
+  float2* eriT = reinterpret_cast<float2*>(smem_raw);  // [n2][LD]
+  int* tgt = reinterpret_cast<int*>(eriT + (size_t)n2 * LD);
+  float2* Crow = reinterpret_cast<float2*>(tgt + CH + 4);  // [Nb]
+  const int64_t Ja = blockIdx.x;
+  const int64_t a_beg = A.a_srow[Ja], a_end = A.a_srow[Ja + 1];
+  if (a_beg == a_end) return;
+  const double* Cg = C + Ja * A.Nb;
+  if (ROW_SMEM) {
+    for (int64_t j = threadIdx.x; j < A.Nb; j += blockDim.x) Crow[j] = df_split(Cg[j]);
+  }
+  for (int64_t a0 = a_beg; a0 < a_end; a0 += CH) {
+    const int cnt = (int)min64(CH, a_end - a0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < n2 * CH; i += blockDim.x) {
+      const int xy = i / CH, a = i % CH;
+      double v = 0.0;
+      if (a < cnt) {
+        const int sp = A.a_slink[a0 + a].y;
+        const int pq = (sp > 0 ? sp : -sp) - 1;
+        v = eri[(int64_t)pq * n2 + xy];
+        if (sp < 0) v = -v;
+      }
+      eriT[xy * LD + a] = df_split(v);
+    }
+    if (threadIdx.x < CH) tgt[threadIdx.x] = (threadIdx.x < cnt) ? A.a_slink[a0 + threadIdx.x].x : 0;
+    __syncthreads();
+    for (int64_t Ib0 = 0; Ib0 < A.Nb; Ib0 += blockDim.x) {
+      const int64_t Ib = Ib0 + threadIdx.x;
+      const bool live = Ib < A.Nb;
+      float eh[CH], el[CH];
+#pragma unroll
+      for (int a = 0; a < CH; ++a) eh[a] = 0.f, el[a] = 0.f;
+      const int nk = live ? A.b_cnt[Ib] : 0;
+      const int2* ell = A.b_ell + Ib;
+      for (int k = 0; k < nk; ++k) {
+        const int2 l0 = ell[(int64_t)k * A.Nb];
+        float2 v = ROW_SMEM ? Crow[l0.x] : df_split(Cg[l0.x]);
+        if (l0.y < 0) v.x = -v.x, v.y = -v.y;
+        const float2* er = eriT + ((l0.y > 0 ? l0.y : -l0.y) - 1) * LD;
+#pragma unroll
+        for (int a = 0; a < CH; ++a) {
+          const float2 b = er[a];
+          df_fma(v.x, v.y, b.x, b.y, eh[a], el[a]);
+        }
+      }
+      if (live) {
+#pragma unroll
+        for (int a = 0; a < CH; ++a)
+          if (a < cnt) atomicAdd(sig + (int64_t)tgt[a] * A.Nb + Ib, (double)eh[a] + (double)el[a]);
+      }
+    }
+  }
+}
+
+template <int CH>
+static int launch_ab_df(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
+                        const hinqs_links_s* lb, const double* c, double* sig, cudaStream_t s,
+                        size_t smem_limit) {
+  AbArgs A{B->Na, B->Nb, H->n, la->srow_ptr, la->slink, lb->sell, lb->scount, B->Nb % 4 == 0};
+  const int n2 = H->n * H->n;
+  size_t base = (size_t)n2 * (CH + 2) * sizeof(float2) + (CH + 4) * sizeof(int);
+  base = (base + 15) & ~(size_t)15;
+  const size_t with_row = base + (((size_t)B->Nb * sizeof(float2) + 15) & ~(size_t)15);
+  if (with_row <= smem_limit) {
+    auto kern = k_sigma_ab_df<CH, true>;
+    HQ_TRY(allow_max_smem(kern));
+    kern<<<(unsigned)B->Na, 256, with_row, s>>>(c, sig, A, H->eri);
+  } else {
+    auto kern = k_sigma_ab_df<CH, false>;
+    HQ_TRY(allow_max_smem(kern));
+    kern<<<(unsigned)B->Na, 256, base, s>>>(c, sig, A, H->eri);
+  }
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
 template <typename T, int CH>
 static int launch_ab(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                      const hinqs_links_s* lb, const T* c, T* sig, cudaStream_t s,
@@ -811,6 +925,8 @@ static int spmm_rows(const T* X, T* Y, int64_t nrows, int64_t ncols, const hinqs
   return HINQS_OK;
 }
 
+constexpr int kDoubleFloat = -1;  // sigma_impl<double>: opposite-spin term in double-float
+
 template <typename T>
 static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                       const hinqs_links_s* lb, const T* c, T* sig, cudaStream_t s,
@@ -841,6 +957,12 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
       if (tc_split) {
         const int r = sigma_ab_tc_launch(H, B, la, lb, c, sig, tc_split, s);
         if (r != kTcNoFit) return r;
+      }
+    } else {
+      if (tc_split == kDoubleFloat) {  // the opposite-spin term in double-float
+        const int ch = (size_t)n2 * 18 * sizeof(float2) + 256 <= limit / 2 ? 16 : 8;
+        return ch == 16 ? launch_ab_df<16>(H, B, la, lb, c, sig, s, limit)
+                        : launch_ab_df<8>(H, B, la, lb, c, sig, s, limit);
       }
     }
     auto need = [&](int ch) { return (size_t)n2 * (ch + 16 / sizeof(T)) * sizeof(T) + 256; };
@@ -945,7 +1067,8 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
   std::vector<int> f32;
   for (int i = 0; i < n; ++i) {
     const SigmaReq& r = reqs[i];
-    if (r.precision == HINQS_PREC_FP64 || r.precision == HINQS_PREC_FP32_BF16C ||
+    if (r.precision == HINQS_PREC_FP64 || r.precision == HINQS_PREC_FP64_DFAB ||
+        r.precision == HINQS_PREC_FP32_BF16C ||
         !r.la->rec32 || !r.lb->rec32 ||
         r.B->Na * r.B->Nb >= kBatchSoloN) {
       HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
@@ -1037,6 +1160,9 @@ int sigma_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_li
                  cudaStream_t s, int parts) {
   if (precision == HINQS_PREC_FP64)
     return sigma_impl<double>(H, B, la, lb, (const double*)c, (double*)sigma, s, 0, parts);
+  if (precision == HINQS_PREC_FP64_DFAB)
+    return sigma_impl<double>(H, B, la, lb, (const double*)c, (double*)sigma, s, kDoubleFloat,
+                              parts);
   if (precision == HINQS_PREC_FP32)
     return sigma_impl<float>(H, B, la, lb, (const float*)c, (float*)sigma, s, 0, parts);
   if (precision == HINQS_PREC_FP32_BF16AB)
@@ -1103,11 +1229,12 @@ extern "C" int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_bet
                                           int precision, size_t* bytes) {
   if (!bytes || n_alpha_strings < 0 || n_beta_strings < 0)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: NULL output or negative size");
-  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16C)
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP64_DFAB)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_workspace_size: unknown precision %d", precision);
   // the transposed vector and the transposed partial result of the same-spin half
   // (BF16C: the two padded BF16 copies and the transposed FP32 partial result)
-  const size_t elem = precision == HINQS_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t elem = (precision == HINQS_PREC_FP64 || precision == HINQS_PREC_FP64_DFAB)
+                          ? sizeof(double) : sizeof(float);
   *bytes = 2 * (size_t)(n_alpha_strings * n_beta_strings) * elem;
   if (precision == HINQS_PREC_FP32_BF16C) {
     const size_t pa = (size_t)(n_alpha_strings + 63) / 64 * 64;
@@ -1138,7 +1265,7 @@ extern "C" int hinqs_sigma_batch(int n, const hinqs_ham* const* hams,
                                  void* const* sigmas, int precision, void* stream) {
   if (n < 0 || (n > 0 && (!hams || !subs || !las || !lbs || !cs || !sigmas)))
     return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: NULL arrays");
-  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP32_BF16C)
+  if (precision < HINQS_PREC_FP64 || precision > HINQS_PREC_FP64_DFAB)
     return fail(HINQS_ERR_ARG, "hinqs_sigma_batch: unknown precision %d", precision);
   std::vector<SigmaReq> reqs;
   for (int g = 0; g < n; ++g) {

@@ -1155,13 +1155,17 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   a.sig = sig;
   a.crow_smem = 0;
   // alpha strings with more than 64 singles take 128-column chunks when the tiles fit,
-  // else 64-column chunks in several passes; kTcNoFit when neither fits
-  const bool wide = la->max_srow > 64;
+  // else 64-column chunks in several passes; at most 32 singles a string: 32-column
+  // chunks (half the MMA and operand work of a 64-column chunk, more CTAs per SM);
+  // kTcNoFit when nothing fits
+  const bool wide = la->max_srow > 64, narrow = la->max_srow <= 32;
   if (split == 3) {
     if (wide && tc::fits<128, 3>(a)) return tc::launch_fit<128, 3>(a, la->tune_stages, s);
+    if (narrow && tc::fits<32, 3>(a)) return tc::launch_fit<32, 3>(a, la->tune_stages, s);
     return tc::fits<64, 3>(a) ? tc::launch_fit<64, 3>(a, la->tune_stages, s) : kTcNoFit;
   }
   if (wide && tc::fits<128, 1>(a)) return tc::launch_fit<128, 1>(a, la->tune_stages, s);
+  if (narrow && tc::fits<32, 1>(a)) return tc::launch_fit<32, 1>(a, la->tune_stages, s);
   return tc::fits<64, 1>(a) ? tc::launch_fit<64, 1>(a, la->tune_stages, s) : kTcNoFit;
 }
 

@@ -329,18 +329,63 @@ def test_sigma_bf16c_full_size(precision_workload):
     assert float(torch.max(torch.abs(s - s32))) <= 2e-2 * float(torch.max(torch.abs(s32)))
 
 
+@pytest.mark.parametrize("name", SMALL)
+def test_sigma_fp64_double_float_opposite_spin(name):
+    """HINQS_PREC_FP64_DFAB: the opposite-spin term in double-float arithmetic (FP32
+    pairs, error-free products, two-sum accumulation, ~2^-44 per term) is held to the
+    FP64 bound against the oracle."""
+    B = built(name)
+    N = len(B.sa) * len(B.sb)
+    for seed in (1, 2):
+        c = synth.random_vector(N, seed)
+        ref = oracle.sigma(B.H, B.sa, B.sb, c)
+        hd = oracle.diag(B.H, B.sa, B.sb)
+        ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+        s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=hq.PREC_FP64_DFAB).cpu().numpy()
+        assert np.all(np.abs(s - ref) <= _sigma_tol(1e-11, hd, c, ref))
+
+
+def test_sigma_double_float_full_size(precision_workload):
+    """Sampled rows against the oracle and the whole vector against the FP64 product."""
+    B = precision_workload
+    c = synth.random_vector(B.sub.N, 5)
+    ct = torch.tensor(c, dtype=torch.float64, device="cuda")
+    s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=hq.PREC_FP64_DFAB)
+    s64 = hq.sigma(B.ham, B.sub, B.la, B.lb, ct)
+    assert float(torch.max(torch.abs(s - s64))) <= 1e-12 * float(torch.max(torch.abs(s64)))
+    rows = np.sort(np.random.default_rng(6).choice(B.sub.N, size=128, replace=False))
+    ref = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
+    hd = oracle.diag(B.H, B.sa, B.sb, rows=rows)
+    assert np.all(np.abs(s.cpu().numpy()[rows] - ref) <= _sigma_tol(1e-11, hd, c[rows], ref))
+
+
+def test_davidson_mixed_refinement_precisions():
+    """The mixed solver's refinement products in double-float (the default) and in FP64
+    reach the same eigenpair."""
+    B = built("hf_12_4_4")
+    E, _ = ground_state(B)
+    kw = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16C,
+              tol_residual=1e-9, tol_energy=1e-12, max_iter=600)
+    a = hq.davidson(B.ham, B.sub, B.la, B.lb, refine_precision=hq.PREC_FP64_DFAB, **kw)
+    b = hq.davidson(B.ham, B.sub, B.la, B.lb, refine_precision=hq.PREC_FP64, **kw)
+    assert a.status == hq.OK and b.status == hq.OK
+    assert abs(a.energy - E) <= 1e-9 and abs(b.energy - E) <= 1e-9
+    assert abs(abs(torch.dot(a.c, b.c).item()) - 1.0) <= 1e-12
+
+
 def test_sigma_halves_sum_to_sigma(precision_workload):
     """hinqs_sigma_same_spin + hinqs_sigma_opposite_spin == hinqs_sigma in every mode."""
     B = precision_workload
     c = torch.tensor(synth.random_vector(B.sub.N, 7), device="cuda")
     for prec, x in ((hq.PREC_FP64, c), (hq.PREC_FP32, c.float()),
                     (hq.PREC_FP32_BF16AB, c.float()), (hq.PREC_FP32_BF16X3AB, c.float()),
-                    (hq.PREC_FP32_BF16C, c.float())):
+                    (hq.PREC_FP32_BF16C, c.float()), (hq.PREC_FP64_DFAB, c)):
         full = hq.sigma(B.ham, B.sub, B.la, B.lb, x, precision=prec)
         part = torch.empty_like(x)
         hq.sigma_part(B.ham, B.sub, B.la, B.lb, x, part, "same", precision=prec)
         hq.sigma_part(B.ham, B.sub, B.la, B.lb, x, part, "opposite", precision=prec)
-        tol = (1e-12 if prec == hq.PREC_FP64 else 1e-5) * float(torch.max(torch.abs(full)))
+        tol = (1e-12 if prec in (hq.PREC_FP64, hq.PREC_FP64_DFAB) else 1e-5) * float(
+            torch.max(torch.abs(full)))
         assert float(torch.max(torch.abs(full - part))) <= tol
 
 
