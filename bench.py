@@ -551,11 +551,10 @@ def run_bond_scan(args):
 
 def run_large(args):
     """n_orb = 26, (7,7), 20000 x 20000 strings (4e8 determinants): one step =
-    Hamiltonian, subspace, links, mixed Davidson (BF16 tensor-core inner sigma, FP64
-    refinement, subspace of 8) to a 1e-5 residual (energy converged far below
-    1e-6 Ha: the error is about residual^2 / gap), RDMs with the backward and the
-    marginals.  The FP64 Davidson is not run here (about 150 FP64 products of ~3 s);
-    one FP64 sigma is timed instead."""
+    Hamiltonian, subspace, links, mixed Davidson (BF16-operand inner sigma, double-float
+    refinement, subspace of 16) to a 1e-5 residual, RDMs with the backward and the
+    marginals.  The FP64 Davidson (about 340 FP64 products of ~2.8 s) runs only with
+    --fp64-ref, as E_ref for both solvers' time-to-1e-6 Ha; one FP64 sigma is timed."""
     import numpy as np
     import torch
 
@@ -576,7 +575,7 @@ def run_large(args):
     b_d = torch.from_numpy(w["beta"].view(np.int64)).to(dev)
     stream = torch.cuda.current_stream()
     opts = dict(precision=hq.DAVIDSON_MIXED, inner_precision=hq.PREC_FP32_BF16C, inner_tol=3e-2,
-                tol_residual=1e-5, tol_energy=1e-7, max_subspace=8, max_iter=300)
+                tol_residual=1e-5, tol_energy=1e-7, max_subspace=16, max_iter=800)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     parts = {}
 
@@ -639,8 +638,9 @@ def run_large(args):
         del g1, g2
         torch.cuda.empty_cache()
         rf = hq.davidson(ham, sub, la, lb, precision=hq.DAVIDSON_FP64, tol_residual=1e-8,
-                         tol_energy=1e-11, max_subspace=8, max_iter=600, trace_cap=1024)
-        rm = hq.davidson(ham, sub, la, lb, trace_cap=1024, **opts)
+                         tol_energy=1e-11, max_subspace=8, max_iter=1000, trace_cap=2048)
+        rm = hq.davidson(ham, sub, la, lb, trace_cap=2048,
+                         **dict(opts, tol_residual=1e-6, tol_energy=1e-8))
 
         def tt(r):
             return next((t for th, t, k in zip(r.trace["theta"], r.trace["time"], r.trace["kind"])
@@ -658,7 +658,7 @@ def run_large(args):
         "dtype": "f32+bf16+f64", "data": "synthetic",
         "config": {"workload": f"large: n_orb={n} n_alpha={na} n_beta={nb} {sub.Na}x{sub.Nb} "
                                f"strings, N={sub.N} determinants",
-                   "step": "ham+subspace+links+mixed Davidson (m_max 8) to 1e-5 residual+RDM "
+                   "step": "ham+subspace+links+mixed Davidson (m_max 16) to 1e-5 residual+RDM "
                            "backward+marginals"},
         "parts_s": parts, "sigma_ms": sig,
         "energy": {"mixed": res.energy, "residual": res.residual, "status": int(res.status),
