@@ -535,6 +535,57 @@ __global__ void __launch_bounds__(kRedThreads) k_anchor_row32(
   acc.finish(m, MB, m, partial, counter, out);  // {x32.V_i, ra.V_i}
 }
 
+// A restart of the mixed solver in one pass over {x, s, V, W}: for the kk lowest Ritz
+// vectors y_k of the pencil (anchor coefficient y_k0, V coefficients y_ki),
+//   k = 0:  xn = y_00 x + sum_i y_0i V_i,  sxn = y_00 s + sum_i y_0i W_i   (FP64 out)
+//   k >= 1: U_{k-1} = y_k0 x32 + sum_i y_ki V_i,
+//           WU_{k-1} = y_k0 (ra + theta_a x32) + sum_i y_ki W_i          (FP32 out)
+// (s = ra + theta_a x up to the FP32 rounding of ra and x32).  The V and W sums are FP32,
+// the corrections they carry; only xn and sxn take FP64 arithmetic.
+template <int MB>
+__global__ void __launch_bounds__(kRedThreads) k_restart32(
+    const double* __restrict__ x, const double* __restrict__ sx, const float* __restrict__ x32,
+    const float* __restrict__ ra, const float* __restrict__ V, const float* __restrict__ W,
+    int64_t ld, int m, const double* __restrict__ all, int kk, const double* __restrict__ theta_a,
+    int64_t N, double* __restrict__ xn, double* __restrict__ sxn, float* __restrict__ U,
+    float* __restrict__ WU) {
+  __shared__ float yv[kMaxSub][kMaxSub];
+  __shared__ double y0[kMaxSub];
+  for (int t = threadIdx.x; t < kMaxSub * kMaxSub; t += blockDim.x) yv[t / kMaxSub][t % kMaxSub] = 0.f;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kk * (m + 1); t += blockDim.x) {
+    const int k = t / (m + 1), i = t % (m + 1);
+    const double v = all[(size_t)k * kRitzStride + 1 + i];
+    if (i == 0) y0[k] = v;
+    else yv[k][i - 1] = (float)v;
+  }
+  __syncthreads();
+  const float tha = (float)*theta_a;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < N;
+       j += (int64_t)gridDim.x * blockDim.x) {
+    float v[MB], w[MB];
+#pragma unroll
+    for (int i = 0; i < MB; ++i) {
+      v[i] = 0.f, w[i] = 0.f;
+      if (i < m) v[i] = V[i * ld + j], w[i] = W[i * ld + j];
+    }
+    const float xf = x32[j], sf = fmaf(tha, xf, ra[j]);
+    for (int k = 0; k < kk; ++k) {
+      float a = 0.f, b = 0.f;
+#pragma unroll
+      for (int i = 0; i < MB; ++i) a = fmaf(yv[k][i], v[i], a), b = fmaf(yv[k][i], w[i], b);
+      if (k == 0) {
+        xn[j] = fma(y0[0], x[j], (double)a);
+        sxn[j] = fma(y0[0], sx[j], (double)b);
+      } else {
+        const float yk = (float)y0[k];
+        U[(k - 1) * ld + j] = fmaf(yk, xf, a);
+        WU[(k - 1) * ld + j] = fmaf(yk, sf, b);
+      }
+    }
+  }
+}
+
 // x32 = fp32(x), ra = fp32(s - theta_a x) with theta_a = G00 / S00 (written to *theta_a)
 __global__ void k_anchor32(const double* __restrict__ x, const double* __restrict__ s,
                            const double* __restrict__ gs, double* __restrict__ theta_a,
@@ -1306,6 +1357,14 @@ struct Col32 {
   }
 };
 template <int MB>
+struct Restart32 {
+  template <typename... A>
+  static void go(cudaStream_t s, A... a) {
+    static const int g = vec_grid(k_restart32<MB>);
+    k_restart32<MB><<<g, kRedThreads, 0, s>>>(a...);
+  }
+};
+template <int MB>
 struct Row32 {
   template <typename... A>
   static void go(cudaStream_t s, A... a) {
@@ -1321,12 +1380,12 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
   const int64_t N = c.N;
   double *x = nullptr, *sx = nullptr, *t = nullptr, *xn = nullptr, *sxn = nullptr, *G = nullptr,
          *S = nullptr, *G1 = nullptr, *ritz = nullptr, *ritz1 = nullptr, *all = nullptr,
-         *col = nullptr, *scol = nullptr, *tmp = nullptr, *vsum = nullptr, *qk = nullptr;
+         *col = nullptr, *scol = nullptr, *vsum = nullptr, *qk = nullptr;
   float *V = nullptr, *W = nullptr, *U = nullptr, *WU = nullptr, *x32 = nullptr, *ra = nullptr,
         *D32 = nullptr;
   int rc = HINQS_OK;
   if ((rc = dalloc(&x, N, c.s)) || (rc = dalloc(&sx, N, c.s)) || (rc = dalloc(&t, N, c.s)) ||
-      (rc = dalloc(&xn, N, c.s)) || (rc = dalloc(&sxn, N, c.s)) || (rc = dalloc(&tmp, N, c.s)) ||
+      (rc = dalloc(&xn, N, c.s)) || (rc = dalloc(&sxn, N, c.s)) ||
       (rc = dalloc(&V, (size_t)mmax * N, c.s)) || (rc = dalloc(&W, (size_t)mmax * N, c.s)) ||
       (rc = dalloc(&U, (size_t)keep * N, c.s)) || (rc = dalloc(&WU, (size_t)keep * N, c.s)) ||
       (rc = dalloc(&G, kMaxSub * kMaxSub, c.s)) || (rc = dalloc(&S, kMaxSub * kMaxSub, c.s)) ||
@@ -1338,7 +1397,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       (rc = dalloc(&x32, N, c.s)) || (rc = dalloc(&ra, N, c.s)) || (rc = dalloc(&D32, N, c.s))) {
   }
   auto cleanup = [&]() {
-    for (double* p : {x, sx, t, xn, sxn, tmp, G, S, G1, ritz, ritz1, all, col, scol, vsum, qk}) {
+    for (double* p : {x, sx, t, xn, sxn, G, S, G1, ritz, ritz1, all, col, scol, vsum, qk}) {
       double* q = p;
       dfree(q, c.s);
     }
@@ -1512,20 +1571,13 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       }
       // restart: anchor = lowest Ritz vector, plus keep-1 FP32 Ritz vectors
       const int kk = std::min(keep, m + 1);
-      // xn = y0 x + V y, sxn = y0 s + W y  (FP64 sums; the FP32 parts carry the correction)
-      HQ_TRY(lincomb<double>(c, xn, x, N, 1, all + 1, 0));
-      HQ_TRY(lincomb<float>(c, xn, V, N, m, all + 2, 1));
-      HQ_TRY(lincomb<double>(c, sxn, sx, N, 1, all + 1, 0));
-      HQ_TRY(lincomb<float>(c, sxn, W, N, m, all + 2, 1));
-      for (int j = 1; j < kk; ++j) {
-        const double* yj = all + (size_t)j * kRitzStride + 1;
-        HQ_TRY(lincomb<double>(c, tmp, x, N, 1, yj, 0));
-        HQ_TRY(lincomb<float>(c, tmp, V, N, m, yj + 1, 1));
-        k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(tmp, U + (size_t)(j - 1) * N, N);
-        HQ_TRY(lincomb<double>(c, tmp, sx, N, 1, yj, 0));
-        HQ_TRY(lincomb<float>(c, tmp, W, N, m, yj + 1, 1));
-        k_f64_to_f32<<<c.grid, 256, 0, c.s>>>(tmp, WU + (size_t)(j - 1) * N, N);
-      }
+      // xn = y0 x + V y, sxn = y0 s + W y (FP64) and the kept FP32 Ritz vectors with their
+      // products, in one pass (the FP32 parts carry the correction)
+      launch_mb<Restart32>(std::max(m, 1), c.s, (const double*)x, (const double*)sx,
+                           (const float*)x32, (const float*)ra, (const float*)V, (const float*)W,
+                           (int64_t)N, m, (const double*)all, kk, (const double*)theta_a, N, xn,
+                           sxn, U, WU);
+      HQ_LAUNCH_CHECK();
       // normalise the anchor (y^T S y = 1 up to rounding) and its product alike
       double* nrm = c.small + 2 * kMaxSub + 1;
       HQ_TRY(dots<double, double>(c, xn, N, 1, xn, nrm));
@@ -1593,7 +1645,7 @@ static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) 
   } else {
     const size_t mmax = (size_t)std::max(4, o.max_subspace);
     const size_t keep = (size_t)restart_keep_mixed(o);
-    b += 6 * (size_t)N * d;                                     // x, sx, t, xn, sxn, tmp
+    b += 5 * (size_t)N * d;                                     // x, sx, t, xn, sxn
     b += (2 * mmax + 2 * keep + 4) * (size_t)N * f;             // V, W, U, WU, t32, x32, ra, D32
     b += (4 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride +
           kVecOut) * d;

@@ -422,9 +422,11 @@ __device__ __forceinline__ void fma_bf16x8(float h, const uint4& x, float* acc) 
 // The row product of k_spmm_rec4 on the BF16 operand: eight columns per lane (one
 // 16-byte load per link and lane, a 512-byte segment of a 128-byte aligned row per
 // warp), records {J * ldx, h} read 32 at a time and broadcast by shuffles.  X32 is
-// the FP32 C for the diagonal term (alpha rows only); VT rows are FP32.
-template <int RPW, bool ALIGNED>
-__global__ void __launch_bounds__(256, 3) k_spmm_bf16(
+// the FP32 C for the diagonal term (alpha rows only); VT rows are FP32.  MODE 2 adds
+// the diagonal term (alpha rows), 1 the alpha-self x beta-single term (beta rows), 0
+// neither; without the diagonal's registers four blocks fit on an SM.
+template <int RPW, bool ALIGNED, int MODE>
+__global__ void __launch_bounds__(256, MODE == 2 ? 3 : 4) k_spmm_bf16(
     const __nv_bfloat16* __restrict__ Xb, int64_t ldx, const float* __restrict__ X32,
     float* __restrict__ Y, int64_t nrows, int64_t ncols, const int64_t* __restrict__ rp,
     const int2* __restrict__ rec, const int64_t* __restrict__ srp, const int2* __restrict__ sl,
@@ -446,7 +448,7 @@ __global__ void __launch_bounds__(256, 3) k_spmm_bf16(
 #pragma unroll
     for (int v = 0; v < 8; ++v) acc[v] = 0.f;
     if (accumulate && active) ld8<ALIGNED>(Y + I * ncols + c0, nv, acc);
-    if (hd_row) {
+    if constexpr (MODE == 2) {
       const float v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : 0.f;
       const float v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : 0.f;
       uint64_t b[8];
@@ -493,7 +495,7 @@ __global__ void __launch_bounds__(256, 3) k_spmm_bf16(
         fma_bf16x8(h, __ldg(reinterpret_cast<const uint4*>(Xc + off)), acc);
       }
     }
-    if (srp && active) {
+    if (MODE == 1 && active) {
       for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
         const int2 l = sl[q];
         const int pair = (l.y > 0 ? l.y : -l.y) - 1;
@@ -993,14 +995,20 @@ static int spmm_bf16(const __nv_bfloat16* Xb, int64_t ldx, const float* X32, flo
     kern<<<g, 32 * kRowWarps, 0, s>>>(Xb, ldx, X32, Y, nrows, ncols, L->row_ptr, L->rec16, srp,
                                       sl, VT, hd_row, hd_col, e_nuc, Vrow, scol, n, accumulate);
   };
+  auto by_rows = [&](auto k2, auto k4, auto k8) {
+    if (rpw == 2) go(k2, 2);
+    else if (rpw == 8) go(k8, 8);
+    else go(k4, 4);
+  };
+  const int mode = hd_row ? 2 : (srp ? 1 : 0);
   if (ncols % 4 == 0) {
-    if (rpw == 2) go(k_spmm_bf16<2, true>, 2);
-    else if (rpw == 8) go(k_spmm_bf16<8, true>, 8);
-    else go(k_spmm_bf16<4, true>, 4);
+    if (mode == 2) by_rows(k_spmm_bf16<2, true, 2>, k_spmm_bf16<4, true, 2>, k_spmm_bf16<8, true, 2>);
+    else if (mode == 1) by_rows(k_spmm_bf16<2, true, 1>, k_spmm_bf16<4, true, 1>, k_spmm_bf16<8, true, 1>);
+    else by_rows(k_spmm_bf16<2, true, 0>, k_spmm_bf16<4, true, 0>, k_spmm_bf16<8, true, 0>);
   } else {
-    if (rpw == 2) go(k_spmm_bf16<2, false>, 2);
-    else if (rpw == 8) go(k_spmm_bf16<8, false>, 8);
-    else go(k_spmm_bf16<4, false>, 4);
+    if (mode == 2) by_rows(k_spmm_bf16<2, false, 2>, k_spmm_bf16<4, false, 2>, k_spmm_bf16<8, false, 2>);
+    else if (mode == 1) by_rows(k_spmm_bf16<2, false, 1>, k_spmm_bf16<4, false, 1>, k_spmm_bf16<8, false, 1>);
+    else by_rows(k_spmm_bf16<2, false, 0>, k_spmm_bf16<4, false, 0>, k_spmm_bf16<8, false, 0>);
   }
   HQ_LAUNCH_CHECK();
   return HINQS_OK;
