@@ -85,11 +85,12 @@ extern "C" {
  * refinement removes the rounding.  Links of more than 2^32 padded elements take the
  * FP32 same-spin half. */
 #define HINQS_PREC_FP32_BF16C 4
-/* c, sigma: double; as HINQS_PREC_FP64 but the opposite-spin term in double-float
+/* c, sigma: double; as HINQS_PREC_FP64 but the off-diagonal terms in double-float
  * arithmetic (each value an unevaluated sum of two FP32 numbers; error-free products by
- * fused multiply-add, two-sum accumulation; about 1e-13 relative), which runs several
- * times faster than FP64 on this part.  Not in the paper: the refinement product of
- * the mixed Davidson (hinqs_davidson_opts.refine_precision). */
+ * fused multiply-add, two-sum accumulation; about 1e-13 relative; the diagonal term in
+ * FP64), which runs several times faster than FP64 on this part.  The same-spin half
+ * takes FP64 when N_alpha or N_beta is not a multiple of 4.  Not in the paper: the
+ * refinement product of the mixed Davidson (hinqs_davidson_opts.refine_precision). */
 #define HINQS_PREC_FP64_DFAB 5
 
 /* Davidson precision */

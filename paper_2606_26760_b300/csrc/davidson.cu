@@ -1650,7 +1650,9 @@ static size_t davidson_workspace_bytes(int64_t N, const hinqs_davidson_opts& o) 
     b += (4 * (size_t)kMaxSub * kMaxSub + 4 * (kMaxSub + 2) + (size_t)kMaxSub * kRitzStride +
           kVecOut) * d;
   }
-  return b + 2 * (size_t)N * d;  // sigma temporaries (FP64 product)
+  // sigma temporaries of the FP64 (or double-float) product
+  const bool df = o.precision == HINQS_DAVIDSON_MIXED && o.refine_precision == HINQS_PREC_FP64_DFAB;
+  return b + (df ? 3 : 2) * (size_t)N * d;
 }
 
 extern "C" int hinqs_davidson_workspace_size(int64_t n_alpha_strings, int64_t n_beta_strings,

@@ -119,6 +119,7 @@ struct hinqs_links_s {
   float* V32 = nullptr;
   double* VT64 = nullptr;  // [n*n][N], transpose of V
   float* VT32 = nullptr;
+  float* VTlo32 = nullptr;  // fp32(VT64 - VT32): VT as a double-float pair with VT32
   // single links plus the n_e diagonal pseudo-links (J = I, pair jj, +1) of every
   // row, slot-major: sell[slot * N + I] = {J, sign * (pair + 1)}, slot < scount[I]
   int ell_width = 0;

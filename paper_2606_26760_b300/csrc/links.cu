@@ -119,7 +119,7 @@ __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n
                                 const double* __restrict__ h, const double* __restrict__ eri,
                                 double* __restrict__ hdiag, double* __restrict__ V64,
                                 float* __restrict__ V32, double* __restrict__ VT64,
-                                float* __restrict__ VT32) {
+                                float* __restrict__ VT32, float* __restrict__ VTlo32) {
   int n2 = n * n;
   for (int64_t I = blockIdx.x; I < N; I += gridDim.x) {
     uint64_t x = S[I];
@@ -135,6 +135,7 @@ __global__ void k_string_tables(const uint64_t* __restrict__ S, int64_t N, int n
       V32[I * n2 + xy] = (float)acc;
       VT64[(int64_t)xy * N + I] = acc;
       VT32[(int64_t)xy * N + I] = (float)acc;
+      VTlo32[(int64_t)xy * N + I] = (float)(acc - (double)(float)acc);
     }
     if (threadIdx.x == 0) {
       double e1 = 0.0, e2 = 0.0;
@@ -243,6 +244,7 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->V32, s);
   dfree(L->VT64, s);
   dfree(L->VT32, s);
+  dfree(L->VTlo32, s);
   dfree(L->sell, s);
   dfree(L->tcell, s);
   dfree(L->scount, s);
@@ -300,7 +302,8 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
         (rc = dalloc(&L->sign, L->nnz, s)) || (rc = dalloc(&L->degree, L->nnz, s)) ||
         (rc = dalloc(&L->slink, L->nsingle, s)) || (rc = dalloc(&L->hdiag, N, s)) ||
         (rc = dalloc(&L->V64, N * n2, s)) || (rc = dalloc(&L->V32, N * n2, s)) ||
-        (rc = dalloc(&L->VT64, N * n2, s)) || (rc = dalloc(&L->VT32, N * n2, s))) {
+        (rc = dalloc(&L->VT64, N * n2, s)) || (rc = dalloc(&L->VT32, N * n2, s)) ||
+        (rc = dalloc(&L->VTlo32, N * n2, s))) {
     }
   }
   if (!rc) {
@@ -308,7 +311,7 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
                                                        L->srow_ptr, L->col, L->hval64, L->hval32,
                                                        L->exc, L->sign, L->degree, L->slink);
     k_string_tables<<<(unsigned)std::min<int64_t>(N, 16 * kNumSMs), 128, 0, s>>>(
-        L->strings, N, n, H->h, H->eri, L->hdiag, L->V64, L->V32, L->VT64, L->VT32);
+        L->strings, N, n, H->h, H->eri, L->hdiag, L->V64, L->V32, L->VT64, L->VT32, L->VTlo32);
     cudaMemsetAsync(dmax, 0, 2 * sizeof(int), s);
     int g2 = (int)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs);
     k_row_max<<<g2, 256, 0, s>>>(L->row_ptr, N, dmax);

@@ -818,6 +818,165 @@ __global__ void __launch_bounds__(256) k_sigma_ab_df(const double* __restrict__ 
   }
 }
 
+// C (rows x cols, FP64) -> the double-float pair (hi, lo) of C and of its transpose,
+// as separate FP32 arrays; 32 x 32 tiles.
+__global__ void k_df_split_pack(const double* __restrict__ C, int64_t rows, int64_t cols,
+                                float* __restrict__ hi, float* __restrict__ lo,
+                                float* __restrict__ hiT, float* __restrict__ loT) {
+  __shared__ double tile[32][33];
+  const int64_t bx = (int64_t)blockIdx.x * 32, by = (int64_t)blockIdx.y * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = by + k, j = bx + threadIdx.x;
+    if (i < rows && j < cols) {
+      const double v = C[i * cols + j];
+      tile[k][threadIdx.x] = v;
+      const float2 d = df_split(v);
+      hi[i * cols + j] = d.x;
+      lo[i * cols + j] = d.y;
+    }
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t j = bx + k, i = by + threadIdx.x;
+    if (i < rows && j < cols) {
+      const float2 d = df_split(tile[threadIdx.x][k]);
+      hiT[j * rows + i] = d.x;
+      loT[j * rows + i] = d.y;
+    }
+  }
+}
+
+// The same-spin row product of the FP64 mode in double-float arithmetic: four columns
+// per lane (one 16-byte load of the high and one of the low parts per link), the FP64
+// link records read 32 at a time and split into a pair once, by the lane that loaded
+// them, before the warp shares them.  MODE 2 adds the diagonal term in FP64 (on the
+// FP64 C), MODE 1 the alpha-self x beta-single term (VT as a pair, VT32 + VTlo32).
+// Requires ncols % 4 == 0.
+template <int RPW, int MODE>
+__global__ void __launch_bounds__(256) k_spmm_df(
+    const float* __restrict__ Xh, const float* __restrict__ Xl, const double* __restrict__ X64,
+    double* __restrict__ Y, int64_t nrows, int64_t ncols, const int64_t* __restrict__ rp,
+    const int4* __restrict__ rec, const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+    const float* __restrict__ VTh, const float* __restrict__ VTl,
+    const double* __restrict__ hd_row, const double* __restrict__ hd_col, double e_nuc,
+    const double* __restrict__ Vrow, const uint64_t* __restrict__ scol, int n, int accumulate) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * 4;
+  const bool active = c0 < ncols;
+  const int64_t cc = active ? c0 : 0;
+  const int n2 = n * n;
+  const unsigned full = 0xffffffffu;
+  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  for (int rr = 0; rr < RPW; ++rr) {
+    const int64_t I = I0 + rr;
+    if (I >= nrows) break;  // warp-uniform
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+    const int4* __restrict__ r = rec + rp[I];
+    const int nk = (int)(rp[I + 1] - rp[I]);
+    for (int k0 = 0; k0 < nk; k0 += 32) {
+      int off = 0;
+      float hh = 0.f, hl = 0.f;
+      if (k0 + lane < nk) {
+        const int4 q = __ldg(r + k0 + lane);
+        off = q.x;
+        const float2 d = df_split(__hiloint2double(q.w, q.z));
+        hh = d.x, hl = d.y;
+      }
+      const int cnt = min(32, nk - k0);
+      for (int u = 0; u < cnt; u += 4) {
+        float4 xh[4], xl[4];
+        float bh[4], bl[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          const int src = min(u + v, cnt - 1);
+          const uint32_t o = (uint32_t)__shfl_sync(full, off, src);
+          bh[v] = __shfl_sync(full, hh, src);
+          bl[v] = __shfl_sync(full, hl, src);
+          if (u + v >= cnt) bh[v] = 0.f, bl[v] = 0.f;
+          xh[v] = __ldg(reinterpret_cast<const float4*>(Xh + o + cc));
+          xl[v] = __ldg(reinterpret_cast<const float4*>(Xl + o + cc));
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          df_fma(bh[v], bl[v], xh[v].x, xl[v].x, ah[0], al[0]);
+          df_fma(bh[v], bl[v], xh[v].y, xl[v].y, ah[1], al[1]);
+          df_fma(bh[v], bl[v], xh[v].z, xl[v].z, ah[2], al[2]);
+          df_fma(bh[v], bl[v], xh[v].w, xl[v].w, ah[3], al[3]);
+        }
+      }
+    }
+    if (MODE == 1 && active) {
+      for (int64_t q = srp[I], qe = srp[I + 1]; q < qe; ++q) {
+        const int2 l = sl[q];
+        const int pair = (l.y > 0 ? l.y : -l.y) - 1;
+        const float4 vh = __ldg(reinterpret_cast<const float4*>(VTh + (int64_t)pair * ncols + c0));
+        const float4 vl = __ldg(reinterpret_cast<const float4*>(VTl + (int64_t)pair * ncols + c0));
+        const float4 xh = __ldg(reinterpret_cast<const float4*>(Xh + (int64_t)l.x * ncols + c0));
+        const float4 xl = __ldg(reinterpret_cast<const float4*>(Xl + (int64_t)l.x * ncols + c0));
+        const float sg = l.y > 0 ? 1.f : -1.f;
+        df_fma(sg * vh.x, sg * vl.x, xh.x, xl.x, ah[0], al[0]);
+        df_fma(sg * vh.y, sg * vl.y, xh.y, xl.y, ah[1], al[1]);
+        df_fma(sg * vh.z, sg * vl.z, xh.z, xl.z, ah[2], al[2]);
+        df_fma(sg * vh.w, sg * vl.w, xh.w, xl.w, ah[3], al[3]);
+      }
+    }
+    double y[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) y[v] = (double)ah[v] + (double)al[v];
+    if constexpr (MODE == 2) {
+      const double v0 = (lane < n) ? Vrow[I * n2 + lane * n + lane] : 0.0;
+      const double v1 = (lane + 32 < n) ? Vrow[I * n2 + (lane + 32) * n + lane + 32] : 0.0;
+      uint64_t b[4];
+      double xs[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+      for (int v = 0; v < 4; ++v) b[v] = active ? scol[cc + v] : 0;
+      for (int j = 0; j < n; ++j) {
+        const double a = __shfl_sync(full, j < 32 ? v0 : v1, j & 31);
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+          if ((b[v] >> j) & 1ull) xs[v] += a;
+      }
+      if (active) {
+        const double hr = hd_row[I] + e_nuc;
+#pragma unroll
+        for (int v = 0; v < 4; ++v) y[v] = fma(hr + hd_col[c0 + v] + xs[v], X64[I * ncols + c0 + v], y[v]);
+      }
+    }
+    if (active) {
+      double* yo = Y + I * ncols + c0;
+#pragma unroll
+      for (int v = 0; v < 4; ++v) yo[v] = accumulate ? yo[v] + y[v] : y[v];
+    }
+  }
+}
+
+// The same-spin half of an FP64 product in double-float: false when it does not apply
+// (records missing or a row length not a multiple of 4), and the caller takes FP64.
+static bool spmm_df_fits(const hinqs_subspace_s* B, const hinqs_links_s* la,
+                         const hinqs_links_s* lb) {
+  return la->rec64 && lb->rec64 && la->VTlo32 && B->Na % 4 == 0 && B->Nb % 4 == 0;
+}
+
+static int spmm_df(const float* Xh, const float* Xl, const double* X64, double* Y, int64_t nrows,
+                   int64_t ncols, const hinqs_links_s* L, const hinqs_links_s* Lsingles,
+                   const float* VTh, const float* VTl, const double* hd_row, const double* hd_col,
+                   double e_nuc, const double* Vrow, const uint64_t* scol, int n, int accumulate,
+                   cudaStream_t s) {
+  const int64_t* srp = Lsingles ? Lsingles->srow_ptr : nullptr;
+  const int2* sl = Lsingles ? Lsingles->slink : nullptr;
+  const int rpw = 2;
+  const dim3 g((unsigned)ceil_div(ncols, 128), (unsigned)ceil_div(nrows, kRowWarps * rpw));
+  auto go = [&](auto kern) {
+    kern<<<g, 32 * kRowWarps, 0, s>>>(Xh, Xl, X64, Y, nrows, ncols, L->row_ptr, L->rec64, srp, sl,
+                                      VTh, VTl, hd_row, hd_col, e_nuc, Vrow, scol, n, accumulate);
+  };
+  if (hd_row) go(k_spmm_df<2, 2>);
+  else if (srp) go(k_spmm_df<2, 1>);
+  else go(k_spmm_df<2, 0>);
+  HQ_LAUNCH_CHECK();
+  return HINQS_OK;
+}
+
 template <int CH>
 static int launch_ab_df(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hinqs_links_s* la,
                         const hinqs_links_s* lb, const double* c, double* sig, cudaStream_t s,
@@ -936,15 +1095,37 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   const size_t limit = 200 * 1024;
   const int n = H->n, n2 = n * n;
   const int64_t Na = B->Na, Nb = B->Nb, N = Na * Nb;
-  T *CT = nullptr, *ST = nullptr;
+  T *CT = nullptr, *ST = nullptr, *DFT = nullptr;
   int rc = HINQS_OK;
-  if ((parts & kSameSpin) && ((rc = dalloc(&CT, N, s)) || (rc = dalloc(&ST, N, s)))) {
+  // double-float same-spin half: CT holds the (hi, lo) pair of C, DFT that of C^T
+  bool df_same = false;
+  if constexpr (sizeof(T) == 8) df_same = tc_split == kDoubleFloat && spmm_df_fits(B, la, lb);
+  if ((parts & kSameSpin) && ((rc = dalloc(&CT, N, s)) || (rc = dalloc(&ST, N, s)) ||
+                              (df_same && (rc = dalloc(&DFT, N, s))))) {
     dfree(CT, s);
     dfree(ST, s);
+    dfree(DFT, s);
     return rc;
   }
   auto run = [&]() -> int {
     if (!(parts & kSameSpin)) goto opposite;
+    if constexpr (sizeof(T) == 8) {
+      if (df_same) {
+        float* Xh = reinterpret_cast<float*>(CT);
+        float* XhT = reinterpret_cast<float*>(DFT);
+        const dim3 tg((unsigned)ceil_div(Nb, 32), (unsigned)ceil_div(Na, 32));
+        k_df_split_pack<<<tg, dim3(32, 8), 0, s>>>(c, Na, Nb, Xh, Xh + N, XhT, XhT + N);
+        HQ_LAUNCH_CHECK();
+        // beta same-spin links and alpha-self x beta singles, rows = beta strings
+        HQ_TRY(spmm_df(XhT, XhT + N, nullptr, ST, Nb, Na, lb, lb, la->VT32, la->VTlo32, nullptr,
+                       nullptr, 0.0, nullptr, nullptr, n, 0, s));
+        HQ_TRY(transpose<T>(ST, sig, Nb, Na, 0, s));
+        // alpha same-spin links and the diagonal, rows = alpha strings
+        HQ_TRY(spmm_df(Xh, Xh + N, c, sig, Na, Nb, la, nullptr, nullptr, nullptr, la->hdiag,
+                       lb->hdiag, H->e_nuc, la->V64, B->sb, n, 1, s));
+        goto opposite;
+      }
+    }
     HQ_TRY(transpose<T>(c, CT, Na, Nb, 0, s));
     // beta same-spin links and alpha-self x beta singles, rows = beta strings
     HQ_TRY(spmm_rows<T>(CT, ST, Nb, Na, lb, lb, VTof<T>(la), nullptr, nullptr, 0.0, nullptr,
@@ -978,6 +1159,7 @@ static int sigma_impl(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hin
   rc = run();
   dfree(CT, s);
   dfree(ST, s);
+  dfree(DFT, s);
   return rc;
 }
 
@@ -1244,6 +1426,8 @@ extern "C" int hinqs_sigma_workspace_size(int64_t n_alpha_strings, int64_t n_bet
   const size_t elem = (precision == HINQS_PREC_FP64 || precision == HINQS_PREC_FP64_DFAB)
                           ? sizeof(double) : sizeof(float);
   *bytes = 2 * (size_t)(n_alpha_strings * n_beta_strings) * elem;
+  if (precision == HINQS_PREC_FP64_DFAB)  // plus the pair (hi, lo) of C^T
+    *bytes = 3 * (size_t)(n_alpha_strings * n_beta_strings) * sizeof(double);
   if (precision == HINQS_PREC_FP32_BF16C) {
     const size_t pa = (size_t)(n_alpha_strings + 63) / 64 * 64;
     const size_t pb = (size_t)(n_beta_strings + 63) / 64 * 64;

@@ -448,6 +448,29 @@ __global__ void k_btable(const float* __restrict__ eri32, int n, int K, int KB,
   }
 }
 
+// Resident CTAs per SM of k_sigma_ab_tc<NW, SPLIT, STAGES> with a CTA of `bytes` of
+// shared memory: as many as shared memory, registers and threads allow, but never more
+// than the 512 tensor-memory columns hold; *req is the shared-memory request that
+// keeps the scheduler there (padding it, so that no CTA waits in tcgen05.alloc for
+// another to finish).  228 KB of shared memory per SM, 1 KB reserved per CTA.
+template <int NW, int SPLIT, int STAGES>
+static int ctas_per_sm(size_t bytes, size_t* req) {
+  auto kern = k_sigma_ab_tc<NW, SPLIT, STAGES>;
+  const int cap = 512 / (STAGES * NW);
+  cudaFuncAttributes fa;
+  if (cudaFuncGetAttributes(&fa, kern) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
+  const int by_regs = 65536 / (warp_regs * (kThreads / 32));
+  const int by_threads = 2048 / kThreads;
+  size_t r = bytes;
+  if ((int)(233472 / (r + 1024)) > cap) r = 233472 / (cap + 1);  // 1 KB margin
+  if (req) *req = r;
+  return std::min(std::min(cap, (int)(233472 / (r + 1024))), std::min(by_regs, by_threads));
+}
+
 template <int NW, int SPLIT, int STAGES>
 static int launch(const Args& a, bool crow, cudaStream_t s) {
   Args b = a;
@@ -455,19 +478,8 @@ static int launch(const Args& a, bool crow, cudaStream_t s) {
   const size_t bytes = smem_bytes(NW, SPLIT, STAGES, a.KB, a.Nb, crow);
   auto kern = k_sigma_ab_tc<NW, SPLIT, STAGES>;
   HQ_TRY(allow_max_smem(kern));
-  // resident CTAs per SM: as many as shared memory, registers and threads allow, but
-  // never more than the 512 tensor-memory columns hold (padding the shared-memory
-  // request keeps the scheduler there, so that no CTA waits in tcgen05.alloc for
-  // another to finish).  228 KB of shared memory per SM, 1 KB reserved per CTA.
-  const int cap = 512 / (STAGES * NW);
-  cudaFuncAttributes fa;
-  HQ_CUDA(cudaFuncGetAttributes(&fa, kern));
-  const int warp_regs = ((fa.numRegs * 32 + 255) / 256) * 256;
-  const int by_regs = 65536 / (warp_regs * (kThreads / 32));
-  const int by_threads = 2048 / kThreads;
   size_t req = bytes;
-  if ((int)(233472 / (req + 1024)) > cap) req = 233472 / (cap + 1);  // 1 KB margin
-  const int per_sm = std::min(std::min(cap, (int)(233472 / (req + 1024))), std::min(by_regs, by_threads));
+  const int per_sm = ctas_per_sm<NW, SPLIT, STAGES>(bytes, &req);
   if (per_sm < 1)
     return fail(HINQS_ERR_ARG, "tensor-core sigma: a CTA of %zu bytes does not fit an SM", bytes);
   const int grid = (int)std::min<int64_t>(a.Na, (int64_t)per_sm * kNumSMs);
@@ -540,6 +552,8 @@ static int launch_fit(const Args& a, int stages, cudaStream_t s) {
     if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 2>(a, true, s);
     if (smem_bytes(NW, SPLIT, 2, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 2>(a, false, s);
   }
+  // one stage, the C row in shared memory when it fits (measured on B300: four CTAs of
+  // 64 registers reading the row through L1 run slower than three that stage it)
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, true) <= lim) return launch<NW, SPLIT, 1>(a, true, s);
   if (smem_bytes(NW, SPLIT, 1, a.KB, a.Nb, false) <= lim) return launch<NW, SPLIT, 1>(a, false, s);
   return kTcNoFit;

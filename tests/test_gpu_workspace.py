@@ -62,10 +62,10 @@ def test_davidson_workspace_matches_pool_usage(problem, prec):
     assert 0.9 * bound <= peak <= bound + SLACK, (peak, bound)
 
 
-@pytest.mark.parametrize("prec", [hq.PREC_FP64, hq.PREC_FP32, hq.PREC_FP32_BF16C])
+@pytest.mark.parametrize("prec", [hq.PREC_FP64, hq.PREC_FP32, hq.PREC_FP32_BF16C, hq.PREC_FP64_DFAB])
 def test_sigma_workspace_matches_pool_usage(problem, prec):
     ham, sub, la, lb = problem
-    dt = torch.float64 if prec == hq.PREC_FP64 else torch.float32
+    dt = torch.float64 if prec in (hq.PREC_FP64, hq.PREC_FP64_DFAB) else torch.float32
     c = torch.ones(sub.N, dtype=dt, device="cuda")
     y = torch.empty_like(c)
     bound = hq.sigma_workspace_size(sub.Na, sub.Nb, prec)
