@@ -749,6 +749,11 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
     for (int i = lane; i < m * m; i += kRRThreads) A[i / m][i % m] = X[i / m][i % m];
     __syncthreads();
   }
+  // converged when the off-diagonal mass is at the rounding floor of the rotations,
+  // (4 m eps)^2 relative to the diagonal's (eps = 2^-53; a fixed 1e-30 is below that
+  // floor from m ~ 10 on and ran all 30 sweeps), or stops falling near it
+  const double floor_rel = 16.0 * (double)m * (double)m * 1.2326e-32;
+  double prev_off = 0.0;
   for (int sweep = 0; sweep < 30; ++sweep) {
     double off = 0.0, dia = 0.0;
     for (int i = lane; i < m * m; i += kRRThreads) {
@@ -773,7 +778,9 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
       dia += red2[w][1];
     }
     __syncthreads();
-    if (off <= 1e-30 * dia || off == 0.0) break;
+    if (off <= floor_rel * dia || off == 0.0) break;
+    if (sweep > 0 && off >= 0.25 * prev_off && off <= 1e-24 * dia) break;
+    prev_off = off;
     for (int step = 0; step < mm - 1; ++step) {
       if (lane < mm / 2) {
         int p = order[lane], q = order[mm - 1 - lane];
