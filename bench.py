@@ -66,6 +66,11 @@ def parse():
                          "(the target of kernel-level ncu captures); ':tune' autotunes first; "
                          "'pt2' -- one classical expansion and PT2 scoring on the converged "
                          "eigenvector")
+    ap.add_argument("--tuning", default=None,
+                    help="R,CH,ST -- pin the sigma tiles (rows per warp, CUDA-core chunk, "
+                         "tensor-core stages) instead of autotuning: under a profiler the "
+                         "autotuner's timings are distorted, so profiled runs pin the tiles "
+                         "it keeps outside one")
     ap.add_argument("--profile", action="store_true",
                     help="run only the warm-up and timed steps (for a profiler's launch list)")
     return ap.parse_args()
@@ -790,7 +795,10 @@ def main():
         sub_p = hq.build_subspace(a_d, b_d, n, na, nb)
         la_p, lb_p = hq.string_links(ham_p, sub_p, 0), hq.string_links(ham_p, sub_p, 1)
         tuning = None
-        if "tune" in rest:  # the autotuner's tiles (its trial launches come first)
+        if args.tuning:
+            hq.set_tuning(la_p, lb_p, *[int(v) for v in args.tuning.split(",")])
+            tuning = la_p.tuning()
+        elif "tune" in rest:  # the autotuner's tiles (its trial launches come first)
             hq.autotune(ham_p, sub_p, la_p, lb_p, prec)
             tuning = la_p.tuning()
         x = torch.tensor(synth.random_vector(sub_p.N, 3), device=dev)
@@ -815,7 +823,10 @@ def main():
         ham_s = hq.Hamiltonian(h_in, eri_in, na, nb, w["e_nuc"])
         sub_s = hq.build_subspace(a_in, b_in, n, na, nb)
         la_s, lb_s = hq.string_links(ham_s, sub_s, 0), hq.string_links(ham_s, sub_s, 1)
-        hq.autotune(ham_s, sub_s, la_s, lb_s, hq.PREC_FP32_BF16C)  # cached after the first step
+        if args.tuning:
+            hq.set_tuning(la_s, lb_s, *[int(v) for v in args.tuning.split(",")])
+        else:
+            hq.autotune(ham_s, sub_s, la_s, lb_s, hq.PREC_FP32_BF16C)  # cached after the first step
         res = hq.davidson(ham_s, sub_s, la_s, lb_s, **solve_opts)
         g1, g2 = hq.rdm(sub_s, la_s, lb_s, res.c)
         gh, ge = hq.energy_backward(n, 1.0, g1, g2)
