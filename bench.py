@@ -36,9 +36,10 @@ if ROOT not in sys.path:
 METRIC = "sigma dets/s and Davidson time-to-1e-6 Ha: mixed vs FP64 on the same B300"
 kNumSMs_B300 = 148
 SM_MAX_MHZ = 2032
-# DRAM bytes (read + write) per launch of a product half, from an ncu capture of the
-# precision workload (profiles/); None until the current kernel has been captured
-PROFILED_TRAFFIC = {"same": None, "opposite": None}
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels on
+# this workload: the two row-product launches of the same-spin half, and the
+# tensor-core opposite-spin kernel
+PROFILED_TRAFFIC = {"same": 63.29e6, "opposite": 33.33e6}
 WORKLOAD = "precision"
 
 
