@@ -1318,13 +1318,16 @@ constexpr int kSoftRestarts = 3;
 // basis-vector bound of the fused passes for m vectors
 static int vec_bound(int m) { return m <= 4 ? 4 : m <= 8 ? 8 : m <= 16 ? 16 : 32; }
 
+// grid: one full wave, but no more blocks than 256-element chunks of the vectors (so
+// that the passes of small problems leave the GPU to other streams' work)
 template <template <int> class F, typename... A>
-static void launch_mb(int m, cudaStream_t s, A... a) {
+static void launch_mb(int m, int64_t n_elems, cudaStream_t s, A... a) {
+  const int cap = (int)std::min<int64_t>(kVecGrid, std::max<int64_t>(1, (n_elems + 255) / 256));
   switch (vec_bound(m)) {
-    case 4: F<4>::go(s, a...); break;
-    case 8: F<8>::go(s, a...); break;
-    case 16: F<16>::go(s, a...); break;
-    default: F<32>::go(s, a...); break;
+    case 4: F<4>::go(s, cap, a...); break;
+    case 8: F<8>::go(s, cap, a...); break;
+    case 16: F<16>::go(s, cap, a...); break;
+    default: F<32>::go(s, cap, a...); break;
   }
 }
 // One full wave of a fused pass: the SMs times the blocks of the kernel that fit on
@@ -1342,41 +1345,41 @@ static int vec_grid(K kern) {
 template <int MB>
 struct Res32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) {
+  static void go(cudaStream_t s, int cap, A... a) {
     static const int g = vec_grid(k_res32<MB>);
-    k_res32<MB><<<g, kRedThreads, 0, s>>>(a...);
+    k_res32<MB><<<std::min(g, cap), kRedThreads, 0, s>>>(a...);
   }
 };
 template <int MB>
 struct Ortho32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) {
+  static void go(cudaStream_t s, int cap, A... a) {
     static const int g = vec_grid(k_ortho32<MB>);
-    k_ortho32<MB><<<g, kRedThreads, 0, s>>>(a...);
+    k_ortho32<MB><<<std::min(g, cap), kRedThreads, 0, s>>>(a...);
   }
 };
 template <int MB>
 struct Col32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) {
+  static void go(cudaStream_t s, int cap, A... a) {
     static const int g = vec_grid(k_col32<MB>);
-    k_col32<MB><<<g, kRedThreads, 0, s>>>(a...);
+    k_col32<MB><<<std::min(g, cap), kRedThreads, 0, s>>>(a...);
   }
 };
 template <int MB>
 struct Restart32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) {
+  static void go(cudaStream_t s, int cap, A... a) {
     static const int g = vec_grid(k_restart32<MB>);
-    k_restart32<MB><<<g, kRedThreads, 0, s>>>(a...);
+    k_restart32<MB><<<std::min(g, cap), kRedThreads, 0, s>>>(a...);
   }
 };
 template <int MB>
 struct Row32 {
   template <typename... A>
-  static void go(cudaStream_t s, A... a) {
+  static void go(cudaStream_t s, int cap, A... a) {
     static const int g = vec_grid(k_anchor_row32<MB>);
-    k_anchor_row32<MB><<<g, kRedThreads, 0, s>>>(a...);
+    k_anchor_row32<MB><<<std::min(g, cap), kRedThreads, 0, s>>>(a...);
   }
 };
 
@@ -1423,7 +1426,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
   const float floor32 = (float)o.denom_floor;
   // the pencil column of V_j (pencil index j + 1) and its product W_j
   auto add_column = [&](int j) -> int {
-    launch_mb<Col32>(j + 1, c.s, (const float*)x32, (const float*)ra, (const float*)V,
+    launch_mb<Col32>(j + 1, N, c.s, (const float*)x32, (const float*)ra, (const float*)V,
                      (const float*)W, (int64_t)N, j, N, c.partial, ctr, vsum);
     k_set_col32<<<1, kMaxSub + 1, 0, c.s>>>(G, S, kMaxSub, j + 1, vsum, j + 1, theta_a);
     HQ_LAUNCH_CHECK();
@@ -1487,7 +1490,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       k_set_G<<<1, kMaxSub, 0, c.s>>>(G, kMaxSub, 0, gs, 1, 0);
       k_set_G<<<1, kMaxSub, 0, c.s>>>(S, kMaxSub, 0, gs + 1, 1, 0);
       if (m > 0) {
-        launch_mb<Row32>(m, c.s, (const float*)x32, (const float*)ra, (const float*)V, (int64_t)N,
+        launch_mb<Row32>(m, N, c.s, (const float*)x32, (const float*)ra, (const float*)V, (int64_t)N,
                          m, N, c.partial, ctr, vsum);
         k_set_row32<<<1, kMaxSub, 0, c.s>>>(G, S, kMaxSub, vsum, m, theta_a);
       }
@@ -1507,7 +1510,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         // of its Gram-Schmidt pass against {x, V}
         k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all, qk, rr_warm);
         rr_warm = 1;
-        launch_mb<Res32>(m, c.s, (const float*)ra, (const float*)x32, (const float*)V,
+        launch_mb<Res32>(m, N, c.s, (const float*)ra, (const float*)x32, (const float*)V,
                          (const float*)W, (int64_t)N, m, (const double*)ritz, (const double*)theta_a,
                          (const float*)D32, floor32, N, c.t32, c.partial, ctr, vsum);
         HQ_LAUNCH_CHECK();
@@ -1546,11 +1549,11 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         }
         if (p2 > 0.5 * tt) {
           cf.scale = (float)(1.0 / std::sqrt(p2));
-          launch_mb<Ortho32>(m, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
+          launch_mb<Ortho32>(m, N, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
                              (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
         } else {
           cf.scale = 1.0f;
-          launch_mb<Ortho32>(m, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
+          launch_mb<Ortho32>(m, N, c.s, (const float*)c.t32, (const float*)x32, (const float*)V,
                              (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
           HQ_CUDA(cudaMemcpyAsync(hs.data(), vsum, (m + 2) * sizeof(double), cudaMemcpyDeviceToHost,
                                   c.s));
@@ -1566,7 +1569,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
             q2 -= hs[i] * hs[i];
           }
           cf.scale = (float)(1.0 / std::sqrt(q2 > 0.5 * oo ? q2 : oo));
-          launch_mb<Ortho32>(m, c.s, (const float*)vm, (const float*)x32, (const float*)V,
+          launch_mb<Ortho32>(m, N, c.s, (const float*)vm, (const float*)x32, (const float*)V,
                              (int64_t)N, m, cf, vm, N, c.partial, ctr, vsum);
         }
         HQ_LAUNCH_CHECK();
@@ -1580,7 +1583,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       const int kk = std::min(keep, m + 1);
       // xn = y0 x + V y, sxn = y0 s + W y (FP64) and the kept FP32 Ritz vectors with their
       // products, in one pass (the FP32 parts carry the correction)
-      launch_mb<Restart32>(std::max(m, 1), c.s, (const double*)x, (const double*)sx,
+      launch_mb<Restart32>(std::max(m, 1), N, c.s, (const double*)x, (const double*)sx,
                            (const float*)x32, (const float*)ra, (const float*)V, (const float*)W,
                            (int64_t)N, m, (const double*)all, kk, (const double*)theta_a, N, xn,
                            sxn, U, WU);

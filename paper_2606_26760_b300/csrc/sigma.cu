@@ -426,21 +426,21 @@ __device__ __forceinline__ void fma_bf16x8(float h, const uint4& x, float* acc) 
 // the diagonal term (alpha rows), 1 the alpha-self x beta-single term (beta rows), 0
 // neither; without the diagonal's registers four blocks fit on an SM.
 template <int RPW, bool ALIGNED, int MODE>
-__global__ void __launch_bounds__(256, MODE == 2 ? 3 : 4) k_spmm_bf16(
+__device__ __forceinline__ void spmm_bf16_block(
     const __nv_bfloat16* __restrict__ Xb, int64_t ldx, const float* __restrict__ X32,
     float* __restrict__ Y, int64_t nrows, int64_t ncols, const int64_t* __restrict__ rp,
     const int2* __restrict__ rec, const int64_t* __restrict__ srp, const int2* __restrict__ sl,
     const float* __restrict__ VT, const double* __restrict__ hd_row,
     const double* __restrict__ hd_col, double e_nuc, const float* __restrict__ Vrow,
-    const uint64_t* __restrict__ scol, int n, int accumulate) {
+    const uint64_t* __restrict__ scol, int n, int accumulate, int64_t bx, int64_t by) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t c0 = ((int64_t)blockIdx.x * 32 + lane) * 8;
+  const int64_t c0 = (bx * 32 + lane) * 8;
   const bool active = c0 < ncols;
   const int64_t cc = active ? c0 : 0;
   const int nv = active ? (int)min64(8, ncols - c0) : 0;  // columns of this lane
   const int n2 = n * n;
   const unsigned full = 0xffffffffu;
-  const int64_t I0 = ((int64_t)blockIdx.y * kRowWarps + warp) * RPW;
+  const int64_t I0 = (by * kRowWarps + warp) * RPW;
   for (int rr = 0; rr < RPW; ++rr) {
     const int64_t I = I0 + rr;
     if (I >= nrows) break;  // warp-uniform
@@ -511,6 +511,19 @@ __global__ void __launch_bounds__(256, MODE == 2 ? 3 : 4) k_spmm_bf16(
     }
     if (active) st8<ALIGNED>(Y + I * ncols + c0, nv, acc);
   }
+}
+
+template <int RPW, bool ALIGNED, int MODE>
+__global__ void __launch_bounds__(256, MODE == 2 ? 3 : 4) k_spmm_bf16(
+    const __nv_bfloat16* __restrict__ Xb, int64_t ldx, const float* __restrict__ X32,
+    float* __restrict__ Y, int64_t nrows, int64_t ncols, const int64_t* __restrict__ rp,
+    const int2* __restrict__ rec, const int64_t* __restrict__ srp, const int2* __restrict__ sl,
+    const float* __restrict__ VT, const double* __restrict__ hd_row,
+    const double* __restrict__ hd_col, double e_nuc, const float* __restrict__ Vrow,
+    const uint64_t* __restrict__ scol, int n, int accumulate) {
+  spmm_bf16_block<RPW, ALIGNED, MODE>(Xb, ldx, X32, Y, nrows, ncols, rp, rec, srp, sl, VT, hd_row,
+                                      hd_col, e_nuc, Vrow, scol, n, accumulate, blockIdx.x,
+                                      blockIdx.y);
 }
 
 // The same row product for several problems in one launch: problem r's blocks are
@@ -618,6 +631,80 @@ __global__ void k_transpose_batch(const __grid_constant__ JobTab<TransJob> tab) 
   const TransJob& J = tab.job[r];
   const int64_t local = b - tab.first[r];
   transpose_tile<float>(J.in, J.out, J.rows, J.cols, 0, local % J.col_tiles, local / J.col_tiles);
+}
+
+// The BF16C same-spin stages of several problems in one launch each (problem r's
+// blocks [first[r], first[r+1]) of the flattened grid).
+struct BfJob {
+  const __nv_bfloat16* Xb;
+  int64_t ldx;
+  const float* X32;
+  float* Y;
+  int64_t nrows, ncols;
+  const int64_t* rp;
+  const int2* rec;
+  const int64_t* srp;
+  const int2* sl;
+  const float* VT;
+  const double* hd_row;
+  const double* hd_col;
+  double e_nuc;
+  const float* Vrow;
+  const uint64_t* scol;
+  int n, accumulate;
+  int64_t col_blocks;
+};
+
+constexpr int kBfBatchRpw = 2;
+
+template <int MODE>
+__global__ void __launch_bounds__(256, MODE == 2 ? 3 : 4) k_spmm_bf16_batch(
+    const __grid_constant__ JobTab<BfJob> tab) {
+  const int64_t b = blockIdx.x;
+  const int r = find_job(tab.first, tab.R, b);
+  const BfJob& J = tab.job[r];
+  const int64_t local = b - tab.first[r];
+  if (J.ncols % 4 == 0)
+    spmm_bf16_block<kBfBatchRpw, true, MODE>(J.Xb, J.ldx, J.X32, J.Y, J.nrows, J.ncols, J.rp,
+                                             J.rec, J.srp, J.sl, J.VT, J.hd_row, J.hd_col, J.e_nuc,
+                                             J.Vrow, J.scol, J.n, J.accumulate,
+                                             local % J.col_blocks, local / J.col_blocks);
+  else
+    spmm_bf16_block<kBfBatchRpw, false, MODE>(J.Xb, J.ldx, J.X32, J.Y, J.nrows, J.ncols, J.rp,
+                                              J.rec, J.srp, J.sl, J.VT, J.hd_row, J.hd_col,
+                                              J.e_nuc, J.Vrow, J.scol, J.n, J.accumulate,
+                                              local % J.col_blocks, local / J.col_blocks);
+}
+
+struct PackJob {
+  const float* C;
+  int64_t rows, cols;
+  __nv_bfloat16* Cb;
+  int64_t ldc;
+  __nv_bfloat16* CTb;
+  int64_t ldr;
+  int64_t tiles_x;  // 32-column tiles over ldc
+};
+
+// k_bf16_pack over several problems (32 x 32 tiles covering ldc columns and ldr rows)
+__global__ void k_bf16_pack_batch(const __grid_constant__ JobTab<PackJob> tab) {
+  __shared__ float tile[32][33];
+  const int64_t b = blockIdx.x;
+  const int r = find_job(tab.first, tab.R, b);
+  const PackJob& J = tab.job[r];
+  const int64_t local = b - tab.first[r];
+  const int64_t bx = (local % J.tiles_x) * 32, by = (local / J.tiles_x) * 32;
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t i = by + k, j = bx + threadIdx.x;
+    const float v = (i < J.rows && j < J.cols) ? J.C[i * J.cols + j] : 0.f;
+    tile[k][threadIdx.x] = v;
+    if (i < J.rows && j < J.ldc) J.Cb[i * J.ldc + j] = __float2bfloat16_rn(v);
+  }
+  __syncthreads();
+  for (int k = threadIdx.y; k < 32; k += blockDim.y) {
+    const int64_t j = bx + k, i = by + threadIdx.x;
+    if (j < J.cols && i < J.ldr) J.CTb[j * J.ldr + i] = __float2bfloat16_rn(tile[threadIdx.x][k]);
+  }
 }
 
 struct AbArgs {
@@ -1254,37 +1341,47 @@ static int launch_jobs(int R, Fill per_job, Kern kern, dim3 block, cudaStream_t 
 }
 
 int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
-  std::vector<int> f32;
+  // f32: same-spin half in FP32 row products (FP32, BF16AB, BF16X3AB); bfc: on BF16
+  // copies of C (BF16C); the rest one problem at a time
+  std::vector<int> f32, bfc;
   for (int i = 0; i < n; ++i) {
     const SigmaReq& r = reqs[i];
-    if (r.precision == HINQS_PREC_FP64 || r.precision == HINQS_PREC_FP64_DFAB ||
-        r.precision == HINQS_PREC_FP32_BF16C ||
-        !r.la->rec32 || !r.lb->rec32 ||
-        r.B->Na * r.B->Nb >= kBatchSoloN) {
-      HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
-    } else {
-      f32.push_back(i);
-    }
+    const bool solo = r.precision == HINQS_PREC_FP64 || r.precision == HINQS_PREC_FP64_DFAB ||
+                      !r.la->rec32 || !r.lb->rec32 || r.B->Na * r.B->Nb >= kBatchSoloN ||
+                      (r.precision == HINQS_PREC_FP32_BF16C && (!r.la->rec16 || !r.lb->rec16));
+    if (solo) HQ_TRY(sigma_launch(r.H, r.B, r.la, r.lb, r.x, r.y, r.precision, s));
+    else if (r.precision == HINQS_PREC_FP32_BF16C) bfc.push_back(i);
+    else f32.push_back(i);
   }
-  if (f32.empty()) return HINQS_OK;
-  const int R = (int)f32.size();
-  std::vector<float*> CT(R, nullptr), ST(R, nullptr);
+  if (f32.empty() && bfc.empty()) return HINQS_OK;
+  const int R = (int)f32.size(), RB = (int)bfc.size();
+  std::vector<float*> CT(R, nullptr), ST(R, nullptr), STb(RB, nullptr);
+  std::vector<__nv_bfloat16*> Cb(RB, nullptr), CTb(RB, nullptr);
   auto run = [&]() -> int {
     for (int i = 0; i < R; ++i) {
       const int64_t N = reqs[f32[i]].B->Na * reqs[f32[i]].B->Nb;
       HQ_TRY(dalloc(&CT[i], N, s));
       HQ_TRY(dalloc(&ST[i], N, s));
     }
-    // a transpose stage over every request: in (rows x cols) -> out
-    auto transpose_all = [&](bool forward) -> int {
+    for (int i = 0; i < RB; ++i) {
+      const SigmaReq& r = reqs[bfc[i]];
+      HQ_TRY(dalloc(&Cb[i], (size_t)(r.B->Na * r.la->ld16), s));
+      HQ_TRY(dalloc(&CTb[i], (size_t)(r.B->Nb * r.lb->ld16), s));
+      HQ_TRY(dalloc(&STb[i], (size_t)(r.B->Na * r.B->Nb), s));
+    }
+    // a transpose stage over requests: in (rows x cols) -> out
+    auto transpose_all = [&](const std::vector<int>& ids, bool forward,
+                             const std::vector<float*>& tmp_in,
+                             const std::vector<float*>& tmp_out) -> int {
       auto fill = [&](int i, TransJob& j) -> int64_t {
-        const SigmaReq& r = reqs[f32[i]];
+        const SigmaReq& r = reqs[ids[i]];
         const int64_t rows = forward ? r.B->Na : r.B->Nb, cols = forward ? r.B->Nb : r.B->Na;
-        j = TransJob{forward ? static_cast<const float*>(r.x) : ST[i],
-                     forward ? CT[i] : static_cast<float*>(r.y), rows, cols, ceil_div(cols, 32)};
+        j = TransJob{forward ? static_cast<const float*>(r.x) : tmp_in[i],
+                     forward ? tmp_out[i] : static_cast<float*>(r.y), rows, cols,
+                     ceil_div(cols, 32)};
         return j.col_tiles * ceil_div(rows, 32);
       };
-      return launch_jobs<TransJob>(R, fill, k_transpose_batch, dim3(32, 8), s);
+      return launch_jobs<TransJob>((int)ids.size(), fill, k_transpose_batch, dim3(32, 8), s);
     };
     // a row-product stage over every request: beta rows on C^T, or alpha rows on C
     auto rows_all = [&](bool beta) -> int {
@@ -1313,16 +1410,65 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
       };
       return launch_jobs<SpmmJob>(R, fill, k_spmm_rec4_batch, dim3(32 * kRowWarps), s);
     };
-    HQ_TRY(transpose_all(true));   // C^T
-    HQ_TRY(rows_all(true));        // beta same-spin + alpha self x beta singles, on C^T
-    HQ_TRY(transpose_all(false));  // sigma = (...)^T
-    HQ_TRY(rows_all(false));       // += alpha same-spin + diagonal
+    if (R > 0) {
+      HQ_TRY(transpose_all(f32, true, CT, CT));    // C^T
+      HQ_TRY(rows_all(true));                      // beta same-spin + alpha self x beta singles
+      HQ_TRY(transpose_all(f32, false, ST, ST));   // sigma = (...)^T
+      HQ_TRY(rows_all(false));                     // += alpha same-spin + diagonal
+    }
+    if (RB > 0) {
+      // BF16 copies of C and C^T, then the row products on them (as sigma_bf16c)
+      auto pack = [&](int i, PackJob& j) -> int64_t {
+        const SigmaReq& r = reqs[bfc[i]];
+        j = PackJob{static_cast<const float*>(r.x), r.B->Na, r.B->Nb, Cb[i], r.la->ld16, CTb[i],
+                    r.lb->ld16, ceil_div(r.la->ld16, 32)};
+        return j.tiles_x * ceil_div(r.lb->ld16, 32);
+      };
+      HQ_TRY(launch_jobs<PackJob>(RB, pack, k_bf16_pack_batch, dim3(32, 8), s));
+      auto bf_rows = [&](bool beta) -> int {
+        auto fill = [&](int i, BfJob& j) -> int64_t {
+          const SigmaReq& r = reqs[bfc[i]];
+          const hinqs_links_s* L = beta ? r.lb : r.la;
+          j = BfJob{};
+          j.Xb = beta ? CTb[i] : Cb[i];
+          j.ldx = beta ? r.lb->ld16 : r.la->ld16;
+          j.X32 = beta ? nullptr : static_cast<const float*>(r.x);
+          j.Y = beta ? STb[i] : static_cast<float*>(r.y);
+          j.nrows = beta ? r.B->Nb : r.B->Na;
+          j.ncols = beta ? r.B->Na : r.B->Nb;
+          j.rp = L->row_ptr;
+          j.rec = L->rec16;
+          j.srp = beta ? r.lb->srow_ptr : nullptr;
+          j.sl = beta ? r.lb->slink : nullptr;
+          j.VT = beta ? r.la->VT32 : nullptr;
+          j.hd_row = beta ? nullptr : r.la->hdiag;
+          j.hd_col = beta ? nullptr : r.lb->hdiag;
+          j.e_nuc = beta ? 0.0 : r.H->e_nuc;
+          j.Vrow = beta ? nullptr : r.la->V32;
+          j.scol = beta ? nullptr : r.B->sb;
+          j.n = r.H->n;
+          j.accumulate = beta ? 0 : 1;
+          j.col_blocks = ceil_div(j.ncols, 256);
+          return j.col_blocks * ceil_div(j.nrows, kRowWarps * kBfBatchRpw);
+        };
+        return beta ? launch_jobs<BfJob>(RB, fill, k_spmm_bf16_batch<1>, dim3(32 * kRowWarps), s)
+                    : launch_jobs<BfJob>(RB, fill, k_spmm_bf16_batch<2>, dim3(32 * kRowWarps), s);
+      };
+      HQ_TRY(bf_rows(true));                          // beta rows on C^T -> STb
+      HQ_TRY(transpose_all(bfc, false, STb, STb));    // sigma = STb^T
+      HQ_TRY(bf_rows(false));                         // += alpha rows + diagonal
+    }
     // the opposite-spin term: one tensor-core launch per split mode, the rest singly
+    std::vector<int> all_fp32(f32);
+    all_fp32.insert(all_fp32.end(), bfc.begin(), bfc.end());
     for (int split : {1, 3}) {
       std::vector<int> ids;
-      const int prec = split == 1 ? HINQS_PREC_FP32_BF16AB : HINQS_PREC_FP32_BF16X3AB;
-      for (int i : f32)
-        if (reqs[i].precision == prec && reqs[i].la->nsingle > 0) ids.push_back(i);
+      for (int i : all_fp32) {
+        const int p = reqs[i].precision;
+        const bool take = split == 1 ? (p == HINQS_PREC_FP32_BF16AB || p == HINQS_PREC_FP32_BF16C)
+                                     : p == HINQS_PREC_FP32_BF16X3AB;
+        if (take && reqs[i].la->nsingle > 0) ids.push_back(i);
+      }
       if (ids.empty()) continue;
       const int rc = sigma_ab_tc_batch(reqs, ids.data(), (int)ids.size(), split, s);
       if (rc < 0) return rc;
@@ -1341,6 +1487,11 @@ int sigma_batch_launch(const SigmaReq* reqs, int n, cudaStream_t s) {
   for (int i = 0; i < R; ++i) {
     dfree(CT[i], s);
     dfree(ST[i], s);
+  }
+  for (int i = 0; i < RB; ++i) {
+    dfree(Cb[i], s);
+    dfree(CTb[i], s);
+    dfree(STb[i], s);
   }
   return rc;
 }

@@ -161,14 +161,15 @@ def test_bond_scan_mixed_batch_vs_fp64_batch():
 # ------------------------------------------------ lockstep batch (one launch per stage)
 
 
-@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6), (2, 1e-5), (3, 1e-6)])
+@pytest.mark.parametrize("prec,tol", [(0, 1e-12), (1, 1e-6), (2, 1e-5), (3, 1e-6), (4, 1e-5),
+                                      (5, 1e-12)])
 def test_sigma_batch_equals_single_products(small_scan, prec, tol):
     """The batched kernels (flattened row products and transposes over every geometry,
     the tensor-core term over a device work queue) against one product per geometry:
     the same arithmetic up to the order of the reductions; the scan's string counts
     are mostly not multiples of 4 (the unaligned row-product path)."""
     ws, gs, probs = small_scan
-    dt = torch.float64 if prec == 0 else torch.float32
+    dt = torch.float64 if prec in (0, 5) else torch.float32
     cs = [torch.tensor(synth.random_vector(p[1].N, 30 + i), dtype=dt, device="cuda")
           for i, p in enumerate(probs)]
     assert any(p[1].Nb % 4 for p in probs) and any(p[1].Na % 4 for p in probs)
@@ -184,7 +185,7 @@ def test_batch_lockstep_matches_oracle(small_scan):
     for r, (_, _, _, E, c) in zip(res, gs):
         assert r.status == hq.OK and abs(r.energy - E) < 1e-9
         assert abs(abs(np.dot(r.c.cpu().numpy(), c)) - 1.0) < 1e-8
-    for inner in (hq.PREC_FP32, hq.PREC_FP32_BF16AB, hq.PREC_FP32_BF16X3AB):
+    for inner in (hq.PREC_FP32, hq.PREC_FP32_BF16AB, hq.PREC_FP32_BF16X3AB, hq.PREC_FP32_BF16C):
         res = hq.davidson_batch(probs, precision=hq.DAVIDSON_MIXED, inner_precision=inner,
                                 tol_residual=1e-7, tol_energy=1e-9, max_iter=600, n_streams=0)
         for r, (_, _, _, E, _) in zip(res, gs):
