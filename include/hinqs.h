@@ -466,8 +466,10 @@ int hinqs_pt2_score(const hinqs_ham* ham, const hinqs_subspace* sub, const doubl
  * kept when the Slater-Condon element is non-zero.  Output ascending in
  * (alpha, beta), duplicates removed, into xa_out/xb_out (device uint64 [cap]);
  * *count (host) = number of candidates.  With xa_out or xb_out NULL only *count is
- * returned.  Requires n_orb <= 32.  Errors: HINQS_ERR_ARG (NULL, n_orb > 32,
- * cap < *count: nothing written), HINQS_ERR_OOM.  Synchronises the stream. */
+ * returned.  Any n_orb <= 64 (from 32 orbitals on, the kept strings are ranked
+ * among their distinct values to form the sort keys; 64 electrons of one spin are
+ * refused).  Errors: HINQS_ERR_ARG (NULL, cap < *count: nothing written),
+ * HINQS_ERR_OOM.  Synchronises the stream. */
 int hinqs_top_amplitudes(const hinqs_subspace* sub, const double* c, int64_t k, int64_t* idx_out,
                          void* stream);
 int hinqs_classical_expansion(const hinqs_ham* ham, const hinqs_subspace* sub, const double* c,
@@ -517,8 +519,10 @@ int hinqs_lookup_determinants(const hinqs_subspace* sub, const uint64_t* xa, con
  * excluded list (ea, eb)[me] (the cumulative basis: Step 1 removes configurations
  * that duplicate it).  Output ascending in (alpha, beta) into ya/yb (device uint64
  * [cap]); *count (host) = number of candidates; with ya or yb NULL only the counts
- * are returned.  Requires n_orb <= 32.  Errors: HINQS_ERR_ARG (NULL, n_orb > 32,
- * cap < *count: nothing written), HINQS_ERR_OOM.  Synchronises the stream. */
+ * are returned.  Any n_orb <= 64 (from 32 orbitals on, the proposals' strings are
+ * ranked among their distinct values to form the sort keys; 64 electrons of one
+ * spin are refused).  Errors: HINQS_ERR_ARG (NULL, cap < *count: nothing written),
+ * HINQS_ERR_OOM.  Synchronises the stream. */
 int hinqs_candidate_pool(const hinqs_ham* ham, const uint64_t* xa1, const uint64_t* xb1,
                          int64_t m1, const uint64_t* xa2, const uint64_t* xb2, int64_t m2,
                          const uint64_t* ea, const uint64_t* eb, int64_t me, uint64_t* ya,

@@ -151,7 +151,7 @@ def pt2_scores(H: Ham, sa, sb, c, E0: float, xa, xb, n_threads: int = 0):
 
 
 def connected(H: Ham, xa: int, xb: int, cap: int = 1 << 20):
-    """Determinants y != x with <y|H|x> != 0: (ya, yb, <y|H|x>), ascending (n <= 32)."""
+    """Determinants y != x with <y|H|x> != 0: (ya, yb, <y|H|x>), ascending (n <= 64)."""
     lib = _load()
     ya, yb, val = np.zeros(cap, np.uint64), np.zeros(cap, np.uint64), np.zeros(cap)
     m = lib.oracle_connected(H.n, H.n_alpha, H.n_beta, _p(H.h), _p(H.eri), int(xa), int(xb),

@@ -439,7 +439,7 @@ int oracle_coupling(int n, int na, int nb, const double *h, const double *eri, d
 /* ------------------------------------------------- connected determinants --- */
 
 typedef struct {
-    uint64_t key; /* alpha string << 32 | beta string (n <= 32) */
+    uint64_t a, b; /* alpha and beta strings */
     double coeff;
 } kterm;
 
@@ -458,24 +458,28 @@ static void conn_emit(const odet *out, double coeff, void *u) {
     }
     uint64_t a, b;
     strings_from_det(cu->n, out, &a, &b);
-    cu->buf[cu->cnt].key = (a << 32) | b;
+    cu->buf[cu->cnt].a = a;
+    cu->buf[cu->cnt].b = b;
     cu->buf[cu->cnt].coeff = coeff;
     cu->cnt++;
 }
 
 static int cmp_kterm(const void *x, const void *y) {
-    uint64_t a = ((const kterm *)x)->key, b = ((const kterm *)y)->key;
-    return a < b ? -1 : (a > b ? 1 : 0);
+    const kterm *u = (const kterm *)x, *v = (const kterm *)y;
+    if (u->a != v->a) return u->a < v->a ? -1 : 1;
+    return u->b < v->b ? -1 : (u->b > v->b ? 1 : 0);
 }
+
+static int same_strings(const kterm *u, const kterm *v) { return u->a == v->a && u->b == v->b; }
 
 /* Every determinant y != x with <y|H|x> != 0 (Eq. classical_expansion's connection
  * test), by applying H to |x> and summing the coefficients of equal results.
  * Outputs y's strings and <y|H|x>, ascending in (alpha, beta); returns the count,
- * or -1 (bad arguments, n > 32) / -2 (cap too small). */
+ * or -1 (bad arguments, n > 64) / -2 (cap too small). */
 int64_t oracle_connected(int n, int na, int nb, const double *h, const double *eri,
                          uint64_t xa, uint64_t xb, uint64_t *ya, uint64_t *yb, double *val,
                          int64_t cap) {
-    if (n < 1 || n > 32 || na < 0 || nb < 0 || na > n || nb > n || !h || !eri) return -1;
+    if (n < 1 || n > 64 || na < 0 || nb < 0 || na > n || nb > n || !h || !eri) return -1;
     oham H = {n, h, eri, 0.0};
     odet D = det_from_strings(n, xa, xb);
     int64_t tcap = 1 << 22;
@@ -487,19 +491,19 @@ int64_t oracle_connected(int n, int na, int nb, const double *h, const double *e
         return -2;
     }
     qsort(cu.buf, cu.cnt, sizeof(kterm), cmp_kterm);
-    const uint64_t self = (xa << 32) | xb;
+    const kterm self = {xa, xb, 0.0};
     int64_t m = 0;
     for (int64_t i = 0; i < cu.cnt;) {
         int64_t j = i;
         double sum = 0.0;
-        while (j < cu.cnt && cu.buf[j].key == cu.buf[i].key) sum += cu.buf[j++].coeff;
-        if (cu.buf[i].key != self && sum != 0.0) {
+        while (j < cu.cnt && same_strings(&cu.buf[j], &cu.buf[i])) sum += cu.buf[j++].coeff;
+        if (!same_strings(&cu.buf[i], &self) && sum != 0.0) {
             if (m >= cap) {
                 free(cu.buf);
                 return -2;
             }
-            ya[m] = cu.buf[i].key >> 32;
-            yb[m] = cu.buf[i].key & 0xffffffffull;
+            ya[m] = cu.buf[i].a;
+            yb[m] = cu.buf[i].b;
             val[m] = sum;
             m++;
         }

@@ -8,8 +8,9 @@
 //  (2) Enumeration: one thread per (selected determinant, excitation): alpha and beta
 //      singles and doubles and alpha-single x beta-single pairs, each with its
 //      Slater-Condon element; kept when the element is non-zero and the result lies
-//      outside S_alpha x S_beta, written as the key alpha << 32 | beta (n_orb <= 32),
-//      else a sentinel.  Every slot is written once: no atomics, a deterministic set.
+//      outside S_alpha x S_beta, written as the key alpha << 32 | beta (n_orb < 32;
+//      above, as the strings' ranks among the distinct kept strings), else a
+//      sentinel.  Every slot is written once: no atomics, a deterministic set.
 //  (3) Bitonic sort of the keys and a compaction of the distinct ones: candidates
 //      ascending in (alpha, beta).
 #include <algorithm>
@@ -109,6 +110,7 @@ struct ExpArgs {
   int64_t n_top;
   int64_t s1a, s1b, d2a, d2b, per;  // excitation counts per determinant
   uint64_t* keys;
+  uint64_t* keys_b;  // n_orb >= 32: keys holds the alpha string, keys_b the beta string
   int64_t total;
   // basis list (list mode): only its determinants are left out, not the whole product
   const int64_t* arow;
@@ -180,7 +182,13 @@ __global__ void k_expand(ExpArgs A) {
     const int64_t yb_i = ya_i >= 0 ? find_string(A.sb, A.Nb, yb) : -1;
     bool inside = ya_i >= 0 && yb_i >= 0;
     if (inside && A.arow) inside = in_list(A.arow, A.lib, ya_i, yb_i);
-    A.keys[g] = (el != 0.0 && !inside) ? ((ya << 32) | yb) : kNoKey;
+    const bool keep = el != 0.0 && !inside;
+    if (A.keys_b) {
+      A.keys[g] = keep ? ya : kNoKey;
+      A.keys_b[g] = keep ? yb : kNoKey;
+    } else {
+      A.keys[g] = keep ? ((ya << 32) | yb) : kNoKey;
+    }
   }
 }
 
@@ -202,14 +210,31 @@ __global__ void k_distinct_flags(const uint64_t* __restrict__ a, int64_t m, int6
     flag[i] = (a[i] != kNoKey && (i == 0 || a[i] != a[i - 1])) ? 1 : 0;
 }
 
+// DA / DB NULL: the key is alpha << 32 | beta; else ranks in the dictionaries
 __global__ void k_split_keys(const uint64_t* __restrict__ a, int64_t m, const int64_t* pos,
+                             const uint64_t* __restrict__ DA, const uint64_t* __restrict__ DB,
                              uint64_t* __restrict__ xa, uint64_t* __restrict__ xb) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
        i += (int64_t)gridDim.x * blockDim.x)
     if (a[i] != kNoKey && (i == 0 || a[i] != a[i - 1])) {
-      xa[pos[i]] = a[i] >> 32;
-      xb[pos[i]] = a[i] & 0xffffffffull;
+      const uint64_t hi = a[i] >> 32, lo = a[i] & 0xffffffffull;
+      xa[pos[i]] = DA ? DA[hi] : hi;
+      xb[pos[i]] = DB ? DB[lo] : lo;
     }
+}
+
+// n_orb >= 32: (alpha, beta) strings -> rank(alpha) << 32 | rank(beta) in place (keys
+// holds alpha, keys_b beta; kNoKey stays kNoKey)
+__global__ void k_rank_keys(uint64_t* __restrict__ keys, const uint64_t* __restrict__ keys_b,
+                            int64_t m, const uint64_t* __restrict__ DA, int64_t ua,
+                            const uint64_t* __restrict__ DB, int64_t ub) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t a = keys[i];
+    if (a == kNoKey) continue;
+    const int64_t ra = find_string(DA, ua, a), rb = find_string(DB, ub, keys_b[i]);
+    keys[i] = (ra >= 0 && rb >= 0) ? (((uint64_t)ra << 32) | (uint64_t)rb) : kNoKey;
+  }
 }
 
 }  // namespace
@@ -286,7 +311,8 @@ static int expansion_impl(const hinqs_ham* H, const hinqs_subspace* B, const hin
   if (H->n != B->n || H->n_alpha != B->n_alpha || H->n_beta != B->n_beta)
     return fail(HINQS_ERR_ARG, "%s: Hamiltonian and subspace disagree", who);
   if (L) HQ_TRY(check_list(B, L, who));
-  if (H->n > 32) return fail(HINQS_ERR_ARG, "%s: n_orb=%d above 32", who, H->n);
+  if (H->n_alpha == 64 || H->n_beta == 64)
+    return fail(HINQS_ERR_ARG, "%s: 64 electrons of one spin are not supported", who);
   *count = 0;
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t N = L ? L->m : B->Na * B->Nb;
@@ -315,8 +341,10 @@ static int expansion_impl(const hinqs_ham* H, const hinqs_subspace* B, const hin
   if (A.per == 0) return HINQS_OK;
   int64_t m_pad = 2;
   while (m_pad < A.total) m_pad <<= 1;
+  // n_orb <= 31: keys alpha << 32 | beta; else ranks in the candidates' distinct strings
+  const bool ranks = H->n >= 32;
   int64_t* top = nullptr;
-  uint64_t* keys = nullptr;
+  uint64_t *keys = nullptr, *keys_b = nullptr, *DA = nullptr, *DB = nullptr;
   int64_t* pos = nullptr;
   auto run = [&]() -> int {
     HQ_TRY(dalloc(&top, n_top, s));
@@ -327,12 +355,26 @@ static int expansion_impl(const hinqs_ham* H, const hinqs_subspace* B, const hin
       HQ_LAUNCH_CHECK();
     }
     HQ_TRY(dalloc(&keys, m_pad, s));
+    if (ranks) HQ_TRY(dalloc(&keys_b, A.total, s));
     A.top = top;
     A.keys = keys;
+    A.keys_b = keys_b;
     const unsigned grid = (unsigned)std::min<int64_t>(ceil_div(m_pad, 256), 16 * kNumSMs);
     k_expand<<<grid, 256, 0, s>>>(A);
     k_fill_key<<<grid, 256, 0, s>>>(keys, A.total, m_pad);
     HQ_LAUNCH_CHECK();
+    int64_t ua = 0, ub = 0;
+    if (ranks) {
+      // dictionaries of the kept alpha and beta strings (kNoKey fails the filter)
+      int64_t drop = 0;
+      int r = build_species(keys, A.total, A.n, A.na, 0, &DA, &ua, &drop, s);
+      if (r < 0 && r != HINQS_ERR_EMPTY) return r;
+      if (r == HINQS_ERR_EMPTY) return HINQS_OK;  // nothing kept
+      r = build_species(keys_b, A.total, A.n, A.nb, 0, &DB, &ub, &drop, s);
+      if (r < 0) return r;
+      k_rank_keys<<<grid, 256, 0, s>>>(keys, keys_b, A.total, DA, ua, DB, ub);
+      HQ_LAUNCH_CHECK();
+    }
     HQ_TRY(bitonic_sort(keys, m_pad, s));
     HQ_TRY(dalloc(&pos, m_pad, s));
     k_distinct_flags<<<grid, 256, 0, s>>>(keys, m_pad, pos);
@@ -344,13 +386,16 @@ static int expansion_impl(const hinqs_ham* H, const hinqs_subspace* B, const hin
     if (cap < uniq)
       return fail(HINQS_ERR_ARG, "%s: cap %lld below the %lld candidates", who, (long long)cap,
                   (long long)uniq);
-    k_split_keys<<<grid, 256, 0, s>>>(keys, m_pad, pos, xa_out, xb_out);
+    k_split_keys<<<grid, 256, 0, s>>>(keys, m_pad, pos, DA, DB, xa_out, xb_out);
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
   };
   const int rc = run();
   dfree(top, s);
   dfree(keys, s);
+  dfree(keys_b, s);
+  dfree(DA, s);
+  dfree(DB, s);
   dfree(pos, s);
   return rc;
 }

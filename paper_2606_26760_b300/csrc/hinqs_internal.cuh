@@ -264,6 +264,11 @@ int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, int64_t* tota
                        cudaStream_t s);
 // ascending bitonic sort of a[m_pad] in place (m_pad a power of two >= 2)
 int bitonic_sort(uint64_t* a, int64_t m_pad, cudaStream_t s);
+// the distinct strings of in[m] with k electrons in n orbitals, ascending, into a new
+// device array *out (*count entries; *dropped strings failed the filter); HINQS_ERR_EMPTY
+// when none is left (flags: HINQS_ERROR_BAD, HINQS_FULL_SPACE as hinqs_build_subspace)
+int build_species(const uint64_t* in, int64_t m, int n, int k, int flags, uint64_t** out,
+                  int64_t* count, int64_t* dropped, cudaStream_t s);
 // Exact top-k selection (radix selection on order-preserving 64-bit keys): positions
 // of the k entries of c[N] with the largest |c| (kSelAbs), the largest value
 // (kSelLargest) or the smallest value (kSelSmallest), ties to the lower position,

@@ -10,8 +10,9 @@
 //   hinqs_nqs_loss             Step 4: teacher weights, advantages, the three loss
 //                              terms and their gradient on a minibatch
 // Selections are exact (radix selection on order-preserving keys, ties to the lower
-// position), sets are sorted keys alpha << 32 | beta (n_orb <= 32), and every sum is
-// a fixed-shape tree, so results do not depend on scheduling.
+// position), sets are sorted keys alpha << 32 | beta (n_orb < 32; above, the strings'
+// ranks among the sorted distinct strings in play), and every sum is a fixed-shape
+// tree, so results do not depend on scheduling.
 #include <algorithm>
 
 #include "hinqs_internal.cuh"
@@ -118,6 +119,67 @@ __global__ void k_pool_keys(const uint64_t* __restrict__ xa1, const uint64_t* __
     keys[i] = ok ? ((a << 32) | b) : kNoKey;
     if (!ok) atomicAdd(dropped, 1ull);
   }
+}
+
+// n_orb >= 32: the key of a determinant is (rank of alpha) << 32 | (rank of beta) in
+// the sorted distinct strings of the proposals (ranks keep the strings' order), so that
+// any n_orb <= 64 packs into 64 bits; a string outside its dictionary gives kNoKey
+__device__ __forceinline__ uint64_t rank_key(const uint64_t* __restrict__ DA, int64_t ua,
+                                             const uint64_t* __restrict__ DB, int64_t ub,
+                                             uint64_t a, uint64_t b) {
+  const int64_t ra = find_string(DA, ua, a), rb = ra >= 0 ? find_string(DB, ub, b) : -1;
+  return (ra >= 0 && rb >= 0) ? (((uint64_t)ra << 32) | (uint64_t)rb) : kNoKey;
+}
+
+__global__ void k_pool_rank_keys(const uint64_t* __restrict__ xa1,
+                                 const uint64_t* __restrict__ xb1, int64_t m1,
+                                 const uint64_t* __restrict__ xa2,
+                                 const uint64_t* __restrict__ xb2, int64_t m2, int n, int na,
+                                 int nb, const uint64_t* __restrict__ DA, int64_t ua,
+                                 const uint64_t* __restrict__ DB, int64_t ub,
+                                 uint64_t* __restrict__ keys, int64_t m_pad,
+                                 unsigned long long* dropped) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t a, b;
+    if (i < m1) {
+      a = xa1[i];
+      b = xb1[i];
+    } else if (i < m1 + m2) {
+      a = xa2[i - m1];
+      b = xb2[i - m1];
+    } else {
+      keys[i] = kNoKey;
+      continue;
+    }
+    const bool ok = string_ok(a, n, na) && string_ok(b, n, nb);
+    keys[i] = ok ? rank_key(DA, ua, DB, ub, a, b) : kNoKey;
+    if (!ok) atomicAdd(dropped, 1ull);
+  }
+}
+
+__global__ void k_exclude_rank_keys(const uint64_t* __restrict__ ea,
+                                    const uint64_t* __restrict__ eb, int64_t me,
+                                    const uint64_t* __restrict__ DA, int64_t ua,
+                                    const uint64_t* __restrict__ DB, int64_t ub,
+                                    uint64_t* __restrict__ keys, int64_t m_pad) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad;
+       i += (int64_t)gridDim.x * blockDim.x)
+    keys[i] = i < me ? rank_key(DA, ua, DB, ub, ea[i], eb[i]) : kNoKey;
+}
+
+__global__ void k_pool_rank_scatter(const uint64_t* __restrict__ keys, int64_t m_pad,
+                                    const int64_t* __restrict__ flag,
+                                    const int64_t* __restrict__ pos,
+                                    const uint64_t* __restrict__ DA,
+                                    const uint64_t* __restrict__ DB, uint64_t* __restrict__ ya,
+                                    uint64_t* __restrict__ yb) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m_pad;
+       i += (int64_t)gridDim.x * blockDim.x)
+    if (flag[i]) {
+      ya[pos[i]] = DA[keys[i] >> 32];
+      yb[pos[i]] = DB[keys[i] & 0xffffffffull];
+    }
 }
 
 // keys of the excluded determinants; entries that cannot be a valid key (bits at or
@@ -444,10 +506,8 @@ extern "C" int hinqs_candidate_pool(const hinqs_ham* H, const uint64_t* xa1, con
   if (!H || !count || m1 < 0 || m2 < 0 || me < 0 || (m1 > 0 && (!xa1 || !xb1)) ||
       (m2 > 0 && (!xa2 || !xb2)) || (me > 0 && (!ea || !eb)))
     return fail(HINQS_ERR_ARG, "hinqs_candidate_pool: NULL argument or negative size");
-  if (H->n > 32)
-    return fail(HINQS_ERR_ARG, "hinqs_candidate_pool: n_orb=%d above 32", H->n);
-  if (H->n == 32 && H->n_alpha == 32 && H->n_beta == 32)
-    return fail(HINQS_ERR_ARG, "hinqs_candidate_pool: the fully occupied 32-orbital sector is not supported");
+  if (H->n_alpha == 64 || H->n_beta == 64)
+    return fail(HINQS_ERR_ARG, "hinqs_candidate_pool: 64 electrons of one spin are not supported");
   *count = 0;
   if (n_dropped) *n_dropped = 0;
   const int64_t m = m1 + m2;
@@ -455,7 +515,10 @@ extern "C" int hinqs_candidate_pool(const hinqs_ham* H, const uint64_t* xa1, con
   cudaStream_t s = (cudaStream_t)stream;
   const int64_t m_pad = pow2_at_least(m);
   const int64_t ex_pad = me > 0 ? pow2_at_least(me) : 0;
-  uint64_t *keys = nullptr, *ex = nullptr;
+  // n_orb <= 31: keys alpha << 32 | beta; else ranks in the proposals' distinct strings
+  const bool ranks = H->n >= 32;
+  uint64_t *keys = nullptr, *ex = nullptr, *DA = nullptr, *DB = nullptr, *tmp = nullptr;
+  int64_t ua = 0, ub = 0;
   int64_t *flag = nullptr, *pos = nullptr;
   unsigned long long* dropped = nullptr;
   auto run = [&]() -> int {
@@ -464,13 +527,36 @@ extern "C" int hinqs_candidate_pool(const hinqs_ham* H, const uint64_t* xa1, con
     HQ_TRY(dalloc(&pos, m_pad, s));
     HQ_TRY(dalloc(&dropped, 1, s));
     HQ_CUDA(cudaMemsetAsync(dropped, 0, sizeof(unsigned long long), s));
-    k_pool_keys<<<grid_for(m_pad), 256, 0, s>>>(xa1, xb1, m1, xa2, xb2, m2, H->n, H->n_alpha,
-                                                H->n_beta, keys, m_pad, dropped);
+    if (ranks) {
+      // the dictionaries: sorted distinct valid alpha (beta) strings of both lists
+      HQ_TRY(dalloc(&tmp, m, s));
+      for (int spin = 0; spin < 2; ++spin) {
+        const uint64_t* p1 = spin ? xb1 : xa1;
+        const uint64_t* p2 = spin ? xb2 : xa2;
+        if (m1) HQ_CUDA(cudaMemcpyAsync(tmp, p1, m1 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        if (m2)
+          HQ_CUDA(cudaMemcpyAsync(tmp + m1, p2, m2 * sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+        int64_t cnt = 0, drop = 0;
+        const int r = build_species(tmp, m, H->n, spin ? H->n_beta : H->n_alpha, 0,
+                                    spin ? &DB : &DA, &cnt, &drop, s);
+        if (r < 0 && r != HINQS_ERR_EMPTY) return r;
+        (spin ? ub : ua) = r < 0 ? 0 : cnt;
+      }
+      k_pool_rank_keys<<<grid_for(m_pad), 256, 0, s>>>(xa1, xb1, m1, xa2, xb2, m2, H->n,
+                                                       H->n_alpha, H->n_beta, DA, ua, DB, ub,
+                                                       keys, m_pad, dropped);
+    } else {
+      k_pool_keys<<<grid_for(m_pad), 256, 0, s>>>(xa1, xb1, m1, xa2, xb2, m2, H->n, H->n_alpha,
+                                                  H->n_beta, keys, m_pad, dropped);
+    }
     HQ_LAUNCH_CHECK();
     HQ_TRY(bitonic_sort(keys, m_pad, s));
     if (me > 0) {
       HQ_TRY(dalloc(&ex, ex_pad, s));
-      k_exclude_keys<<<grid_for(ex_pad), 256, 0, s>>>(ea, eb, me, ex, ex_pad);
+      if (ranks)
+        k_exclude_rank_keys<<<grid_for(ex_pad), 256, 0, s>>>(ea, eb, me, DA, ua, DB, ub, ex, ex_pad);
+      else
+        k_exclude_keys<<<grid_for(ex_pad), 256, 0, s>>>(ea, eb, me, ex, ex_pad);
       HQ_LAUNCH_CHECK();
       HQ_TRY(bitonic_sort(ex, ex_pad, s));
     }
@@ -487,13 +573,19 @@ extern "C" int hinqs_candidate_pool(const hinqs_ham* H, const uint64_t* xa1, con
     if (cap < uniq)
       return fail(HINQS_ERR_ARG, "hinqs_candidate_pool: cap %lld below the %lld candidates",
                   (long long)cap, (long long)uniq);
-    k_pool_scatter<<<grid_for(m_pad), 256, 0, s>>>(keys, m_pad, flag, pos, ya, yb);
+    if (ranks)
+      k_pool_rank_scatter<<<grid_for(m_pad), 256, 0, s>>>(keys, m_pad, flag, pos, DA, DB, ya, yb);
+    else
+      k_pool_scatter<<<grid_for(m_pad), 256, 0, s>>>(keys, m_pad, flag, pos, ya, yb);
     HQ_LAUNCH_CHECK();
     return HINQS_OK;
   };
   const int rc = run();
   dfree(keys, s);
   dfree(ex, s);
+  dfree(tmp, s);
+  dfree(DA, s);
+  dfree(DB, s);
   dfree(flag, s);
   dfree(pos, s);
   dfree(dropped, s);

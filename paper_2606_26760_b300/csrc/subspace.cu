@@ -140,7 +140,7 @@ __global__ void k_unrank(uint64_t* out, int64_t count, int n, int k, const uint6
   }
 }
 
-static int build_species(const uint64_t* in, int64_t m, int n, int k, int flags, uint64_t** out,
+int build_species(const uint64_t* in, int64_t m, int n, int k, int flags, uint64_t** out,
                          int64_t* count, int64_t* dropped, cudaStream_t s) {
   *out = nullptr;
   *count = 0;

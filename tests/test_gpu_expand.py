@@ -86,9 +86,28 @@ def test_classical_expansion_degenerate_and_errors():
     assert xa.numel() == 0 and xb.numel() == 0
     xa, xb = hq.classical_expansion(ham, sub, c, 0)
     assert xa.numel() == 0
-    h, eri, _ = synth.integrals(33, 5)
-    big = hq.Hamiltonian(h, eri, 1, 1, 0.0)
-    sub33 = hq.build_subspace(np.array([1, 2], np.uint64), np.array([1, 4], np.uint64), 33, 1, 1)
     with pytest.raises(hq.HinqsError) as e:
-        hq.classical_expansion(big, sub33, torch.ones(4, dtype=torch.float64, device="cuda"), 2)
+        hq.classical_expansion(ham, sub, c, -1)
     assert e.value.code == hq.ERR_ARG
+
+
+@pytest.mark.parametrize("n,na,nb,seed,n_top", [(33, 1, 1, 81, 4), (40, 2, 2, 82, 6),
+                                                (36, 3, 2, 83, 3), (64, 1, 2, 84, 5),
+                                                (32, 2, 2, 85, 5)])
+def test_classical_expansion_wide_orbitals_matches_oracle(n, na, nb, seed, n_top):
+    """From 32 orbitals on the candidates are keyed by the ranks of their distinct
+    strings: the same set and order as the oracle's (orbitals up to 64 use the upper
+    half of the 64-bit word)."""
+    h, eri, _ = synth.integrals(n, seed)
+    rng = np.random.default_rng(seed)
+    fa, fb = synth.hf_weighted_samples(n, na, 60, seed), synth.hf_weighted_samples(n, nb, 50, seed + 1)
+    sa, sb = np.unique(fa), np.unique(fb)
+    ham = hq.Hamiltonian(h, eri, na, nb, 0.0)
+    sub = hq.build_subspace(sa, sb, n, na, nb)
+    H = oracle.Ham(h, eri, 0.0, na, nb)
+    osa, osb = oracle.build_subspace(sa, sb, na, nb)
+    c = rng.standard_normal(len(osa) * len(osb))
+    xa, xb = hq.classical_expansion(ham, sub, torch.tensor(c, device="cuda"), n_top)
+    ra, rb = oracle.classical_expansion(H, osa, osb, c, n_top)
+    assert len(ra) > 0
+    assert np.array_equal(_u64(xa), ra) and np.array_equal(_u64(xb), rb)

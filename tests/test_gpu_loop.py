@@ -121,6 +121,33 @@ def test_candidate_pool_matches_oracle(m1, m2, me):
     assert dropped == rd
 
 
+@pytest.mark.parametrize("n,na,nb", [(33, 4, 3), (40, 3, 5), (64, 2, 2), (32, 4, 4)])
+def test_candidate_pool_wide_orbitals_matches_oracle(n, na, nb):
+    """From 32 orbitals on the pool sorts ranks of the proposals' distinct strings
+    instead of packed strings: the same set and order as the oracle's, wrong electron
+    counts and bits above n_orb dropped, the basis excluded."""
+    h, eri, _ = synth.integrals(n, 8)
+    ham = hq.Hamiltonian(h, eri, na, nb, 0.0)
+    rng = np.random.default_rng(n)
+
+    def dets(m, seed):
+        xa = synth.hf_weighted_samples(n, na, m, seed)
+        xb = synth.hf_weighted_samples(n, nb, m, seed + 1)
+        bad = rng.random(m) < 0.03
+        xa[bad] ^= np.uint64(1)
+        if n < 64:
+            far = rng.random(m) < 0.02
+            xb[far] |= np.uint64(1 << (n + (63 - n) // 2))   # a bit at or above n_orb
+        return xa, xb
+    p1, p2, ex = dets(3000, 11), dets(800, 13), dets(500, 15)
+    ex = (np.concatenate([ex[0], p1[0][:40]]), np.concatenate([ex[1], p1[1][:40]]))
+    got_a, got_b, dropped = hq.candidate_pool(ham, p1, p2, ex)
+    ra, rb, rd = oracle.candidate_pool([p1, p2], ex, na, nb)
+    assert len(ra) > 0
+    assert np.array_equal(_np_u64(got_a), ra) and np.array_equal(_np_u64(got_b), rb)
+    assert dropped == rd
+
+
 def test_candidate_pool_everything_excluded():
     n, na, nb = 8, 3, 3
     h, eri, _ = synth.integrals(n, 1)

@@ -434,6 +434,38 @@ def test_connected_counts_generic_integrals():
     assert len(ya) == 2 * s1 + 2 * comb(ne, 2) * comb(n - ne, 2) + s1 * s1
 
 
+def test_connected_wide_orbitals_embeds_small_problem():
+    """Strings above bit 32: an 8-orbital problem placed, order-preserving, on eight of
+    40 orbitals (integrals zero elsewhere) has the same connected set and elements,
+    relabelled, since the phases count occupied orbitals between two positions and the
+    embedding keeps that order.  With generic 40-orbital integrals the count of
+    singles and doubles holds as on small n."""
+    from math import comb
+    n, N, na, nb = 8, 40, 3, 2
+    pos = np.array([1, 6, 17, 31, 32, 33, 38, 39])
+    h, eri, _ = synth.integrals(n, 62)
+    hw, eriw = np.zeros((N, N)), np.zeros((N, N, N, N))
+    hw[np.ix_(pos, pos)] = h
+    eriw[np.ix_(pos, pos, pos, pos)] = eri
+
+    def up(s):
+        return sum(1 << int(pos[p]) for p in range(n) if (int(s) >> p) & 1)
+
+    Hs, Hw = oracle.Ham(h, eri, 0.0, na, nb), oracle.Ham(hw, eriw, 0.0, na, nb)
+    for xa, xb in [(0b10101, 0b11), (0b11100000, 0b10000001), (0b1011, 0b1100000)]:
+        ya, yb, val = oracle.connected(Hs, xa, xb)
+        wa, wb, wval = oracle.connected(Hw, up(xa), up(xb))
+        ref = {(up(a), up(b)): v for a, b, v in zip(ya, yb, val)}
+        got = dict(zip(zip(wa.tolist(), wb.tolist()), wval.tolist()))
+        assert set(got) == set(ref) and len(ref) > 10
+        assert max(abs(got[k] - ref[k]) for k in ref) < 1e-12
+        assert list(zip(wa.tolist(), wb.tolist())) == sorted(got)
+    hg, erig, _ = synth.integrals(N, 63)
+    ya, _, _ = oracle.connected(oracle.Ham(hg, erig, 0.0, na, nb), (1 << 35) | 0b110, (1 << 39) | 1)
+    s = [na * (N - na), nb * (N - nb)]
+    assert len(ya) == sum(s) + comb(na, 2) * comb(N - na, 2) + comb(nb, 2) * comb(N - nb, 2) + s[0] * s[1]
+
+
 def test_classical_expansion_excludes_subspace_and_is_union():
     w = synth.workload("fp64_small")
     H = oracle.Ham(w["h"], w["eri"], 0.0, 3, 3)
