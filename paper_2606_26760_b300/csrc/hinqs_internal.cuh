@@ -130,6 +130,10 @@ struct hinqs_links_s {
   // K-major core-matrix row, (kf / 8) * 128 + (kf % 8) * 2; pair-major, slot k of row
   // I at ((k / 2) * N + I) * 2 + k % 2, so one 16-byte load brings two slots
   int2* tcell = nullptr;
+  // the same slots packed into 32 bits, J | kpart << 17 | (sign < 0) << 31, quad-major:
+  // slot k of row I at ((k / 4) * N + I) * 4 + k % 4, so one 16-byte load brings four
+  // (kpart < 2^14 for n <= kTcMaxOrb); null when N > 2^17 or n > kTcMaxOrb
+  uint32_t* tcq = nullptr;
   // all links as packed records for the row products: element offset of the linked
   // row (J * other dimension, uint32) with the element: rec32 {off, float bits},
   // rec64 {off, 0, double bits}; null when N_a * N_b >= 2^32

@@ -167,7 +167,7 @@ __device__ __forceinline__ int tc_kpart(int pair, int n) {
 __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
                             const int64_t* __restrict__ srp, const int2* __restrict__ sl,
                             int width, int2* __restrict__ ell, int2* __restrict__ tcell,
-                            int* __restrict__ cnt) {
+                            uint32_t* __restrict__ tcq, int* __restrict__ cnt) {
   for (int64_t I = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; I < N;
        I += (int64_t)gridDim.x * blockDim.x) {
     int k = 0;
@@ -177,6 +177,9 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
       const int kp = tc_kpart((l.y > 0 ? l.y : -l.y) - 1, n);
       tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] =
           make_int2(l.x, l.y > 0 ? kp : (int)((unsigned)kp | 0x80000000u));
+      if (tcq)
+        tcq[(((int64_t)(k >> 2) * N + I) << 2) + (k & 3)] =
+            (uint32_t)l.x | ((uint32_t)kp << 17) | (l.y > 0 ? 0u : 0x80000000u);
     }
     uint64_t o = S[I];
     while (o) {
@@ -184,12 +187,17 @@ __global__ void k_build_ell(const uint64_t* __restrict__ S, int64_t N, int n,
       o &= o - 1;
       ell[(int64_t)k * N + I] = make_int2((int)I, j * n + j + 1);
       tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] = make_int2((int)I, tc_kpart(j * n + j, n));
+      if (tcq)
+        tcq[(((int64_t)(k >> 2) * N + I) << 2) + (k & 3)] =
+            (uint32_t)I | ((uint32_t)tc_kpart(j * n + j, n) << 17);
       ++k;
     }
     cnt[I] = k;
     for (; k < width; ++k) ell[(int64_t)k * N + I] = make_int2(0, 0);
     for (k = cnt[I]; k < ((width + 1) & ~1); ++k)
       tcell[(((int64_t)(k >> 1) * N + I) << 1) + (k & 1)] = make_int2(0, 0);
+    if (tcq)
+      for (k = cnt[I]; k < ((width + 3) & ~3); ++k) tcq[(((int64_t)(k >> 2) * N + I) << 2) + (k & 3)] = 0u;
   }
 }
 
@@ -247,6 +255,7 @@ static void free_links(hinqs_links_s* L, cudaStream_t s) {
   dfree(L->VTlo32, s);
   dfree(L->sell, s);
   dfree(L->tcell, s);
+  dfree(L->tcq, s);
   dfree(L->scount, s);
   dfree(L->rec32, s);
   dfree(L->rec64, s);
@@ -328,9 +337,12 @@ extern "C" int hinqs_string_links(const hinqs_ham* H, const hinqs_subspace* B, i
     L->ell_width = L->max_srow + L->n_e;
     if (!(rc = dalloc(&L->sell, (size_t)std::max(1, L->ell_width) * N, s)) &&
         !(rc = dalloc(&L->tcell, (size_t)std::max(2, (L->ell_width + 1) & ~1) * N, s)) &&
-        !(rc = dalloc(&L->scount, N, s))) {
+        !(rc = dalloc(&L->scount, N, s)) &&
+        !(N <= (int64_t(1) << 17) && n <= kTcMaxOrb &&
+          (rc = dalloc(&L->tcq, (size_t)std::max(4, (L->ell_width + 3) & ~3) * N, s)))) {
       k_build_ell<<<(unsigned)std::min<int64_t>(ceil_div(N, 256), 4 * kNumSMs), 256, 0, s>>>(
-          L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->tcell, L->scount);
+          L->strings, N, n, L->srow_ptr, L->slink, L->ell_width, L->sell, L->tcell, L->tcq,
+          L->scount);
       cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) rc = cuda_fail(e, "k_build_ell", __FILE__, __LINE__);
     }

@@ -37,6 +37,9 @@ namespace tc {
 
 constexpr int kThreads = 256;
 constexpr int kTileM = 128;
+// packed slot quads a gather thread has in flight (measured on B300: six, or an L1
+// prefetch of the next tile's quads during the MMA, gain nothing)
+constexpr int kQuads = 4;
 constexpr long long kWaitLimit = 1ll << 26;  // try_wait polls before giving up
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -125,7 +128,9 @@ struct Args {
   int n, KB;  // KB = padded folded K / 8 (16-byte chunks per operand row)
   const int64_t* a_srow;
   const int2* a_slink;
-  const int2* b_ell;  // slot-major {Jb, kpart | sign bit} (tensor-core gather slots)
+  const int2* b_ell;  // pair-major {Jb, kpart | sign bit} (tensor-core gather slots)
+  const uint4* b_q;   // the same slots packed, quad-major (null: use b_ell)
+  int wq;             // quads per row of b_q
   const int* b_cnt;
   const uint4* Bhi;  // [n*n][KB] BF16 rows of (pq|.) over the folded pairs
   const uint4* Blo;  // low parts (SPLIT = 3)
@@ -162,7 +167,7 @@ __host__ __device__ inline size_t smem_bytes(int NW, int SPLIT, int STAGES, int 
   const size_t np = SPLIT == 3 ? 2 : 1;
   size_t x = STAGES * np * (size_t)kTileM * KB * 16 + np * (size_t)NW * KB * 16 + 32 + 8 * NW;
   x = (x + 15) & ~(size_t)15;
-  if (crow) x += 4 * (size_t)Nb;
+  if (crow) x += (SPLIT == 1 ? 2 : 4) * (size_t)Nb;  // the row as BF16 (SPLIT 1) or FP32
   return x;
 }
 
@@ -226,33 +231,67 @@ __device__ __forceinline__ void sigma_ab_tc_body(const Args& A0, const Queue& Q)
     const int m = tid & (kTileM - 1), hh = tid >> 7;
     unsigned char* ah = a_buf + (size_t)st * NP * a_bytes + (m >> 3) * (KB * 128) + (m & 7) * 16;
     const int64_t Ib = (int64_t)t * kTileM + m;
-    if (Ib < Nb) {
+    // D(Ib, kf) = sign * C(Ja, Jb) at byte offset off of the row; with one BF16 term and
+    // the row staged, the row is BF16 already (BF16 rounding commutes with the sign)
+    auto put16 = [&](uint32_t jb, uint32_t off, uint32_t neg) {
+      const unsigned short b = reinterpret_cast<const unsigned short*>(crow)[jb];
+      *reinterpret_cast<unsigned short*>(ah + off) = b ^ (unsigned short)(neg >> 16);
+    };
+    auto put32 = [&](uint32_t jb, uint32_t off, uint32_t neg) {
+      const float v = __uint_as_float(__float_as_uint(crow[jb]) ^ neg);
+      const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+      *reinterpret_cast<__nv_bfloat16*>(ah + off) = hi;
+      if (SPLIT == 3)
+        *reinterpret_cast<__nv_bfloat16*>(ah + a_bytes + off) =
+            __float2bfloat16_rn(v - __bfloat162float(hi));
+    };
+    auto gather = [&](auto put) {
       const int nk = __ldg(A.b_cnt + Ib);
-      // pair-major slots: thread hh takes slot pairs hh, hh + 2, ...; one 16-byte load
-      // per pair, four pairs (eight records) in flight before any shared-memory store
-      const int4* __restrict__ ell = reinterpret_cast<const int4*>(A.b_ell) + Ib;
-      const int np = (nk + 1) >> 1;
-      for (int j0 = hh; j0 < np; j0 += 8) {
-        int4 l[4];
+      if (A.b_q) {
+        // packed quad-major slots: thread hh takes quads hh, hh + 2, ...; four quads
+        // (sixteen records) in flight, the first four loaded without waiting for nk
+        // (every quad below wq exists, zero-padded)
+        const uint4* __restrict__ q4 = A.b_q + Ib;
+        for (int j0 = hh; j0 < A.wq && (j0 == hh || 4 * j0 < nk); j0 += 2 * kQuads) {
+          uint4 l[kQuads];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          l[u] = (j0 + 2 * u < np) ? __ldg(ell + (int64_t)(j0 + 2 * u) * Nb)
-                                   : make_int4(0, 0, 0, 0);
+          for (int u = 0; u < kQuads; ++u)
+            l[u] = (j0 + 2 * u < A.wq) ? __ldg(q4 + (int64_t)(j0 + 2 * u) * Nb)
+                                       : make_uint4(0, 0, 0, 0);
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int k = 2 * (j0 + 2 * (u >> 1)) + (u & 1);
-          if (k >= nk) break;
-          const int x = (u & 1) ? l[u >> 1].z : l[u >> 1].x;
-          const uint32_t y = (uint32_t)((u & 1) ? l[u >> 1].w : l[u >> 1].y);
-          const float v = __uint_as_float(__float_as_uint(crow[x]) ^ (y & 0x80000000u));
-          const uint32_t off = y & 0x7fffffffu;  // kpart of the folded pair
-          const __nv_bfloat16 hi = __float2bfloat16_rn(v);
-          *reinterpret_cast<__nv_bfloat16*>(ah + off) = hi;
-          if (SPLIT == 3)
-            *reinterpret_cast<__nv_bfloat16*>(ah + a_bytes + off) =
-                __float2bfloat16_rn(v - __bfloat162float(hi));
+          for (int u = 0; u < 4 * kQuads; ++u) {
+            const int k = 4 * (j0 + 2 * (u >> 2)) + (u & 3);
+            if (k >= nk) break;
+            const uint4 q = l[u >> 2];
+            const uint32_t y = (u & 3) == 0 ? q.x : (u & 3) == 1 ? q.y : (u & 3) == 2 ? q.z : q.w;
+            put(y & 0x1ffffu, (y >> 17) & 0x3fffu, y & 0x80000000u);
+          }
+        }
+      } else {
+        // pair-major slots: thread hh takes slot pairs hh, hh + 2, ...; one 16-byte load
+        // per pair, four pairs (eight records) in flight before any shared-memory store
+        const int4* __restrict__ ell = reinterpret_cast<const int4*>(A.b_ell) + Ib;
+        const int np = (nk + 1) >> 1;
+        for (int j0 = hh; j0 < np; j0 += 8) {
+          int4 l[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            l[u] = (j0 + 2 * u < np) ? __ldg(ell + (int64_t)(j0 + 2 * u) * Nb)
+                                     : make_int4(0, 0, 0, 0);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            const int k = 2 * (j0 + 2 * (u >> 1)) + (u & 1);
+            if (k >= nk) break;
+            const int x = (u & 1) ? l[u >> 1].z : l[u >> 1].x;
+            const uint32_t y = (uint32_t)((u & 1) ? l[u >> 1].w : l[u >> 1].y);
+            put((uint32_t)x, y & 0x7fffffffu, y & 0x80000000u);
+          }
         }
       }
+    };
+    if (Ib < Nb) {
+      if (SPLIT == 1 && A.crow_smem) gather(put16);
+      else gather(put32);
     }
     fence_proxy_async();  // generic-proxy writes (zeroing and gather) -> tensor-core reads
   };
@@ -309,7 +348,13 @@ __device__ __forceinline__ void sigma_ab_tc_body(const Args& A0, const Queue& Q)
     const float* crow = A.C + Ja * Nb;
     __syncthreads();  // the previous string's readers of crow_s, b_buf and tgt are done
     if (A.crow_smem) {
-      for (int64_t j = tid; j < Nb; j += kThreads) crow_s[j] = crow[j];
+      if (SPLIT == 1) {
+        unsigned short* c16 = reinterpret_cast<unsigned short*>(crow_s);
+        for (int64_t j = tid; j < Nb; j += kThreads)
+          c16[j] = __bfloat16_as_ushort(__float2bfloat16_rn(crow[j]));
+      } else {
+        for (int64_t j = tid; j < Nb; j += kThreads) crow_s[j] = crow[j];
+      }
       crow = crow_s;
     }
     for (int64_t a0 = a_beg; a0 < a_end && ok; a0 += NW) {
@@ -410,14 +455,16 @@ __device__ __forceinline__ void sigma_ab_tc_body(const Args& A0, const Queue& Q)
   }
 }
 
+// One stage of at most 64 columns is meant to run three CTAs per SM: the register cap
+// keeps them there (80 a thread).
 template <int NW, int SPLIT, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc(Args A) {
+__global__ void __launch_bounds__(kThreads) __maxnreg__((NW <= 64 && STAGES == 1) ? 80 : 128) k_sigma_ab_tc(Args A) {
   sigma_ab_tc_body<NW, SPLIT, STAGES>(A, Queue{});
 }
 
 // The batched form: the table lives in the parameter space for the whole launch.
 template <int NW, int SPLIT, int STAGES>
-__global__ void __launch_bounds__(kThreads, 1) k_sigma_ab_tc_batch(
+__global__ void __launch_bounds__(kThreads, (NW <= 64 && STAGES == 1) ? 3 : 1) k_sigma_ab_tc_batch(
     const __grid_constant__ BatchTab tab, unsigned long long* counter) {
   Queue q;
   q.reqs = tab.reqs;
@@ -1132,6 +1179,8 @@ int sigma_ab_tc_batch(const SigmaReq* reqs, const int* idx, int n, int split, cu
     a.a_srow = r.la->srow_ptr;
     a.a_slink = r.la->slink;
     a.b_ell = r.lb->tcell;
+    a.b_q = reinterpret_cast<const uint4*>(r.lb->tcq);
+    a.wq = (r.lb->ell_width + 3) >> 2;
     a.b_cnt = r.lb->scount;
     a.Bhi = reinterpret_cast<const uint4*>(r.H->tc_bhi);
     a.Blo = reinterpret_cast<const uint4*>(r.H->tc_blo);
@@ -1162,6 +1211,8 @@ int sigma_ab_tc_launch(const hinqs_ham_s* H, const hinqs_subspace_s* B, const hi
   a.a_srow = la->srow_ptr;
   a.a_slink = la->slink;
   a.b_ell = lb->tcell;
+  a.b_q = reinterpret_cast<const uint4*>(lb->tcq);
+  a.wq = (lb->ell_width + 3) >> 2;
   a.b_cnt = lb->scount;
   a.Bhi = reinterpret_cast<const uint4*>(H->tc_bhi);
   a.Blo = reinterpret_cast<const uint4*>(H->tc_blo);

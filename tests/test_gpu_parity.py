@@ -259,6 +259,30 @@ def test_sigma_tensor_core_full_size(precision_workload):
         assert float(torch.max(torch.abs(s - s32))) <= rel * float(torch.max(torch.abs(s32)))
 
 
+def test_sigma_tensor_core_wide_beta_space():
+    """More than 2^17 beta strings (n = 24, 6 beta electrons: the whole space of 134,596
+    strings, three alpha strings): the tensor-core gather takes its 8-byte slots and
+    reads the C row from global memory.  BF16 and split-BF16 products against the
+    oracle on sampled rows, and against the FP32 CUDA-core product everywhere."""
+    n, na, nb = 24, 1, 6
+    h, eri, _ = synth.integrals(n, 107)
+    a = np.array([1, 1 << 5, 1 << 23], dtype=np.uint64)
+    b = synth.all_strings(n, nb)
+    B = Built(h, eri, 0.3, n, na, nb, a, b)
+    assert B.sub.Nb > (1 << 17)
+    c = synth.random_vector(B.sub.N, 11)
+    ct = torch.tensor(c, dtype=torch.float32, device="cuda")
+    rows = np.sort(np.random.default_rng(12).choice(B.sub.N, size=48, replace=False))
+    ref = oracle.sigma(B.H, B.sa, B.sb, c, rows=rows)
+    hd = oracle.diag(B.H, B.sa, B.sb, rows=rows)
+    s32 = hq.sigma(B.ham, B.sub, B.la, B.lb, ct).double()
+    for prec, rel in ((hq.PREC_FP32_BF16AB, 2e-2), (hq.PREC_FP32_BF16X3AB, 2e-4)):
+        s = hq.sigma(B.ham, B.sub, B.la, B.lb, ct, precision=prec).double()
+        sr = s.cpu().numpy()[rows]
+        assert np.all(np.abs(sr - ref) <= _sigma_tol(rel, hd, c[rows], ref)), prec
+        assert float(torch.max(torch.abs(s - s32))) <= rel * float(torch.max(torch.abs(s32)))
+
+
 def _bf16(x):
     """Round to BF16 (round to nearest, ties to even), returned as float64."""
     b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).astype(np.uint64)
