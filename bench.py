@@ -39,7 +39,7 @@ SM_MAX_MHZ = 2032
 # DRAM bytes (read + write) per launch from one ncu capture of the current kernels on
 # this workload: the two row-product launches of the same-spin half, and the
 # tensor-core opposite-spin kernel
-PROFILED_TRAFFIC = {"same": 63.29e6, "opposite": 33.33e6}
+PROFILED_TRAFFIC = {"same": 63.29e6, "opposite": 33.10e6}
 WORKLOAD = "precision"
 
 
