@@ -628,265 +628,555 @@ __global__ void k_set_row32(double* G, double* S, int ldg, const double* sums, i
   }
 }
 
-// Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim
-// ldg; S == NULL means S = I) by cyclic Jacobi with the round-robin parallel
-// ordering, in one block of kRRThreads threads (m <= kMaxSub).  FP64 runs at a small
-// fraction of the FP32 rate on this part and one warp issues to one sub-partition's
-// FP64 unit, so the rotation updates are spread over four warps; each rotation's
-// tangent is solved in FP32 and its cosine refined to FP64 accuracy by Newton steps
-// on 1/sqrt(1 + t^2), which keeps every rotation orthogonal to FP64 rounding while
-// avoiding FP64 division and square root in the serial part of each step (a rotation
-// that zeroes A_pq only to FP32 accuracy is still a valid Jacobi rotation; the
-// remainder is removed by later sweeps).  With S the pencil is reduced
-// to C = L^-1 G L^-T by the Cholesky factor S = L L^T and eigenvectors are mapped
-// back, y = L^-T z, so that y^T S y = 1.  out[0] = theta, out[1..m] = y (largest
-// |component| > 0).  If all != NULL every eigenpair is written in ascending order,
-// all[j * kRitzStride] = lambda_j, all[j * kRitzStride + 1 ..] = y_j.
+// 1/sqrt(x) for x > 0 to FP64 accuracy: an FP32 estimate refined by two Newton steps
+// (each roughly squares the relative error), which keeps FP64 division and square root
+// (long instruction sequences on this part's FP64 pipe) out of the serial chains below.
+__device__ __forceinline__ double rsqrt64(double x) {
+  const float xf = (float)x;
+  if (!(xf > 1e-30f && xf < 1e30f)) return 1.0 / sqrt(x);
+  double y = (double)rsqrtf(xf);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return y;
+}
+
+__device__ __forceinline__ double warp_sum64(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;  // the same in every lane (each butterfly step adds the same two terms)
+}
+
+// Rotation (c, s) that zeroes A_pq of the symmetric 2 x 2 block (app, apq; apq, aqq):
+// t = tan(angle) from tau = (aqq - app) / (2 apq), the root of t^2 + 2 tau t - 1 = 0 of
+// smaller magnitude, c = 1 / sqrt(1 + t^2), s = t c.  In FP64 the tangent is formed in
+// FP32 and the cosine refined by Newton steps on 1 / sqrt(1 + t^2), so the rotation is
+// orthogonal to FP64 rounding (a rotation that zeroes A_pq only to FP32 accuracy is
+// still a valid Jacobi rotation; later sweeps remove the remainder).
+__device__ __forceinline__ void jacobi_rotation(float app, float aqq, float apq, float& c,
+                                                float& s) {
+  // approximate division and square root: the rotation only has to be orthogonal, which
+  // c = 1 / sqrt(1 + t^2), s = t c is for any t, to FP32 rounding
+  const float tau = __fdividef(aqq - app, 2.0f * apq);
+  float t = 0.0f;  // tau not finite: A_pq is negligible, no rotation
+  if (fabsf(tau) < 1e18f) {
+    const float x = fmaf(tau, tau, 1.0f);
+    t = __fdividef(tau >= 0.0f ? 1.0f : -1.0f, fabsf(tau) + x * rsqrtf(x));
+  } else if (isfinite(tau)) {
+    t = __fdividef(0.5f, tau);
+  }
+  c = rsqrtf(fmaf(t, t, 1.0f));
+  s = t * c;
+}
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& c,
+                                                double& s) {
+  const float tau = (float)(aqq - app) / (2.0f * (float)apq);
+  float tf = 0.0f;
+  if (isfinite(tau))
+    tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
+  const double t = (double)tf, x = fma(t, t, 1.0);
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  c = y;
+  s = t * y;
+}
+
+template <typename T>
+struct JacobiFloor;
+template <>
+struct JacobiFloor<float> {  // eps = 2^-24
+  static constexpr double eps2 = 3.5527136788005009e-15, stall = 1e-10;
+};
+template <>
+struct JacobiFloor<double> {  // eps = 2^-53
+  static constexpr double eps2 = 1.2325951644078310e-32, stall = 1e-24;
+};
+
+// Cyclic Jacobi on the symmetric mm x mm matrix A (m real rows, mm = m rounded up to
+// even; a padding row is isolated with a huge diagonal), round-robin parallel ordering
+// in one block of kRRThreads threads, rotations accumulated into Q.  Converged when the
+// off-diagonal mass of the m x m block is at the rounding floor of the rotations,
+// (4 m eps)^2 relative to the diagonal's, or stops falling near it; 30 sweeps at most.
+// The pairing is the round-robin tournament in closed form: at step t position 0 holds
+// index 0 and position k >= 1 holds 1 + ((k - 1 - t) mod (mm - 1)), and position k meets
+// position mm - 1 - k; each step moves the index at a position k >= 1 one down (1 wraps
+// to mm - 1).  In the updates thread (w, l) takes row or column l of the pairs w, w + 4,
+// ...  cs holds mm/2 (c, s) pairs of T, pr is int scratch, red2 [4][2] of T.
+template <typename T>
+__device__ void jacobi_sweeps(T (*A)[kMaxSub + 1], T (*Q)[kMaxSub + 1], int m, int mm, T* cs,
+                              int (*pr)[2], T (*red2)[2]) {
+  const int lane = threadIdx.x, w = lane >> 5, l = lane & 31;
+  constexpr int kW = kRRThreads / 32;
+  const int h = mm / 2, nm = mm - 1;
+  const T floor_rel = (T)(16.0 * (double)m * (double)m * JacobiFloor<T>::eps2);
+  const T stall = (T)JacobiFloor<T>::stall;
+  T prev_off = 0;
+  for (int sweep = 0; sweep < 30; ++sweep) {
+    T off = 0, dia = 0;
+    for (int r = w; r < m; r += kW)
+      if (l < m) {
+        const T v = A[r][l];
+        if (r != l) off += v * v;
+        else dia += v * v;
+      }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dia += __shfl_xor_sync(0xffffffffu, dia, o);
+    }
+    if (l == 0) {
+      red2[w][0] = off;
+      red2[w][1] = dia;
+    }
+    __syncthreads();
+    off = 0;
+    dia = 0;
+    for (int k = 0; k < kW; ++k) {
+      off += red2[k][0];
+      dia += red2[k][1];
+    }
+    __syncthreads();
+    if (off <= floor_rel * dia || off == (T)0) break;
+    if (sweep > 0 && off >= (T)0.25 * prev_off && off <= stall * dia) break;
+    prev_off = off;
+    int a = lane, b = mm - 1 - lane;  // indices at positions lane and mm - 1 - lane
+    for (int step = 0; step < nm; ++step) {
+      if (lane < h) {
+        const int p = min(a, b), q = max(a, b);
+        pr[lane][0] = p;
+        pr[lane][1] = q;
+        const T apq = A[p][q];
+        T c = 1, sn = 0;
+        if (apq != (T)0 && p < m && q < m) jacobi_rotation(A[p][p], A[q][q], apq, c, sn);
+        cs[2 * lane] = c;
+        cs[2 * lane + 1] = sn;
+        if (a != 0) a = a == 1 ? nm : a - 1;
+        b = b == 1 ? nm : b - 1;
+      }
+      __syncthreads();
+      if (l < mm)  // A <- J^T A (rows p, q), column l
+        for (int k = w; k < h; k += kW) {
+          const int p = pr[k][0], q = pr[k][1];
+          const T c = cs[2 * k], sn = cs[2 * k + 1];
+          const T ap = A[p][l], aq = A[q][l];
+          A[p][l] = c * ap - sn * aq;
+          A[q][l] = sn * ap + c * aq;
+        }
+      __syncthreads();
+      if (l < mm)  // A <- A J, Q <- Q J (cols p, q), row l
+        for (int k = w; k < h; k += kW) {
+          const int p = pr[k][0], q = pr[k][1];
+          const T c = cs[2 * k], sn = cs[2 * k + 1];
+          const T ap = A[l][p], aq = A[l][q];
+          A[l][p] = c * ap - sn * aq;
+          A[l][q] = sn * ap + c * aq;
+          const T qp = Q[l][p], qq = Q[l][q];
+          Q[l][p] = c * qp - sn * qq;
+          Q[l][q] = sn * qp + c * qq;
+        }
+      __syncthreads();
+    }
+  }
+}
+
+// Lowest eigenpair of the symmetric m x m pencil (G, S) (row-major, leading dim ldg;
+// S == NULL means S = I), in one block of kRRThreads threads (m <= kMaxSub).  FP64 runs
+// at a small fraction of the FP32 rate on this part, so the FP64 work is kept to what
+// fixes the result's accuracy:
+//   1. The pencil is reduced to a symmetric C with a factor M, M^T S M = I, C = M^T G M:
+//      near the identity (m max|S - I| <= 1e-4) M = S^-1/2 by its series; otherwise the
+//      Cholesky factor S = L L^T (FP64, right-looking, the pivots' 1/sqrt by rsqrt64),
+//      M = L^-T; without S, C = (G + G^T) / 2.
+//   2. Cyclic Jacobi on fp32(C) in FP32 (warm-started, when the pencil grew
+//      by one row and column since the last call, from the previous eigenvectors in
+//      qkeep: the transformed matrix is then diagonal but for its last row and column,
+//      up to FP32 rounding).
+//   3. The lowest pair refined in FP64 against C: with r = C z - theta z and
+//      theta = z^T C z (|z| = 1), z <- z - sum_{j != 0} q_j (q_j^T r) / (lambda_j - theta)
+//      over the FP32 eigenpairs (q_j, lambda_j), the Newton correction for an eigenvector
+//      with the FP32 spectral inverse of C - theta on the complement of q_0, until |r| is
+//      at the rounding floor (16 m eps64 max|lambda|); each step gains about the FP32
+//      accuracy times the spectral spread over the gap.
+//   4. If the two lowest FP32 eigenvalues are closer than 1e-5 of the spectral scale, or
+//      the refinement does not reach the floor in 8 steps, FP64 Jacobi on C instead (the
+//      rotations' tangents in FP32, cosines refined to FP64).
+// Eigenvectors are mapped back, y = M z, so that y^T S y = 1.  out[0] = theta,
+// out[1..m] = y (largest |component| > 0).  If all != NULL every eigenpair is written in
+// ascending order, all[j * kRitzStride] = lambda_j, all[j * kRitzStride + 1 ..] = y_j
+// (pairs other than the lowest to the FP32 solve's accuracy when it was kept).
 __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G, int ldg, int m,
                                            double* __restrict__ out,
                                            const double* __restrict__ S,
                                            double* __restrict__ all = nullptr,
                                            double* __restrict__ qkeep = nullptr, int warm = 0) {
-  __shared__ double A[kMaxSub][kMaxSub + 1];
-  __shared__ double Q[kMaxSub][kMaxSub + 1];
-  __shared__ double L[kMaxSub][kMaxSub + 1];
-  __shared__ double X[kMaxSub][kMaxSub + 1];
-  __shared__ double cs[kMaxSub / 2][2];
+  __shared__ double Cm[kMaxSub][kMaxSub + 1];  // the reduced matrix C (FP64)
+  __shared__ double L[kMaxSub][kMaxSub + 1];   // Cholesky factor of S
+  __shared__ double X[kMaxSub][kMaxSub + 1];   // scratch; A of the FP64 fallback
+  __shared__ double U[kMaxSub][kMaxSub + 1];   // Q of the FP64 fallback, or A32 | Q32
+  __shared__ double Linv[kMaxSub];
+  __shared__ double z[kMaxSub];
+  __shared__ double part[kRRThreads / 32][kMaxSub];
+  __shared__ double cs64[kMaxSub];
+  __shared__ double red64[kRRThreads / 32][2];
+  __shared__ float lam[kMaxSub];
+  __shared__ float rbuf[kMaxSub];
+  __shared__ float pbuf[kMaxSub];
   __shared__ int pr[kMaxSub / 2][2];
-  __shared__ int order[kMaxSub];
   __shared__ int rank_of[kMaxSub];
+  __shared__ int s_flag;
+  __shared__ int s_emax;
+  __shared__ double s_theta;
+  float (*A32)[kMaxSub + 1] = reinterpret_cast<float (*)[kMaxSub + 1]>(&U[0][0]);
+  float (*Q32)[kMaxSub + 1] = A32 + kMaxSub;
+  float (*T32)[kMaxSub + 1] = reinterpret_cast<float (*)[kMaxSub + 1]>(&X[0][0]);
   const int lane = threadIdx.x;  // thread index in the block
+  const int w = lane >> 5, l = lane & 31;
   const unsigned full = 0xffffffffu;
-  __shared__ double red2[kRRThreads / 32][2];
-  __shared__ double Linv[kMaxSub];  // 1 / L[j][j]: one division per pivot, products after
   const int mm = m + (m & 1);  // even size for the tournament; the pad row/col is isolated
-  bool use_s = false;
+
+  // ---- 1. C (FP64)
+  bool use_s = false, use_m = false;
   if (S) {
-    // Cholesky S = L L^T, column by column; lanes take the rows below the pivot
+    // E = S - I.  Near the identity (a basis orthonormal up to FP32 rounding, as the
+    // mixed solver's), the symmetric factor M = S^-1/2 = I - E/2 + 3E^2/8 - 5E^3/16 +
+    // O(E^4) (exact to FP64 rounding while m max|E_ij| <= 1e-4) takes the Cholesky
+    // factor's place: C = M G M and y = M z, from small matrix products that every
+    // thread shares, instead of m serial pivots and triangular solves.
+    if (lane == 0) s_emax = 0;
+    __syncthreads();
+    float e = 0.0f;
+    for (int i = lane; i < m * m; i += kRRThreads) {
+      const int r = i / m, c = i % m;
+      const double v = 0.5 * (S[r * ldg + c] + S[c * ldg + r]) - (r == c ? 1.0 : 0.0);
+      X[r][c] = v;
+      Cm[r][c] = 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
+      e = fmaxf(e, fabsf((float)v));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) e = fmaxf(e, __shfl_xor_sync(full, e, o));
+    if (l == 0) atomicMax(&s_emax, __float_as_int(e));  // non-negative: ordered as integers
+    __syncthreads();
+    use_m = (float)m * __int_as_float(s_emax) <= 1e-4f;
+  }
+  if (use_m) {
+    for (int i = lane; i < m * m; i += kRRThreads) {  // U = E^2
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v = fma(X[r][k], X[k][c], v);
+      U[r][c] = v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // L = M
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v = fma(X[r][k], U[k][c], v);
+      L[r][c] = (r == c ? 1.0 : 0.0) - 0.5 * X[r][c] + 0.375 * U[r][c] - 0.3125 * v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // U = G M
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v = fma(Cm[r][k], L[k][c], v);
+      U[r][c] = v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // X = M G M
+      const int r = i / m, c = i % m;
+      double v = 0.0;
+      for (int k = 0; k < m; ++k) v = fma(L[r][k], U[k][c], v);
+      X[r][c] = v;
+    }
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {
+      const int r = i / m, c = i % m;
+      Cm[r][c] = 0.5 * (X[r][c] + X[c][r]);
+    }
+  } else if (S) {
+    for (int i = lane; i < m * m; i += kRRThreads) {
+      const int r = i / m, c = i % m;
+      if (c <= r) L[r][c] = 0.5 * (S[r * ldg + c] + S[c * ldg + r]);
+    }
+    __syncthreads();
     use_s = true;
     for (int j = 0; j < m; ++j) {
-      // every lane forms the pivot from values stored before the last barrier
-      double d = S[j * ldg + j];
-      for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+      const double d = L[j][j];  // the same in every thread
       if (!(d > 0.0)) {
         use_s = false;
         break;
       }
-      const double ljj = sqrt(d), inv = 1.0 / ljj;
-      for (int i = j + 1 + lane; i < m; i += kRRThreads) {
-        double v = 0.5 * (S[i * ldg + j] + S[j * ldg + i]);
-        for (int k = 0; k < j; ++k) v -= L[i][k] * L[j][k];
-        L[i][j] = v * inv;
+      const double inv = rsqrt64(d);
+      for (int i = j + 1 + lane; i < m; i += kRRThreads) L[i][j] *= inv;
+      __syncthreads();
+      const int r = m - j - 1;  // trailing block rows j+1..m-1
+      for (int t = lane; t < r * r; t += kRRThreads) {
+        const int i = j + 1 + t / r, k = j + 1 + t % r;
+        if (k <= i) L[i][k] -= L[i][j] * L[k][j];
       }
       if (lane == 0) {
-        L[j][j] = ljj;
         Linv[j] = inv;
+        L[j][j] = d * inv;
       }
       __syncthreads();
     }
   }
+  // columns spread over the four warps: thread (w, l) takes column 4 l + w
+  const int my_col = 4 * l + w;
   if (use_s) {
-    // X = L^-1 Gs (lane = column), then C = L^-1 X^T (lane = column)
-    if (lane < m) {
+    // X = L^-1 Gs, then C = L^-1 X^T, column by column (forward substitution)
+    if (my_col < m) {
       for (int i = 0; i < m; ++i) {
-        double v = 0.5 * (G[i * ldg + lane] + G[lane * ldg + i]);
-        for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][lane];
-        X[i][lane] = v * Linv[i];
+        double v = 0.5 * (G[i * ldg + my_col] + G[my_col * ldg + i]);
+        for (int k = 0; k < i; ++k) v -= L[i][k] * X[k][my_col];
+        X[i][my_col] = v * Linv[i];
       }
     }
     __syncthreads();
-    if (lane < m) {
+    if (my_col < m) {
       for (int i = 0; i < m; ++i) {
-        double v = X[lane][i];
-        for (int k = 0; k < i; ++k) v -= L[i][k] * A[k][lane];
-        A[i][lane] = v * Linv[i];
+        double v = X[my_col][i];
+        for (int k = 0; k < i; ++k) v -= L[i][k] * Cm[k][my_col];
+        Cm[i][my_col] = v * Linv[i];
       }
     }
     __syncthreads();
-    for (int i = lane; i < m * m; i += kRRThreads) X[i / m][i % m] = 0.5 * (A[i / m][i % m] + A[i % m][i / m]);
-    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {
+      const int r = i / m, c = i % m;
+      if (c < r) {
+        const double v = 0.5 * (Cm[r][c] + Cm[c][r]);
+        Cm[r][c] = v;
+        Cm[c][r] = v;
+      }
+    }
+  } else if (!use_m) {
+    for (int i = lane; i < m * m; i += kRRThreads) {
+      const int r = i / m, c = i % m;
+      Cm[r][c] = 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
+    }
   }
+  __syncthreads();
+
+  // ---- 2. FP32 Jacobi on fp32(C)
   for (int i = lane; i < mm * mm; i += kRRThreads) {
     const int r = i / mm, c = i % mm;
-    double v = 0.0;
-    if (r < m && c < m) v = use_s ? X[r][c] : 0.5 * (G[r * ldg + c] + G[c * ldg + r]);
-    else if (r == c) v = 1e300;  // padding: never the lowest
-    A[r][c] = v;
-    Q[r][c] = (r == c) ? 1.0 : 0.0;
+    A32[r][c] = (r < m && c < m) ? (float)Cm[r][c] : (r == c ? 1e30f : 0.0f);
+    Q32[r][c] = (r == c) ? 1.0f : 0.0f;
   }
-  if (lane < mm) order[lane] = lane;
   __syncthreads();
   if (qkeep && warm && m >= 2) {
-    // The pencil grew by one row and column since the last call, whose eigenvectors
-    // (of the same leading block, the Cholesky factor's leading block being the same)
-    // are in qkeep: start from Q0 = diag(Q_old, 1), so that A = Q0^T C Q0 is diagonal
-    // but for its last row and column and the sweeps converge in a few passes.
+    // start from Q0 = diag(Q_old, 1): A = Q0^T C Q0 is diagonal but for its last row and
+    // column (the leading block of C is the previous call's, as is the Cholesky factor's)
     const int mo = m - 1;
-    for (int i = lane; i < mm * mm; i += kRRThreads) {
-      const int r = i / mm, c = i % mm;
-      Q[r][c] = (r < mo && c < mo) ? qkeep[r * kMaxSub + c] : (r == c ? 1.0 : 0.0);
+    for (int i = lane; i < mo * mo; i += kRRThreads)
+      Q32[i / mo][i % mo] = (float)qkeep[(i / mo) * kMaxSub + i % mo];
+    __syncthreads();
+    for (int i = lane; i < m * m; i += kRRThreads) {  // T = A Q0
+      const int r = i / m, c = i % m;
+      float v = 0.0f;
+      for (int k = 0; k < m; ++k) v = fmaf(A32[r][k], Q32[k][c], v);
+      T32[r][c] = v;
     }
     __syncthreads();
-    for (int i = lane; i < m * m; i += kRRThreads) {  // X = A Q0
+    for (int i = lane; i < m * m; i += kRRThreads) {  // A = Q0^T T
       const int r = i / m, c = i % m;
-      double v = 0.0;
-      for (int k = 0; k < m; ++k) v += A[r][k] * Q[k][c];
-      X[r][c] = v;
-    }
-    __syncthreads();
-    for (int i = lane; i < m * m; i += kRRThreads) {  // A = Q0^T X
-      const int r = i / m, c = i % m;
-      double v = 0.0;
-      for (int k = 0; k < m; ++k) v += Q[k][r] * X[k][c];
-      A[r][c] = v;
+      float v = 0.0f;
+      for (int k = 0; k < m; ++k) v = fmaf(Q32[k][r], T32[k][c], v);
+      A32[r][c] = v;
     }
     __syncthreads();
     for (int i = lane; i < m * m; i += kRRThreads) {  // symmetric part
       const int r = i / m, c = i % m;
-      X[r][c] = 0.5 * (A[r][c] + A[c][r]);
+      T32[r][c] = 0.5f * (A32[r][c] + A32[c][r]);
     }
     __syncthreads();
-    for (int i = lane; i < m * m; i += kRRThreads) A[i / m][i % m] = X[i / m][i % m];
+    for (int i = lane; i < m * m; i += kRRThreads) A32[i / m][i % m] = T32[i / m][i % m];
     __syncthreads();
   }
-  // converged when the off-diagonal mass is at the rounding floor of the rotations,
-  // (4 m eps)^2 relative to the diagonal's (eps = 2^-53; a fixed 1e-30 is below that
-  // floor from m ~ 10 on and ran all 30 sweeps), or stops falling near it
-  const double floor_rel = 16.0 * (double)m * (double)m * 1.2326e-32;
-  double prev_off = 0.0;
-  for (int sweep = 0; sweep < 30; ++sweep) {
-    double off = 0.0, dia = 0.0;
-    for (int i = lane; i < m * m; i += kRRThreads) {
-      const double v = A[i / m][i % m];
-      if (i / m != i % m) off += v * v;
-      else dia += v * v;
+  jacobi_sweeps<float>(A32, Q32, m, mm, reinterpret_cast<float*>(cs64), pr,
+                       reinterpret_cast<float (*)[2]>(red64));
+  if (lane < m) lam[lane] = A32[lane][lane];
+  __syncthreads();
+  // lowest and second-lowest FP32 eigenvalues (lowest index on ties), spectral scale
+  int c0 = 0;
+  float l0 = lam[0], l1 = 3.0e38f, sc = fabsf(lam[0]);
+  for (int j = 1; j < m; ++j) {
+    const float v = lam[j];
+    sc = fmaxf(sc, fabsf(v));
+    if (v < l0) {
+      l1 = l0;
+      l0 = v;
+      c0 = j;
+    } else if (v < l1) {
+      l1 = v;
     }
+  }
+  const double tol_r = 16.0 * (double)m * 1.1102230246251565e-16 * fmax((double)sc, 1e-300);
+
+  // ---- 3. FP64 refinement of the lowest pair
+  bool refined = false;
+  if (m == 1 || (double)l1 - (double)l0 > 1e-5 * (double)sc) {
+    if (w == 0) {
+      double zi = l < m ? (double)Q32[l][c0] : 0.0;
+      zi *= rsqrt64(warp_sum64(zi * zi));
+      if (l < m) z[l] = zi;
+    }
+    __syncthreads();
+    for (int it = 0; it <= 8; ++it) {
+      if (l < m) {  // partial C z over the columns j = w, w + 4, ...
+        double v = 0.0;
+        for (int j = w; j < m; j += kRRThreads / 32) v = fma(Cm[l][j], z[j], v);
+        part[w][l] = v;
+      }
+      __syncthreads();
+      if (w == 0) {
+        double czi = 0.0, zi = 0.0;
+        if (l < m) {
+          zi = z[l];
+          for (int p = 0; p < kRRThreads / 32; ++p) czi += part[p][l];
+        }
+        const double th = warp_sum64(zi * czi);
+        const double ri = czi - th * zi;
+        float rr = (float)ri * (float)ri;  // the test needs no more than FP32
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) rr += __shfl_xor_sync(full, rr, o);
+        const bool done = (double)rr <= tol_r * tol_r;
+        if (done || it == 8) {
+          if (l == 0) {
+            s_flag = done ? 1 : 2;
+            s_theta = th;
+          }
+        } else {
+          if (l < m) rbuf[l] = (float)ri;
+          __syncwarp();
+          if (l < m) {
+            float pj = 0.0f;
+            for (int i = 0; i < m; ++i) pj = fmaf(Q32[i][l], rbuf[i], pj);
+            pbuf[l] = (l == c0) ? 0.0f : pj / (lam[l] - (float)th);
+          }
+          __syncwarp();
+          float di = 0.0f;
+          if (l < m)
+            for (int j = 0; j < m; ++j) di = fmaf(Q32[l][j], pbuf[j], di);
+          double zn = l < m ? zi - (double)di : 0.0;
+          zn *= rsqrt64(warp_sum64(zn * zn));
+          if (l < m) z[l] = zn;
+          if (l == 0) s_flag = 0;
+        }
+      }
+      __syncthreads();
+      if (s_flag) break;
+    }
+    refined = s_flag == 1;
+    __syncthreads();
+  }
+
+  // ---- 4. FP64 Jacobi on C when the FP32 solve is not enough
+  double (*Q64)[kMaxSub + 1] = U;
+  if (!refined) {
+    for (int i = lane; i < mm * mm; i += kRRThreads) {
+      const int r = i / mm, c = i % mm;
+      X[r][c] = (r < m && c < m) ? Cm[r][c] : (r == c ? 1e300 : 0.0);
+      Q64[r][c] = (r == c) ? 1.0 : 0.0;
+    }
+    __syncthreads();
+    jacobi_sweeps<double>(X, Q64, m, mm, cs64, pr, red64);
+    if (lane == 0) {
+      c0 = 0;
+      for (int j = 1; j < m; ++j)
+        if (X[j][j] < X[c0][c0]) c0 = j;
+      s_theta = X[c0][c0];
+    }
+    __syncthreads();
+    c0 = 0;
+    for (int j = 1; j < m; ++j)
+      if (X[j][j] < X[c0][c0]) c0 = j;
+    if (w == 0) {  // the lowest eigenvector, normalised, into z
+      double zi = l < m ? Q64[l][c0] : 0.0;
+      zi *= rsqrt64(warp_sum64(zi * zi));
+      if (l < m) z[l] = zi;
+    }
+  }
+  __syncthreads();
+  if (qkeep)
+    for (int i = lane; i < m * m; i += kRRThreads)
+      qkeep[(i / m) * kMaxSub + i % m] = refined ? (double)Q32[i / m][i % m] : Q64[i / m][i % m];
+
+  // ---- 5. outputs: the lowest pair (y = L^-T z by columns of L in warp 0)
+  const double theta = s_theta;
+  if (w == 0) {
+    double v = l < m ? z[l] : 0.0;
+    if (use_m) {  // y = M z (M symmetric)
+      v = 0.0;
+      if (l < m)
+        for (int j = 0; j < m; ++j) v = fma(L[l][j], z[j], v);
+    } else if (use_s) {
+      for (int i = m - 1; i >= 0; --i) {
+        const double yi = __shfl_sync(full, v * Linv[l < m ? l : 0], i);
+        if (l < i) v = fma(-L[i][l], yi, v);
+        else if (l == i) v = yi;
+      }
+    }
+    // sign: largest |component| positive (lowest index on ties)
+    double big = l < m ? fabs(v) : -1.0;
+    int arg = l;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(full, off, o);
-      dia += __shfl_xor_sync(full, dia, o);
+      const double b2 = __shfl_xor_sync(full, big, o);
+      const int a2 = __shfl_xor_sync(full, arg, o);
+      if (b2 > big || (b2 == big && a2 < arg)) {
+        big = b2;
+        arg = a2;
+      }
     }
-    if ((lane & 31) == 0) {
-      red2[lane >> 5][0] = off;
-      red2[lane >> 5][1] = dia;
-    }
-    __syncthreads();
-    off = 0.0;
-    dia = 0.0;
-    for (int w = 0; w < kRRThreads / 32; ++w) {
-      off += red2[w][0];
-      dia += red2[w][1];
-    }
-    __syncthreads();
-    if (off <= floor_rel * dia || off == 0.0) break;
-    if (sweep > 0 && off >= 0.25 * prev_off && off <= 1e-24 * dia) break;
-    prev_off = off;
-    for (int step = 0; step < mm - 1; ++step) {
-      if (lane < mm / 2) {
-        int p = order[lane], q = order[mm - 1 - lane];
-        if (p > q) {
-          const int t = p;
-          p = q;
-          q = t;
-        }
-        pr[lane][0] = p;
-        pr[lane][1] = q;
-        const double apq = A[p][q];
-        double c = 1.0, sn = 0.0;
-        if (apq != 0.0 && p < m && q < m) {
-          const float tau = (float)(A[q][q] - A[p][p]) / (2.0f * (float)apq);
-          float tf = 0.0f;  // tau overflowing FP32: A_pq is negligible, no rotation
-          if (isfinite(tau))
-            tf = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(fmaf(tau, tau, 1.0f)));
-          const double t = (double)tf, x = fma(t, t, 1.0);
-          double y = (double)rsqrtf((float)x);
-          y = y * fma(-0.5 * x * y, y, 1.5);
-          y = y * fma(-0.5 * x * y, y, 1.5);
-          c = y;
-          sn = t * y;
-        }
-        cs[lane][0] = c;
-        cs[lane][1] = sn;
-      }
-      __syncthreads();
-      for (int i = lane; i < (mm / 2) * mm; i += kRRThreads) {  // A <- J^T A (rows p, q)
-        const int k = i / mm, col = i % mm;
-        const int p = pr[k][0], q = pr[k][1];
-        const double c = cs[k][0], sn = cs[k][1];
-        const double ap = A[p][col], aq = A[q][col];
-        A[p][col] = c * ap - sn * aq;
-        A[q][col] = sn * ap + c * aq;
-      }
-      __syncthreads();
-      for (int i = lane; i < (mm / 2) * mm; i += kRRThreads) {  // A <- A J, Q <- Q J (cols p, q)
-        const int k = i / mm, row = i % mm;
-        const int p = pr[k][0], q = pr[k][1];
-        const double c = cs[k][0], sn = cs[k][1];
-        const double ap = A[row][p], aq = A[row][q];
-        A[row][p] = c * ap - sn * aq;
-        A[row][q] = sn * ap + c * aq;
-        const double qp = Q[row][p], qq = Q[row][q];
-        Q[row][p] = c * qp - sn * qq;
-        Q[row][q] = sn * qp + c * qq;
-      }
-      __syncthreads();
-      if (lane == 0) {  // rotate the tournament, order[0] fixed
-        const int last = order[mm - 1];
-        for (int k = mm - 1; k > 1; --k) order[k] = order[k - 1];
-        order[1] = last;
-      }
-      __syncthreads();
+    const double sv = __shfl_sync(full, v, arg);
+    const double sg = sv < 0.0 ? -1.0 : 1.0;
+    if (l == 0) out[0] = theta;
+    out[1 + l] = l < m ? sg * v : 0.0;
+    if (all) {  // rank 0 of the ordered list: the same pair without the sign choice
+      if (l == 0) all[0] = theta;
+      all[1 + l] = l < m ? v : 0.0;
     }
   }
-  if (qkeep)
-    for (int i = lane; i < m * m; i += kRRThreads) qkeep[(i / m) * kMaxSub + i % m] = Q[i / m][i % m];
-  // rank of each eigenvalue (ascending, ties by index)
+  if (!all) return;
+  // ranks of the other eigenvalues (ascending, ties by index); rank 0 is c0
   if (lane < m) {
-    const double lj = A[lane][lane];
+    const double lj = refined ? (double)lam[lane] : X[lane][lane];
     int r = 0;
     for (int k = 0; k < m; ++k) {
-      const double lk = A[k][k];
+      const double lk = refined ? (double)lam[k] : X[k][k];
       if (lk < lj || (lk == lj && k < lane)) ++r;
     }
     rank_of[lane] = r;
   }
   __syncthreads();
-  // lane j maps eigenvector j back (z -> y) and writes it where its rank says
-  if (lane < m) {
-    const int col = lane, rank = rank_of[lane];
-    if (all || rank == 0) {
-      double z[kMaxSub];
-      double nz = 0.0;
-      for (int r = 0; r < m; ++r) nz += Q[r][col] * Q[r][col];
-      nz = 1.0 / sqrt(nz);
-      for (int r = 0; r < m; ++r) z[r] = Q[r][col] * nz;
-      if (use_s) {
+  if (my_col < m && my_col != c0) {  // one thread per column, spread over the warps
+    const int col = my_col;
+    double zz[kMaxSub];
+    double nz = 0.0;
+    for (int r = 0; r < m; ++r) {
+      zz[r] = refined ? (double)Q32[r][col] : Q64[r][col];
+      nz = fma(zz[r], zz[r], nz);
+    }
+    nz = rsqrt64(nz);
+    for (int r = 0; r < m; ++r) zz[r] *= nz;
+    double* o = all + (size_t)rank_of[col] * kRitzStride;
+    if (use_m) {  // y = M z
+      for (int r = 0; r < m; ++r) {
+        double v = 0.0;
+        for (int k = 0; k < m; ++k) v = fma(L[r][k], zz[k], v);
+        o[1 + r] = v;
+      }
+    } else {
+      if (use_s) {  // y = L^-T z
         for (int i = m - 1; i >= 0; --i) {
-          double v = z[i];
-          for (int k = i + 1; k < m; ++k) v -= L[k][i] * z[k];
-          z[i] = v * Linv[i];
+          double v = zz[i];
+          for (int k = i + 1; k < m; ++k) v -= L[k][i] * zz[k];
+          zz[i] = v * Linv[i];
         }
       }
-      if (rank == 0) {
-        double big = 0.0;
-        int arg = 0;
-        for (int r = 0; r < m; ++r)
-          if (fabs(z[r]) > big) {
-            big = fabs(z[r]);
-            arg = r;
-          }
-        const double sg = z[arg] < 0.0 ? -1.0 : 1.0;
-        out[0] = A[col][col];
-        for (int r = 0; r < m; ++r) out[1 + r] = sg * z[r];
-        for (int r = m; r < kMaxSub; ++r) out[1 + r] = 0.0;
-      }
-      if (all) {
-        double* o = all + (size_t)rank * kRitzStride;
-        o[0] = A[col][col];
-        for (int r = 0; r < m; ++r) o[1 + r] = z[r];
-        for (int r = m; r < kMaxSub; ++r) o[1 + r] = 0.0;
-      }
+      for (int r = 0; r < m; ++r) o[1 + r] = zz[r];
     }
+    o[0] = refined ? (double)lam[col] : X[col][col];
+    for (int r = m; r < kMaxSub; ++r) o[1 + r] = 0.0;
   }
 }
 
@@ -1508,7 +1798,7 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
       for (;;) {
         // residual and correction of the pencil's lowest Ritz pair, with the dot products
         // of its Gram-Schmidt pass against {x, V}
-        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all, qk, rr_warm);
+        k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, nullptr, qk, rr_warm);
         rr_warm = 1;
         launch_mb<Res32>(m, N, c.s, (const float*)ra, (const float*)x32, (const float*)V,
                          (const float*)W, (int64_t)N, m, (const double*)ritz, (const double*)theta_a,
@@ -1579,8 +1869,10 @@ static int davidson_mixed(Ctx& c, const double* guess, const hinqs_davidson_opts
         HQ_TRY(add_column(m));
         m++;
       }
-      // restart: anchor = lowest Ritz vector, plus keep-1 FP32 Ritz vectors
+      // restart: anchor = lowest Ritz vector, plus keep-1 FP32 Ritz vectors (every
+      // eigenpair of the final pencil, solved again: the iterations ask for the lowest only)
       const int kk = std::min(keep, m + 1);
+      k_rr<<<1, kRRThreads, 0, c.s>>>(G, kMaxSub, m + 1, ritz, S, all);
       // xn = y0 x + V y, sxn = y0 s + W y (FP64) and the kept FP32 Ritz vectors with their
       // products, in one pass (the FP32 parts carry the correction)
       launch_mb<Restart32>(std::max(m, 1), N, c.s, (const double*)x, (const double*)sx,
