@@ -427,6 +427,26 @@ int hinqs_davidson_batch(int n_geom, const hinqs_ham* const* hams,
  * stream.  Errors: HINQS_ERR_ARG (polls out of range), HINQS_ERR_CUDA. */
 int hinqs_selftest_bounded_wait(long long polls, void* stream);
 
+/* Not in the paper: the projected eigensolver of hinqs_davidson (the Rayleigh-Ritz step
+ * on the pencil (G, S) of the search space, Sec. 2.2 Step 3's diagonalisation restricted
+ * to it) on a pencil given by the caller, for tests of its paths.  Lowest eigenpair of
+ * G y = theta S y with y^T S y = 1:
+ *   G      host FP64 [m * m], row-major, symmetric (its symmetric part is used)
+ *   S      host FP64 [m * m] symmetric positive definite, or NULL for S = I
+ *   theta_y  host FP64 [m + 1]: theta, then y with its largest |component| positive
+ *   pairs  host FP64 [m * (m + 1)] or NULL: every pair in ascending order, (lambda_j,
+ *          y_j) per row; pairs other than the lowest carry the FP32 solve's accuracy
+ *          (about 1e-6 relative) when the FP64 fallback was not taken
+ *   path   host int or NULL: bit 0 S reduced by the series of S^-1/2 (S within 1e-4 of
+ *          the identity), bit 1 by its Cholesky factor, bit 2 the lowest pair refined to
+ *          FP64 from an FP32 Jacobi solve (clear: FP64 Jacobi, taken when the two lowest
+ *          FP32 eigenvalues are within 1e-5 of the spectral scale or the refinement
+ *          stalls)
+ * m is 1..32 (the solvers' largest search space).  Synchronises the stream.
+ * Errors: HINQS_ERR_ARG (NULL G or theta_y, m out of range), HINQS_ERR_CUDA. */
+int hinqs_selftest_projected_eig(const double* G, const double* S, int m, double* theta_y,
+                                 double* pairs, int* path, void* stream);
+
 /* ------------------------------------------------------ measurement probe --
  * Not in the paper: the rate of this GPU's fused multiply-add pipe for `precision`
  * (HINQS_PREC_FP64 or HINQS_PREC_FP32), the roofline of the CUDA-core kernels.  Runs

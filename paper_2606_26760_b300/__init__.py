@@ -89,6 +89,7 @@ EXPORTED = [
     "hinqs_select_top", "hinqs_determinant_diag", "hinqs_lookup_determinants",
     "hinqs_candidate_pool", "hinqs_basis_update", "hinqs_remap_vector", "hinqs_nqs_loss",
     "hinqs_sigma_workspace_size", "hinqs_davidson_workspace_size", "hinqs_selftest_bounded_wait",
+    "hinqs_selftest_projected_eig",
     "hinqs_probe_fma_rate", "hinqs_detlist_create", "hinqs_detlist_size",
     "hinqs_detlist_positions", "hinqs_detlist_destroy", "hinqs_detlist_scatter",
     "hinqs_detlist_gather", "hinqs_diag_list", "hinqs_sigma_list", "hinqs_davidson_list",
@@ -151,6 +152,7 @@ def load_library(path: str = LIB_PATH):
     lib.hinqs_davidson_workspace_size.argtypes = [I64, I64, ctypes.POINTER(_Opts),
                                                   ctypes.POINTER(ctypes.c_size_t)]
     lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, P]
+    lib.hinqs_selftest_projected_eig.argtypes = [P, P, I, P, P, P, P]
     lib.hinqs_probe_fma_rate.argtypes = [I, ctypes.POINTER(ctypes.c_double), P]
     lib.hinqs_detlist_create.argtypes = [P, P, P, I64, PP, P]
     lib.hinqs_detlist_size.argtypes = [P, PI64]
@@ -565,6 +567,24 @@ def selftest_bounded_wait(polls: int = 4096) -> int:
     lib = load_library()
     _dev()
     return lib.hinqs_selftest_bounded_wait(int(polls), _stream())
+
+
+def selftest_projected_eig(G, S=None, want_pairs: bool = False):
+    """hinqs_selftest_projected_eig: the Davidson solvers' projected eigensolver on the
+    pencil (G, S) (host arrays, m x m, m <= 32).  Returns (theta, y, pairs, path); pairs
+    is an m x (m + 1) array of (lambda_j, y_j) rows when asked for, else None."""
+    lib = load_library()
+    import numpy as np
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    m = G.shape[0]
+    Sa = None if S is None else np.ascontiguousarray(S, dtype=np.float64)
+    ty = np.zeros(m + 1)
+    pairs = np.zeros((m, m + 1)) if want_pairs else None
+    path = ctypes.c_int(0)
+    _check(lib.hinqs_selftest_projected_eig(
+        G.ctypes.data, None if Sa is None else Sa.ctypes.data, m, ty.ctypes.data,
+        None if pairs is None else pairs.ctypes.data, ctypes.byref(path), _stream()))
+    return ty[0], ty[1:], pairs, path.value
 
 
 def probe_fma_rate(precision: int = PREC_FP64) -> float:

@@ -803,12 +803,15 @@ __device__ void jacobi_sweeps(T (*A)[kMaxSub + 1], T (*Q)[kMaxSub + 1], int m, i
 // Eigenvectors are mapped back, y = M z, so that y^T S y = 1.  out[0] = theta,
 // out[1..m] = y (largest |component| > 0).  If all != NULL every eigenpair is written in
 // ascending order, all[j * kRitzStride] = lambda_j, all[j * kRitzStride + 1 ..] = y_j
-// (pairs other than the lowest to the FP32 solve's accuracy when it was kept).
+// (pairs other than the lowest to the FP32 solve's accuracy when it was kept).  path
+// (optional): bit 0 the series factor, bit 1 the Cholesky factor, bit 2 the refined FP32
+// solve (else FP64 Jacobi).
 __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G, int ldg, int m,
                                            double* __restrict__ out,
                                            const double* __restrict__ S,
                                            double* __restrict__ all = nullptr,
-                                           double* __restrict__ qkeep = nullptr, int warm = 0) {
+                                           double* __restrict__ qkeep = nullptr, int warm = 0,
+                                           int* __restrict__ path = nullptr) {
   __shared__ double Cm[kMaxSub][kMaxSub + 1];  // the reduced matrix C (FP64)
   __shared__ double L[kMaxSub][kMaxSub + 1];   // Cholesky factor of S
   __shared__ double X[kMaxSub][kMaxSub + 1];   // scratch; A of the FP64 fallback
@@ -1129,7 +1132,10 @@ __global__ void __launch_bounds__(kRRThreads) k_rr(const double* __restrict__ G,
     }
     const double sv = __shfl_sync(full, v, arg);
     const double sg = sv < 0.0 ? -1.0 : 1.0;
-    if (l == 0) out[0] = theta;
+    if (l == 0) {
+      out[0] = theta;
+      if (path) *path = (use_m ? 1 : 0) | (use_s ? 2 : 0) | (refined ? 4 : 0);
+    }
     out[1 + l] = l < m ? sg * v : 0.0;
     if (all) {  // rank 0 of the ordered list: the same pair without the sign choice
       if (l == 0) all[0] = theta;
@@ -2062,4 +2068,60 @@ extern "C" int hinqs_davidson_list(const hinqs_ham* H, const hinqs_subspace* B,
                                    hinqs_davidson_info* info_out, void* stream) {
   return davidson_run(H, B, la, lb, L, guess, opts, energy, c_out, info_out, stream,
                       "hinqs_davidson_list", nullptr, nullptr);
+}
+
+extern "C" int hinqs_selftest_projected_eig(const double* G, const double* S, int m,
+                                            double* theta_y, double* pairs, int* path,
+                                            void* stream) {
+  using namespace hinqs;
+  if (!G || !theta_y)
+    return fail(HINQS_ERR_ARG, "hinqs_selftest_projected_eig: NULL G or theta_y");
+  if (m < 1 || m > kMaxSub)
+    return fail(HINQS_ERR_ARG, "hinqs_selftest_projected_eig: m outside 1..%d", kMaxSub);
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t mat = (size_t)kMaxSub * kMaxSub;
+  std::vector<double> hg(mat, 0.0), hs(mat, 0.0);
+  for (int r = 0; r < m; ++r)
+    for (int c = 0; c < m; ++c) {
+      hg[(size_t)r * kMaxSub + c] = G[(size_t)r * m + c];
+      if (S) hs[(size_t)r * kMaxSub + c] = S[(size_t)r * m + c];
+    }
+  double *dg = nullptr, *ds = nullptr, *dout = nullptr, *dall = nullptr;
+  int* dpath = nullptr;
+  int rc = HINQS_OK;
+  if ((rc = dalloc(&dg, mat, s)) || (rc = dalloc(&ds, mat, s)) ||
+      (rc = dalloc(&dout, (size_t)kRitzStride, s)) ||
+      (rc = dalloc(&dall, (size_t)kMaxSub * kRitzStride, s)) || (rc = dalloc(&dpath, 1, s))) {
+  }
+  std::vector<double> hout(kRitzStride), hall((size_t)kMaxSub * kRitzStride);
+  int hpath = 0;
+  if (!rc) {
+    cudaError_t e = cudaMemcpyAsync(dg, hg.data(), mat * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ds, hs.data(), mat * sizeof(double), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) {
+      k_rr<<<1, kRRThreads, 0, s>>>(dg, kMaxSub, m, dout, S ? ds : nullptr, pairs ? dall : nullptr,
+                                    nullptr, 0, dpath);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hout.data(), dout, hout.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(hall.data(), dall, hall.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hpath, dpath, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) rc = cuda_fail(e, "hinqs_selftest_projected_eig", __FILE__, __LINE__);
+  }
+  dfree(dg, s);
+  dfree(ds, s);
+  dfree(dout, s);
+  dfree(dall, s);
+  dfree(dpath, s);
+  if (rc) return rc;
+  for (int i = 0; i <= m; ++i) theta_y[i] = hout[i];
+  if (pairs)
+    for (int j = 0; j < m; ++j)
+      for (int i = 0; i <= m; ++i) pairs[(size_t)j * (m + 1) + i] = hall[(size_t)j * kRitzStride + i];
+  if (path) *path = hpath;
+  return HINQS_OK;
 }

@@ -60,6 +60,12 @@ def test_argument_errors_without_gpu(lib):
     lib.hinqs_selftest_bounded_wait.argtypes = [ctypes.c_longlong, ctypes.c_void_p]
     assert lib.hinqs_selftest_bounded_wait(0, None) == -1
     assert lib.hinqs_selftest_bounded_wait((1 << 26) + 1, None) == -1
+    P = ctypes.c_void_p
+    lib.hinqs_selftest_projected_eig.argtypes = [P, P, ctypes.c_int, P, P, P, P]
+    buf = (ctypes.c_double * 4)()
+    assert lib.hinqs_selftest_projected_eig(None, None, 1, buf, None, None, None) == -1
+    assert lib.hinqs_selftest_projected_eig(buf, None, 0, buf, None, None, None) == -1
+    assert lib.hinqs_selftest_projected_eig(buf, None, 33, buf, None, None, None) == -1
 
 
 def test_product_path_has_no_cpu_fallback():
