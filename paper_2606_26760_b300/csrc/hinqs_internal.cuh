@@ -53,6 +53,40 @@ void dfree(T*& p, cudaStream_t s) {
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 __host__ __device__ __forceinline__ int64_t min64(int64_t a, int64_t b) { return a < b ? a : b; }
 
+// Double-float arithmetic: a value is the unevaluated sum hi + lo of two FP32 numbers
+// (about 48 significant bits).  FP64 runs at 1/64 of the FP32 rate on this part and a
+// double-float multiply-add is about twelve FP32 operations.  Products are exact up to
+// the dropped lo*lo term (the error-free product by fused multiply-add), sums use the
+// two-sum of Knuth, so each accumulated term carries about 2^-44 relative error.
+
+// (sh, sl) += (ah + al) * (bh + bl)
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh,
+                                       float& sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float t = sh + p;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (p - z);
+  sh = t;
+  sl += err + e;
+}
+
+// (sh, sl) += (bh, bl)
+__device__ __forceinline__ void df_add(float bh, float bl, float& sh, float& sl) {
+  const float t = sh + bh;
+  const float z = t - sh;
+  const float err = (sh - (t - z)) + (bh - z);
+  sh = t;
+  sl += err + bl;
+}
+
+__device__ __forceinline__ float2 df_split(double x) {
+  const float h = (float)x;
+  return make_float2(h, (float)(x - (double)h));
+}
+
 constexpr int kNumSMs = 148;
 
 }  // namespace hinqs

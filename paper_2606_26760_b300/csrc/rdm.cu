@@ -1,5 +1,7 @@
-// K9: spin-summed 1- and 2-RDMs of a state on the product subspace (FP64),
-// the Hellmann-Feynman gradients of the energy; K10: spin marginals (Step 4).
+// K9: spin-summed 1- and 2-RDMs of a state on the product subspace (FP64 results;
+// the string-pair weights and the staged opposite-spin sums in double-float
+// arithmetic, about 1e-13 relative), the Hellmann-Feynman gradients of the energy;
+// K10: spin marginals (Step 4).
 //
 //   gamma_pq   = sum_s <a+_ps a_qs>
 //   Gamma_pqrs = sum_{s,t} <a+_ps a+_rt a_st a_qs>
@@ -18,25 +20,50 @@
 
 namespace hinqs {
 
-// M[k] = dot(row_a, row_b) for every link k of rows of the matrix X (n_rows x len),
-// plus Mdiag[I] = |row_I|^2.  One warp per link.
-__global__ void k_link_dots(const double* __restrict__ X, int64_t len, const int64_t* __restrict__ rp,
-                            const int32_t* __restrict__ col, int64_t nrows, double* __restrict__ M,
-                            double* __restrict__ Mdiag) {
-  int lane = threadIdx.x & 31;
+// X2[i] = (hi, lo) double-float pair of X[i]
+__global__ void k_df_split(const double* __restrict__ X, int64_t m, float2* __restrict__ X2) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < m;
+       i += (int64_t)gridDim.x * blockDim.x)
+    X2[i] = df_split(X[i]);
+}
+
+// (sh, sl) += a * b in double-float with the two cross terms rounded separately and
+// then added, so that swapping a and b gives the same bits (M(I, J) = M(J, I))
+__device__ __forceinline__ void df_fma_sym(float2 a, float2 b, float& sh, float& sl) {
+  const float p = a.x * b.x;
+  const float e = fmaf(a.x, b.x, -p) + (a.x * b.y + a.y * b.x);
+  df_add(p, e, sh, sl);
+}
+
+// M[k] = dot(row_I, row_J) for every link k (I -> J = col[k]) of the rows of X
+// (n_rows x len, double-float pairs), plus Mdiag[I] = |row_I|^2; one warp per row, the
+// sums as double-float pairs (FP64 runs at 1/64 of the FP32 rate on this part, and
+// these dot products are the bulk of the same-spin RDM work).
+__global__ void k_link_dots_df(const float2* __restrict__ X, int64_t len,
+                               const int64_t* __restrict__ rp, const int32_t* __restrict__ col,
+                               int64_t nrows, double* __restrict__ M, double* __restrict__ Mdiag) {
+  const int lane = threadIdx.x & 31;
+  const unsigned full = 0xffffffffu;
   int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  auto reduce = [&](float h, float l) {
+    for (int o = 16; o > 0; o >>= 1) {
+      const float oh = __shfl_down_sync(full, h, o), ol = __shfl_down_sync(full, l, o);
+      df_add(oh, ol, h, l);
+    }
+    return (double)h + (double)l;
+  };
   for (int64_t I = warp; I < nrows; I += nw) {
-    const double* xi = X + I * len;
-    double d = 0.0;
-    for (int64_t j = lane; j < len; j += 32) d += xi[j] * xi[j];
-    for (int o = 16; o > 0; o >>= 1) d += __shfl_down_sync(0xffffffffu, d, o);
+    const float2* xi = X + I * len;
+    float dh = 0.f, dl = 0.f;
+    for (int64_t j = lane; j < len; j += 32) df_fma_sym(xi[j], xi[j], dh, dl);
+    const double d = reduce(dh, dl);
     if (lane == 0) Mdiag[I] = d;
     for (int64_t k = rp[I]; k < rp[I + 1]; ++k) {
-      const double* xj = X + (int64_t)col[k] * len;
-      double v = 0.0;
-      for (int64_t j = lane; j < len; j += 32) v += xi[j] * xj[j];
-      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      const float2* xj = X + (int64_t)col[k] * len;
+      float vh = 0.f, vl = 0.f;
+      for (int64_t j = lane; j < len; j += 32) df_fma_sym(xi[j], xj[j], vh, vl);
+      const double v = reduce(vh, vl);
       if (lane == 0) M[k] = v;
     }
   }
@@ -216,9 +243,11 @@ __global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, in
 // single links); the bra rows C(I_a, :) of the chunk and the ket row C(J_a, :) are
 // copied to shared memory.  The beta transitions, grouped by pair rs, are cut into
 // segments of at most kRdmSeg entries so that the lanes of a warp carry equal work;
-// a thread walks a segment once and updates U accumulators, one FP64 FMA per term:
+// a thread walks a segment once and updates U accumulators, one double-float
+// multiply-add per term (C split once into (hi, lo) FP32 pairs, the same eight bytes an
+// element as in FP64):
 //   X[u][rs] += C(I_a,u, I_b) * s_b C(J_a, J_b),
-// then adds s_a X[u][rs] into gab[pq_u][rs].
+// then adds s_a X[u][rs] into gab[pq_u][rs] (FP64).
 constexpr int kRdmSeg = 128;
 
 __global__ void k_seg_count(const int64_t* __restrict__ off, int n2, int64_t* __restrict__ cnt) {
@@ -235,12 +264,12 @@ __global__ void k_seg_fill(const int64_t* __restrict__ off, int n2,
 }
 
 template <int U>
-__global__ void __launch_bounds__(256) k_rdm_ab_staged(
-    const double* __restrict__ C, int64_t Nb, int n, const uint64_t* __restrict__ Sa,
+__global__ void __launch_bounds__(256) k_rdm_ab_staged_df(
+    const float2* __restrict__ C2, int64_t Nb, int n, const uint64_t* __restrict__ Sa,
     const int64_t* __restrict__ a_srp, const int2* __restrict__ a_sl,
     const int64_t* __restrict__ off, const int4* __restrict__ trans,
     const int4* __restrict__ seg, int64_t nseg, double* __restrict__ gab) {
-  extern __shared__ __align__(16) double sm[];  // crow[Nb], rows[U][Nb]
+  extern __shared__ __align__(16) float2 sm2[];  // crow[Nb], rows[U][Nb]
   __shared__ int tI[U], tpq[U], ts[U];
   const int n2 = n * n;
   const int64_t Ja = blockIdx.x;
@@ -272,11 +301,11 @@ __global__ void __launch_bounds__(256) k_rdm_ab_staged(
     ts[threadIdx.x] = sg;
   }
   __syncthreads();
-  double* crow = sm;
-  double* rows = sm + Nb;
-  for (int64_t j = threadIdx.x; j < Nb; j += blockDim.x) crow[j] = C[Ja * Nb + j];
+  float2* crow = sm2;
+  float2* rows = sm2 + Nb;
+  for (int64_t j = threadIdx.x; j < Nb; j += blockDim.x) crow[j] = C2[Ja * Nb + j];
   for (int u = 0; u < U; ++u) {
-    const double* src = C + (int64_t)tI[u] * Nb;
+    const float2* src = C2 + (int64_t)tI[u] * Nb;
     for (int64_t j = threadIdx.x; j < Nb; j += blockDim.x) rows[u * Nb + j] = src[j];
   }
   __syncthreads();
@@ -284,19 +313,25 @@ __global__ void __launch_bounds__(256) k_rdm_ab_staged(
     const int4 sgm = seg[q];
     const int rs = sgm.x;
     const int4* __restrict__ tr = trans + off[rs] + sgm.y;
-    double acc[U];
+    float ah[U], al[U];
 #pragma unroll
-    for (int u = 0; u < U; ++u) acc[u] = 0.0;
+    for (int u = 0; u < U; ++u) ah[u] = 0.f, al[u] = 0.f;
     for (int k = 0; k < sgm.z; ++k) {
       const int4 t = tr[k];  // {bra I_b, ket J_b, s_b}
-      const double cj = t.z > 0 ? crow[t.y] : -crow[t.y];
-      const double* rb = rows + t.x;
+      float2 cj = crow[t.y];
+      if (t.z < 0) cj.x = -cj.x, cj.y = -cj.y;
+      const float2* rb = rows + t.x;
 #pragma unroll
-      for (int u = 0; u < U; ++u) acc[u] = fma(rb[u * Nb], cj, acc[u]);
+      for (int u = 0; u < U; ++u) {
+        const float2 r = rb[u * Nb];
+        df_fma(r.x, r.y, cj.x, cj.y, ah[u], al[u]);
+      }
     }
 #pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (u < cnt && acc[u] != 0.0) atomicAdd(gab + (int64_t)tpq[u] * n2 + rs, ts[u] * acc[u]);
+    for (int u = 0; u < U; ++u) {
+      const double v = (double)ah[u] + (double)al[u];
+      if (u < cnt && v != 0.0) atomicAdd(gab + (int64_t)tpq[u] * n2 + rs, ts[u] * v);
+    }
   }
 }
 
@@ -435,6 +470,7 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
   const int64_t n2 = (int64_t)n * n, n4 = n2 * n2, Na = B->Na, Nb = B->Nb, N = Na * Nb;
   double *Ma = nullptr, *Mad = nullptr, *Mb = nullptr, *Mbd = nullptr, *CT = nullptr,
          *same = nullptr, *gab = nullptr;
+  float2 *C2 = nullptr, *CT2 = nullptr;  // double-float copies of C and C^T
   int64_t *cnt = nullptr, *off = nullptr;
   int4* trans = nullptr;
   auto cleanup = [&]() {
@@ -443,6 +479,8 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
     dfree(Mb, s);
     dfree(Mbd, s);
     dfree(CT, s);
+    dfree(C2, s);
+    dfree(CT2, s);
     dfree(same, s);
     dfree(gab, s);
     dfree(cnt, s);
@@ -452,7 +490,8 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
   int rc = HINQS_OK;
   const int64_t ntrans = lb->nsingle + Nb * B->n_beta;
   if ((rc = dalloc(&Ma, la->nnz, s)) || (rc = dalloc(&Mad, Na, s)) || (rc = dalloc(&Mb, lb->nnz, s)) ||
-      (rc = dalloc(&Mbd, Nb, s)) || (rc = dalloc(&CT, N, s)) || (rc = dalloc(&same, n4, s)) ||
+      (rc = dalloc(&Mbd, Nb, s)) || (rc = dalloc(&CT, N, s)) || (rc = dalloc(&C2, N, s)) ||
+      (rc = dalloc(&CT2, N, s)) || (rc = dalloc(&same, n4, s)) ||
       (rc = dalloc(&gab, n4, s)) || (rc = dalloc(&cnt, n2 + 1, s)) || (rc = dalloc(&off, n2 + 1, s)) ||
       (rc = dalloc(&trans, ntrans, s))) {
     cleanup();
@@ -460,11 +499,14 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
   }
   auto run = [&]() -> int {
     const int g = 16 * kNumSMs;
-    // string-pair weights
-    k_link_dots<<<g, 256, 0, s>>>(c, Nb, la->row_ptr, la->col, Na, Ma, Mad);
+    // string-pair weights (double-float rows of C and C^T)
     dim3 tb(32, 8), tg((unsigned)ceil_div(Nb, 32), (unsigned)ceil_div(Na, 32));
     k_transpose<<<tg, tb, 0, s>>>(c, CT, Na, Nb);
-    k_link_dots<<<g, 256, 0, s>>>(CT, Na, lb->row_ptr, lb->col, Nb, Mb, Mbd);
+    const unsigned gs = (unsigned)std::min<int64_t>(ceil_div(N, 256), 8 * kNumSMs);
+    k_df_split<<<gs, 256, 0, s>>>(c, N, C2);
+    k_df_split<<<gs, 256, 0, s>>>(CT, N, CT2);
+    k_link_dots_df<<<g, 256, 0, s>>>(C2, Nb, la->row_ptr, la->col, Na, Ma, Mad);
+    k_link_dots_df<<<g, 256, 0, s>>>(CT2, Na, lb->row_ptr, lb->col, Nb, Mb, Mbd);
     HQ_CUDA(cudaMemsetAsync(rdm1, 0, n2 * sizeof(double), s));
     HQ_CUDA(cudaMemsetAsync(same, 0, n4 * sizeof(double), s));
     HQ_CUDA(cudaMemsetAsync(gab, 0, n4 * sizeof(double), s));
@@ -506,12 +548,12 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
         const size_t smem = (size_t)(U + 1) * Nb * sizeof(double);
         auto go = [&](auto kern) -> int {
           HQ_TRY(allow_max_smem(kern));
-          kern<<<grid, 256, smem, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink, off,
+          kern<<<grid, 256, smem, s>>>(C2, Nb, n, la->strings, la->srow_ptr, la->slink, off,
                                        trans, seg, nseg, gab);
           return HINQS_OK;
         };
-        return U == 16 ? go(k_rdm_ab_staged<16>) : U == 8 ? go(k_rdm_ab_staged<8>)
-                                                          : go(k_rdm_ab_staged<4>);
+        return U == 16 ? go(k_rdm_ab_staged_df<16>) : U == 8 ? go(k_rdm_ab_staged_df<8>)
+                                                             : go(k_rdm_ab_staged_df<4>);
       };
       const int r3 = staged();
       dfree(sstart, s);

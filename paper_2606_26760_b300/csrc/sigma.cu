@@ -815,31 +815,10 @@ __global__ void __launch_bounds__(256) k_sigma_ab(const T* __restrict__ C, T* __
 
 // ---------------------------------------------------------------------------
 // HINQS_PREC_FP64_DFAB: the opposite-spin term of an FP64 product in double-float
-// arithmetic (a value is an unevaluated sum hi + lo of two FP32 numbers): FP64 runs at
-// 1/64 of the FP32 rate on this part, and a double-float multiply-add is about twelve
-// FP32 operations.  Products are exact up to the dropped lo*lo term (the error-free
-// product by fused multiply-add), sums use the two-sum of Knuth, so each term carries
-// about 2^-44 relative error and the result about 1e-13 relative: far below what the
+// arithmetic (df_fma and df_split in hinqs_internal.cuh): FP64 runs at 1/64 of the
+// FP32 rate on this part, and a double-float multiply-add is about twelve FP32
+// operations; the result carries about 1e-13 relative error, far below what the
 // refinement residual of the mixed solver needs.
-
-// (sh, sl) += (ah + al) * (bh + bl)
-__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh,
-                                       float& sl) {
-  const float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  const float t = sh + p;
-  const float z = t - sh;
-  const float err = (sh - (t - z)) + (p - z);
-  sh = t;
-  sl += err + e;
-}
-
-__device__ __forceinline__ float2 df_split(double x) {
-  const float h = (float)x;
-  return make_float2(h, (float)(x - (double)h));
-}
 
 // The structure of k_sigma_ab (one block per alpha string Ja, CH alpha singles per
 // pass, (pq|.) rows transposed in shared memory), with the rows and C split into
