@@ -524,6 +524,23 @@ def test_rdm_matches_oracle(name):
     assert np.max(np.abs(g2.cpu().numpy() - r2)) < 1e-11 * scale
 
 
+def test_rdm_long_beta_rows_matches_oracle():
+    """Beta rows too long for the staged opposite-spin kernel (n = 20, 5 beta electrons:
+    the whole space of 15,504 strings, three alpha strings), so the unstaged FP64 form
+    runs; every element against the oracle."""
+    n, na, nb = 20, 1, 5
+    h, eri, _ = synth.integrals(n, 108)
+    a = np.array([1, 1 << 7, 1 << 19], dtype=np.uint64)
+    B = Built(h, eri, 0.0, n, na, nb, a, synth.all_strings(n, nb))
+    assert B.sub.Nb == 15504
+    c = synth.random_vector(B.sub.N, 31)
+    g1, g2 = hq.rdm(B.sub, B.la, B.lb, torch.tensor(c, dtype=torch.float64, device="cuda"))
+    r1, r2 = oracle.rdm(B.n, B.sa, B.sb, c)
+    scale = float(c @ c)
+    assert np.max(np.abs(g1.cpu().numpy() - r1)) < 1e-11 * scale
+    assert np.max(np.abs(g2.cpu().numpy() - r2)) < 1e-11 * scale
+
+
 def test_energy_autograd_hellmann_feynman():
     h, eri, e_nuc, n, na, nb, a, b = make_case("hf_12_4_4")
     sub = hq.build_subspace(a, b, n, na, nb)
