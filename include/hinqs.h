@@ -608,9 +608,9 @@ int hinqs_nqs_loss(const hinqs_ham* ham, const hinqs_subspace* sub, const hinqs_
  * eigenvector these are the Hellmann-Feynman derivatives dE/dh_pq = rdm1_pq and
  * dE/d(pq|rs) = rdm2_pqrs / 2 entrywise (not in the paper: the gradient the
  * integrals receive when the energy is differentiated).  rdm2 may be NULL.  The
- * results are FP64; the string-pair weights and, when the rows fit in shared memory,
- * the opposite-spin sums are formed in double-float arithmetic (pairs of FP32 numbers,
- * about 1e-13 relative), which runs several times faster than FP64 on this part. */
+ * results are FP64; the string-pair weights and the opposite-spin sums are formed in
+ * double-float arithmetic (pairs of FP32 numbers, about 1e-13 relative), which runs
+ * several times faster than FP64 on this part. */
 int hinqs_rdm(const hinqs_subspace* sub, const hinqs_links* la, const hinqs_links* lb,
               const double* c, double* rdm1, double* rdm2, void* stream);
 

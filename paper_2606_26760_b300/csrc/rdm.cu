@@ -1,6 +1,6 @@
 // K9: spin-summed 1- and 2-RDMs of a state on the product subspace (FP64 results;
-// the string-pair weights and the staged opposite-spin sums in double-float
-// arithmetic, about 1e-13 relative), the Hellmann-Feynman gradients of the energy;
+// the string-pair weights and the opposite-spin sums in double-float arithmetic, about
+// 1e-13 relative), the Hellmann-Feynman gradients of the energy;
 // K10: spin marginals (Step 4).
 //
 //   gamma_pq   = sum_s <a+_ps a_qs>
@@ -185,10 +185,11 @@ __global__ void k_trans_place(const uint64_t* __restrict__ S, int64_t N, int n,
   }
 }
 
-// Opposite-spin 2-RDM, one block per ket alpha string J_a; CH alpha transitions
-// at a time; thread per (transition, rs) bin.
+// Opposite-spin 2-RDM for rows too long to stage, one block per ket alpha string J_a;
+// CH alpha transitions at a time; thread per (transition, rs) bin, the rows read from
+// the double-float copy of C and the sum kept as a double-float pair.
 template <int CH>
-__global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, int64_t Nb, int n,
+__global__ void __launch_bounds__(256) k_rdm_ab_df(const float2* __restrict__ C2, int64_t Nb, int n,
                                                 const uint64_t* __restrict__ Sa,
                                                 const int64_t* __restrict__ a_srp,
                                                 const int2* __restrict__ a_sl,
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, in
   const int nd = __popcll(x);
   const int64_t nl = a_srp[Ja + 1] - a_srp[Ja];
   const int64_t total = nd + nl;
-  const double* cj = C + Ja * Nb;
+  const float2* cj = C2 + Ja * Nb;
   for (int64_t t0 = 0; t0 < total; t0 += CH) {
     const int cnt = (int)min64(CH, total - t0);
     __syncthreads();
@@ -227,12 +228,16 @@ __global__ void __launch_bounds__(256) k_rdm_ab(const double* __restrict__ C, in
     __syncthreads();
     for (int bin = threadIdx.x; bin < cnt * n2; bin += blockDim.x) {
       const int a = bin / n2, rs = bin % n2;
-      const double* ci = C + (int64_t)tI[a] * Nb;
-      double acc = 0.0;
+      const float2* ci = C2 + (int64_t)tI[a] * Nb;
+      float ah = 0.f, al = 0.f;
       for (int64_t k = off[rs]; k < off[rs + 1]; ++k) {
         const int4 tr = trans[k];
-        acc += tr.z * ci[tr.x] * cj[tr.y];
+        const float2 x = ci[tr.x];
+        float2 y = cj[tr.y];
+        if (tr.z < 0) y.x = -y.x, y.y = -y.y;
+        df_fma(x.x, x.y, y.x, y.y, ah, al);
       }
+      const double acc = (double)ah + (double)al;
       if (acc != 0.0) atomicAdd(gab + (int64_t)tpq[a] * n2 + rs, ts[a] * acc);
     }
   }
@@ -560,8 +565,8 @@ extern "C" int hinqs_rdm(const hinqs_subspace* B, const hinqs_links* la, const h
       dfree(seg, s);
       HQ_TRY(r3);
     } else {
-      k_rdm_ab<16><<<(unsigned)Na, 256, 0, s>>>(c, Nb, n, la->strings, la->srow_ptr, la->slink,
-                                                 off, trans, gab);
+      k_rdm_ab_df<16><<<(unsigned)Na, 256, 0, s>>>(C2, Nb, n, la->strings, la->srow_ptr,
+                                                    la->slink, off, trans, gab);
     }
     k_rdm2_combine<<<(unsigned)std::min<int64_t>(ceil_div(n4, 256), g), 256, 0, s>>>(same, gab, n,
                                                                                    rdm2);

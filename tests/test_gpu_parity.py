@@ -526,8 +526,8 @@ def test_rdm_matches_oracle(name):
 
 def test_rdm_long_beta_rows_matches_oracle():
     """Beta rows too long for the staged opposite-spin kernel (n = 20, 5 beta electrons:
-    the whole space of 15,504 strings, three alpha strings), so the unstaged FP64 form
-    runs; every element against the oracle."""
+    the whole space of 15,504 strings, three alpha strings), so the unstaged form runs;
+    every element against the oracle."""
     n, na, nb = 20, 1, 5
     h, eri, _ = synth.integrals(n, 108)
     a = np.array([1, 1 << 7, 1 << 19], dtype=np.uint64)
