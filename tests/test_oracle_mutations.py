@@ -29,6 +29,8 @@ MUTANTS = [
      "if (xa[mid] == a) return mid;"),
     ("list-matrix-transposed", "if (K >= 0) lu->Hcol[K * lu->M + lu->col] += coeff;",
      "if (K >= 0) lu->Hcol[K * lu->M + lu->col] += (K < lu->col ? 1.01 : 1.0) * coeff;"),
+    ("connected-merges-beta", "return u->a == v->a && u->b == v->b;", "return u->a == v->a;"),
+    ("connected-32-bit-strings", "cu->buf[cu->cnt].a = a;", "cu->buf[cu->cnt].a = a & 0xffffffffull;"),
 ]
 
 
